@@ -1,0 +1,167 @@
+/*
+ * kmc.h -- C ABI of libkmc, the GB300 (sm_103a) implementation of the kinetic
+ * Monte-Carlo hysteresis step of Tan, Carrey & Respaud, "Magnetic hyperthermia
+ * properties of nanoparticles inside lysosomes using kinetic Monte-Carlo
+ * simulations" (arXiv:1407.2737).
+ *
+ * One call of kmc_run advances every nanoparticle (NP) of every lysosome of a
+ * context through S steps per field period, each step being the paper's
+ * steps i)-viii) of Sec. II.1:
+ *   ii)  total field = applied field along z + dipolar field of all other NPs
+ *        of the same lysosome (Eq. 1, exact sum, no cutoff);
+ *   iii) working plane through the easy axis and the total field, previous
+ *        moment projected onto it;
+ *   iv)  extrema of the Stoner-Wohlfarth energy (Eq. 2) by a 200-point scan of
+ *        dE/dtheta refined by Newton's method;
+ *   v)   fall into the minimum whose basin holds the moment;
+ *   vi)  Neel-Arrhenius rates from the lower maximum (Eqs. 3-4) and the jump
+ *        probability over one step (Eq. 5);
+ *   vii) a counter-based Philox4x32-10 draw u decides the jump (u < P);
+ * and accumulates each NP's share of the hysteresis area (Sec. III.2.a).
+ *
+ * Conventions shared by every entry point:
+ *   - SI units: positions in m, volumes in m^3, M_S in A/m, K_eff in J/m^3,
+ *     T in K, tau0 in s, fields as mu0*H in tesla, energies in J.
+ *   - All pointers are HOST pointers. Inputs are owned by the caller and are
+ *     copied before the call returns; outputs go to caller buffers of the
+ *     stated capacity (in elements).
+ *   - Every call returns a kmc_status and never aborts the process;
+ *     kmc_last_error() describes the last failure of the calling thread.
+ *   - Device memory is allocated by kmc_create and freed by kmc_destroy.
+ *   - Work is queued on the context's CUDA stream (a private stream unless
+ *     kmc_set_stream gave one); kmc_run returns once the work is queued.
+ *     kmc_read, kmc_sync, kmc_debug_step and kmc_save wait for it, and report
+ *     KMC_ETIMEOUT if a device-side wait ran out of time.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef KMC_H
+#define KMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kmc_ctx kmc_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  KMC_OK = 0,
+  KMC_EINVAL = 1,    /* bad argument (NULL, negative size, non-finite value) */
+  KMC_ENOMEM = 2,    /* host or device allocation failed                     */
+  KMC_ECUDA = 3,     /* a CUDA runtime call failed (no device, launch error) */
+  KMC_ETIMEOUT = 4,  /* a device-side wait gave up; results are not valid    */
+  KMC_ESTATE = 5,    /* call out of order (e.g. kmc_read before kmc_run)     */
+  KMC_ECAPACITY = 6, /* output buffer too small; *written = elements needed  */
+  KMC_EIO = 7        /* checkpoint file could not be read or written         */
+} kmc_status;
+
+typedef enum {
+  KMC_FP64_PLAIN = 0, /* every step of the path in FP64                      */
+  KMC_FP32_MIXED = 1  /* FP32 pair sum with compensated combine, FP32 scan and
+                         Newton; FP64 barrier near switching, FP64 rate
+                         exponent and probability, FP64 energy accumulation  */
+} kmc_precision;
+
+/* One lysosome (Sec. II.1): NPs of one material (M_S, K_eff) at temperature
+ * T with attempt time tau0 = 1/nu0 (nu1^0 = nu2^0 = nu0 in Eqs. 3-4). */
+typedef struct {
+  int32_t n;            /* number of NPs, >= 1                                 */
+  const double *pos;    /* [n][3] centres, m; pairwise distinct              */
+  const double *axis;   /* [n][3] easy axes, normalised by the library       */
+  const double *vol;    /* [n] magnetic volumes, m^3, > 0                    */
+  const double *center; /* [3] origin of the float32 frame, m, or NULL for
+                           the centroid of pos                               */
+  double Ms;            /* A/m, > 0                                          */
+  double Keff;          /* J/m^3, >= 0                                       */
+  double T;             /* K, >= 0; T = 0 skips steps vi-vii (no jumps)      */
+  double tau0;          /* s, > 0                                            */
+  double rho;           /* kg/m^3 for the SAR; <= 0 means 5200 (magnetite)   */
+} kmc_lysosome;
+
+/* What kmc_read returns (per lysosome `lys` unless stated). */
+enum {
+  KMC_READ_LOOP_H = 0,    /* [S*(periods-discard)] mu0 H_ext,k (T), recorded steps */
+  KMC_READ_LOOP_M = 1,    /* [same] volume-weighted mean m_z after step k (M/M_S)  */
+  KMC_READ_NP_ENERGY = 2, /* [n] energy dissipated by each NP per recorded period, J:
+                             mu0 M_S V_i sum_k H_ext,k (m_z,k+1 - m_z,k) / periods */
+  KMC_READ_AREA = 3,      /* [1] hysteresis area A, J/m^3 per cycle (Sec. III.2.a) */
+  KMC_READ_SAR = 4,       /* [1] SAR = A f / rho, W/kg                             */
+  KMC_READ_MOMENTS = 5,   /* [n][3] current unit moments                           */
+  KMC_READ_COUNTERS = 6   /* [4] over the last run: jumps, near-threshold draws
+                             (|u - P| < 1e-9), NP-steps with one minimum, NP-steps
+                             whose working plane needed the fallback               */
+};
+
+/* Creates a context holding n_lys lysosomes (copied to the device). Moments
+ * start along the easy axis with m_z >= 0. The global step counter, which
+ * keys the random draws, starts at 0. */
+kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec,
+                      kmc_ctx **out);
+
+/* Queues later work on `cuda_stream` (a cudaStream_t of the current device,
+ * not owned; NULL selects the context's private stream). */
+kmc_status kmc_set_stream(kmc_ctx *ctx, void *cuda_stream);
+
+/* Runs `periods` periods of the sinusoidal field mu0 H_ext,k = mu0Hmax
+ * cos(2 pi k / S) along z (each period starts at +Hmax, Sec. III.1), frequency
+ * f, S = steps_per_period steps of t_step = 1/(f S). The first
+ * discard_periods periods are not recorded (Sec. III.1 runs two loops and keeps
+ * the second). mu0Hmax holds n_amp = n_lys amplitudes, or n_amp = 1 for all.
+ * Moments and the global step counter carry over between runs; the loop,
+ * energy and counter outputs are those of the latest run. The draw of NP i of
+ * lysosome l at global step s is Philox4x32-10 with key (seed low, seed high)
+ * and counter (s low, s high, i, l). */
+kmc_status kmc_run(kmc_ctx *ctx, const double *mu0Hmax, int32_t n_amp, double f,
+                   int32_t steps_per_period, int32_t periods, int32_t discard_periods,
+                   uint64_t seed);
+
+/* Copies output `what` (KMC_READ_*) of lysosome `lys` into buf[cap]. Sets
+ * *written to the number of elements (also on KMC_ECAPACITY). Waits for
+ * queued work. */
+kmc_status kmc_read(kmc_ctx *ctx, int32_t what, int32_t lys, double *buf, int64_t cap,
+                    int64_t *written);
+
+/* Waits for queued work and reports device-side errors. */
+kmc_status kmc_sync(kmc_ctx *ctx);
+
+/* Test hook: one step (steps i-vii) of every NP from the moments m_in
+ * ([N][3], all lysosomes in order) under applied fields mu0Hext ([n_lys], T,
+ * along z), step length t_step and draws keyed by (seed, step). Runs the
+ * kernels of kmc_run. The context's moments become m_out. Outputs, each
+ * [N]-major and optional (NULL to skip): m_out [N][3]; B_dip [N][3] dipolar
+ * field mu0 H_dip (T); dE [N][2] barriers E3 - E_a (current well a) and
+ * E3 - E_b (J, 0 with a single minimum); P [N] jump probability; u [N] draw;
+ * flags [N] = n_min | jumped << 2 | near-threshold << 3 | fallback plane << 4. */
+kmc_status kmc_debug_step(kmc_ctx *ctx, const double *mu0Hext, double t_step,
+                          uint64_t seed, int64_t step, const double *m_in, double *m_out,
+                          double *B_dip, double *dE, double *P, double *u,
+                          int32_t *flags);
+
+/* Checkpoint: writes the moments and the global step counter to `path`;
+ * kmc_load restores them into a context built from the same lysosomes and
+ * precision, so that the next kmc_run continues bit for bit. */
+kmc_status kmc_save(kmc_ctx *ctx, const char *path);
+kmc_status kmc_load(kmc_ctx *ctx, const char *path);
+
+/* Total NPs, lysosomes and global step counter of a context. */
+kmc_status kmc_info(const kmc_ctx *ctx, int64_t *n_total, int32_t *n_lys,
+                    int64_t *global_step);
+
+/* Launch shape of the fused step kernel: warps per block splitting the source
+ * range, sources per shared-memory tile; 0 lets the autotuner choose on the
+ * next kmc_run. Returns the shape in use through the out pointers (may be
+ * NULL). */
+kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t *warps_out,
+                      int32_t *tile_out);
+
+/* Frees the context and its device memory. NULL-safe. */
+void kmc_destroy(kmc_ctx *ctx);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *kmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KMC_H */

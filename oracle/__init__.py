@@ -81,6 +81,8 @@ def lib():
             L.kmc_oracle_uniform.argtypes = [C.c_uint64, C.c_int64, C.c_int32, C.c_int32]
             L.kmc_oracle_uniform.restype = C.c_double
             L.kmc_oracle_dipolar_field.argtypes = [C.c_int32, _D, _D, C.c_double, _D, _D]
+            L.kmc_oracle_dipolar_field_at.argtypes = [C.c_int32, _D, _D, C.c_double, _D,
+                                                      C.c_int32, _I32, _D]
             L.kmc_oracle_extrema.argtypes = [C.c_double] * 5 + [_D, _D, _I32]
             L.kmc_oracle_extrema.restype = C.c_int32
             L.kmc_oracle_np_update.argtypes = [_D, _D, _D] + [C.c_double] * 7 + [
@@ -149,6 +151,18 @@ def dipolar_field(pos, vol, Ms, m):
     m = _f64(m, (-1, 3))
     B = np.zeros_like(pos)
     lib().kmc_oracle_dipolar_field(len(vol), _dp(pos), _dp(vol), float(Ms), _dp(m), _dp(B))
+    return B
+
+
+def dipolar_field_at(pos, vol, Ms, m, idx):
+    """Eq. 1 at the listed target NPs only; returns (len(idx), 3) in T."""
+    pos = _f64(pos, (-1, 3))
+    vol = _f64(vol, (-1,))
+    m = _f64(m, (-1, 3))
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    B = np.zeros((len(idx), 3))
+    lib().kmc_oracle_dipolar_field_at(len(vol), _dp(pos), _dp(vol), float(Ms), _dp(m),
+                                      len(idx), idx.ctypes.data_as(_I32), _dp(B))
     return B
 
 

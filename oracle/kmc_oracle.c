@@ -124,6 +124,12 @@ void kmc_oracle_dipolar_field(int32_t n, const double *pos, const double *vol,
   for (int32_t i = 0; i < n; ++i) dipolar_on(i, n, pos, vol, Ms, m, &B[3 * i]);
 }
 
+void kmc_oracle_dipolar_field_at(int32_t n, const double *pos, const double *vol,
+                                 double Ms, const double *m, int32_t n_t,
+                                 const int32_t *idx, double *B) {
+  for (int32_t t = 0; t < n_t; ++t) dipolar_on(idx[t], n, pos, vol, Ms, m, &B[3 * t]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Eq. 2 and its first two derivatives in theta. */
 typedef struct {

@@ -76,6 +76,11 @@ double kmc_oracle_uniform(uint64_t seed, int64_t step, int32_t np, int32_t lys);
 void kmc_oracle_dipolar_field(int32_t n, const double *pos, const double *vol,
                               double Ms, const double *m, double *B);
 
+/* Eq. 1 at n_t listed targets only (idx[t] in [0, n)); B is [n_t][3]. */
+void kmc_oracle_dipolar_field_at(int32_t n, const double *pos, const double *vol,
+                                 double Ms, const double *m, int32_t n_t,
+                                 const int32_t *idx, double *B);
+
 /* Step iv: extrema of Eq. 2 for field magnitude B = mu0*H_tot (T) at angle phi
  * (rad) from the easy axis. Writes up to 4 extrema in scan order: angle in
  * [0, 2 pi), energy (J) and 1 for a minimum / 0 for a maximum. Returns the

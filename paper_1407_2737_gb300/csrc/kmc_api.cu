@@ -1,0 +1,870 @@
+// kmc_api.cu -- the C ABI of libkmc (include/kmc.h): contexts, device memory,
+// the CUDA-graph step loop, the launch-shape autotuner, checkpoints and the
+// test hook. All arithmetic of the kMC step itself lives in kmc_step.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kmc.h"
+#include "kmc_launch.h"
+
+using kmc::dbl4;
+using kmc::LysDev;
+using kmc::RunState;
+using kmc::StepArgs;
+
+namespace {
+
+constexpr double kMu0 = 4.0e-7 * 3.14159265358979323846;
+constexpr double kKB = 1.380649e-23;
+constexpr double kPi = 3.14159265358979323846;
+
+thread_local std::string g_last_error;
+
+kmc_status fail(kmc_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define KMC_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(KMC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+// Fills a float4 / dbl4 from doubles.
+template <typename V>
+V make4(double x, double y, double z, double w) {
+  V v;
+  v.x = static_cast<decltype(v.x)>(x);
+  v.y = static_cast<decltype(v.y)>(y);
+  v.z = static_cast<decltype(v.z)>(z);
+  v.w = static_cast<decltype(v.w)>(w);
+  return v;
+}
+
+// mu[par][i] = w_i m_i for every NP: the source copy of the moments.
+template <typename V>
+__global__ void sources_from_moments(const V *__restrict__ pos, const V *__restrict__ m,
+                                     V *__restrict__ mu, long long n) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const V p = pos[i], q = m[i];
+  V r;
+  r.x = p.w * q.x;
+  r.y = p.w * q.y;
+  r.z = p.w * q.z;
+  r.w = 0;
+  mu[i] = r;
+}
+
+struct TuneKey {
+  int prec;
+  long long N;
+  int n_lys, max_n;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(prec, N, n_lys, max_n) < std::tie(o.prec, o.N, o.n_lys, o.max_n);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+std::mutex g_tables_mu;
+std::vector<int> g_tables_done;  // per device ordinal
+
+kmc_status ensure_tables() {
+  int dev = 0;
+  KMC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tables_mu);
+  if (static_cast<int>(g_tables_done.size()) <= dev) g_tables_done.resize(dev + 1, 0);
+  if (!g_tables_done[dev]) {
+    KMC_CUDA(kmc::init_device());
+    g_tables_done[dev] = 1;
+  }
+  return KMC_OK;
+}
+
+}  // namespace
+
+struct kmc_ctx {
+  int fp32 = 0;
+  int n_lys = 0;
+  long long N = 0;
+  size_t vbytes = 0;  // sizeof(float4) or sizeof(dbl4)
+  std::vector<int> off, n;
+  std::vector<double> Ms, Keff, T, tau0, rho, vsum;
+  std::vector<double> vol;  // [N]
+  std::vector<int4> items;
+  std::vector<LysDev> h_lys;
+  // device memory
+  int4 *d_items = nullptr;
+  LysDev *d_lys = nullptr;
+  void *d_pos = nullptr, *d_axis = nullptr, *d_m = nullptr, *d_mu[2] = {nullptr, nullptr};
+  double *d_beta = nullptr, *d_vfrac = nullptr, *d_eacc = nullptr, *d_loop = nullptr;
+  unsigned long long *d_cnt = nullptr;
+  int32_t *d_err = nullptr;
+  RunState *d_rs = nullptr;
+  size_t loop_cap = 0;
+  // debug outputs, allocated on first use
+  double *d_dbg = nullptr;
+  int32_t *d_dbg_flags = nullptr;
+  // streams
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  long long step_global = 0;
+  // latest run
+  bool have_run = false;
+  int S = 0, periods = 0, discard = 0, n_rec = 0;
+  double f = 0.0;
+  std::vector<double> Hmax;
+  // launch shape and the captured one-period graph
+  int warps = 0, tile = 0;
+  cudaGraphExec_t gexec = nullptr;
+  int g_S = -1, g_discard = -1, g_nrec = -1, g_warps = -1, g_tile = -1;
+  unsigned long long g_seed = 0;
+};
+
+namespace {
+
+StepArgs base_args(kmc_ctx *c) {
+  StepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.items = c->d_items;
+  a.lys = c->d_lys;
+  a.pos = c->d_pos;
+  a.axis = c->d_axis;
+  a.m = c->d_m;
+  a.mu[0] = c->d_mu[0];
+  a.mu[1] = c->d_mu[1];
+  a.beta = c->d_beta;
+  a.vfrac = c->d_vfrac;
+  a.e_acc = c->d_eacc;
+  a.loop_m = c->d_loop;
+  a.counters = c->d_cnt;
+  a.err = c->d_err;
+  a.rs = c->d_rs;
+  return a;
+}
+
+kmc_status refresh_sources(kmc_ctx *c, int par) {
+  const int bs = 256;
+  const long long nb = (c->N + bs - 1) / bs;
+  if (c->fp32)
+    sources_from_moments<float4><<<static_cast<unsigned>(nb), bs, 0, c->stream>>>(
+        static_cast<const float4 *>(c->d_pos), static_cast<const float4 *>(c->d_m),
+        static_cast<float4 *>(c->d_mu[par]), c->N);
+  else
+    sources_from_moments<dbl4><<<static_cast<unsigned>(nb), bs, 0, c->stream>>>(
+        static_cast<const dbl4 *>(c->d_pos), static_cast<const dbl4 *>(c->d_m),
+        static_cast<dbl4 *>(c->d_mu[par]), c->N);
+  KMC_CUDA(cudaGetLastError());
+  return KMC_OK;
+}
+
+kmc_status check_device_error(kmc_ctx *c) {
+  int32_t e = 0;
+  KMC_CUDA(cudaMemcpyAsync(&e, c->d_err, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  if (e & kmc::kErrTimeout)
+    return fail(KMC_ETIMEOUT, "a device-side wait for a shared-memory copy timed out");
+  if (e & kmc::kErrExtrema)
+    return fail(KMC_ESTATE, "an energy profile had more than two minima or maxima");
+  return KMC_OK;
+}
+
+kmc_status upload_lys(kmc_ctx *c) {
+  KMC_CUDA(cudaMemcpyAsync(c->d_lys, c->h_lys.data(), sizeof(LysDev) * c->n_lys,
+                           cudaMemcpyHostToDevice, c->stream));
+  return KMC_OK;
+}
+
+int max_tile(int fp32, int warps) {
+  // keep two blocks' worth of shared memory per SM
+  const size_t budget = 100 * 1024;
+  int t = 1024;
+  while (t > 32 && kmc::step_smem_bytes(fp32, warps, t) > budget) t /= 2;
+  return t;
+}
+
+// Times one candidate launch shape on the current state (restored afterwards
+// by the caller). Returns milliseconds per step, or a negative value on error.
+float time_shape(kmc_ctx *c, int warps, int tile) {
+  StepArgs a = base_args(c);
+  a.cos_k = 1.0;
+  a.seed = 0;
+  a.S = 1;
+  a.discard = 0;
+  a.n_rec = 1;
+  a.k_local = 0;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.f;
+  }
+  float ms = -1.f;
+  bool ok = true;
+  for (int r = 0; r < 3 && ok; ++r)
+    ok = kmc::launch_step(c->fp32, warps, tile, a, static_cast<int>(c->items.size()), c->stream) ==
+         cudaSuccess;
+  const int reps = 6;
+  if (ok) ok = cudaEventRecord(e0, c->stream) == cudaSuccess;
+  for (int r = 0; r < reps && ok; ++r)
+    ok = kmc::launch_step(c->fp32, warps, tile, a, static_cast<int>(c->items.size()), c->stream) ==
+         cudaSuccess;
+  if (ok) ok = cudaEventRecord(e1, c->stream) == cudaSuccess;
+  if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
+  if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms /= reps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ok ? ms : -1.f;
+}
+
+kmc_status autotune(kmc_ctx *c) {
+  int max_n = 0;
+  for (int x : c->n) max_n = std::max(max_n, x);
+  const TuneKey key{c->fp32, c->N, c->n_lys, max_n};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      c->warps = it->second.first;
+      c->tile = it->second.second;
+      return KMC_OK;
+    }
+  }
+  // save the moments: the timed launches advance a scratch copy of the state
+  std::vector<unsigned char> saved(c->vbytes * c->N);
+  KMC_CUDA(cudaMemcpyAsync(saved.data(), c->d_m, saved.size(), cudaMemcpyDeviceToHost, c->stream));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  RunState rs{c->step_global, -1, 0};
+  KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
+  for (auto &L : c->h_lys) {
+    L.bmax = 0.0;
+    L.lognu0t = std::log(5e-8 / 1e-10);
+  }
+  kmc_status st = upload_lys(c);
+  if (st != KMC_OK) return st;
+  float best = 1e30f;
+  int bw = 8, bt = 256;
+  const int warps_c[] = {4, 8, 16};
+  const int tiles_c[] = {64, 128, 256, 512, 1024};
+  for (int w : warps_c) {
+    for (int t : tiles_c) {
+      if (t > max_tile(c->fp32, w)) continue;
+      if (t > 2 * std::max(max_n, 32) && t != 64) continue;
+      st = refresh_sources(c, static_cast<int>(c->step_global & 1));
+      if (st != KMC_OK) return st;
+      const float ms = time_shape(c, w, t);
+      if (ms > 0.f && ms < best) {
+        best = ms;
+        bw = w;
+        bt = t;
+      }
+    }
+  }
+  KMC_CUDA(cudaGetLastError());
+  KMC_CUDA(cudaMemcpyAsync(c->d_m, saved.data(), saved.size(), cudaMemcpyHostToDevice, c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  c->warps = bw;
+  c->tile = bt;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {bw, bt};
+  return KMC_OK;
+}
+
+void free_ctx(kmc_ctx *c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  void *ptrs[] = {c->d_items, c->d_lys, c->d_pos,  c->d_axis,  c->d_m,   c->d_mu[0],
+                  c->d_mu[1], c->d_beta, c->d_vfrac, c->d_eacc, c->d_loop, c->d_cnt,
+                  c->d_err,   c->d_rs,   c->d_dbg,   c->d_dbg_flags};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+template <typename T>
+kmc_status dalloc(T **p, size_t bytes) {
+  if (cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(KMC_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+  }
+  return KMC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *kmc_last_error(void) { return g_last_error.c_str(); }
+
+kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec,
+                      kmc_ctx **out) {
+  g_last_error.clear();
+  if (!out) return fail(KMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!lys || n_lys < 1) return fail(KMC_EINVAL, "need at least one lysosome");
+  if (prec != KMC_FP64_PLAIN && prec != KMC_FP32_MIXED)
+    return fail(KMC_EINVAL, "unknown precision %d", static_cast<int>(prec));
+  long long N = 0;
+  for (int l = 0; l < n_lys; ++l) {
+    const kmc_lysosome &L = lys[l];
+    if (L.n < 1) return fail(KMC_EINVAL, "lysosome %d: n = %d", l, L.n);
+    if (!L.pos || !L.axis || !L.vol) return fail(KMC_EINVAL, "lysosome %d: NULL array", l);
+    if (!(L.Ms > 0) || !is_finite(L.Ms)) return fail(KMC_EINVAL, "lysosome %d: Ms must be > 0", l);
+    if (!(L.Keff >= 0) || !is_finite(L.Keff)) return fail(KMC_EINVAL, "lysosome %d: Keff < 0", l);
+    if (!(L.T >= 0) || !is_finite(L.T)) return fail(KMC_EINVAL, "lysosome %d: T < 0", l);
+    if (!(L.tau0 > 0) || !is_finite(L.tau0)) return fail(KMC_EINVAL, "lysosome %d: tau0 <= 0", l);
+    for (int i = 0; i < L.n; ++i) {
+      if (!(L.vol[i] > 0) || !is_finite(L.vol[i]))
+        return fail(KMC_EINVAL, "lysosome %d NP %d: volume must be > 0", l, i);
+      double a2 = 0;
+      for (int q = 0; q < 3; ++q) {
+        if (!is_finite(L.pos[3 * i + q]) || !is_finite(L.axis[3 * i + q]))
+          return fail(KMC_EINVAL, "lysosome %d NP %d: non-finite input", l, i);
+        a2 += L.axis[3 * i + q] * L.axis[3 * i + q];
+      }
+      if (!(a2 > 0)) return fail(KMC_EINVAL, "lysosome %d NP %d: zero easy axis", l, i);
+    }
+    N += L.n;
+    if (N > (1ll << 30)) return fail(KMC_EINVAL, "too many NPs");
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(KMC_ECUDA, "no CUDA device available");
+  }
+  kmc_status st = ensure_tables();
+  if (st != KMC_OK) return st;
+
+  kmc_ctx *c = new (std::nothrow) kmc_ctx();
+  if (!c) return fail(KMC_ENOMEM, "host allocation failed");
+  c->fp32 = prec == KMC_FP32_MIXED;
+  c->n_lys = n_lys;
+  c->N = N;
+  c->vbytes = c->fp32 ? sizeof(float4) : sizeof(dbl4);
+  std::vector<unsigned char> h_pos(c->vbytes * N), h_axis(c->vbytes * N), h_m(c->vbytes * N);
+  std::vector<double> h_beta(N), h_vfrac(N);
+  c->vol.resize(N);
+  c->h_lys.resize(n_lys);
+  long long o = 0;
+  for (int l = 0; l < n_lys; ++l) {
+    const kmc_lysosome &L = lys[l];
+    c->off.push_back(static_cast<int>(o));
+    c->n.push_back(L.n);
+    c->Ms.push_back(L.Ms);
+    c->Keff.push_back(L.Keff);
+    c->T.push_back(L.T);
+    c->tau0.push_back(L.tau0);
+    c->rho.push_back(L.rho > 0 ? L.rho : 5200.0);
+    double vs = 0, cx = 0, cy = 0, cz = 0;
+    for (int i = 0; i < L.n; ++i) {
+      vs += L.vol[i];
+      cx += L.pos[3 * i];
+      cy += L.pos[3 * i + 1];
+      cz += L.pos[3 * i + 2];
+    }
+    if (L.center) {
+      cx = L.center[0];
+      cy = L.center[1];
+      cz = L.center[2];
+    } else {
+      cx /= L.n;
+      cy /= L.n;
+      cz /= L.n;
+    }
+    c->vsum.push_back(vs);
+    const double vmean = vs / L.n;
+    const double len = std::cbrt(6.0 * vmean / kPi);  // diameter of the mean volume
+    const double w_scale = 1.0 / (4.0 * kPi * len * len * len);
+    LysDev &D = c->h_lys[l];
+    D.off = static_cast<int>(o);
+    D.n = L.n;
+    D.t_zero = L.T == 0.0;
+    D.k = L.Keff / (kMu0 * L.Ms * L.Ms);
+    D.bmax = 0.0;
+    D.lognu0t = 0.0;
+    for (int i = 0; i < L.n; ++i, ++o) {
+      const double *p = &L.pos[3 * i];
+      const double *a = &L.axis[3 * i];
+      const double an = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      const double ax = a[0] / an, ay = a[1] / an, az = a[2] / an;
+      const double sgn = az >= 0 ? 1.0 : -1.0;  // initial m along the axis, m_z >= 0
+      const double x = (p[0] - cx) / len, y = (p[1] - cy) / len, z = (p[2] - cz) / len;
+      const double w = L.vol[i] * w_scale;
+      c->vol[o] = L.vol[i];
+      h_beta[o] = L.T > 0 ? kMu0 * L.Ms * L.Ms * L.vol[i] / (kKB * L.T) : 0.0;
+      h_vfrac[o] = L.vol[i] / vs;
+      if (c->fp32) {
+        reinterpret_cast<float4 *>(h_pos.data())[o] = make4<float4>(x, y, z, w);
+        const float4 af = make4<float4>(ax, ay, az, 0.0);
+        reinterpret_cast<float4 *>(h_axis.data())[o] = af;
+        reinterpret_cast<float4 *>(h_m.data())[o] =
+            make4<float4>(sgn * af.x, sgn * af.y, sgn * af.z, 0.0);
+      } else {
+        reinterpret_cast<dbl4 *>(h_pos.data())[o] = make4<dbl4>(x, y, z, w);
+        reinterpret_cast<dbl4 *>(h_axis.data())[o] = make4<dbl4>(ax, ay, az, 0.0);
+        reinterpret_cast<dbl4 *>(h_m.data())[o] = make4<dbl4>(sgn * ax, sgn * ay, sgn * az, 0.0);
+      }
+    }
+  }
+  // work items: (lysosome, 32 targets), largest lysosomes first
+  std::vector<int> order(n_lys);
+  for (int l = 0; l < n_lys; ++l) order[l] = l;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return c->n[x] > c->n[y]; });
+  for (int l : order)
+    for (int i0 = 0; i0 < c->n[l]; i0 += kmc::kTargets)
+      c->items.push_back(make_int4(l, i0, std::min(kmc::kTargets, c->n[l] - i0), 0));
+
+#define KMC_TRY(x)          \
+  do {                      \
+    kmc_status s_ = (x);    \
+    if (s_ != KMC_OK) {     \
+      free_ctx(c);          \
+      return s_;            \
+    }                       \
+  } while (0)
+#define KMC_TRYC(x)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (x);                                                             \
+    if (e_ != cudaSuccess) {                                                          \
+      free_ctx(c);                                                                    \
+      return fail(KMC_ECUDA, "%s failed: %s", #x, cudaGetErrorString(e_));            \
+    }                                                                                 \
+  } while (0)
+
+  KMC_TRYC(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+  c->stream = c->own_stream;
+  const size_t vb = c->vbytes * N;
+  KMC_TRY(dalloc(&c->d_items, sizeof(int4) * c->items.size()));
+  KMC_TRY(dalloc(&c->d_lys, sizeof(LysDev) * n_lys));
+  KMC_TRY(dalloc(&c->d_pos, vb));
+  KMC_TRY(dalloc(&c->d_axis, vb));
+  KMC_TRY(dalloc(&c->d_m, vb));
+  KMC_TRY(dalloc(&c->d_mu[0], vb));
+  KMC_TRY(dalloc(&c->d_mu[1], vb));
+  KMC_TRY(dalloc(&c->d_beta, sizeof(double) * N));
+  KMC_TRY(dalloc(&c->d_vfrac, sizeof(double) * N));
+  KMC_TRY(dalloc(&c->d_eacc, sizeof(double) * N));
+  KMC_TRY(dalloc(&c->d_cnt, sizeof(unsigned long long) * 4 * n_lys));
+  KMC_TRY(dalloc(&c->d_err, sizeof(int32_t)));
+  KMC_TRY(dalloc(&c->d_rs, sizeof(RunState)));
+  KMC_TRYC(cudaMemcpyAsync(c->d_items, c->items.data(), sizeof(int4) * c->items.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+  KMC_TRYC(cudaMemcpyAsync(c->d_pos, h_pos.data(), vb, cudaMemcpyHostToDevice, c->stream));
+  KMC_TRYC(cudaMemcpyAsync(c->d_axis, h_axis.data(), vb, cudaMemcpyHostToDevice, c->stream));
+  KMC_TRYC(cudaMemcpyAsync(c->d_m, h_m.data(), vb, cudaMemcpyHostToDevice, c->stream));
+  KMC_TRYC(cudaMemcpyAsync(c->d_beta, h_beta.data(), sizeof(double) * N, cudaMemcpyHostToDevice,
+                           c->stream));
+  KMC_TRYC(cudaMemcpyAsync(c->d_vfrac, h_vfrac.data(), sizeof(double) * N,
+                           cudaMemcpyHostToDevice, c->stream));
+  KMC_TRYC(cudaMemsetAsync(c->d_eacc, 0, sizeof(double) * N, c->stream));
+  KMC_TRYC(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long) * 4 * n_lys, c->stream));
+  KMC_TRYC(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  KMC_TRY(upload_lys(c));
+  KMC_TRYC(cudaStreamSynchronize(c->stream));  // host staging buffers go out of scope
+#undef KMC_TRY
+#undef KMC_TRYC
+  *out = c;
+  return KMC_OK;
+}
+
+kmc_status kmc_set_stream(kmc_ctx *c, void *cuda_stream) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  c->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->own_stream;
+  return KMC_OK;
+}
+
+kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t *warps_out,
+                      int32_t *tile_out) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (warps != 0 || tile != 0) {
+    if (warps != 4 && warps != 8 && warps != 16)
+      return fail(KMC_EINVAL, "warps must be 4, 8 or 16");
+    if (tile < 32 || tile > max_tile(c->fp32, warps) || (tile & (tile - 1)))
+      return fail(KMC_EINVAL, "tile must be a power of two in [32, %d]", max_tile(c->fp32, warps));
+    c->warps = warps;
+    c->tile = tile;
+  } else if (warps_out == nullptr && tile_out == nullptr) {
+    c->warps = c->tile = 0;
+  }
+  if (warps_out) *warps_out = c->warps;
+  if (tile_out) *tile_out = c->tile;
+  return KMC_OK;
+}
+
+kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f,
+                   int32_t S, int32_t periods, int32_t discard, uint64_t seed) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (!mu0Hmax || (n_amp != 1 && n_amp != c->n_lys))
+    return fail(KMC_EINVAL, "need 1 or n_lys = %d amplitudes", c->n_lys);
+  for (int q = 0; q < n_amp; ++q)
+    if (!is_finite(mu0Hmax[q])) return fail(KMC_EINVAL, "non-finite field amplitude");
+  if (!(f > 0) || !is_finite(f)) return fail(KMC_EINVAL, "f must be > 0");
+  if (S < 1) return fail(KMC_EINVAL, "steps_per_period must be >= 1");
+  if (periods < 0 || discard < 0 || discard > periods)
+    return fail(KMC_EINVAL, "need 0 <= discard_periods <= periods");
+  const long long n_rec = static_cast<long long>(S) * (periods - discard);
+  if (n_rec > (1ll << 28)) return fail(KMC_EINVAL, "too many recorded steps");
+  if (c->warps == 0) {
+    kmc_status st = autotune(c);
+    if (st != KMC_OK) return st;
+  }
+  const double t_step = 1.0 / (f * S);
+  c->Hmax.assign(c->n_lys, 0.0);
+  for (int l = 0; l < c->n_lys; ++l) {
+    c->Hmax[l] = mu0Hmax[n_amp == 1 ? 0 : l];
+    c->h_lys[l].bmax = c->Hmax[l] / (kMu0 * c->Ms[l]);
+    c->h_lys[l].lognu0t = std::log(t_step / c->tau0[l]);
+  }
+  kmc_status st = upload_lys(c);
+  if (st != KMC_OK) return st;
+  const size_t need = static_cast<size_t>(c->n_lys) * static_cast<size_t>(std::max(n_rec, 1ll));
+  if (need > c->loop_cap) {
+    if (c->d_loop) cudaFree(c->d_loop);
+    c->d_loop = nullptr;
+    c->loop_cap = 0;
+    st = dalloc(&c->d_loop, sizeof(double) * need);
+    if (st != KMC_OK) return st;
+    c->loop_cap = need;
+    if (c->gexec) {  // the graph holds the old pointer
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+  }
+  KMC_CUDA(cudaMemsetAsync(c->d_loop, 0, sizeof(double) * need, c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_eacc, 0, sizeof(double) * c->N, c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long) * 4 * c->n_lys, c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  st = refresh_sources(c, static_cast<int>(c->step_global & 1));
+  if (st != KMC_OK) return st;
+  RunState rs{c->step_global, 0, 0};
+  KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
+  // capture one field period (S step launches + the period advance) as a graph
+  if (!c->gexec || c->g_S != S || c->g_discard != discard || c->g_nrec != n_rec ||
+      c->g_warps != c->warps || c->g_tile != c->tile || c->g_seed != seed) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    StepArgs a = base_args(c);
+    a.seed = seed;
+    a.S = S;
+    a.discard = discard;
+    a.n_rec = static_cast<int>(std::max(n_rec, 1ll));
+    cudaGraph_t g = nullptr;
+    KMC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < S && ce == cudaSuccess; ++k) {
+      a.k_local = k;
+      a.cos_k = std::cos(2.0 * kPi * k / S);
+      ce = kmc::launch_step(c->fp32, c->warps, c->tile, a, static_cast<int>(c->items.size()),
+                            c->stream);
+    }
+    if (ce == cudaSuccess) ce = kmc::launch_advance(c->d_rs, S, c->stream);
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return fail(KMC_ECUDA, "graph capture failed: %s",
+                  cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      c->gexec = nullptr;
+      return fail(KMC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+    }
+    c->g_S = S;
+    c->g_discard = discard;
+    c->g_nrec = static_cast<int>(n_rec);
+    c->g_warps = c->warps;
+    c->g_tile = c->tile;
+    c->g_seed = seed;
+  }
+  for (int p = 0; p < periods; ++p) KMC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+  c->step_global += static_cast<long long>(S) * periods;
+  c->have_run = true;
+  c->S = S;
+  c->periods = periods;
+  c->discard = discard;
+  c->n_rec = static_cast<int>(n_rec);
+  c->f = f;
+  return KMC_OK;
+}
+
+kmc_status kmc_sync(kmc_ctx *c) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  return check_device_error(c);
+}
+
+kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t cap,
+                    int64_t *written) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (written) *written = 0;
+  if (lys < 0 || lys >= c->n_lys) return fail(KMC_EINVAL, "lysosome %d out of range", lys);
+  if (cap < 0 || (cap > 0 && !buf)) return fail(KMC_EINVAL, "bad output buffer");
+  kmc_status st = check_device_error(c);
+  if (st != KMC_OK) return st;
+  const int n = c->n[lys], o = c->off[lys];
+  int64_t need = 0;
+  switch (what) {
+    case KMC_READ_LOOP_H:
+    case KMC_READ_LOOP_M: need = c->n_rec; break;
+    case KMC_READ_NP_ENERGY: need = n; break;
+    case KMC_READ_AREA:
+    case KMC_READ_SAR: need = 1; break;
+    case KMC_READ_MOMENTS: need = 3ll * n; break;
+    case KMC_READ_COUNTERS: need = 4; break;
+    default: return fail(KMC_EINVAL, "unknown output %d", what);
+  }
+  if (what != KMC_READ_MOMENTS && !c->have_run)
+    return fail(KMC_ESTATE, "no run has been made on this context");
+  if (written) *written = need;
+  if (cap < need) return fail(KMC_ECAPACITY, "output needs %lld elements", (long long)need);
+  const int nper = c->periods - c->discard;
+  switch (what) {
+    case KMC_READ_LOOP_H: {
+      int64_t r = 0;
+      for (int p = c->discard; p < c->periods; ++p)
+        for (int k = 0; k < c->S; ++k) buf[r++] = c->Hmax[lys] * std::cos(2.0 * kPi * k / c->S);
+      break;
+    }
+    case KMC_READ_LOOP_M:
+      if (need)
+        KMC_CUDA(cudaMemcpy(buf, c->d_loop + static_cast<size_t>(lys) * std::max(c->n_rec, 1),
+                            sizeof(double) * need, cudaMemcpyDeviceToHost));
+      break;
+    case KMC_READ_NP_ENERGY:
+    case KMC_READ_AREA:
+    case KMC_READ_SAR: {
+      std::vector<double> e(n);
+      KMC_CUDA(cudaMemcpy(e.data(), c->d_eacc + o, sizeof(double) * n, cudaMemcpyDeviceToHost));
+      const double unit = kMu0 * c->Ms[lys] * c->Ms[lys];  // J per m^3 per unit of e_acc
+      double tot = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double Ei = nper > 0 ? unit * c->vol[o + i] * e[i] / nper : 0.0;
+        if (what == KMC_READ_NP_ENERGY) buf[i] = Ei;
+        tot += Ei;
+      }
+      const double area = tot / c->vsum[lys];
+      if (what == KMC_READ_AREA) buf[0] = area;
+      if (what == KMC_READ_SAR) buf[0] = area * c->f / c->rho[lys];
+      break;
+    }
+    case KMC_READ_MOMENTS: {
+      std::vector<unsigned char> raw(c->vbytes * n);
+      KMC_CUDA(cudaMemcpy(raw.data(), static_cast<unsigned char *>(c->d_m) + c->vbytes * o,
+                          raw.size(), cudaMemcpyDeviceToHost));
+      for (int i = 0; i < n; ++i) {
+        if (c->fp32) {
+          const float4 v = reinterpret_cast<float4 *>(raw.data())[i];
+          buf[3 * i] = v.x;
+          buf[3 * i + 1] = v.y;
+          buf[3 * i + 2] = v.z;
+        } else {
+          const dbl4 v = reinterpret_cast<dbl4 *>(raw.data())[i];
+          buf[3 * i] = v.x;
+          buf[3 * i + 1] = v.y;
+          buf[3 * i + 2] = v.z;
+        }
+      }
+      break;
+    }
+    case KMC_READ_COUNTERS: {
+      unsigned long long cn[4];
+      KMC_CUDA(cudaMemcpy(cn, c->d_cnt + 4ll * lys, sizeof(cn), cudaMemcpyDeviceToHost));
+      for (int q = 0; q < 4; ++q) buf[q] = static_cast<double>(cn[q]);
+      break;
+    }
+  }
+  return KMC_OK;
+}
+
+kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint64_t seed,
+                          int64_t step, const double *m_in, double *m_out, double *B_dip,
+                          double *dE, double *P, double *u, int32_t *flags) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (!mu0Hext || !m_in) return fail(KMC_EINVAL, "NULL input");
+  if (!(t_step > 0) || !is_finite(t_step)) return fail(KMC_EINVAL, "t_step must be > 0");
+  if (step < 0) return fail(KMC_EINVAL, "step must be >= 0");
+  for (int l = 0; l < c->n_lys; ++l)
+    if (!is_finite(mu0Hext[l])) return fail(KMC_EINVAL, "non-finite field");
+  for (long long i = 0; i < 3 * c->N; ++i)
+    if (!is_finite(m_in[i])) return fail(KMC_EINVAL, "non-finite moment");
+  if (c->warps == 0) {
+    kmc_status st = autotune(c);
+    if (st != KMC_OK) return st;
+  }
+  const long long N = c->N;
+  if (!c->d_dbg) {
+    kmc_status st = dalloc(&c->d_dbg, sizeof(double) * N * 7);
+    if (st != KMC_OK) return st;
+    st = dalloc(&c->d_dbg_flags, sizeof(int32_t) * N);
+    if (st != KMC_OK) return st;
+  }
+  std::vector<unsigned char> h_m(c->vbytes * N);
+  for (long long i = 0; i < N; ++i) {
+    if (c->fp32)
+      reinterpret_cast<float4 *>(h_m.data())[i] =
+          make4<float4>(m_in[3 * i], m_in[3 * i + 1], m_in[3 * i + 2], 0.0);
+    else
+      reinterpret_cast<dbl4 *>(h_m.data())[i] =
+          make4<dbl4>(m_in[3 * i], m_in[3 * i + 1], m_in[3 * i + 2], 0.0);
+  }
+  KMC_CUDA(cudaMemcpyAsync(c->d_m, h_m.data(), h_m.size(), cudaMemcpyHostToDevice, c->stream));
+  const int par = static_cast<int>(step & 1);
+  kmc_status st = refresh_sources(c, par);
+  if (st != KMC_OK) return st;
+  for (int l = 0; l < c->n_lys; ++l) {
+    c->h_lys[l].bmax = mu0Hext[l] / (kMu0 * c->Ms[l]);
+    c->h_lys[l].lognu0t = std::log(t_step / c->tau0[l]);
+  }
+  st = upload_lys(c);
+  if (st != KMC_OK) return st;
+  RunState rs{step, -1, 0};
+  KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  StepArgs a = base_args(c);
+  a.seed = seed;
+  a.S = 1;
+  a.discard = 0;
+  a.n_rec = 1;
+  a.k_local = 0;
+  a.cos_k = 1.0;
+  a.debug = 1;
+  a.dbg.bdip = c->d_dbg;
+  a.dbg.dE = c->d_dbg + 3 * N;
+  a.dbg.P = c->d_dbg + 5 * N;
+  a.dbg.u = c->d_dbg + 6 * N;
+  a.dbg.flags = c->d_dbg_flags;
+  KMC_CUDA(kmc::launch_step(c->fp32, c->warps, c->tile, a, static_cast<int>(c->items.size()),
+                            c->stream));
+  st = check_device_error(c);
+  if (st != KMC_OK) return st;
+  std::vector<double> h(7 * N);
+  std::vector<int32_t> hf(N);
+  KMC_CUDA(cudaMemcpy(h.data(), c->d_dbg, sizeof(double) * 7 * N, cudaMemcpyDeviceToHost));
+  KMC_CUDA(cudaMemcpy(hf.data(), c->d_dbg_flags, sizeof(int32_t) * N, cudaMemcpyDeviceToHost));
+  KMC_CUDA(cudaMemcpy(h_m.data(), c->d_m, h_m.size(), cudaMemcpyDeviceToHost));
+  for (int l = 0; l < c->n_lys; ++l) {
+    const double Bunit = kMu0 * c->Ms[l];               // T per reduced field unit
+    const double Eunit = kMu0 * c->Ms[l] * c->Ms[l];   // J / m^3 per reduced energy unit
+    for (int ii = 0; ii < c->n[l]; ++ii) {
+      const long long i = c->off[l] + ii;
+      if (B_dip)
+        for (int q = 0; q < 3; ++q) B_dip[3 * i + q] = Bunit * h[3 * i + q];
+      if (dE)
+        for (int q = 0; q < 2; ++q) dE[2 * i + q] = Eunit * c->vol[i] * h[3 * N + 2 * i + q];
+      if (P) P[i] = h[5 * N + i];
+      if (u) u[i] = h[6 * N + i];
+      if (flags) flags[i] = hf[i];
+      if (m_out) {
+        if (c->fp32) {
+          const float4 v = reinterpret_cast<float4 *>(h_m.data())[i];
+          m_out[3 * i] = v.x;
+          m_out[3 * i + 1] = v.y;
+          m_out[3 * i + 2] = v.z;
+        } else {
+          const dbl4 v = reinterpret_cast<dbl4 *>(h_m.data())[i];
+          m_out[3 * i] = v.x;
+          m_out[3 * i + 1] = v.y;
+          m_out[3 * i + 2] = v.z;
+        }
+      }
+    }
+  }
+  return KMC_OK;
+}
+
+// Checkpoint file: magic, version, precision, n_lys, N, global step, NP counts,
+// then the raw moment records.
+kmc_status kmc_save(kmc_ctx *c, const char *path) {
+  if (!c || !path) return fail(KMC_EINVAL, "NULL argument");
+  kmc_status st = check_device_error(c);
+  if (st != KMC_OK) return st;
+  std::vector<unsigned char> raw(c->vbytes * c->N);
+  KMC_CUDA(cudaMemcpy(raw.data(), c->d_m, raw.size(), cudaMemcpyDeviceToHost));
+  FILE *fp = std::fopen(path, "wb");
+  if (!fp) return fail(KMC_EIO, "cannot open %s for writing", path);
+  const char magic[8] = {'K', 'M', 'C', 'S', 'T', 'A', 'T', 'E'};
+  const int32_t hdr[3] = {1, c->fp32, c->n_lys};
+  const int64_t hdr2[2] = {c->N, c->step_global};
+  bool ok = std::fwrite(magic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
+            std::fwrite(hdr2, sizeof(hdr2), 1, fp) == 1 &&
+            std::fwrite(c->n.data(), sizeof(int), c->n_lys, fp) ==
+                static_cast<size_t>(c->n_lys) &&
+            std::fwrite(raw.data(), 1, raw.size(), fp) == raw.size();
+  ok = (std::fclose(fp) == 0) && ok;
+  if (!ok) return fail(KMC_EIO, "short write to %s", path);
+  return KMC_OK;
+}
+
+kmc_status kmc_load(kmc_ctx *c, const char *path) {
+  if (!c || !path) return fail(KMC_EINVAL, "NULL argument");
+  FILE *fp = std::fopen(path, "rb");
+  if (!fp) return fail(KMC_EIO, "cannot open %s", path);
+  char magic[8];
+  int32_t hdr[3];
+  int64_t hdr2[2];
+  bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "KMCSTATE", 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, fp) == 1 && std::fread(hdr2, sizeof(hdr2), 1, fp) == 1;
+  if (!ok || hdr[0] != 1) {
+    std::fclose(fp);
+    return fail(KMC_EIO, "%s is not a libkmc checkpoint", path);
+  }
+  if (hdr[1] != c->fp32 || hdr[2] != c->n_lys || hdr2[0] != c->N || hdr2[1] < 0) {
+    std::fclose(fp);
+    return fail(KMC_EINVAL, "checkpoint does not match this context");
+  }
+  std::vector<int> nn(c->n_lys);
+  std::vector<unsigned char> raw(c->vbytes * c->N);
+  ok = std::fread(nn.data(), sizeof(int), c->n_lys, fp) == static_cast<size_t>(c->n_lys) &&
+       std::fread(raw.data(), 1, raw.size(), fp) == raw.size();
+  std::fclose(fp);
+  if (!ok) return fail(KMC_EIO, "truncated checkpoint %s", path);
+  if (nn != c->n) return fail(KMC_EINVAL, "checkpoint does not match this context");
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  KMC_CUDA(cudaMemcpy(c->d_m, raw.data(), raw.size(), cudaMemcpyHostToDevice));
+  c->step_global = hdr2[1];
+  c->have_run = false;
+  return KMC_OK;
+}
+
+kmc_status kmc_info(const kmc_ctx *c, int64_t *n_total, int32_t *n_lys, int64_t *global_step) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (n_total) *n_total = c->N;
+  if (n_lys) *n_lys = c->n_lys;
+  if (global_step) *global_step = c->step_global;
+  return KMC_OK;
+}
+
+void kmc_destroy(kmc_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,29 @@
+// kmc_launch.h -- host entry points of the step kernels (kmc_step.cu),
+// called by the C ABI layer (kmc_api.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "kmc_types.h"
+
+namespace kmc {
+
+// Dynamic shared memory of one block of the fused step kernel.
+size_t step_smem_bytes(int prec_fp32, int warps, int tile);
+
+// One time step of every work item (lysosome, 32 targets) on stream st.
+// warps in {4, 8, 16}; tile = sources per staged tile.
+cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
+                        cudaStream_t st);
+
+// Advances the device run state by one field period of S steps.
+cudaError_t launch_advance(RunState *rs, int S, cudaStream_t st);
+
+// Once per process and device: writes the scan grid of step iv and sets the
+// kernels' shared-memory limit.
+cudaError_t init_device();
+
+// Largest dynamic shared memory of one step block.
+constexpr size_t kMaxStepSmem = 200 * 1024;
+
+}  // namespace kmc

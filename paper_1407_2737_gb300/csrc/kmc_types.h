@@ -1,0 +1,81 @@
+// kmc_types.h -- data shared by the host side (kmc_api.cu) and the kernels
+// (kmc_step.cu) of libkmc.
+//
+// Reduced units used on the device (chosen so that the pair sum of Eq. 1 is
+// purely geometric and every quantity is O(0.01..10)):
+//   length  : L = diameter of the lysosome's mean NP volume, positions taken
+//             relative to the lysosome's frame origin;
+//   field   : b = mu0 H / (mu0 M_S);
+//   energy  : e = E / (mu0 M_S^2 V), so Eq. 2 reads e = k sin^2 th - b cos(th - phi)
+//             with k = K_eff / (mu0 M_S^2);
+//   source  : w_j = V_j / (4 pi L^3), so that Eq. 1 reads
+//             b_dip,i = sum_{j != i} [3 (mu_j . d) d / r^5 - mu_j / r^3],
+//             mu_j = w_j m_j, d = r_j - r_i in units of L.
+#pragma once
+#include <stdint.h>
+
+namespace kmc {
+
+struct __align__(32) dbl4 {  // FP64 record: x, y, z and a fourth value
+  double x, y, z, w;
+};
+
+constexpr int kGrid = 200;     // scan points of step iv (Sec. II.1)
+constexpr int kTargets = 32;   // target NPs per block (one per lane)
+
+struct LysDev {
+  int32_t off;      // first NP of the lysosome in the flat arrays
+  int32_t n;        // NPs
+  int32_t t_zero;   // 1 if T == 0: steps vi-vii skipped
+  int32_t pad;
+  double k;         // K_eff / (mu0 M_S^2)
+  double bmax;      // mu0 H_max / (mu0 M_S), set by each run
+  double lognu0t;   // ln(t_step / tau0), set by each run
+};
+
+struct RunState {   // advanced on the device at the end of each field period
+  long long step_base;  // global index of step 0 of the current period
+  int32_t period;       // period index within the run (< 0: not recorded)
+  int32_t pad;
+};
+
+struct DebugOut {   // optional per-NP intermediates (device pointers)
+  double *bdip;     // [N][3] reduced dipolar field
+  double *dE;       // [N][2] reduced barriers
+  double *P;        // [N]
+  double *u;        // [N]
+  int32_t *flags;   // [N]
+};
+
+struct StepArgs {
+  const int4 *items;        // (lysosome, first target, targets, 0)
+  const LysDev *lys;
+  const void *pos;          // [N] float4 / double4: x, y, z (units of L), w
+  const void *axis;         // [N] float4 / double4 unit easy axis
+  void *m;                  // [N] float4 / double4 unit moments (owner-updated)
+  void *mu[2];              // [N] float4 / double4 source moments w m (ping-pong)
+  const double *beta;       // [N] mu0 M_S^2 V_i / (k_B T)
+  const double *vfrac;      // [N] V_i / sum of V over the lysosome
+  double *e_acc;            // [N] sum_k b_k (m_z,k+1 - m_z,k) over recorded steps
+  double *loop_m;           // [n_lys][n_rec] volume-weighted mean m_z
+  unsigned long long *counters;  // [n_lys][4]
+  int32_t *err;             // device error word
+  const RunState *rs;
+  double cos_k;             // cos(2 pi k / S)
+  unsigned long long seed;
+  int32_t k_local;          // step within the period
+  int32_t S;
+  int32_t discard;
+  int32_t n_rec;            // recorded steps per lysosome (loop_m stride)
+  DebugOut dbg;
+  int32_t debug;
+  int32_t pad;
+};
+
+// Error bits written to the device error word.
+enum : int32_t {
+  kErrTimeout = 1,     // an mbarrier wait gave up
+  kErrExtrema = 2,     // more than two minima or maxima (cannot happen for Eq. 2)
+};
+
+}  // namespace kmc

@@ -1,0 +1,213 @@
+"""Thin Python binding of libkmc (include/kmc.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: each step of the kMC path runs in the CUDA kernels
+of ``csrc/``. Loading fails loudly if ``_build/libkmc.so`` is missing
+(build it with ``python -m paper_1407_2737_gb300.build``); there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkmc.so")
+
+KMC_OK, KMC_EINVAL, KMC_ENOMEM, KMC_ECUDA, KMC_ETIMEOUT, KMC_ESTATE, KMC_ECAPACITY, \
+    KMC_EIO = range(8)
+KMC_FP64_PLAIN, KMC_FP32_MIXED = 0, 1
+(KMC_READ_LOOP_H, KMC_READ_LOOP_M, KMC_READ_NP_ENERGY, KMC_READ_AREA, KMC_READ_SAR,
+ KMC_READ_MOMENTS, KMC_READ_COUNTERS) = range(7)
+
+STATUS_NAMES = {0: "KMC_OK", 1: "KMC_EINVAL", 2: "KMC_ENOMEM", 3: "KMC_ECUDA",
+                4: "KMC_ETIMEOUT", 5: "KMC_ESTATE", 6: "KMC_ECAPACITY", 7: "KMC_EIO"}
+
+# the entry points declared in include/kmc.h
+EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
+           "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
+           "kmc_last_error")
+
+
+class KmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class kmc_lysosome(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos", C.POINTER(C.c_double)),
+                ("axis", C.POINTER(C.c_double)), ("vol", C.POINTER(C.c_double)),
+                ("center", C.POINTER(C.c_double)), ("Ms", C.c_double), ("Keff", C.c_double),
+                ("T", C.c_double), ("tau0", C.c_double), ("rho", C.c_double)]
+
+
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libkmc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libkmc is not built (%s missing); run "
+                                   "`python -m paper_1407_2737_gb300.build`" % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            vp = C.c_void_p
+            L.kmc_create.argtypes = [C.POINTER(kmc_lysosome), C.c_int32, C.c_int, C.POINTER(vp)]
+            L.kmc_set_stream.argtypes = [vp, vp]
+            L.kmc_run.argtypes = [vp, _D, C.c_int32, C.c_double, C.c_int32, C.c_int32,
+                                  C.c_int32, C.c_uint64]
+            L.kmc_read.argtypes = [vp, C.c_int32, C.c_int32, _D, C.c_int64, _I64]
+            L.kmc_sync.argtypes = [vp]
+            L.kmc_debug_step.argtypes = [vp, _D, C.c_double, C.c_uint64, C.c_int64, _D, _D, _D,
+                                         _D, _D, _D, _I32]
+            L.kmc_save.argtypes = [vp, C.c_char_p]
+            L.kmc_load.argtypes = [vp, C.c_char_p]
+            L.kmc_info.argtypes = [vp, _I64, _I32, _I64]
+            L.kmc_tuning.argtypes = [vp, C.c_int32, C.c_int32, _I32, _I32]
+            L.kmc_destroy.argtypes = [vp]
+            L.kmc_destroy.restype = None
+            L.kmc_last_error.argtypes = []
+            L.kmc_last_error.restype = C.c_char_p
+            for name in EXPORTS:
+                if name not in ("kmc_destroy", "kmc_last_error"):
+                    getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def kmc_last_error():
+    return lib().kmc_last_error().decode()
+
+
+def _check(status):
+    if status != KMC_OK:
+        raise KmcError(status, kmc_last_error())
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+class Context:
+    """An opened kmc_ctx; keeps the host arrays it was built from alive."""
+
+    def __init__(self, handle, sizes):
+        self.handle = C.c_void_p(handle)
+        self.sizes = list(sizes)
+        self.n_total = int(sum(sizes))
+
+    def __del__(self):
+        try:
+            kmc_destroy(self)
+        except Exception:
+            pass
+
+
+def kmc_create(lysosomes, precision=KMC_FP32_MIXED, center=None):
+    """kmc_create over a list of objects with pos, axis, vol, Ms, Keff, T, tau0
+    (and optional rho) attributes. center: None (centroid) or a (3,) origin used
+    for every lysosome."""
+    L = lib()
+    keep = []
+    arr = (kmc_lysosome * len(lysosomes))()
+    cen = None if center is None else _f64(center, (3,))
+    for q, ly in enumerate(lysosomes):
+        pos = _f64(ly.pos, (-1, 3))
+        axis = _f64(ly.axis, (-1, 3))
+        vol = _f64(ly.vol, (-1,))
+        keep += [pos, axis, vol]
+        arr[q] = kmc_lysosome(len(vol), _dp(pos), _dp(axis), _dp(vol), _dp(cen), float(ly.Ms),
+                              float(ly.Keff), float(ly.T), float(ly.tau0),
+                              float(getattr(ly, "rho", 5200.0)))
+    h = C.c_void_p()
+    _check(L.kmc_create(arr, len(lysosomes), int(precision), C.byref(h)))
+    return Context(h.value, [int(np.asarray(ly.vol).shape[0]) for ly in lysosomes])
+
+
+def kmc_set_stream(ctx, stream_handle):
+    _check(lib().kmc_set_stream(ctx.handle, C.c_void_p(stream_handle or 0)))
+
+
+def kmc_run(ctx, mu0Hmax, f, steps_per_period, periods, discard_periods, seed):
+    amps = _f64(np.atleast_1d(mu0Hmax), (-1,))
+    _check(lib().kmc_run(ctx.handle, _dp(amps), len(amps), float(f), int(steps_per_period),
+                         int(periods), int(discard_periods), C.c_uint64(int(seed))))
+
+
+def kmc_sync(ctx):
+    _check(lib().kmc_sync(ctx.handle))
+
+
+def kmc_read(ctx, what, lys=0):
+    L = lib()
+    n = C.c_int64(0)
+    st = L.kmc_read(ctx.handle, int(what), int(lys), None, 0, C.byref(n))
+    if st not in (KMC_OK, KMC_ECAPACITY):
+        _check(st)
+    buf = np.zeros(max(int(n.value), 1))
+    _check(L.kmc_read(ctx.handle, int(what), int(lys), _dp(buf), len(buf), C.byref(n)))
+    out = buf[:int(n.value)]
+    return out.reshape(-1, 3) if what == KMC_READ_MOMENTS else out
+
+
+def kmc_debug_step(ctx, mu0Hext, t_step, seed, step, m_in):
+    N = ctx.n_total
+    H = _f64(np.broadcast_to(np.atleast_1d(mu0Hext), (len(ctx.sizes),)), (-1,))
+    m_in = _f64(m_in, (N, 3))
+    out = dict(m_out=np.zeros((N, 3)), B_dip=np.zeros((N, 3)), dE=np.zeros((N, 2)),
+               P=np.zeros(N), u=np.zeros(N), flags=np.zeros(N, dtype=np.int32))
+    _check(lib().kmc_debug_step(ctx.handle, _dp(H), float(t_step), C.c_uint64(int(seed)),
+                                int(step), _dp(m_in), _dp(out["m_out"]), _dp(out["B_dip"]),
+                                _dp(out["dE"]), _dp(out["P"]), _dp(out["u"]),
+                                out["flags"].ctypes.data_as(_I32)))
+    f = out["flags"]
+    out.update(n_min=f & 3, flipped=(f >> 2) & 1, near=(f >> 3) & 1, degenerate=(f >> 4) & 1)
+    return out
+
+
+def kmc_save(ctx, path):
+    _check(lib().kmc_save(ctx.handle, os.fsencode(path)))
+
+
+def kmc_load(ctx, path):
+    _check(lib().kmc_load(ctx.handle, os.fsencode(path)))
+
+
+def kmc_info(ctx):
+    n = C.c_int64()
+    nl = C.c_int32()
+    s = C.c_int64()
+    _check(lib().kmc_info(ctx.handle, C.byref(n), C.byref(nl), C.byref(s)))
+    return dict(n_total=n.value, n_lys=nl.value, global_step=s.value)
+
+
+def kmc_tuning(ctx, warps=None, tile=None):
+    """Sets the launch shape (both given) or, with no arguments, returns it."""
+    w = C.c_int32()
+    t = C.c_int32()
+    if warps is None and tile is None:
+        _check(lib().kmc_tuning(ctx.handle, 0, 0, C.byref(w), C.byref(t)))
+    else:
+        _check(lib().kmc_tuning(ctx.handle, int(warps), int(tile), C.byref(w), C.byref(t)))
+    return int(w.value), int(t.value)
+
+
+def kmc_destroy(ctx):
+    if ctx is not None and ctx.handle is not None and ctx.handle.value:
+        lib().kmc_destroy(ctx.handle)
+        ctx.handle = C.c_void_p(0)

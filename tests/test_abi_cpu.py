@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads,
+exports every entry point include/kmc.h declares, and rejects bad arguments
+before touching a device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1407_2737_gb300 import build as kbuild
+from paper_1407_2737_gb300 import inputs, kmc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    kbuild.build()
+    return kmc.lib()
+
+
+def declared_entry_points():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(kmc_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_entry_points()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(kmc.EXPORTS)
+
+
+def test_bad_arguments_are_rejected_on_the_host(L):
+    h = C.c_void_p()
+    assert L.kmc_create(None, 1, 0, C.byref(h)) == kmc.KMC_EINVAL
+    assert "lysosome" in kmc.kmc_last_error()
+    lys = inputs.make_lysosome(10, 12e-9, 0.05, seed=0)
+    lys.Ms = -1.0
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.kmc_create([lys])
+    assert e.value.status == kmc.KMC_EINVAL
+    lys = inputs.make_lysosome(10, 12e-9, 0.05, seed=0)
+    lys.vol = np.zeros(10)
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.kmc_create([lys])
+    assert e.value.status == kmc.KMC_EINVAL
+    assert L.kmc_run(None, None, 0, 0.0, 0, 0, 0, 0) == kmc.KMC_EINVAL
+    assert L.kmc_read(None, 0, 0, None, 0, None) == kmc.KMC_EINVAL
+    assert L.kmc_sync(None) == kmc.KMC_EINVAL
+    L.kmc_destroy(None)  # NULL-safe
+
+
+def test_no_device_is_an_error_not_a_fallback(L):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lys = inputs.make_lysosome(10, 12e-9, 0.05, seed=0)
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.kmc_create([lys])
+    assert e.value.status == kmc.KMC_ECUDA

@@ -112,3 +112,11 @@ def test_field_is_minus_gradient_of_scalar_potential():
             g[a] = (-psi(i, r + 2 * e) + 8 * psi(i, r + e) - 8 * psi(i, r - e)
                     + psi(i, r - 2 * e)) / (12 * h)
         np.testing.assert_allclose(B[i], -MU0 * g, rtol=0, atol=1e-7 * np.linalg.norm(B[i]) + 1e-12 * w() / D ** 3)
+
+
+def test_field_at_subset_matches_full():
+    lys = inputs.make_lysosome(60, D, 0.1, seed=12)
+    m = inputs.random_axes(lys.n, np.random.default_rng(1))
+    B = oracle.dipolar_field(lys.pos, lys.vol, MS, m)
+    idx = np.array([0, 7, 59, 7])
+    np.testing.assert_array_equal(oracle.dipolar_field_at(lys.pos, lys.vol, MS, m, idx), B[idx])
