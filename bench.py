@@ -1,0 +1,339 @@
+"""Benchmark of the kMC hysteresis hot path on GB300 (prints one JSON line).
+
+Workload (one bench step): the 2000-NP lysosome (d = 14 nm, K_eff = 2e4 J/m^3,
+M_S = 1e6 A/m, 10 % volume concentration, T = 300 K, tau0 = 1e-10 s) run as 8
+independent random streams (seeds), field along z with mu0 H_max = 20 mT,
+f = 100 kHz, 200 steps per period, 20 periods of which 5 are discarded: one
+complete kmc_run, i.e. 8 x 2000 x 4000 particle-steps, each step being the
+whole hot path (dipolar field, Stoner-Wohlfarth extrema, rates, draw, flip,
+loop energy). Inputs are seeded synthetic lysosomes (random sequential
+addition, easy axes uniform on the sphere).
+
+Reported: particle-steps/s of the FP32-mixed path with state resident on the
+GPU (value), the same through the C ABI from host buffers (e2e), the FP64-plain
+GPU path on a bounded sample, the SAR error of FP32-mixed against FP64 on the
+same seeds, the roofline of the fused step kernel (FP32 pipe) and the FP64
+oracle timed on the host cores (cpu_baseline).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s, FP32-mixed vs FP64 plain at SAR err <=1%; % FP32 peak"
+UNIT = "particle-steps/s"
+WORKLOAD = ("single lysosome N=2000 x 8 seeds, d=14 nm, Keff=2e4 J/m^3, Ms=1e6 A/m, "
+            "c=10%, T=300 K, tau0=1e-10 s, mu0Hmax=20 mT, f=100 kHz, "
+            "200 steps/period x 20 periods (5 discarded)")
+FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def fp32_peak_tflops():
+    """FP32 pipe peak: SMs x FP32 lanes x 2 flops x maximum SM clock."""
+    return SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        self.uuid = device_uuid
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["--id=" + self.uuid]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(lys, run, budget_s=10.0):
+    """The FP64 oracle, as it stands, on the host cores: one period of the
+    2000-NP lysosome (one of the 8 streams), repeated up to ~budget_s."""
+    import oracle
+    threads = os.cpu_count() or 1
+    done_steps, t0 = 0, time.perf_counter()
+    m = None
+    while True:
+        out = oracle.run(lys, 0, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"], m=m,
+                         step0=done_steps, nthreads=threads)
+        m = out["m"]
+        done_steps += run["S"]
+        el = time.perf_counter() - t0
+        if el > budget_s or el * (done_steps + run["S"]) / done_steps > 3 * budget_s:
+            break
+    value = lys.n * done_steps / el
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d steps (%d periods of %d) of one 2000-NP stream, %.1f s" % (
+                done_steps, done_steps // run["S"], run["S"], el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1407_2737_gb300 import inputs
+    lyss, run = inputs.config_single2000(replicas=8, seed=0)
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.run(lyss[0], k % 8, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"],
+                   nthreads=threads)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    units = lyss[0].n * run["S"]
+    value = units * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "one 200-step period of one 2000-NP "
+                       "stream per step (FP64 oracle, OpenMP over NPs)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "one 200-step period of one 2000-NP stream per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1407_2737_gb300 import build as kbuild
+    from paper_1407_2737_gb300 import inputs, kmc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(kbuild.LIB):
+        kbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    lyss, run = inputs.config_single2000(replicas=8, seed=0)
+    n_steps = run["S"] * run["periods"]
+    n_np = sum(l.n for l in lyss)
+    units_per_step = n_np * n_steps
+    pairs_per_launch = sum(l.n * (l.n - 1) for l in lyss)
+    # a non-default stream: its handle is what libkmc queues on and what the
+    # CUDA events below are recorded on
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    # --- FP32-mixed, state resident in HBM ---------------------------------
+    ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+    kmc.kmc_set_stream(ctx, stream.cuda_stream)
+    for _ in range(args.warmup):
+        kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
+                    run["seed"])
+    kmc.kmc_sync(ctx)
+    warps, tile, chunk = kmc.kmc_tuning(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    barrier_sync()
+    with Clocks(uuid) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"],
+                        run["discard"], run["seed"])
+            ev[k][1].record(stream)
+        barrier_sync()
+    kmc.kmc_sync(ctx)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = max_over_ranks(sum(ms) / 1e3)
+    value = world * units_per_step * args.steps / t_total
+    ms_per_step = 1e3 * t_total / args.steps
+    sar32 = [kmc.kmc_read(ctx, kmc.KMC_READ_SAR, l)[0] for l in range(len(lyss))]
+    launches_per_step = 1 + run["periods"] * (run["S"] + 1)
+    # roofline of the fused step kernel: one launch per kMC step
+    launch_s = t_total / (args.steps * n_steps)
+    achieved = FLOPS_PER_PAIR * pairs_per_launch / launch_s / 1e12
+    peak = fp32_peak_tflops()
+    kmc.kmc_destroy(ctx)
+
+    # --- end to end through the C ABI from host buffers ---------------------
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+        kmc.kmc_run(c, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
+                    run["seed"])
+        for l in range(len(lyss)):
+            kmc.kmc_read(c, kmc.KMC_READ_SAR, l)
+            kmc.kmc_read(c, kmc.KMC_READ_LOOP_M, l)
+            kmc.kmc_read(c, kmc.KMC_READ_NP_ENERGY, l)
+        kmc.kmc_destroy(c)
+        if k >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_t = max_over_ranks(sum(e2e_times))
+    n_rec = run["S"] * (run["periods"] - run["discard"])
+    h2d = sum(l.n * 7 * 8 for l in lyss) + 8 * 3
+    d2h = sum(8 + 8 * n_rec + 8 * l.n for l in lyss)
+
+    # --- FP64-plain GPU path: bounded sample + full-run SAR on the same seeds
+    fp64 = None
+    if not args.no_fp64:
+        c64 = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
+        kmc.kmc_set_stream(c64, stream.cuda_stream)
+        kmc.kmc_run(c64, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"])  # tune
+        kmc.kmc_destroy(c64)
+        c64 = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
+        kmc.kmc_set_stream(c64, stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kmc.kmc_run(c64, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
+                    run["seed"])
+        e1.record(stream)
+        kmc.kmc_sync(c64)
+        t64 = e0.elapsed_time(e1) / 1e3
+        sar64 = [kmc.kmc_read(c64, kmc.KMC_READ_SAR, l)[0] for l in range(len(lyss))]
+        kmc.kmc_destroy(c64)
+        rel = abs(np.mean(sar32) - np.mean(sar64)) / abs(np.mean(sar64))
+        fp64 = {"value": units_per_step / t64, "unit": UNIT, "ms_per_step": 1e3 * t64,
+                "sar_W_per_g": float(np.mean(sar64)) / 1e3,
+                "sar_rel_err_fp32_vs_fp64": float(rel),
+                "speedup_fp32_mixed": float(value / world / (units_per_step / t64))}
+
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_cpu and args.gpus == 1:
+        cpu = cpu_oracle_sample(lyss[0], run)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-mixed", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "KMC_FP32_MIXED",
+                       "kmc_steps_per_bench_step": n_steps, "particles": n_np,
+                       "launch": {"warps": warps, "tile": tile, "chunk": chunk},
+                       "l2": "256 MB buffer written between timed steps (state < L2)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "pair_interactions_per_s": world * pairs_per_launch * n_steps * args.steps / t_total,
+            "sar_W_per_g": float(np.mean(sar32)) / 1e3,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "kmc_step_f32<%d>" % warps,
+                         "note": "FP32 pipe: 30 flops per ordered pair; launch time = timed "
+                                 "region / step launches (includes graph gaps); peak = "
+                                 "152 SM x 128 lanes x 2 x 2070 MHz"},
+            "fp64_plain": fp64,
+            "e2e": {"value": world * units_per_step * args.steps / e2e_t, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

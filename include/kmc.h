@@ -148,12 +148,16 @@ kmc_status kmc_load(kmc_ctx *ctx, const char *path);
 kmc_status kmc_info(const kmc_ctx *ctx, int64_t *n_total, int32_t *n_lys,
                     int64_t *global_step);
 
-/* Launch shape of the fused step kernel: warps per block splitting the source
- * range, sources per shared-memory tile; 0 lets the autotuner choose on the
- * next kmc_run. Returns the shape in use through the out pointers (may be
- * NULL). */
-kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t *warps_out,
-                      int32_t *tile_out);
+/* Launch shape of the fused step kernel. warps: warps per block, each taking
+ * every warps-th source record of a tile (4, 8 or 16). tile: source records per
+ * shared-memory tile (a power of two, 32..1024; an FP32 record holds two NPs,
+ * an FP64 record one). chunk: sources per work item when a lysosome's sources
+ * are split over several blocks (0 = never split; else a multiple of 64).
+ * All three 0 (or warps = 0) lets the autotuner choose on the next kmc_run or
+ * kmc_debug_step. The shape in use is returned through the out pointers (each
+ * may be NULL); call with warps = tile = chunk = -1 to only read it. */
+kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
+                      int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out);
 
 /* Frees the context and its device memory. NULL-safe. */
 void kmc_destroy(kmc_ctx *ctx);

@@ -1,6 +1,7 @@
 // kmc_api.cu -- the C ABI of libkmc (include/kmc.h): contexts, device memory,
-// the CUDA-graph step loop, the launch-shape autotuner, checkpoints and the
-// test hook. All arithmetic of the kMC step itself lives in kmc_step.cu.
+// work items, the CUDA-graph step loop, the launch-shape autotuner,
+// checkpoints and the test hook. All arithmetic of the kMC step itself lives
+// in kmc_step.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,8 +19,10 @@
 #include "kmc_launch.h"
 
 using kmc::dbl4;
+using kmc::Item;
 using kmc::LysDev;
 using kmc::RunState;
+using kmc::SrcPair;
 using kmc::StepArgs;
 
 namespace {
@@ -47,9 +50,14 @@ kmc_status fail(kmc_status s, const char *fmt, ...) {
       return fail(KMC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
   } while (0)
 
+#define KMC_TRY(x)                 \
+  do {                             \
+    kmc_status s_ = (x);           \
+    if (s_ != KMC_OK) return s_;   \
+  } while (0)
+
 bool is_finite(double x) { return std::isfinite(x); }
 
-// Fills a float4 / dbl4 from doubles.
 template <typename V>
 V make4(double x, double y, double z, double w) {
   V v;
@@ -60,20 +68,35 @@ V make4(double x, double y, double z, double w) {
   return v;
 }
 
-// mu[par][i] = w_i m_i for every NP: the source copy of the moments.
-template <typename V>
-__global__ void sources_from_moments(const V *__restrict__ pos, const V *__restrict__ m,
-                                     V *__restrict__ mu, long long n) {
+// Source moments w_i m_i of every NP into the source buffer of parity par.
+__global__ void sources_f32(const float4 *__restrict__ pos, const float4 *__restrict__ m,
+                            const int *__restrict__ slot, SrcPair *__restrict__ src, long long n) {
   const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
-  const V p = pos[i], q = m[i];
-  V r;
+  const float4 p = pos[i], q = m[i];
+  const int s = slot[i];
+  SrcPair &r = src[s >> 1];
+  r.mx[s & 1] = p.w * q.x;
+  r.my[s & 1] = p.w * q.y;
+  r.mz[s & 1] = p.w * q.z;
+}
+
+__global__ void sources_f64(const dbl4 *__restrict__ pos, const dbl4 *__restrict__ m,
+                            dbl4 *__restrict__ mu, long long n) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const dbl4 p = pos[i], q = m[i];
+  dbl4 r;
   r.x = p.w * q.x;
   r.y = p.w * q.y;
   r.z = p.w * q.z;
-  r.w = 0;
+  r.w = 0.0;
   mu[i] = r;
 }
+
+struct Shape {
+  int warps = 0, tile = 0, chunk = 0;
+};
 
 struct TuneKey {
   int prec;
@@ -84,19 +107,19 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::map<TuneKey, Shape> g_tune_cache;
 
-std::mutex g_tables_mu;
-std::vector<int> g_tables_done;  // per device ordinal
+std::mutex g_init_mu;
+std::vector<int> g_init_done;  // per device ordinal
 
-kmc_status ensure_tables() {
+kmc_status ensure_device_init() {
   int dev = 0;
   KMC_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(g_tables_mu);
-  if (static_cast<int>(g_tables_done.size()) <= dev) g_tables_done.resize(dev + 1, 0);
-  if (!g_tables_done[dev]) {
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (static_cast<int>(g_init_done.size()) <= dev) g_init_done.resize(dev + 1, 0);
+  if (!g_init_done[dev]) {
     KMC_CUDA(kmc::init_device());
-    g_tables_done[dev] = 1;
+    g_init_done[dev] = 1;
   }
   return KMC_OK;
 }
@@ -108,24 +131,33 @@ struct kmc_ctx {
   int n_lys = 0;
   long long N = 0;
   size_t vbytes = 0;  // sizeof(float4) or sizeof(dbl4)
-  std::vector<int> off, n;
+  std::vector<int> off, n, roff;
+  long long n_records = 0;  // source records over all lysosomes
   std::vector<double> Ms, Keff, T, tau0, rho, vsum;
   std::vector<double> vol;  // [N]
-  std::vector<int4> items;
   std::vector<LysDev> h_lys;
   // device memory
-  int4 *d_items = nullptr;
   LysDev *d_lys = nullptr;
-  void *d_pos = nullptr, *d_axis = nullptr, *d_m = nullptr, *d_mu[2] = {nullptr, nullptr};
-  double *d_beta = nullptr, *d_vfrac = nullptr, *d_eacc = nullptr, *d_loop = nullptr;
+  void *d_pos = nullptr, *d_axis = nullptr, *d_m = nullptr, *d_src[2] = {nullptr, nullptr};
+  int *d_slot = nullptr;  // FP32: record * 2 + half of each NP
+  double *d_beta = nullptr, *d_vfrac = nullptr, *d_eacc = nullptr;
+  long long *d_loop = nullptr;  // fixed point, units of 2^-62
   unsigned long long *d_cnt = nullptr;
   int32_t *d_err = nullptr;
   RunState *d_rs = nullptr;
   size_t loop_cap = 0;
+  // work items for the current shape and their scratch
+  Item *d_items = nullptr;
+  size_t items_cap = 0;
+  int n_items = 0;
+  float *d_partial = nullptr;
+  size_t partial_cap = 0;  // items
+  int32_t *d_arrivals = nullptr;
+  size_t arrivals_cap = 0;
+  int items_chunk = -1;
   // debug outputs, allocated on first use
   double *d_dbg = nullptr;
   int32_t *d_dbg_flags = nullptr;
-  // streams
   cudaStream_t own_stream = nullptr, stream = nullptr;
   long long step_global = 0;
   // latest run
@@ -134,13 +166,96 @@ struct kmc_ctx {
   double f = 0.0;
   std::vector<double> Hmax;
   // launch shape and the captured one-period graph
-  int warps = 0, tile = 0;
+  Shape shape;
   cudaGraphExec_t gexec = nullptr;
-  int g_S = -1, g_discard = -1, g_nrec = -1, g_warps = -1, g_tile = -1;
+  int g_S = -1, g_discard = -1, g_nrec = -1;
+  Shape g_shape;
   unsigned long long g_seed = 0;
 };
 
 namespace {
+
+template <typename T>
+kmc_status dalloc(T **p, size_t bytes) {
+  if (cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(KMC_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+  }
+  return KMC_OK;
+}
+
+void drop_graph(kmc_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+}
+
+// Work items for source chunk `chunk` (0 = one item per 32 targets), largest
+// lysosomes first; the items of a target group are consecutive.
+std::vector<Item> build_items(const kmc_ctx *c, int chunk, int *n_groups) {
+  std::vector<int> order(c->n_lys);
+  for (int l = 0; l < c->n_lys; ++l) order[l] = l;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return c->n[x] > c->n[y]; });
+  std::vector<Item> items;
+  int gid = 0;
+  for (int l : order) {
+    const int n = c->n[l];
+    const int nrec = c->fp32 ? (n + 1) / 2 : n;
+    const int rchunk = chunk > 0 ? (c->fp32 ? chunk / 2 : chunk) : nrec;
+    const int S = std::max(1, (nrec + rchunk - 1) / rchunk);
+    for (int t0 = 0; t0 < n; t0 += kmc::kTargets, ++gid) {
+      for (int s = 0; s < S; ++s) {
+        Item it;
+        it.l = l;
+        it.t0 = t0;
+        it.nt = std::min(kmc::kTargets, n - t0);
+        it.gid = gid;
+        it.j0 = static_cast<int>(static_cast<long long>(s) * nrec / S);
+        it.j1 = static_cast<int>(static_cast<long long>(s + 1) * nrec / S);
+        it.split = s;
+        it.nsplit = S;
+        items.push_back(it);
+      }
+    }
+  }
+  *n_groups = gid;
+  return items;
+}
+
+kmc_status set_items(kmc_ctx *c, int chunk) {
+  if (c->items_chunk == chunk && c->d_items) return KMC_OK;
+  int groups = 0;
+  const std::vector<Item> items = build_items(c, chunk, &groups);
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  if (items.size() > c->items_cap) {
+    if (c->d_items) cudaFree(c->d_items);
+    KMC_TRY(dalloc(&c->d_items, sizeof(Item) * items.size()));
+    c->items_cap = items.size();
+    drop_graph(c);
+  }
+  bool split = false;
+  for (const Item &it : items) split = split || it.nsplit > 1;
+  const size_t need_partial = split ? items.size() : 1;
+  if (need_partial > c->partial_cap) {
+    if (c->d_partial) cudaFree(c->d_partial);
+    KMC_TRY(dalloc(&c->d_partial, sizeof(float) * 12 * kmc::kTargets * need_partial));
+    c->partial_cap = need_partial;
+    drop_graph(c);
+  }
+  if (static_cast<size_t>(groups) > c->arrivals_cap) {
+    if (c->d_arrivals) cudaFree(c->d_arrivals);
+    KMC_TRY(dalloc(&c->d_arrivals, sizeof(int32_t) * groups));
+    c->arrivals_cap = groups;
+    drop_graph(c);
+  }
+  KMC_CUDA(cudaMemcpy(c->d_items, items.data(), sizeof(Item) * items.size(),
+                      cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemset(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap));
+  c->n_items = static_cast<int>(items.size());
+  c->items_chunk = chunk;
+  return KMC_OK;
+}
 
 StepArgs base_args(kmc_ctx *c) {
   StepArgs a;
@@ -150,29 +265,32 @@ StepArgs base_args(kmc_ctx *c) {
   a.pos = c->d_pos;
   a.axis = c->d_axis;
   a.m = c->d_m;
-  a.mu[0] = c->d_mu[0];
-  a.mu[1] = c->d_mu[1];
+  a.src[0] = c->d_src[0];
+  a.src[1] = c->d_src[1];
+  a.src_pos = c->fp32 ? nullptr : c->d_pos;
   a.beta = c->d_beta;
   a.vfrac = c->d_vfrac;
   a.e_acc = c->d_eacc;
   a.loop_m = c->d_loop;
   a.counters = c->d_cnt;
   a.err = c->d_err;
+  a.partial = c->d_partial;
+  a.arrivals = c->d_arrivals;
   a.rs = c->d_rs;
   return a;
 }
 
 kmc_status refresh_sources(kmc_ctx *c, int par) {
   const int bs = 256;
-  const long long nb = (c->N + bs - 1) / bs;
+  const unsigned nb = static_cast<unsigned>((c->N + bs - 1) / bs);
   if (c->fp32)
-    sources_from_moments<float4><<<static_cast<unsigned>(nb), bs, 0, c->stream>>>(
-        static_cast<const float4 *>(c->d_pos), static_cast<const float4 *>(c->d_m),
-        static_cast<float4 *>(c->d_mu[par]), c->N);
+    sources_f32<<<nb, bs, 0, c->stream>>>(static_cast<const float4 *>(c->d_pos),
+                                          static_cast<const float4 *>(c->d_m), c->d_slot,
+                                          static_cast<SrcPair *>(c->d_src[par]), c->N);
   else
-    sources_from_moments<dbl4><<<static_cast<unsigned>(nb), bs, 0, c->stream>>>(
-        static_cast<const dbl4 *>(c->d_pos), static_cast<const dbl4 *>(c->d_m),
-        static_cast<dbl4 *>(c->d_mu[par]), c->N);
+    sources_f64<<<nb, bs, 0, c->stream>>>(static_cast<const dbl4 *>(c->d_pos),
+                                          static_cast<const dbl4 *>(c->d_m),
+                                          static_cast<dbl4 *>(c->d_src[par]), c->N);
   KMC_CUDA(cudaGetLastError());
   return KMC_OK;
 }
@@ -195,23 +313,28 @@ kmc_status upload_lys(kmc_ctx *c) {
 }
 
 int max_tile(int fp32, int warps) {
-  // keep two blocks' worth of shared memory per SM
+  // keep at least two blocks' worth of shared memory per SM
   const size_t budget = 100 * 1024;
   int t = 1024;
   while (t > 32 && kmc::step_smem_bytes(fp32, warps, t) > budget) t /= 2;
   return t;
 }
 
-// Times one candidate launch shape on the current state (restored afterwards
-// by the caller). Returns milliseconds per step, or a negative value on error.
-float time_shape(kmc_ctx *c, int warps, int tile) {
+bool shape_ok(const kmc_ctx *c, const Shape &s) {
+  if (s.warps != 4 && s.warps != 8 && s.warps != 16) return false;
+  if (s.tile < 32 || s.tile > max_tile(c->fp32, s.warps) || (s.tile & (s.tile - 1))) return false;
+  if (s.chunk < 0 || (s.chunk % 64) != 0) return false;
+  return true;
+}
+
+// Times one candidate shape on the current state (restored by the caller).
+// Returns milliseconds per step, or a negative value on error.
+float time_shape(kmc_ctx *c, const Shape &s) {
+  if (set_items(c, s.chunk) != KMC_OK) return -1.f;
   StepArgs a = base_args(c);
   a.cos_k = 1.0;
-  a.seed = 0;
   a.S = 1;
-  a.discard = 0;
   a.n_rec = 1;
-  a.k_local = 0;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -220,14 +343,12 @@ float time_shape(kmc_ctx *c, int warps, int tile) {
   }
   float ms = -1.f;
   bool ok = true;
-  for (int r = 0; r < 3 && ok; ++r)
-    ok = kmc::launch_step(c->fp32, warps, tile, a, static_cast<int>(c->items.size()), c->stream) ==
-         cudaSuccess;
-  const int reps = 6;
+  for (int r = 0; r < 2 && ok; ++r)
+    ok = kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream) == cudaSuccess;
+  const int reps = 5;
   if (ok) ok = cudaEventRecord(e0, c->stream) == cudaSuccess;
   for (int r = 0; r < reps && ok; ++r)
-    ok = kmc::launch_step(c->fp32, warps, tile, a, static_cast<int>(c->items.size()), c->stream) ==
-         cudaSuccess;
+    ok = kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream) == cudaSuccess;
   if (ok) ok = cudaEventRecord(e1, c->stream) == cudaSuccess;
   if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
   if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms /= reps;
@@ -244,38 +365,50 @@ kmc_status autotune(kmc_ctx *c) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      c->warps = it->second.first;
-      c->tile = it->second.second;
-      return KMC_OK;
+      c->shape = it->second;
+      return set_items(c, c->shape.chunk);
     }
   }
-  // save the moments: the timed launches advance a scratch copy of the state
+  // the timed launches advance a scratch copy of the state: save the moments
   std::vector<unsigned char> saved(c->vbytes * c->N);
   KMC_CUDA(cudaMemcpyAsync(saved.data(), c->d_m, saved.size(), cudaMemcpyDeviceToHost, c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   RunState rs{c->step_global, -1, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
+  std::vector<LysDev> keep = c->h_lys;
   for (auto &L : c->h_lys) {
-    L.bmax = 0.0;
+    L.bmax = 0.01;
     L.lognu0t = std::log(5e-8 / 1e-10);
   }
-  kmc_status st = upload_lys(c);
-  if (st != KMC_OK) return st;
+  KMC_TRY(upload_lys(c));
+  c->h_lys = keep;
+  KMC_TRY(refresh_sources(c, static_cast<int>(c->step_global & 1)));
   float best = 1e30f;
-  int bw = 8, bt = 256;
-  const int warps_c[] = {4, 8, 16};
-  const int tiles_c[] = {64, 128, 256, 512, 1024};
+  Shape bs;
+  bs.warps = 4;
+  bs.tile = 64;
+  bs.chunk = 0;
+  const int warps_c[] = {4, 8};
+  const int tiles_f32[] = {64, 128, 256};
+  const int tiles_f64[] = {32, 64, 128};
+  const int chunks[] = {0, 256, 512, 1024, 2048, 4096, 8192};
   for (int w : warps_c) {
-    for (int t : tiles_c) {
+    for (int q = 0; q < 3; ++q) {
+      const int t = c->fp32 ? tiles_f32[q] : tiles_f64[q];
       if (t > max_tile(c->fp32, w)) continue;
-      if (t > 2 * std::max(max_n, 32) && t != 64) continue;
-      st = refresh_sources(c, static_cast<int>(c->step_global & 1));
-      if (st != KMC_OK) return st;
-      const float ms = time_shape(c, w, t);
-      if (ms > 0.f && ms < best) {
-        best = ms;
-        bw = w;
-        bt = t;
+      if ((c->fp32 ? 2 : 1) * t > 2 * std::max(max_n, 64) && q > 0) continue;
+      for (int ch : chunks) {
+        if (ch > 0 && ch >= max_n) continue;
+        if (ch > 0 && ch < (c->fp32 ? 2 : 1) * t) continue;
+        Shape s;
+        s.warps = w;
+        s.tile = t;
+        s.chunk = ch;
+        const float ms = time_shape(c, s);
+        if (ms > 0.f && ms < best) {
+          best = ms;
+          bs = s;
+        }
       }
     }
   }
@@ -283,31 +416,69 @@ kmc_status autotune(kmc_ctx *c) {
   KMC_CUDA(cudaMemcpyAsync(c->d_m, saved.data(), saved.size(), cudaMemcpyHostToDevice, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
-  c->warps = bw;
-  c->tile = bt;
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = {bw, bt};
-  return KMC_OK;
+  c->shape = bs;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = bs;
+  }
+  return set_items(c, bs.chunk);
+}
+
+kmc_status ensure_shape(kmc_ctx *c) {
+  if (c->shape.warps == 0) return autotune(c);
+  return set_items(c, c->shape.chunk);
 }
 
 void free_ctx(kmc_ctx *c) {
   if (!c) return;
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  void *ptrs[] = {c->d_items, c->d_lys, c->d_pos,  c->d_axis,  c->d_m,   c->d_mu[0],
-                  c->d_mu[1], c->d_beta, c->d_vfrac, c->d_eacc, c->d_loop, c->d_cnt,
-                  c->d_err,   c->d_rs,   c->d_dbg,   c->d_dbg_flags};
+  drop_graph(c);
+  void *ptrs[] = {c->d_lys,   c->d_pos,    c->d_axis,    c->d_m,        c->d_src[0],
+                  c->d_src[1], c->d_slot,  c->d_beta,    c->d_vfrac,    c->d_eacc,
+                  c->d_loop,  c->d_cnt,    c->d_err,     c->d_rs,       c->d_items,
+                  c->d_partial, c->d_arrivals, c->d_dbg, c->d_dbg_flags};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
 
-template <typename T>
-kmc_status dalloc(T **p, size_t bytes) {
-  if (cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(KMC_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
-  }
+kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_pos,
+                               const std::vector<unsigned char> &h_axis,
+                               const std::vector<unsigned char> &h_m,
+                               const std::vector<unsigned char> &h_src,
+                               const std::vector<int> &h_slot, const std::vector<double> &h_beta,
+                               const std::vector<double> &h_vfrac) {
+  const long long N = c->N;
+  KMC_CUDA(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+  c->stream = c->own_stream;
+  const size_t vb = c->vbytes * N;
+  KMC_TRY(dalloc(&c->d_lys, sizeof(LysDev) * c->n_lys));
+  KMC_TRY(dalloc(&c->d_pos, vb));
+  KMC_TRY(dalloc(&c->d_axis, vb));
+  KMC_TRY(dalloc(&c->d_m, vb));
+  KMC_TRY(dalloc(&c->d_src[0], h_src.size()));
+  KMC_TRY(dalloc(&c->d_src[1], h_src.size()));
+  if (c->fp32) KMC_TRY(dalloc(&c->d_slot, sizeof(int) * N));
+  KMC_TRY(dalloc(&c->d_beta, sizeof(double) * N));
+  KMC_TRY(dalloc(&c->d_vfrac, sizeof(double) * N));
+  KMC_TRY(dalloc(&c->d_eacc, sizeof(double) * N));
+  KMC_TRY(dalloc(&c->d_cnt, sizeof(unsigned long long) * 4 * c->n_lys));
+  KMC_TRY(dalloc(&c->d_err, sizeof(int32_t)));
+  KMC_TRY(dalloc(&c->d_rs, sizeof(RunState)));
+  KMC_CUDA(cudaMemcpy(c->d_pos, h_pos.data(), vb, cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemcpy(c->d_axis, h_axis.data(), vb, cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemcpy(c->d_m, h_m.data(), vb, cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemcpy(c->d_src[0], h_src.data(), h_src.size(), cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemcpy(c->d_src[1], h_src.data(), h_src.size(), cudaMemcpyHostToDevice));
+  if (c->fp32)
+    KMC_CUDA(cudaMemcpy(c->d_slot, h_slot.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemcpy(c->d_beta, h_beta.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemcpy(c->d_vfrac, h_vfrac.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemset(c->d_eacc, 0, sizeof(double) * N));
+  KMC_CUDA(cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * 4 * c->n_lys));
+  KMC_CUDA(cudaMemset(c->d_err, 0, sizeof(int32_t)));
+  KMC_CUDA(cudaMemcpy(c->d_lys, c->h_lys.data(), sizeof(LysDev) * c->n_lys,
+                      cudaMemcpyHostToDevice));
   return KMC_OK;
 }
 
@@ -354,8 +525,7 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
     cudaGetLastError();
     return fail(KMC_ECUDA, "no CUDA device available");
   }
-  kmc_status st = ensure_tables();
-  if (st != KMC_OK) return st;
+  KMC_TRY(ensure_device_init());
 
   kmc_ctx *c = new (std::nothrow) kmc_ctx();
   if (!c) return fail(KMC_ENOMEM, "host allocation failed");
@@ -363,14 +533,22 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
   c->n_lys = n_lys;
   c->N = N;
   c->vbytes = c->fp32 ? sizeof(float4) : sizeof(dbl4);
+  long long nrec = 0;
+  for (int l = 0; l < n_lys; ++l) nrec += c->fp32 ? (lys[l].n + 1) / 2 : lys[l].n;
+  c->n_records = nrec;
   std::vector<unsigned char> h_pos(c->vbytes * N), h_axis(c->vbytes * N), h_m(c->vbytes * N);
+  std::vector<unsigned char> h_src((c->fp32 ? sizeof(SrcPair) : sizeof(dbl4)) * nrec);
+  std::vector<int> h_slot(c->fp32 ? N : 0);
   std::vector<double> h_beta(N), h_vfrac(N);
   c->vol.resize(N);
   c->h_lys.resize(n_lys);
-  long long o = 0;
+  SrcPair *src32 = reinterpret_cast<SrcPair *>(h_src.data());
+  dbl4 *src64 = reinterpret_cast<dbl4 *>(h_src.data());
+  long long o = 0, r = 0;
   for (int l = 0; l < n_lys; ++l) {
     const kmc_lysosome &L = lys[l];
     c->off.push_back(static_cast<int>(o));
+    c->roff.push_back(static_cast<int>(r));
     c->n.push_back(L.n);
     c->Ms.push_back(L.Ms);
     c->Keff.push_back(L.Keff);
@@ -394,16 +572,21 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
       cz /= L.n;
     }
     c->vsum.push_back(vs);
-    const double vmean = vs / L.n;
-    const double len = std::cbrt(6.0 * vmean / kPi);  // diameter of the mean volume
+    const double len = std::cbrt(6.0 * (vs / L.n) / kPi);  // diameter of the mean volume
     const double w_scale = 1.0 / (4.0 * kPi * len * len * len);
     LysDev &D = c->h_lys[l];
     D.off = static_cast<int>(o);
     D.n = L.n;
+    D.roff = static_cast<int>(r);
     D.t_zero = L.T == 0.0;
     D.k = L.Keff / (kMu0 * L.Ms * L.Ms);
     D.bmax = 0.0;
     D.lognu0t = 0.0;
+    if (c->fp32 && (L.n & 1)) {  // padding NP of the last record: far away, no moment
+      SrcPair &pad = src32[r + L.n / 2];
+      pad.x[1] = pad.y[1] = pad.z[1] = kmc::kPadCoord;
+      pad.mx[1] = pad.my[1] = pad.mz[1] = 0.0f;
+    }
     for (int i = 0; i < L.n; ++i, ++o) {
       const double *p = &L.pos[3 * i];
       const double *a = &L.axis[3 * i];
@@ -416,76 +599,35 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
       h_beta[o] = L.T > 0 ? kMu0 * L.Ms * L.Ms * L.vol[i] / (kKB * L.T) : 0.0;
       h_vfrac[o] = L.vol[i] / vs;
       if (c->fp32) {
-        reinterpret_cast<float4 *>(h_pos.data())[o] = make4<float4>(x, y, z, w);
+        const float4 pf = make4<float4>(x, y, z, w);
+        reinterpret_cast<float4 *>(h_pos.data())[o] = pf;
         const float4 af = make4<float4>(ax, ay, az, 0.0);
         reinterpret_cast<float4 *>(h_axis.data())[o] = af;
-        reinterpret_cast<float4 *>(h_m.data())[o] =
-            make4<float4>(sgn * af.x, sgn * af.y, sgn * af.z, 0.0);
+        const float4 mf = make4<float4>(sgn * af.x, sgn * af.y, sgn * af.z, 0.0);
+        reinterpret_cast<float4 *>(h_m.data())[o] = mf;
+        SrcPair &rec = src32[r + i / 2];
+        const int h = i & 1;
+        rec.x[h] = pf.x;
+        rec.y[h] = pf.y;
+        rec.z[h] = pf.z;
+        rec.mx[h] = pf.w * mf.x;
+        rec.my[h] = pf.w * mf.y;
+        rec.mz[h] = pf.w * mf.z;
+        h_slot[o] = static_cast<int>(2 * (r + i / 2) + h);
       } else {
         reinterpret_cast<dbl4 *>(h_pos.data())[o] = make4<dbl4>(x, y, z, w);
         reinterpret_cast<dbl4 *>(h_axis.data())[o] = make4<dbl4>(ax, ay, az, 0.0);
         reinterpret_cast<dbl4 *>(h_m.data())[o] = make4<dbl4>(sgn * ax, sgn * ay, sgn * az, 0.0);
+        src64[r + i] = make4<dbl4>(w * sgn * ax, w * sgn * ay, w * sgn * az, 0.0);
       }
     }
+    r += c->fp32 ? (L.n + 1) / 2 : L.n;
   }
-  // work items: (lysosome, 32 targets), largest lysosomes first
-  std::vector<int> order(n_lys);
-  for (int l = 0; l < n_lys; ++l) order[l] = l;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return c->n[x] > c->n[y]; });
-  for (int l : order)
-    for (int i0 = 0; i0 < c->n[l]; i0 += kmc::kTargets)
-      c->items.push_back(make_int4(l, i0, std::min(kmc::kTargets, c->n[l] - i0), 0));
-
-#define KMC_TRY(x)          \
-  do {                      \
-    kmc_status s_ = (x);    \
-    if (s_ != KMC_OK) {     \
-      free_ctx(c);          \
-      return s_;            \
-    }                       \
-  } while (0)
-#define KMC_TRYC(x)                                                                   \
-  do {                                                                                \
-    cudaError_t e_ = (x);                                                             \
-    if (e_ != cudaSuccess) {                                                          \
-      free_ctx(c);                                                                    \
-      return fail(KMC_ECUDA, "%s failed: %s", #x, cudaGetErrorString(e_));            \
-    }                                                                                 \
-  } while (0)
-
-  KMC_TRYC(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
-  c->stream = c->own_stream;
-  const size_t vb = c->vbytes * N;
-  KMC_TRY(dalloc(&c->d_items, sizeof(int4) * c->items.size()));
-  KMC_TRY(dalloc(&c->d_lys, sizeof(LysDev) * n_lys));
-  KMC_TRY(dalloc(&c->d_pos, vb));
-  KMC_TRY(dalloc(&c->d_axis, vb));
-  KMC_TRY(dalloc(&c->d_m, vb));
-  KMC_TRY(dalloc(&c->d_mu[0], vb));
-  KMC_TRY(dalloc(&c->d_mu[1], vb));
-  KMC_TRY(dalloc(&c->d_beta, sizeof(double) * N));
-  KMC_TRY(dalloc(&c->d_vfrac, sizeof(double) * N));
-  KMC_TRY(dalloc(&c->d_eacc, sizeof(double) * N));
-  KMC_TRY(dalloc(&c->d_cnt, sizeof(unsigned long long) * 4 * n_lys));
-  KMC_TRY(dalloc(&c->d_err, sizeof(int32_t)));
-  KMC_TRY(dalloc(&c->d_rs, sizeof(RunState)));
-  KMC_TRYC(cudaMemcpyAsync(c->d_items, c->items.data(), sizeof(int4) * c->items.size(),
-                           cudaMemcpyHostToDevice, c->stream));
-  KMC_TRYC(cudaMemcpyAsync(c->d_pos, h_pos.data(), vb, cudaMemcpyHostToDevice, c->stream));
-  KMC_TRYC(cudaMemcpyAsync(c->d_axis, h_axis.data(), vb, cudaMemcpyHostToDevice, c->stream));
-  KMC_TRYC(cudaMemcpyAsync(c->d_m, h_m.data(), vb, cudaMemcpyHostToDevice, c->stream));
-  KMC_TRYC(cudaMemcpyAsync(c->d_beta, h_beta.data(), sizeof(double) * N, cudaMemcpyHostToDevice,
-                           c->stream));
-  KMC_TRYC(cudaMemcpyAsync(c->d_vfrac, h_vfrac.data(), sizeof(double) * N,
-                           cudaMemcpyHostToDevice, c->stream));
-  KMC_TRYC(cudaMemsetAsync(c->d_eacc, 0, sizeof(double) * N, c->stream));
-  KMC_TRYC(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long) * 4 * n_lys, c->stream));
-  KMC_TRYC(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
-  KMC_TRY(upload_lys(c));
-  KMC_TRYC(cudaStreamSynchronize(c->stream));  // host staging buffers go out of scope
-#undef KMC_TRY
-#undef KMC_TRYC
+  const kmc_status st = create_device_state(c, h_pos, h_axis, h_m, h_src, h_slot, h_beta, h_vfrac);
+  if (st != KMC_OK) {
+    free_ctx(c);
+    return st;
+  }
   *out = c;
   return KMC_OK;
 }
@@ -497,26 +639,33 @@ kmc_status kmc_set_stream(kmc_ctx *c, void *cuda_stream) {
   return KMC_OK;
 }
 
-kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t *warps_out,
-                      int32_t *tile_out) {
+kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
+                      int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
-  if (warps != 0 || tile != 0) {
-    if (warps != 4 && warps != 8 && warps != 16)
-      return fail(KMC_EINVAL, "warps must be 4, 8 or 16");
-    if (tile < 32 || tile > max_tile(c->fp32, warps) || (tile & (tile - 1)))
-      return fail(KMC_EINVAL, "tile must be a power of two in [32, %d]", max_tile(c->fp32, warps));
-    c->warps = warps;
-    c->tile = tile;
-  } else if (warps_out == nullptr && tile_out == nullptr) {
-    c->warps = c->tile = 0;
+  if (warps == -1 && tile == -1 && chunk == -1) {
+    // read only
+  } else if (warps == 0) {
+    c->shape = Shape();
+  } else {
+    Shape s;
+    s.warps = warps;
+    s.tile = tile;
+    s.chunk = chunk;
+    if (!shape_ok(c, s))
+      return fail(KMC_EINVAL,
+                  "bad shape: warps in {4, 8, 16}, tile a power of two in [32, %d], chunk a "
+                  "multiple of 64",
+                  max_tile(c->fp32, warps == 4 || warps == 8 || warps == 16 ? warps : 4));
+    c->shape = s;
   }
-  if (warps_out) *warps_out = c->warps;
-  if (tile_out) *tile_out = c->tile;
+  if (warps_out) *warps_out = c->shape.warps;
+  if (tile_out) *tile_out = c->shape.tile;
+  if (chunk_out) *chunk_out = c->shape.chunk;
   return KMC_OK;
 }
 
-kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f,
-                   int32_t S, int32_t periods, int32_t discard, uint64_t seed) {
+kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, int32_t S,
+                   int32_t periods, int32_t discard, uint64_t seed) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (!mu0Hmax || (n_amp != 1 && n_amp != c->n_lys))
     return fail(KMC_EINVAL, "need 1 or n_lys = %d amplitudes", c->n_lys);
@@ -528,10 +677,7 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f,
     return fail(KMC_EINVAL, "need 0 <= discard_periods <= periods");
   const long long n_rec = static_cast<long long>(S) * (periods - discard);
   if (n_rec > (1ll << 28)) return fail(KMC_EINVAL, "too many recorded steps");
-  if (c->warps == 0) {
-    kmc_status st = autotune(c);
-    if (st != KMC_OK) return st;
-  }
+  KMC_TRY(ensure_shape(c));
   const double t_step = 1.0 / (f * S);
   c->Hmax.assign(c->n_lys, 0.0);
   for (int l = 0; l < c->n_lys; ++l) {
@@ -539,36 +685,31 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f,
     c->h_lys[l].bmax = c->Hmax[l] / (kMu0 * c->Ms[l]);
     c->h_lys[l].lognu0t = std::log(t_step / c->tau0[l]);
   }
-  kmc_status st = upload_lys(c);
-  if (st != KMC_OK) return st;
+  KMC_TRY(upload_lys(c));
   const size_t need = static_cast<size_t>(c->n_lys) * static_cast<size_t>(std::max(n_rec, 1ll));
   if (need > c->loop_cap) {
+    KMC_CUDA(cudaStreamSynchronize(c->stream));
     if (c->d_loop) cudaFree(c->d_loop);
     c->d_loop = nullptr;
     c->loop_cap = 0;
-    st = dalloc(&c->d_loop, sizeof(double) * need);
-    if (st != KMC_OK) return st;
+    KMC_TRY(dalloc(&c->d_loop, sizeof(long long) * need));
     c->loop_cap = need;
-    if (c->gexec) {  // the graph holds the old pointer
-      cudaGraphExecDestroy(c->gexec);
-      c->gexec = nullptr;
-    }
+    drop_graph(c);
   }
-  KMC_CUDA(cudaMemsetAsync(c->d_loop, 0, sizeof(double) * need, c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_loop, 0, sizeof(long long) * need, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_eacc, 0, sizeof(double) * c->N, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long) * 4 * c->n_lys, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
-  st = refresh_sources(c, static_cast<int>(c->step_global & 1));
-  if (st != KMC_OK) return st;
+  KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  KMC_TRY(refresh_sources(c, static_cast<int>(c->step_global & 1)));
   RunState rs{c->step_global, 0, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
-  // capture one field period (S step launches + the period advance) as a graph
+  // one field period (S step launches + the period advance) as a CUDA graph
+  const Shape &sh = c->shape;
   if (!c->gexec || c->g_S != S || c->g_discard != discard || c->g_nrec != n_rec ||
-      c->g_warps != c->warps || c->g_tile != c->tile || c->g_seed != seed) {
-    if (c->gexec) {
-      cudaGraphExecDestroy(c->gexec);
-      c->gexec = nullptr;
-    }
+      c->g_shape.warps != sh.warps || c->g_shape.tile != sh.tile ||
+      c->g_shape.chunk != sh.chunk || c->g_seed != seed) {
+    drop_graph(c);
     StepArgs a = base_args(c);
     a.seed = seed;
     a.S = S;
@@ -580,18 +721,17 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f,
     for (int k = 0; k < S && ce == cudaSuccess; ++k) {
       a.k_local = k;
       a.cos_k = std::cos(2.0 * kPi * k / S);
-      ce = kmc::launch_step(c->fp32, c->warps, c->tile, a, static_cast<int>(c->items.size()),
-                            c->stream);
+      ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, a, c->n_items, c->stream);
     }
     if (ce == cudaSuccess) ce = kmc::launch_advance(c->d_rs, S, c->stream);
-    cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
     if (ce != cudaSuccess || ee != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
       return fail(KMC_ECUDA, "graph capture failed: %s",
                   cudaGetErrorString(ce != cudaSuccess ? ce : ee));
     }
-    cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+    const cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) {
       c->gexec = nullptr;
@@ -600,8 +740,7 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f,
     c->g_S = S;
     c->g_discard = discard;
     c->g_nrec = static_cast<int>(n_rec);
-    c->g_warps = c->warps;
-    c->g_tile = c->tile;
+    c->g_shape = sh;
     c->g_seed = seed;
   }
   for (int p = 0; p < periods; ++p) KMC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
@@ -626,8 +765,7 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
   if (written) *written = 0;
   if (lys < 0 || lys >= c->n_lys) return fail(KMC_EINVAL, "lysosome %d out of range", lys);
   if (cap < 0 || (cap > 0 && !buf)) return fail(KMC_EINVAL, "bad output buffer");
-  kmc_status st = check_device_error(c);
-  if (st != KMC_OK) return st;
+  KMC_TRY(check_device_error(c));
   const int n = c->n[lys], o = c->off[lys];
   int64_t need = 0;
   switch (what) {
@@ -647,22 +785,27 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
   const int nper = c->periods - c->discard;
   switch (what) {
     case KMC_READ_LOOP_H: {
-      int64_t r = 0;
+      int64_t q = 0;
       for (int p = c->discard; p < c->periods; ++p)
-        for (int k = 0; k < c->S; ++k) buf[r++] = c->Hmax[lys] * std::cos(2.0 * kPi * k / c->S);
+        for (int k = 0; k < c->S; ++k) buf[q++] = c->Hmax[lys] * std::cos(2.0 * kPi * k / c->S);
       break;
     }
     case KMC_READ_LOOP_M:
-      if (need)
-        KMC_CUDA(cudaMemcpy(buf, c->d_loop + static_cast<size_t>(lys) * std::max(c->n_rec, 1),
-                            sizeof(double) * need, cudaMemcpyDeviceToHost));
+      if (need) {
+        std::vector<long long> fx(need);
+        KMC_CUDA(cudaMemcpy(fx.data(),
+                            c->d_loop + static_cast<size_t>(lys) * std::max(c->n_rec, 1),
+                            sizeof(long long) * need, cudaMemcpyDeviceToHost));
+        for (int64_t q = 0; q < need; ++q)
+          buf[q] = static_cast<double>(fx[q]) / kmc::kLoopScale;
+      }
       break;
     case KMC_READ_NP_ENERGY:
     case KMC_READ_AREA:
     case KMC_READ_SAR: {
       std::vector<double> e(n);
       KMC_CUDA(cudaMemcpy(e.data(), c->d_eacc + o, sizeof(double) * n, cudaMemcpyDeviceToHost));
-      const double unit = kMu0 * c->Ms[lys] * c->Ms[lys];  // J per m^3 per unit of e_acc
+      const double unit = kMu0 * c->Ms[lys] * c->Ms[lys];  // J / m^3 per unit of e_acc
       double tot = 0.0;
       for (int i = 0; i < n; ++i) {
         const double Ei = nper > 0 ? unit * c->vol[o + i] * e[i] / nper : 0.0;
@@ -714,16 +857,11 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
     if (!is_finite(mu0Hext[l])) return fail(KMC_EINVAL, "non-finite field");
   for (long long i = 0; i < 3 * c->N; ++i)
     if (!is_finite(m_in[i])) return fail(KMC_EINVAL, "non-finite moment");
-  if (c->warps == 0) {
-    kmc_status st = autotune(c);
-    if (st != KMC_OK) return st;
-  }
+  KMC_TRY(ensure_shape(c));
   const long long N = c->N;
   if (!c->d_dbg) {
-    kmc_status st = dalloc(&c->d_dbg, sizeof(double) * N * 7);
-    if (st != KMC_OK) return st;
-    st = dalloc(&c->d_dbg_flags, sizeof(int32_t) * N);
-    if (st != KMC_OK) return st;
+    KMC_TRY(dalloc(&c->d_dbg, sizeof(double) * N * 7));
+    KMC_TRY(dalloc(&c->d_dbg_flags, sizeof(int32_t) * N));
   }
   std::vector<unsigned char> h_m(c->vbytes * N);
   for (long long i = 0; i < N; ++i) {
@@ -734,25 +872,23 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
       reinterpret_cast<dbl4 *>(h_m.data())[i] =
           make4<dbl4>(m_in[3 * i], m_in[3 * i + 1], m_in[3 * i + 2], 0.0);
   }
-  KMC_CUDA(cudaMemcpyAsync(c->d_m, h_m.data(), h_m.size(), cudaMemcpyHostToDevice, c->stream));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  KMC_CUDA(cudaMemcpy(c->d_m, h_m.data(), h_m.size(), cudaMemcpyHostToDevice));
   const int par = static_cast<int>(step & 1);
-  kmc_status st = refresh_sources(c, par);
-  if (st != KMC_OK) return st;
+  KMC_TRY(refresh_sources(c, par));
   for (int l = 0; l < c->n_lys; ++l) {
     c->h_lys[l].bmax = mu0Hext[l] / (kMu0 * c->Ms[l]);
     c->h_lys[l].lognu0t = std::log(t_step / c->tau0[l]);
   }
-  st = upload_lys(c);
-  if (st != KMC_OK) return st;
+  KMC_TRY(upload_lys(c));
   RunState rs{step, -1, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
   StepArgs a = base_args(c);
   a.seed = seed;
   a.S = 1;
-  a.discard = 0;
   a.n_rec = 1;
-  a.k_local = 0;
   a.cos_k = 1.0;
   a.debug = 1;
   a.dbg.bdip = c->d_dbg;
@@ -760,18 +896,16 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
   a.dbg.P = c->d_dbg + 5 * N;
   a.dbg.u = c->d_dbg + 6 * N;
   a.dbg.flags = c->d_dbg_flags;
-  KMC_CUDA(kmc::launch_step(c->fp32, c->warps, c->tile, a, static_cast<int>(c->items.size()),
-                            c->stream));
-  st = check_device_error(c);
-  if (st != KMC_OK) return st;
+  KMC_CUDA(kmc::launch_step(c->fp32, c->shape.warps, c->shape.tile, a, c->n_items, c->stream));
+  KMC_TRY(check_device_error(c));
   std::vector<double> h(7 * N);
   std::vector<int32_t> hf(N);
   KMC_CUDA(cudaMemcpy(h.data(), c->d_dbg, sizeof(double) * 7 * N, cudaMemcpyDeviceToHost));
   KMC_CUDA(cudaMemcpy(hf.data(), c->d_dbg_flags, sizeof(int32_t) * N, cudaMemcpyDeviceToHost));
   KMC_CUDA(cudaMemcpy(h_m.data(), c->d_m, h_m.size(), cudaMemcpyDeviceToHost));
   for (int l = 0; l < c->n_lys; ++l) {
-    const double Bunit = kMu0 * c->Ms[l];               // T per reduced field unit
-    const double Eunit = kMu0 * c->Ms[l] * c->Ms[l];   // J / m^3 per reduced energy unit
+    const double Bunit = kMu0 * c->Ms[l];              // T per reduced field unit
+    const double Eunit = kMu0 * c->Ms[l] * c->Ms[l];  // J / m^3 per reduced energy unit
     for (int ii = 0; ii < c->n[l]; ++ii) {
       const long long i = c->off[l] + ii;
       if (B_dip)
@@ -803,8 +937,7 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
 // then the raw moment records.
 kmc_status kmc_save(kmc_ctx *c, const char *path) {
   if (!c || !path) return fail(KMC_EINVAL, "NULL argument");
-  kmc_status st = check_device_error(c);
-  if (st != KMC_OK) return st;
+  KMC_TRY(check_device_error(c));
   std::vector<unsigned char> raw(c->vbytes * c->N);
   KMC_CUDA(cudaMemcpy(raw.data(), c->d_m, raw.size(), cudaMemcpyDeviceToHost));
   FILE *fp = std::fopen(path, "wb");

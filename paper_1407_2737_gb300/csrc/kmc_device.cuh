@@ -8,11 +8,13 @@
 
 namespace kmc {
 
-// Grid of step iv: theta_j = 2 pi (j + 1/2) / 200 with its sine and cosine,
+// Grid of step iv: theta_j = 2 pi (j + 1/2) / 200 and (sin, cos) of it,
 // written once per device by init_device (kmc_step.cu, the only translation
 // unit that includes this header).
-__device__ float g_grid_f[3][kGrid];   // theta_j, sin, cos
-__device__ double g_grid_d[3][kGrid];
+__device__ float g_theta_f[kGrid];
+__device__ float2 g_sc_f[kGrid];
+__device__ double g_theta_d[kGrid];
+__device__ double2 g_sc_d[kGrid];
 
 // ---------------------------------------------------------------------------
 // Shared-memory staging by bulk asynchronous copies (TMA engine).
@@ -124,9 +126,8 @@ struct Prec<float> {
   static constexpr float plane_tol = 1e-6f;   // |b x a| below this: plane from m
   static constexpr float newton_tol = 2e-9f;  // absolute, on the offset in a cell
   static constexpr int newton_max = 24;
-  __device__ static float theta(int j) { return g_grid_f[0][j]; }
-  __device__ static float sn(int j) { return g_grid_f[1][j]; }
-  __device__ static float cs(int j) { return g_grid_f[2][j]; }
+  __device__ static float theta(int j) { return g_theta_f[j]; }
+  __device__ static float2 sc(int j) { return g_sc_f[j]; }
   // sin and cos of 0 <= d <= 2 pi / 200 by their Taylor series (error < 1e-11)
   __device__ static void sincos_small(float d, float &s, float &c) {
     const float d2 = d * d;
@@ -140,9 +141,8 @@ struct Prec<double> {
   static constexpr double plane_tol = 1e-12;
   static constexpr double newton_tol = 1e-14;
   static constexpr int newton_max = 100;
-  __device__ static double theta(int j) { return g_grid_d[0][j]; }
-  __device__ static double sn(int j) { return g_grid_d[1][j]; }
-  __device__ static double cs(int j) { return g_grid_d[2][j]; }
+  __device__ static double theta(int j) { return g_theta_d[j]; }
+  __device__ static double2 sc(int j) { return g_sc_d[j]; }
   // Taylor series to d^9 / d^10: truncation below 1e-24 for d <= 2 pi / 200
   __device__ static void sincos_small(double d, double &s, double &c) {
     const double d2 = d * d;
@@ -210,222 +210,6 @@ __device__ __forceinline__ bool on_arc(R x, R from, R to) {
   if (dx < R(0)) dx += Prec<R>::two_pi;
   if (dt < R(0)) dt += Prec<R>::two_pi;
   return dx > R(0) && dx <= dt;
-}
-
-// Element i of a 4-array without dynamic indexing (keeps it in registers).
-template <typename T>
-__device__ __forceinline__ T sel4(const T (&a)[4], int i) {
-  return i == 0 ? a[0] : (i == 1 ? a[1] : (i == 2 ? a[2] : a[3]));
-}
-
-struct NPResult {
-  double dEa, dEb, P;  // reduced barriers from the current / other well, jump probability
-  int nmin, flipped, near, degenerate, bad;
-};
-
-// One NP: axis a, previous unit moment m, total reduced field b. On return m
-// holds the new unit moment. beta = mu0 M_S^2 V / k_B T, lognu0t = ln(t_step / tau0).
-// MIXED: near the switching field (smallest barrier below 2 % of k) the four
-// extrema are polished by one FP64 Newton step and their energies taken in
-// FP64, so that E3 - E_a does not lose its digits to cancellation.
-template <typename R, bool MIXED>
-__device__ __forceinline__ NPResult np_update(R ax, R ay, R az, R &mx, R &my, R &mz, R bx, R by,
-                                              R bz, R k, double beta, double lognu0t,
-                                              bool t_zero, double u) {
-  NPResult o;
-  o.dEa = o.dEb = o.P = 0.0;
-  o.nmin = o.flipped = o.near = o.degenerate = o.bad = 0;
-  // iii) working plane through the axis a and the total field b
-  const R bmag = sqrt(fma(bx, bx, fma(by, by, bz * bz)));
-  R ex = R(0), ey = R(0), ez = R(0), cphi = R(1), sphi = R(0);
-  bool degenerate = true;
-  if (bmag > R(0)) {
-    const R inv = R(1) / bmag;
-    const R hx = bx * inv, hy = by * inv, hz = bz * inv;
-    cphi = fma(ax, hx, fma(ay, hy, az * hz));
-    const R px = fma(-cphi, ax, hx), py = fma(-cphi, ay, hy), pz = fma(-cphi, az, hz);
-    const R sp = sqrt(fma(px, px, fma(py, py, pz * pz)));
-    if (sp >= Prec<R>::plane_tol) {
-      ex = px / sp;
-      ey = py / sp;
-      ez = pz / sp;
-      sphi = sp;
-      degenerate = false;
-    } else {
-      cphi = (cphi >= R(0)) ? R(1) : R(-1);
-    }
-  }
-  if (degenerate) {
-    const R ma = fma(mx, ax, fma(my, ay, mz * az));
-    R px = fma(-ma, ax, mx), py = fma(-ma, ay, my), pz = fma(-ma, az, mz);
-    R sp = sqrt(fma(px, px, fma(py, py, pz * pz)));
-    if (sp < Prec<R>::plane_tol) {
-      if (fabs(ax) > R(0.9)) {  // a x y-hat
-        px = -az;
-        py = R(0);
-        pz = ax;
-      } else {  // a x x-hat
-        px = R(0);
-        py = az;
-        pz = -ay;
-      }
-      sp = sqrt(fma(px, px, fma(py, py, pz * pz)));
-    }
-    ex = px / sp;
-    ey = py / sp;
-    ez = pz / sp;
-  }
-  o.degenerate = degenerate;
-  const R m_a = fma(mx, ax, fma(my, ay, mz * az));
-  const R m_e = fma(mx, ex, fma(my, ey, mz * ez));
-  R th0 = atan2(m_e, m_a);
-  if (th0 < R(0)) th0 += Prec<R>::two_pi;
-
-  // iv) 200-point scan of de/dth, sign changes refined by Newton
-  Profile<R> pf;
-  pf.k = k;
-  pf.k2 = R(2) * k;
-  pf.bc = bmag * cphi;
-  pf.bs = bmag * sphi;
-  int cnt = 0;
-  int jq0 = 0, jq1 = 0, jq2 = 0, jq3 = 0;
-  R dq0 = R(0), dq1 = R(0), dq2 = R(0), dq3 = R(0);
-  const R dfirst = pf.d1(Prec<R>::sn(0), Prec<R>::cs(0));
-  R dprev = dfirst;
-  for (int j = 1; j <= kGrid; ++j) {
-    const R d = (j < kGrid) ? pf.d1(Prec<R>::sn(j), Prec<R>::cs(j)) : dfirst;
-    if ((d < R(0)) != (dprev < R(0))) {
-      if (cnt == 0) {
-        jq0 = j - 1;
-        dq0 = dprev;
-      } else if (cnt == 1) {
-        jq1 = j - 1;
-        dq1 = dprev;
-      } else if (cnt == 2) {
-        jq2 = j - 1;
-        dq2 = dprev;
-      } else if (cnt == 3) {
-        jq3 = j - 1;
-        dq3 = dprev;
-      }
-      ++cnt;
-    }
-    dprev = d;
-  }
-  if (cnt > 4) {
-    o.bad = 1;
-    cnt = 4;
-  }
-  R th[4], en[4], sq[4], cq[4];
-  bool ismin[4];
-  int jq[4] = {jq0, jq1, jq2, jq3};
-  R dq[4] = {dq0, dq1, dq2, dq3};
-  R off[4];
-  const R hcell = Prec<R>::theta(1) - Prec<R>::theta(0);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    th[q] = en[q] = sq[q] = cq[q] = off[q] = R(0);
-    ismin[q] = false;
-    if (q < cnt) {
-      const int j = jq[q];
-      R s, c;
-      off[q] = refine_in_cell(pf, Prec<R>::sn(j), Prec<R>::cs(j), hcell, dq[q], s, c);
-      R t = Prec<R>::theta(j) + off[q];
-      if (t >= Prec<R>::two_pi) t -= Prec<R>::two_pi;
-      th[q] = t;
-      sq[q] = s;
-      cq[q] = c;
-      en[q] = pf.e(s, c);
-      ismin[q] = dq[q] < R(0);
-    }
-  }
-  int nmin = 0, nmax = 0, imin0 = 0, imin1 = 0, imax0 = 0, imax1 = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (q < cnt) {
-      if (ismin[q]) {
-        if (nmin == 0) imin0 = q; else imin1 = q;
-        ++nmin;
-      } else {
-        if (nmax == 0) imax0 = q; else imax1 = q;
-        ++nmax;
-      }
-    }
-  }
-  if (nmin > 2 || nmax > 2) {
-    o.bad = 1;
-    nmin = 1;
-  }
-  o.nmin = nmin;
-  // new angle of the moment, as its sine and cosine in the plane
-  R s_new, c_new;
-  if (nmin == 0) {  // flat profile (K_eff = 0 and no field): keep the projection
-    const R nrm = sqrt(fma(m_a, m_a, m_e * m_e));
-    s_new = (nrm > R(0)) ? m_e / nrm : R(0);
-    c_new = (nrm > R(0)) ? m_a / nrm : R(1);
-  } else if (nmin == 1) {
-    s_new = sel4(sq, imin0);
-    c_new = sel4(cq, imin0);
-  } else {
-    // v) basins: the two maxima split the circle into two arcs
-    const R M1 = sel4(th, imax0), M2 = sel4(th, imax1);
-    const bool arc0 = on_arc<R>(th0, M1, M2);
-    const bool arcA = on_arc<R>(sel4(th, imin0), M1, M2);
-    const int wa = (arc0 == arcA) ? imin0 : imin1;
-    const int wb = (wa == imin0) ? imin1 : imin0;
-    const R e3 = fmin(sel4(en, imax0), sel4(en, imax1));
-    double dEa = static_cast<double>(e3 - sel4(en, wa));
-    double dEb = static_cast<double>(e3 - sel4(en, wb));
-    if (MIXED && fmin(dEa, dEb) < 0.02 * static_cast<double>(k)) {
-      // FP64 polish: one Newton step from each FP32 root, energies in FP64
-      Profile<double> pd;
-      pd.k = static_cast<double>(k);
-      pd.k2 = 2.0 * pd.k;
-      pd.bc = static_cast<double>(bmag) * static_cast<double>(cphi);
-      pd.bs = static_cast<double>(bmag) * static_cast<double>(sphi);
-      double e64[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = jq[q];
-        const double S0 = g_grid_d[1][j], C0 = g_grid_d[2][j];
-        double x = static_cast<double>(off[q]), sd, cd;
-        Prec<double>::sincos_small(x, sd, cd);
-        double s = fma(S0, cd, C0 * sd), c = fma(C0, cd, -S0 * sd);
-        const double dd = pd.d2(s, c);
-        if (dd != 0.0) x -= pd.d1(s, c) / dd;
-        Prec<double>::sincos_small(x, sd, cd);
-        s = fma(S0, cd, C0 * sd);
-        c = fma(C0, cd, -S0 * sd);
-        e64[q] = pd.e(s, c);
-      }
-      const double e3d = fmin(sel4(e64, imax0), sel4(e64, imax1));
-      dEa = e3d - sel4(e64, wa);
-      dEb = e3d - sel4(e64, wb);
-    }
-    o.dEa = dEa;
-    o.dEb = dEb;
-    int w = wa;
-    if (!t_zero) {
-      // vi) Eqs. 3-5 with nu t = exp(ln(nu0 t_step) - beta dE)
-      const double ea = exp(lognu0t - beta * dEa);
-      const double eb = exp(lognu0t - beta * dEb);
-      const double sum = ea + eb;
-      const double P = (sum > 0.0) ? (ea / sum) * (-expm1(-sum)) : 0.0;
-      o.P = P;
-      // vii) jump iff u < P
-      o.near = fabs(u - P) < 1e-9;
-      if (u < P) {
-        o.flipped = 1;
-        w = wb;
-      }
-    }
-    s_new = sel4(sq, w);
-    c_new = sel4(cq, w);
-  }
-  mx = fma(c_new, ax, s_new * ex);
-  my = fma(c_new, ay, s_new * ey);
-  mz = fma(c_new, az, s_new * ez);
-  return o;
 }
 
 }  // namespace kmc

@@ -1,29 +1,75 @@
 // kmc_step.cu -- the fused kMC step kernels of libkmc (sm_103a).
 //
 // One launch = one time step of every NP of every lysosome (Sec. II.1 steps
-// i-vii; the update is synchronous, Sec. II.2, so every block reads the
-// moments of the start of the step and writes the other ping-pong buffer).
+// i-vii). The update is synchronous (Sec. II.2): every block reads the source
+// moments of the start of the step from one ping-pong buffer and writes the
+// new ones to the other.
 //
-// Block = (lysosome l, 32 target NPs), NW warps. The lysosome's sources are
-// streamed through shared memory in tiles of TJ NPs by bulk asynchronous
-// copies (cp.async.bulk, double-buffered, completion on an mbarrier). Each warp
-// takes every NW-th source of a tile for the same 32 targets (one per lane),
-// so each shared-memory load is a broadcast. Partial sums of each tile are
-// folded into a compensated (Kahan) per-warp sum, the NW warp sums are combined
-// with Neumaier's compensated summation, and warp 0 runs steps iii-vii for its
-// 32 NPs straight from registers: the dipolar field never goes to memory.
+// Work item = one block of NW warps: 32 target NPs of one lysosome against a
+// contiguous range of that lysosome's sources. Sources are staged in shared
+// memory, tile by tile, by bulk asynchronous copies (cp.async.bulk, double
+// buffered, completion on an mbarrier). Warp w takes every NW-th source record
+// of a tile for the same 32 targets (one per lane), so every shared-memory
+// load is a broadcast.
 //
-// Pair term (Eq. 1 in reduced units), 19 FP32 operations + 1 reciprocal
-// square root: d = r_j - r_i; r2 = |d|^2; q = rsqrt(r2); q3 = q^3;
-// s = (mu_j . d) q^2 q3; A += s d; B += q3 mu_j; b_dip = 3A - B.
+// FP32-mixed pair term (Eq. 1 in reduced units) on two sources at once with
+// packed f32x2 instructions: d = r_j - r_i; r2 = |d|^2; q = rsqrt(r2) per
+// half; q3 = q^3; s = (mu_j . d) q^2 q3; A += s d; B += q3 mu_j; b_dip = 3A - B.
+// That is 19 packed instructions and 2 reciprocal square roots for 2 pairs.
+// Each tile's partial sums are folded into a compensated (Kahan) running sum;
+// the NW warp sums are combined in a fixed order with Neumaier's summation.
+//
+// When a target group's sources are split over several items, each item writes
+// its compensated partial sums to scratch; the last item of the group to arrive
+// (arrival counter) adds all partials in split order (deterministic) and runs
+// steps iii-vii. The dipolar field never leaves the chip otherwise.
+//
+// Steps iii-vii are shared by the whole block: warp 0 sets up the working
+// plane of each target, all warps scan the 200-point energy-derivative grid
+// (lanes over grid points), all threads run Newton's method (one root per
+// thread), and warp 0 takes the decision (basins, barrier, rates, draw).
 #include <cuda_runtime.h>
 #include <math.h>
-#include <stdio.h>
+
+#include <type_traits>
 
 #include "kmc_device.cuh"
 #include "kmc_launch.h"
 
 namespace kmc {
+
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs (f32x2) in 64-bit registers.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float hsum(f2 v) {
+  float lo, hi;
+  upk(v, lo, hi);
+  return lo + hi;
+}
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
@@ -31,7 +77,7 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
-// Kahan step: adds x to (s, c).
+// Kahan step: adds x to (s, c); the exact sum is s - c.
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   const float y = x - c;
   const float t = s + y;
@@ -39,7 +85,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
   s = t;
 }
 
-// Neumaier step: adds x to (s, c) where c collects the rounding errors.
+// Neumaier step: adds x to (s, c); the exact sum is s + c.
 __device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
   const float t = s + x;
   if (fabsf(s) >= fabsf(x))
@@ -49,54 +95,51 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
   s = t;
 }
 
-template <typename V>
-struct SrcTraits;
-template <>
-struct SrcTraits<float4> {
-  using R = float;
-};
-template <>
-struct SrcTraits<dbl4> {
-  using R = double;
-};
-
 // ---------------------------------------------------------------------------
 // Pair loops over one staged tile. MASK: the tile holds some of the block's
 // own targets, so the self term (r2 = 0; distinct NPs are never coincident)
 // is dropped.
 
+struct AccF32 {
+  f2 ax, ay, az, bx, by, bz;  // packed partial sums (even / odd sources)
+};
+
 template <bool MASK>
-__device__ __forceinline__ void pair_tile_f32(const float4 *__restrict__ sp,
-                                              const float4 *__restrict__ sm, int cnt,
-                                              int first, int stride, float xi, float yi,
-                                              float zi, float &ax, float &ay, float &az,
-                                              float &bx, float &by, float &bz) {
-#pragma unroll 4
-  for (int j = first; j < cnt; j += stride) {
-    const float4 p = sp[j];
-    const float4 q = sm[j];
-    const float dx = p.x - xi, dy = p.y - yi, dz = p.z - zi;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float inv = rsqrt_approx(r2);
-    if (MASK) inv = (r2 > 0.0f) ? inv : 0.0f;
-    const float inv2 = inv * inv;
-    const float inv3 = inv * inv2;
-    const float md = fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz));
-    const float s = md * inv2 * inv3;
-    ax = fmaf(s, dx, ax);
-    ay = fmaf(s, dy, ay);
-    az = fmaf(s, dz, az);
-    bx = fmaf(inv3, q.x, bx);
-    by = fmaf(inv3, q.y, by);
-    bz = fmaf(inv3, q.z, bz);
+__device__ __forceinline__ void pair_tile_f32(const ulonglong2 *__restrict__ sp, int cnt,
+                                              int first, int stride, f2 X, f2 Y, f2 Z,
+                                              AccF32 &acc) {
+#pragma unroll 2
+  for (int r = first; r < cnt; r += stride) {
+    const ulonglong2 a = sp[3 * r];      // x0 x1 | y0 y1
+    const ulonglong2 b = sp[3 * r + 1];  // z0 z1 | mx0 mx1
+    const ulonglong2 c = sp[3 * r + 2];  // my0 my1 | mz0 mz1
+    const f2 dx = sub2(a.x, X), dy = sub2(a.y, Y), dz = sub2(b.x, Z);
+    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    float r2l, r2h;
+    upk(r2, r2l, r2h);
+    float il = rsqrt_approx(r2l), ih = rsqrt_approx(r2h);
+    if (MASK) {
+      il = (r2l > 0.0f) ? il : 0.0f;
+      ih = (r2h > 0.0f) ? ih : 0.0f;
+    }
+    const f2 q = pk(il, ih);
+    const f2 q2 = mul2(q, q);
+    const f2 q3 = mul2(q, q2);
+    const f2 md = fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx)));
+    const f2 s = mul2(mul2(md, q2), q3);
+    acc.ax = fma2(s, dx, acc.ax);
+    acc.ay = fma2(s, dy, acc.ay);
+    acc.az = fma2(s, dz, acc.az);
+    acc.bx = fma2(q3, b.y, acc.bx);
+    acc.by = fma2(q3, c.x, acc.by);
+    acc.bz = fma2(q3, c.y, acc.bz);
   }
 }
 
 __device__ __forceinline__ void pair_tile_f64(const dbl4 *__restrict__ sp,
                                               const dbl4 *__restrict__ sm, int cnt, int first,
                                               int stride, double xi, double yi, double zi,
-                                              double &ax, double &ay, double &az, double &bx,
-                                              double &by, double &bz) {
+                                              double (&acc)[6]) {
   for (int j = first; j < cnt; j += stride) {
     const dbl4 p = sp[j];
     const dbl4 q = sm[j];
@@ -108,79 +151,362 @@ __device__ __forceinline__ void pair_tile_f64(const dbl4 *__restrict__ sp,
       const double inv3 = inv * inv2;
       const double md = fma(q.x, dx, fma(q.y, dy, q.z * dz));
       const double s = md * inv2 * inv3;
-      ax = fma(s, dx, ax);
-      ay = fma(s, dy, ay);
-      az = fma(s, dz, az);
-      bx = fma(inv3, q.x, bx);
-      by = fma(inv3, q.y, by);
-      bz = fma(inv3, q.z, bz);
+      acc[0] = fma(s, dx, acc[0]);
+      acc[1] = fma(s, dy, acc[1]);
+      acc[2] = fma(s, dz, acc[2]);
+      acc[3] = fma(inv3, q.x, acc[3]);
+      acc[4] = fma(inv3, q.y, acc[4]);
+      acc[5] = fma(inv3, q.z, acc[5]);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Per-NP epilogue shared by both precisions: steps iii-vii, outputs, energy,
-// loop and counters. Runs in warp 0; lane = target within the block.
+// Steps iii-vii, shared by the block.
 
+template <typename R>
+struct EpiShared {
+  R h[3][kTargets];    // combined dipolar field
+  R k2[kTargets], k[kTargets], bc[kTargets], bs[kTargets];  // profile of Eq. 2
+  int cnt[kTargets];   // sign changes found by the scan
+  int jq[kTargets][4];
+  R dq[kTargets][4];   // derivative at the left node of each bracket
+  R th[kTargets][4], en[kTargets][4], sq[kTargets][4], cq[kTargets][4], off[kTargets][4];
+};
+
+template <typename R>
+__device__ __forceinline__ R profile_d1(R k2, R bc, R bs, R s, R c) {
+  return s * fma(k2, c, bc) - bs * c;
+}
+
+// Scan of step iv for target t by one warp: lane l evaluates de/dth at grid
+// points j = l + 32 q (q = 0..6) and tests the cell (j, j+1), cyclically.
+template <typename R>
+__device__ __forceinline__ void warp_scan(EpiShared<R> &sm, int t, int lane) {
+  const R k2 = sm.k2[t], bc = sm.bc[t], bs = sm.bs[t];
+  R d[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const int j = lane + 32 * q;
+    d[q] = R(0);
+    if (j < kGrid) {
+      const auto sc = Prec<R>::sc(j);
+      d[q] = profile_d1<R>(k2, bc, bs, sc.x, sc.y);
+    }
+  }
+  const R dfirst = __shfl_sync(0xffffffffu, d[0], 0);
+  int base = 0;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const int j = lane + 32 * q;
+    R nx = __shfl_down_sync(0xffffffffu, d[q], 1);
+    const R w0 = __shfl_sync(0xffffffffu, d[q < 6 ? q + 1 : 0], 0);
+    if (lane == 31) nx = w0;
+    if (j == kGrid - 1) nx = dfirst;
+    const bool chg = (j < kGrid) && ((d[q] < R(0)) != (nx < R(0)));
+    const unsigned m = __ballot_sync(0xffffffffu, chg);
+    if (chg) {
+      const int slot = base + __popc(m & ((1u << lane) - 1u));
+      if (slot < 4) {
+        sm.jq[t][slot] = j;
+        sm.dq[t][slot] = d[q];
+      }
+    }
+    base += __popc(m);
+  }
+  if (lane == 0) sm.cnt[t] = base;
+}
+
+// Newton refinement of bracket q of target t (one thread).
+template <typename R>
+__device__ __forceinline__ void refine_bracket(EpiShared<R> &sm, int t, int q) {
+  Profile<R> pf;
+  pf.k2 = sm.k2[t];
+  pf.k = sm.k[t];
+  pf.bc = sm.bc[t];
+  pf.bs = sm.bs[t];
+  const int j = min(max(sm.jq[t][q], 0), kGrid - 1);
+  const auto sc = Prec<R>::sc(j);
+  const R h = Prec<R>::theta(1) - Prec<R>::theta(0);
+  R s, c;
+  const R off = refine_in_cell(pf, sc.x, sc.y, h, sm.dq[t][q], s, c);
+  R th = Prec<R>::theta(j) + off;
+  if (th >= Prec<R>::two_pi) th -= Prec<R>::two_pi;
+  sm.th[t][q] = th;
+  sm.off[t][q] = off;
+  sm.sq[t][q] = s;
+  sm.cq[t][q] = c;
+  sm.en[t][q] = pf.e(s, c);
+}
+
+// Per-target values warp 0 keeps in registers between the stages.
+template <typename R>
+struct TargetState {
+  R ax, ay, az, ex, ey, ez, m_a, m_e, th0, mz_old, bmag, cphi, sphi;
+  bool degenerate;
+};
+
+// Step iii: working plane through the axis a and the total field b.
+template <typename R>
+__device__ __forceinline__ TargetState<R> setup_plane(R ax, R ay, R az, R mx, R my, R mz,
+                                                      R bx, R by, R bz) {
+  TargetState<R> s;
+  s.ax = ax;
+  s.ay = ay;
+  s.az = az;
+  s.mz_old = mz;
+  s.bmag = sqrt(fma(bx, bx, fma(by, by, bz * bz)));
+  s.ex = s.ey = s.ez = R(0);
+  s.cphi = R(1);
+  s.sphi = R(0);
+  s.degenerate = true;
+  if (s.bmag > R(0)) {
+    const R inv = R(1) / s.bmag;
+    const R hx = bx * inv, hy = by * inv, hz = bz * inv;
+    R cphi = fma(ax, hx, fma(ay, hy, az * hz));
+    const R px = fma(-cphi, ax, hx), py = fma(-cphi, ay, hy), pz = fma(-cphi, az, hz);
+    const R sp = sqrt(fma(px, px, fma(py, py, pz * pz)));
+    if (sp >= Prec<R>::plane_tol) {
+      s.ex = px / sp;
+      s.ey = py / sp;
+      s.ez = pz / sp;
+      s.sphi = sp;
+      s.degenerate = false;
+    } else {
+      cphi = (cphi >= R(0)) ? R(1) : R(-1);
+    }
+    s.cphi = cphi;
+  }
+  if (s.degenerate) {
+    const R ma = fma(mx, ax, fma(my, ay, mz * az));
+    R px = fma(-ma, ax, mx), py = fma(-ma, ay, my), pz = fma(-ma, az, mz);
+    R sp = sqrt(fma(px, px, fma(py, py, pz * pz)));
+    if (sp < Prec<R>::plane_tol) {
+      if (fabs(ax) > R(0.9)) {  // a x y-hat
+        px = -az;
+        py = R(0);
+        pz = ax;
+      } else {  // a x x-hat
+        px = R(0);
+        py = az;
+        pz = -ay;
+      }
+      sp = sqrt(fma(px, px, fma(py, py, pz * pz)));
+    }
+    s.ex = px / sp;
+    s.ey = py / sp;
+    s.ez = pz / sp;
+  }
+  s.m_a = fma(mx, ax, fma(my, ay, mz * az));
+  s.m_e = fma(mx, s.ex, fma(my, s.ey, mz * s.ez));
+  R th0 = atan2(s.m_e, s.m_a);
+  if (th0 < R(0)) th0 += Prec<R>::two_pi;
+  s.th0 = th0;
+  return s;
+}
+
+struct Decision {
+  double dEa, dEb, P;
+  int nmin, flipped, near, bad;
+};
+
+// Steps v-vii for target t: basins, barrier (FP64 polish near the switching
+// field in the mixed path), Eqs. 3-5 in FP64, draw u < P. Returns (sin, cos)
+// of the new angle in the plane.
+template <typename R, bool MIXED>
+__device__ __forceinline__ Decision decide(const EpiShared<R> &sm, int t,
+                                           const TargetState<R> &st, double beta,
+                                           double lognu0t, bool t_zero, double u, R &s_new,
+                                           R &c_new) {
+  Decision o;
+  o.dEa = o.dEb = o.P = 0.0;
+  o.flipped = o.near = o.bad = 0;
+  int cnt = sm.cnt[t];
+  if (cnt > 4 || cnt < 0) {
+    o.bad = 1;
+    cnt = cnt < 0 ? 0 : 4;
+  }
+  int nmin = 0, nmax = 0, imin0 = 0, imin1 = 0, imax0 = 0, imax1 = 0;
+  for (int q = 0; q < cnt; ++q) {
+    if (sm.dq[t][q] < R(0)) {
+      if (nmin == 0) imin0 = q; else imin1 = q;
+      ++nmin;
+    } else {
+      if (nmax == 0) imax0 = q; else imax1 = q;
+      ++nmax;
+    }
+  }
+  if (nmin > 2 || nmax > 2) {
+    o.bad = 1;
+    nmin = 1;
+  }
+  o.nmin = nmin;
+  if (nmin == 0) {  // flat profile (K_eff = 0 and no field): keep the projection
+    const R nrm = sqrt(fma(st.m_a, st.m_a, st.m_e * st.m_e));
+    s_new = (nrm > R(0)) ? st.m_e / nrm : R(0);
+    c_new = (nrm > R(0)) ? st.m_a / nrm : R(1);
+    return o;
+  }
+  if (nmin == 1) {
+    s_new = sm.sq[t][imin0];
+    c_new = sm.cq[t][imin0];
+    return o;
+  }
+  // v) basins: the two maxima split the circle into two arcs
+  const R M1 = sm.th[t][imax0], M2 = sm.th[t][imax1];
+  const bool arc0 = on_arc<R>(st.th0, M1, M2);
+  const bool arcA = on_arc<R>(sm.th[t][imin0], M1, M2);
+  const int wa = (arc0 == arcA) ? imin0 : imin1;
+  const int wb = (wa == imin0) ? imin1 : imin0;
+  const R e3 = fmin(sm.en[t][imax0], sm.en[t][imax1]);
+  double dEa = static_cast<double>(e3 - sm.en[t][wa]);
+  double dEb = static_cast<double>(e3 - sm.en[t][wb]);
+  if (MIXED && fmin(dEa, dEb) < 0.02 * static_cast<double>(sm.k[t])) {
+    // FP64 polish: one Newton step from each FP32 root, energies in FP64
+    Profile<double> pd;
+    pd.k = static_cast<double>(sm.k[t]);
+    pd.k2 = 2.0 * pd.k;
+    pd.bc = static_cast<double>(st.bmag) * static_cast<double>(st.cphi);
+    pd.bs = static_cast<double>(st.bmag) * static_cast<double>(st.sphi);
+    double e64[4];
+    for (int q = 0; q < 4; ++q) {
+      const double2 sc = g_sc_d[min(max(sm.jq[t][q], 0), kGrid - 1)];
+      double x = static_cast<double>(sm.off[t][q]), sd, cd;
+      Prec<double>::sincos_small(x, sd, cd);
+      double s = fma(sc.x, cd, sc.y * sd), c = fma(sc.y, cd, -sc.x * sd);
+      const double dd = pd.d2(s, c);
+      if (dd != 0.0) x -= pd.d1(s, c) / dd;
+      Prec<double>::sincos_small(x, sd, cd);
+      s = fma(sc.x, cd, sc.y * sd);
+      c = fma(sc.y, cd, -sc.x * sd);
+      e64[q] = pd.e(s, c);
+    }
+    const double e3d = fmin(e64[imax0], e64[imax1]);
+    dEa = e3d - e64[wa];
+    dEb = e3d - e64[wb];
+  }
+  o.dEa = dEa;
+  o.dEb = dEb;
+  int w = wa;
+  if (!t_zero) {
+    // vi) Eqs. 3-5 with nu t = exp(ln(nu0 t_step) - beta dE)
+    const double ea = exp(lognu0t - beta * dEa);
+    const double eb = exp(lognu0t - beta * dEb);
+    const double sum = ea + eb;
+    const double P = (sum > 0.0) ? (ea / sum) * (-expm1(-sum)) : 0.0;
+    o.P = P;
+    // vii) jump iff u < P
+    o.near = fabs(u - P) < 1e-9;
+    if (u < P) {
+      o.flipped = 1;
+      w = wb;
+    }
+  }
+  s_new = sm.sq[t][w];
+  c_new = sm.cq[t][w];
+  return o;
+}
+
+// Steps iii-vii for the block's targets; sm.h holds their dipolar fields.
+// V = float4 (mixed) or dbl4 (plain).
 template <typename V, bool MIXED>
-__device__ __forceinline__ void epilogue(const StepArgs &a, const LysDev &L, int l, int i0,
-                                         int nt, int lane, typename SrcTraits<V>::R hx,
-                                         typename SrcTraits<V>::R hy,
-                                         typename SrcTraits<V>::R hz, long long step,
-                                         int rec) {
-  using R = typename SrcTraits<V>::R;
-  const bool active = lane < nt;
-  const int il = i0 + (active ? lane : 0);  // NP index within the lysosome
-  const int i = L.off + il;                 // flat NP index
+__device__ __forceinline__ void block_update(
+    const StepArgs &a, const LysDev &L, const Item &it, long long step, int rec,
+    EpiShared<typename std::conditional<MIXED, float, double>::type> &sm) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  const int nt = it.nt;
   const double bext = L.bmax * a.cos_k;
-  const V ax4 = static_cast<const V *>(a.axis)[i];
-  V m4 = static_cast<V *>(a.m)[i];
-  const R mz_old = m4.z;
-  R mx = m4.x, my = m4.y, mz = m4.z;
-  const double u = kmc_uniform(a.seed, step, il, l);
-  const NPResult r = np_update<R, MIXED>(ax4.x, ax4.y, ax4.z, mx, my, mz, hx, hy,
-                                         hz + static_cast<R>(bext), static_cast<R>(L.k),
-                                         a.beta[i], L.lognu0t, L.t_zero != 0, u);
+  TargetState<R> st;
+  V m4;
+  int i = 0, il = 0;
+  // iii) working planes (warp 0, one target per lane)
+  if (warp == 0) {
+    il = it.t0 + min(lane, nt - 1);
+    i = L.off + il;
+    const V ax4 = static_cast<const V *>(a.axis)[i];
+    m4 = static_cast<V *>(a.m)[i];
+    st = setup_plane<R>(ax4.x, ax4.y, ax4.z, m4.x, m4.y, m4.z, sm.h[0][lane], sm.h[1][lane],
+                        sm.h[2][lane] + static_cast<R>(bext));
+    sm.k[lane] = static_cast<R>(L.k);
+    sm.k2[lane] = R(2) * static_cast<R>(L.k);
+    sm.bc[lane] = st.bmag * st.cphi;
+    sm.bs[lane] = st.bmag * st.sphi;
+  }
+  __syncthreads();
+  // iv) scan: warps over targets, lanes over grid points
+  for (int t = warp; t < nt; t += nw) warp_scan<R>(sm, t, lane);
+  __syncthreads();
+  // iv) Newton: one bracket per thread
+  for (int x = threadIdx.x; x < 4 * nt; x += blockDim.x) {
+    const int t = x >> 2, q = x & 3;
+    if (q < min(sm.cnt[t], 4)) refine_bracket<R>(sm, t, q);
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  // v-vii) decision and outputs (warp 0)
+  const bool active = lane < nt;
+  const double u = kmc_uniform(a.seed, step, il, it.l);
+  R s_new, c_new;
+  // lanes past the last target repeat the last target (same state as st);
+  // only targets < nt have scan results in shared memory
+  const Decision r = decide<R, MIXED>(sm, min(lane, nt - 1), st, a.beta[i], L.lognu0t,
+                                      L.t_zero != 0, u, s_new, c_new);
+  const R mx = fma(c_new, st.ax, s_new * st.ex);
+  const R my = fma(c_new, st.ay, s_new * st.ey);
+  const R mz = fma(c_new, st.az, s_new * st.ez);
+  const int par = static_cast<int>(step & 1);
   if (active) {
     m4.x = mx;
     m4.y = my;
     m4.z = mz;
     static_cast<V *>(a.m)[i] = m4;
     const R w = static_cast<const V *>(a.pos)[i].w;
-    V mu4;
-    mu4.x = w * mx;
-    mu4.y = w * my;
-    mu4.z = w * mz;
-    mu4.w = R(0);
-    const int par = static_cast<int>(step & 1);
-    static_cast<V *>(a.mu[par ^ 1])[i] = mu4;
+    if constexpr (MIXED) {
+      SrcPair *rec_out = static_cast<SrcPair *>(a.src[par ^ 1]) + L.roff + (il >> 1);
+      const int hf = il & 1;
+      rec_out->mx[hf] = w * mx;
+      rec_out->my[hf] = w * my;
+      rec_out->mz[hf] = w * mz;
+    } else {
+      dbl4 mu;
+      mu.x = w * mx;
+      mu.y = w * my;
+      mu.z = w * mz;
+      mu.w = 0.0;
+      static_cast<dbl4 *>(a.src[par ^ 1])[i] = mu;
+    }
     if (rec >= 0)
-      a.e_acc[i] += bext * (static_cast<double>(mz) - static_cast<double>(mz_old));
+      a.e_acc[i] += bext * (static_cast<double>(mz) - static_cast<double>(st.mz_old));
     if (a.debug) {
-      a.dbg.bdip[3 * i + 0] = static_cast<double>(hx);
-      a.dbg.bdip[3 * i + 1] = static_cast<double>(hy);
-      a.dbg.bdip[3 * i + 2] = static_cast<double>(hz);
+      a.dbg.bdip[3 * i + 0] = static_cast<double>(sm.h[0][lane]);
+      a.dbg.bdip[3 * i + 1] = static_cast<double>(sm.h[1][lane]);
+      a.dbg.bdip[3 * i + 2] = static_cast<double>(sm.h[2][lane]);
       a.dbg.dE[2 * i + 0] = r.dEa;
       a.dbg.dE[2 * i + 1] = r.dEb;
       a.dbg.P[i] = r.P;
       a.dbg.u[i] = u;
-      a.dbg.flags[i] = r.nmin | (r.flipped << 2) | (r.near << 3) | (r.degenerate << 4);
+      a.dbg.flags[i] = r.nmin | (r.flipped << 2) | (r.near << 3) | (st.degenerate << 4);
     }
   }
-  // loop record and counters: one atomic per block
+  // loop record and counters: one atomic each per block
   if (rec >= 0) {
     double c = active ? a.vfrac[i] * static_cast<double>(mz) : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if (lane == 0) atomicAdd(&a.loop_m[static_cast<long long>(l) * a.n_rec + rec], c);
+    if (lane == 0)
+      atomicAdd(reinterpret_cast<unsigned long long *>(
+                    &a.loop_m[static_cast<long long>(it.l) * a.n_rec + rec]),
+                static_cast<unsigned long long>(__double2ll_rn(c * kLoopScale)));
   }
   const unsigned fl = __ballot_sync(0xffffffffu, active && r.flipped);
   const unsigned ne = __ballot_sync(0xffffffffu, active && r.near);
   const unsigned mo = __ballot_sync(0xffffffffu, active && r.nmin == 1);
-  const unsigned dg = __ballot_sync(0xffffffffu, active && r.degenerate);
+  const unsigned dg = __ballot_sync(0xffffffffu, active && st.degenerate);
   const unsigned bd = __ballot_sync(0xffffffffu, active && r.bad);
   if (lane == 0) {
-    unsigned long long *c = a.counters + 4ll * l;
+    unsigned long long *c = a.counters + 4ll * it.l;
     if (fl) atomicAdd(c + 0, static_cast<unsigned long long>(__popc(fl)));
     if (ne) atomicAdd(c + 1, static_cast<unsigned long long>(__popc(ne)));
     if (mo) atomicAdd(c + 2, static_cast<unsigned long long>(__popc(mo)));
@@ -190,140 +516,249 @@ __device__ __forceinline__ void epilogue(const StepArgs &a, const LysDev &L, int
 }
 
 // ---------------------------------------------------------------------------
-// The fused step kernel. V = float4 (FP32-mixed) or dbl4 (FP64-plain).
-
-template <typename V, int NW>
-__global__ void __launch_bounds__(NW * 32) kmc_step_kernel(const StepArgs a, int TJ) {
-  using R = typename SrcTraits<V>::R;
-  constexpr bool MIXED = sizeof(R) == 4;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  V *spos = reinterpret_cast<V *>(smem_raw);  // [2][TJ]
-  V *smu = spos + 2 * TJ;                     // [2][TJ]
-  R *red = reinterpret_cast<R *>(smu + 2 * TJ);  // [NW][12][32]
-  uint64_t *bar = reinterpret_cast<uint64_t *>(red + NW * 12 * 32);  // [2]
-
-  const int4 it = a.items[blockIdx.x];
-  const int l = it.x, i0 = it.y, nt = it.z;
-  const LysDev L = a.lys[l];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long step = a.rs->step_base + a.k_local;
-  const int per = a.rs->period;
-  const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
-  const int par = static_cast<int>(step & 1);
-  const V *__restrict__ gpos = static_cast<const V *>(a.pos) + L.off;
-  const V *__restrict__ gmu = static_cast<const V *>(a.mu[par]) + L.off;
-
-  const int ti = i0 + min(lane, nt - 1);
-  const V pi = gpos[ti];
-  R ax = R(0), ay = R(0), az = R(0), bx = R(0), by = R(0), bz = R(0);
-  // compensated per-warp running sums (FP32 path): value and Kahan term
-  R sax = R(0), say = R(0), saz = R(0), sbx = R(0), sby = R(0), sbz = R(0);
-  R cax = R(0), cay = R(0), caz = R(0), cbx = R(0), cby = R(0), cbz = R(0);
-
-  const int ntiles = (L.n + TJ - 1) / TJ;
+// Bounded double-buffered staging of source tiles. issue(t) queues tile t on
+// mbarrier t & 1; body(buffer, tile) consumes it. Returns false if a copy
+// never landed (error word set); the decision is block-uniform.
+template <typename Issue, typename Body>
+__device__ __forceinline__ bool staged_loop(int ntiles, uint64_t *bar, int32_t *err,
+                                            Issue issue, Body body) {
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_init_fence();
   }
   __syncthreads();
-  auto issue = [&](int t) {
-    const int b = t & 1;
-    const int j0 = t * TJ;
-    const int cnt = min(TJ, L.n - j0);
-    const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(V);
-    mbar_expect_tx(&bar[b], 2 * bytes);
-    bulk_g2s(spos + b * TJ, gpos + j0, bytes, &bar[b]);
-    bulk_g2s(smu + b * TJ, gmu + j0, bytes, &bar[b]);
-  };
   if (threadIdx.x == 0) {
-    issue(0);
+    if (ntiles > 0) issue(0);
     if (ntiles > 1) issue(1);
   }
   for (int t = 0; t < ntiles; ++t) {
     const int b = t & 1;
-    const int j0 = t * TJ;
-    const int cnt = min(TJ, L.n - j0);
-    const bool ok = mbar_wait_bounded(&bar[b], (t >> 1) & 1, a.err);
-    const bool mask = (j0 < i0 + nt) && (i0 < j0 + cnt);
-    if (!ok) {
-      // the copy never landed: error word set, results invalid
-    } else if constexpr (MIXED) {
-      float tax = 0.f, tay = 0.f, taz = 0.f, tbx = 0.f, tby = 0.f, tbz = 0.f;
-      if (mask)
-        pair_tile_f32<true>(spos + b * TJ, smu + b * TJ, cnt, warp, NW, pi.x, pi.y, pi.z, tax,
-                            tay, taz, tbx, tby, tbz);
-      else
-        pair_tile_f32<false>(spos + b * TJ, smu + b * TJ, cnt, warp, NW, pi.x, pi.y, pi.z, tax,
-                             tay, taz, tbx, tby, tbz);
-      kahan_add(sax, cax, tax);
-      kahan_add(say, cay, tay);
-      kahan_add(saz, caz, taz);
-      kahan_add(sbx, cbx, tbx);
-      kahan_add(sby, cby, tby);
-      kahan_add(sbz, cbz, tbz);
-    } else {
-      pair_tile_f64(spos + b * TJ, smu + b * TJ, cnt, warp, NW, pi.x, pi.y, pi.z, ax, ay, az, bx,
-                    by, bz);
-    }
+    const bool ok = mbar_wait_bounded(&bar[b], (t >> 1) & 1, err);
+    if (ok) body(b, t);
     // every warp is done with buffer b; a failed wait anywhere stops all
-    if (!__syncthreads_and(ok)) return;
+    if (!__syncthreads_and(ok)) return false;
     if (threadIdx.x == 0 && t + 2 < ntiles) {
       proxy_fence_shared();
       issue(t + 2);
     }
   }
-  if constexpr (MIXED) {
-    ax = sax;
-    ay = say;
-    az = saz;
-    bx = sbx;
-    by = sby;
-    bz = sbz;
-  }
-  // cross-warp combine through shared memory (fixed order: deterministic)
-  R *rw = red + warp * 12 * 32;
-  rw[0 * 32 + lane] = ax;
-  rw[1 * 32 + lane] = ay;
-  rw[2 * 32 + lane] = az;
-  rw[3 * 32 + lane] = bx;
-  rw[4 * 32 + lane] = by;
-  rw[5 * 32 + lane] = bz;
-  rw[6 * 32 + lane] = cax;
-  rw[7 * 32 + lane] = cay;
-  rw[8 * 32 + lane] = caz;
-  rw[9 * 32 + lane] = cbx;
-  rw[10 * 32 + lane] = cby;
-  rw[11 * 32 + lane] = cbz;
-  __syncthreads();
-  if (warp != 0) return;
-  R h[3];
+  return true;
+}
+
+// After the pair loop the staging bytes hold the warp partials and then the
+// update state.
+template <typename R>
+constexpr size_t epi_bytes(int warps) {
+  return static_cast<size_t>(warps) * 12 * kTargets * sizeof(float) + sizeof(EpiShared<R>) + 64;
+}
+
+// ---------------------------------------------------------------------------
+// FP32-mixed step kernel.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int tile) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *dyn = smem + 16;
+  __shared__ int s_last;
+  const Item it = a.items[blockIdx.x];
+  const LysDev L = a.lys[it.l];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long step = a.rs->step_base + a.k_local;
+  const int per = a.rs->period;
+  const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
+  const int par = static_cast<int>(step & 1);
+  const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
+
+  const float4 pi = static_cast<const float4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
+  const f2 X = pk(pi.x, pi.x), Y = pk(pi.y, pi.y), Z = pk(pi.z, pi.z);
+  float s6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, c6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int nrec = it.j1 - it.j0;
+  const int ntiles = (nrec + tile - 1) / tile;
+  const int own0 = it.t0 >> 1, own1 = (it.t0 + it.nt - 1) >> 1;  // records holding targets
+  ulonglong2 *buf = reinterpret_cast<ulonglong2 *>(dyn);          // [2][tile][3]
+  auto issue = [&](int t) {
+    const int b = t & 1;
+    const int r0 = it.j0 + t * tile;
+    const int cnt = min(tile, it.j1 - r0);
+    const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
+    mbar_expect_tx(&bar[b], bytes);
+    bulk_g2s(buf + static_cast<size_t>(b) * tile * 3, gsrc + r0, bytes, &bar[b]);
+  };
+  auto body = [&](int b, int t) {
+    const int r0 = it.j0 + t * tile;
+    const int cnt = min(tile, it.j1 - r0);
+    const bool mask = (r0 <= own1) && (own0 < r0 + cnt);
+    AccF32 acc;
+    acc.ax = acc.ay = acc.az = acc.bx = acc.by = acc.bz = 0ull;
+    const ulonglong2 *sp = buf + static_cast<size_t>(b) * tile * 3;
+    if (mask)
+      pair_tile_f32<true>(sp, cnt, warp, NW, X, Y, Z, acc);
+    else
+      pair_tile_f32<false>(sp, cnt, warp, NW, X, Y, Z, acc);
+    kahan_add(s6[0], c6[0], hsum(acc.ax));
+    kahan_add(s6[1], c6[1], hsum(acc.ay));
+    kahan_add(s6[2], c6[2], hsum(acc.az));
+    kahan_add(s6[3], c6[3], hsum(acc.bx));
+    kahan_add(s6[4], c6[4], hsum(acc.by));
+    kahan_add(s6[5], c6[5], hsum(acc.bz));
+  };
+  if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
+
+  // cross-warp combine in a fixed order: value = hi + lo per component
+  float *wp = reinterpret_cast<float *>(dyn);  // [NW][12][32]
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if constexpr (MIXED) {
-      float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
+  for (int c = 0; c < 6; ++c) {
+    wp[(warp * 12 + c) * 32 + lane] = s6[c];
+    wp[(warp * 12 + 6 + c) * 32 + lane] = -c6[c];  // Kahan keeps minus the error
+  }
+  __syncthreads();
+  EpiShared<float> &sm =
+      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 12 * 32 * 4);
+  float hi[6], lo[6];
+  if (warp == 0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float s = 0.f, e = 0.f;
       for (int w = 0; w < NW; ++w) {
-        neumaier_add(sa, ca, red[w * 384 + c * 32 + lane]);
-        ca -= red[w * 384 + (6 + c) * 32 + lane];  // Kahan terms hold minus the error
-        neumaier_add(sb, cb, red[w * 384 + (3 + c) * 32 + lane]);
-        cb -= red[w * 384 + (9 + c) * 32 + lane];
+        neumaier_add(s, e, wp[(w * 12 + c) * 32 + lane]);
+        e += wp[(w * 12 + 6 + c) * 32 + lane];
       }
-      // b_dip = 3A - B with the compensations added last
-      float s = 0.f, cc = 0.f;
-      neumaier_add(s, cc, 3.0f * sa);
-      neumaier_add(s, cc, -sb);
-      neumaier_add(s, cc, 3.0f * ca - cb);
-      h[c] = s + cc;
-    } else {
-      double sa = 0.0, sb = 0.0;
-      for (int w = 0; w < NW; ++w) {
-        sa += red[w * 384 + c * 32 + lane];
-        sb += red[w * 384 + (3 + c) * 32 + lane];
+      hi[c] = s;
+      lo[c] = e;
+    }
+    if (it.nsplit > 1) {
+      float *part = a.partial + static_cast<size_t>(blockIdx.x) * 12 * 32;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        __stcg(part + c * 32 + lane, hi[c]);
+        __stcg(part + (6 + c) * 32 + lane, lo[c]);
       }
-      h[c] = 3.0 * sa - sb;
+      __threadfence();
     }
   }
-  epilogue<V, MIXED>(a, L, l, i0, nt, lane, h[0], h[1], h[2], step, rec);
+  if (it.nsplit > 1) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
+    __syncthreads();
+    if (!s_last) return;  // another item of the group finishes the step
+    __threadfence();
+    if (warp == 0) {
+      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * 12 * 32;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        float s = 0.f, e = 0.f;
+        for (int q = 0; q < it.nsplit; ++q) {
+          neumaier_add(s, e, __ldcg(base + (q * 12 + c) * 32 + lane));
+          e += __ldcg(base + (q * 12 + 6 + c) * 32 + lane);
+        }
+        hi[c] = s;
+        lo[c] = e;
+      }
+      if (lane == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
+    }
+  }
+  if (warp == 0) {
+    // b_dip = 3A - B, compensation terms added last
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float s = 0.f, e = 0.f;
+      neumaier_add(s, e, 3.0f * hi[c]);
+      neumaier_add(s, e, -hi[3 + c]);
+      neumaier_add(s, e, 3.0f * lo[c] - lo[3 + c]);
+      sm.h[c][lane] = s + e;
+    }
+  }
+  __syncthreads();
+  block_update<float4, true>(a, L, it, step, rec, sm);
+}
+
+// ---------------------------------------------------------------------------
+// FP64-plain step kernel (same structure, scalar FP64 pair loop).
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int tile) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *dyn = smem + 16;
+  __shared__ int s_last;
+  const Item it = a.items[blockIdx.x];
+  const LysDev L = a.lys[it.l];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long step = a.rs->step_base + a.k_local;
+  const int per = a.rs->period;
+  const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
+  const int par = static_cast<int>(step & 1);
+  const dbl4 *__restrict__ gpos = static_cast<const dbl4 *>(a.src_pos) + L.roff;
+  const dbl4 *__restrict__ gmu = static_cast<const dbl4 *>(a.src[par]) + L.roff;
+
+  const dbl4 pi = static_cast<const dbl4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const int nrec = it.j1 - it.j0;
+  const int ntiles = (nrec + tile - 1) / tile;
+  dbl4 *spos = reinterpret_cast<dbl4 *>(dyn);  // [2][tile]
+  dbl4 *smu = spos + 2 * tile;                 // [2][tile]
+  auto issue = [&](int t) {
+    const int b = t & 1;
+    const int r0 = it.j0 + t * tile;
+    const int cnt = min(tile, it.j1 - r0);
+    const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(dbl4);
+    mbar_expect_tx(&bar[b], 2 * bytes);
+    bulk_g2s(spos + b * tile, gpos + r0, bytes, &bar[b]);
+    bulk_g2s(smu + b * tile, gmu + r0, bytes, &bar[b]);
+  };
+  auto body = [&](int b, int t) {
+    const int r0 = it.j0 + t * tile;
+    const int cnt = min(tile, it.j1 - r0);
+    pair_tile_f64(spos + b * tile, smu + b * tile, cnt, warp, NW, pi.x, pi.y, pi.z, acc);
+  };
+  if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
+
+  double *wp = reinterpret_cast<double *>(dyn);  // [NW][6][32]
+#pragma unroll
+  for (int c = 0; c < 6; ++c) wp[(warp * 6 + c) * 32 + lane] = acc[c];
+  __syncthreads();
+  EpiShared<double> &sm =
+      *reinterpret_cast<EpiShared<double> *>(dyn + static_cast<size_t>(NW) * 12 * 32 * 4);
+  double tot[6];
+  if (warp == 0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double s = 0.0;
+      for (int w = 0; w < NW; ++w) s += wp[(w * 6 + c) * 32 + lane];
+      tot[c] = s;
+    }
+    if (it.nsplit > 1) {
+      double *part =
+          reinterpret_cast<double *>(a.partial + static_cast<size_t>(blockIdx.x) * 12 * 32);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) __stcg(part + c * 32 + lane, tot[c]);
+      __threadfence();
+    }
+  }
+  if (it.nsplit > 1) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (warp == 0) {
+      const double *base = reinterpret_cast<const double *>(
+          a.partial + static_cast<size_t>(blockIdx.x - it.split) * 12 * 32);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        double s = 0.0;
+        for (int q = 0; q < it.nsplit; ++q) s += __ldcg(base + (q * 6 + c) * 32 + lane);
+        tot[c] = s;
+      }
+      if (lane == 0) a.arrivals[it.gid] = 0;
+    }
+  }
+  if (warp == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sm.h[c][lane] = 3.0 * tot[c] - tot[3 + c];
+  }
+  __syncthreads();
+  block_update<dbl4, false>(a, L, it, step, rec, sm);
 }
 
 // Ends a field period on the device: the next period starts S steps later.
@@ -336,22 +771,21 @@ __global__ void kmc_advance_kernel(RunState *rs, int S) {
 // Host side of the launches.
 
 size_t step_smem_bytes(int prec_fp32, int warps, int tile) {
-  const size_t v = prec_fp32 ? sizeof(float4) : sizeof(dbl4);
-  const size_t r = prec_fp32 ? sizeof(float) : sizeof(double);
-  return 4 * static_cast<size_t>(tile) * v + static_cast<size_t>(warps) * 12 * 32 * r + 16;
+  const size_t stage = prec_fp32 ? 2 * static_cast<size_t>(tile) * sizeof(SrcPair)
+                                 : 4 * static_cast<size_t>(tile) * sizeof(dbl4);
+  const size_t epi = prec_fp32 ? epi_bytes<float>(warps) : epi_bytes<double>(warps);
+  return 16 + (stage > epi ? stage : epi);
 }
 
-template <typename V, int NW>
-static cudaError_t launch_t(const StepArgs &a, int n_items, int tile, cudaStream_t st) {
-  const size_t smem = step_smem_bytes(sizeof(V) == sizeof(float4), NW, tile);
-  kmc_step_kernel<V, NW><<<n_items, NW * 32, smem, st>>>(a, tile);
+template <int NW>
+static cudaError_t launch_f32(const StepArgs &a, int n_items, int tile, cudaStream_t st) {
+  kmc_step_f32<NW><<<n_items, NW * 32, step_smem_bytes(1, NW, tile), st>>>(a, tile);
   return cudaGetLastError();
 }
-
-template <typename V, int NW>
-static cudaError_t allow_smem() {
-  return cudaFuncSetAttribute(kmc_step_kernel<V, NW>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStepSmem);
+template <int NW>
+static cudaError_t launch_f64(const StepArgs &a, int n_items, int tile, cudaStream_t st) {
+  kmc_step_f64<NW><<<n_items, NW * 32, step_smem_bytes(0, NW, tile), st>>>(a, tile);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
@@ -359,16 +793,16 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
   if (n_items <= 0) return cudaSuccess;
   if (prec_fp32) {
     switch (warps) {
-      case 4: return launch_t<float4, 4>(a, n_items, tile, st);
-      case 8: return launch_t<float4, 8>(a, n_items, tile, st);
-      case 16: return launch_t<float4, 16>(a, n_items, tile, st);
+      case 4: return launch_f32<4>(a, n_items, tile, st);
+      case 8: return launch_f32<8>(a, n_items, tile, st);
+      case 16: return launch_f32<16>(a, n_items, tile, st);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (warps) {
-    case 4: return launch_t<dbl4, 4>(a, n_items, tile, st);
-    case 8: return launch_t<dbl4, 8>(a, n_items, tile, st);
-    case 16: return launch_t<dbl4, 16>(a, n_items, tile, st);
+    case 4: return launch_f64<4>(a, n_items, tile, st);
+    case 8: return launch_f64<8>(a, n_items, tile, st);
+    case 16: return launch_f64<16>(a, n_items, tile, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -378,25 +812,35 @@ cudaError_t launch_advance(RunState *rs, int S, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename K>
+static cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kMaxStepSmem));
+}
+
 cudaError_t init_device() {
-  float f[3][kGrid];
-  double d[3][kGrid];
+  float th_f[kGrid];
+  float2 sc_f[kGrid];
+  double th_d[kGrid];
+  double2 sc_d[kGrid];
   const double two_pi = 6.283185307179586476925286766559;
   for (int j = 0; j < kGrid; ++j) {
-    d[0][j] = two_pi * (static_cast<double>(j) + 0.5) / static_cast<double>(kGrid);
-    d[1][j] = sin(d[0][j]);
-    d[2][j] = cos(d[0][j]);
-    for (int q = 0; q < 3; ++q) f[q][j] = static_cast<float>(d[q][j]);
+    th_d[j] = two_pi * (static_cast<double>(j) + 0.5) / static_cast<double>(kGrid);
+    sc_d[j] = make_double2(sin(th_d[j]), cos(th_d[j]));
+    th_f[j] = static_cast<float>(th_d[j]);
+    sc_f[j] = make_float2(static_cast<float>(sc_d[j].x), static_cast<float>(sc_d[j].y));
   }
-  cudaError_t e = cudaMemcpyToSymbol(g_grid_f, f, sizeof(f));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_grid_d, d, sizeof(d));
+  cudaError_t e = cudaMemcpyToSymbol(g_theta_f, th_f, sizeof(th_f));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_sc_f, sc_f, sizeof(sc_f));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_theta_d, th_d, sizeof(th_d));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_sc_d, sc_d, sizeof(sc_d));
   // kernel attributes are set here, never inside a stream capture
-  if (e == cudaSuccess) e = allow_smem<float4, 4>();
-  if (e == cudaSuccess) e = allow_smem<float4, 8>();
-  if (e == cudaSuccess) e = allow_smem<float4, 16>();
-  if (e == cudaSuccess) e = allow_smem<dbl4, 4>();
-  if (e == cudaSuccess) e = allow_smem<dbl4, 8>();
-  if (e == cudaSuccess) e = allow_smem<dbl4, 16>();
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32<8>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32<16>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f64<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f64<8>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f64<16>);
   return e;
 }
 

@@ -20,17 +20,43 @@ struct __align__(32) dbl4 {  // FP64 record: x, y, z and a fourth value
   double x, y, z, w;
 };
 
-constexpr int kGrid = 200;     // scan points of step iv (Sec. II.1)
-constexpr int kTargets = 32;   // target NPs per block (one per lane)
+// FP32 source record: two NPs (even, odd) interleaved so that each 8-byte
+// pair of lanes feeds one packed f32x2 instruction. 48 bytes, three 16-byte
+// shared-memory loads. A lysosome with an odd NP count ends with a padding NP
+// far away (x = y = z = 1e4 L) whose moment is zero.
+struct __align__(16) SrcPair {
+  float x[2], y[2];
+  float z[2], mx[2];
+  float my[2], mz[2];
+};
+
+constexpr int kGrid = 200;   // scan points of step iv (Sec. II.1)
+constexpr int kTargets = 32; // target NPs per work item (one per lane of a warp)
+constexpr float kPadCoord = 1e4f;
+constexpr double kLoopScale = 4611686018427387904.0;  // 2^62, fixed point of the loop
 
 struct LysDev {
-  int32_t off;      // first NP of the lysosome in the flat arrays
+  int32_t off;      // first NP of the lysosome in the flat per-NP arrays
   int32_t n;        // NPs
+  int32_t roff;     // first source record (FP32: NP pairs, FP64: NPs)
   int32_t t_zero;   // 1 if T == 0: steps vi-vii skipped
-  int32_t pad;
   double k;         // K_eff / (mu0 M_S^2)
   double bmax;      // mu0 H_max / (mu0 M_S), set by each run
   double lognu0t;   // ln(t_step / tau0), set by each run
+};
+
+// One work item = one block: 32 targets of lysosome l against the source
+// records [j0, j1). A target group whose sources are split over nsplit items
+// has its items stored consecutively (split = 0 .. nsplit-1); the last of
+// them to finish combines the partial sums and runs steps iii-vii.
+struct Item {
+  int32_t l;       // lysosome
+  int32_t t0;      // first target (index within the lysosome)
+  int32_t nt;      // targets, 1..32
+  int32_t gid;     // target group (index of its arrival counter)
+  int32_t j0, j1;  // source records of this item (relative to the lysosome)
+  int32_t split;   // index of this item within its group
+  int32_t nsplit;  // items in the group
 };
 
 struct RunState {   // advanced on the device at the end of each field period
@@ -48,18 +74,23 @@ struct DebugOut {   // optional per-NP intermediates (device pointers)
 };
 
 struct StepArgs {
-  const int4 *items;        // (lysosome, first target, targets, 0)
+  const Item *items;
   const LysDev *lys;
-  const void *pos;          // [N] float4 / double4: x, y, z (units of L), w
-  const void *axis;         // [N] float4 / double4 unit easy axis
-  void *m;                  // [N] float4 / double4 unit moments (owner-updated)
-  void *mu[2];              // [N] float4 / double4 source moments w m (ping-pong)
+  const void *pos;          // [N] float4 / dbl4: x, y, z (units of L), w (targets)
+  const void *axis;         // [N] float4 / dbl4 unit easy axis
+  void *m;                  // [N] float4 / dbl4 unit moments (owner-updated)
+  void *src[2];             // source records, ping-pong: FP32 SrcPair, FP64 dbl4 moments
+  const void *src_pos;      // FP64 only: [N] dbl4 source positions (static)
   const double *beta;       // [N] mu0 M_S^2 V_i / (k_B T)
   const double *vfrac;      // [N] V_i / sum of V over the lysosome
   double *e_acc;            // [N] sum_k b_k (m_z,k+1 - m_z,k) over recorded steps
-  double *loop_m;           // [n_lys][n_rec] volume-weighted mean m_z
+  long long *loop_m;        // [n_lys][n_rec] volume-weighted mean m_z in fixed point
+                            // (units of 2^-62): integer sums do not depend on the
+                            // order in which blocks add, so runs are reproducible
   unsigned long long *counters;  // [n_lys][4]
   int32_t *err;             // device error word
+  float *partial;           // scratch: [items][12][32] floats of partial sums
+  int32_t *arrivals;        // scratch: [groups] arrival counters, zero between launches
   const RunState *rs;
   double cos_k;             // cos(2 pi k / S)
   unsigned long long seed;

@@ -73,7 +73,7 @@ def lib():
             L.kmc_save.argtypes = [vp, C.c_char_p]
             L.kmc_load.argtypes = [vp, C.c_char_p]
             L.kmc_info.argtypes = [vp, _I64, _I32, _I64]
-            L.kmc_tuning.argtypes = [vp, C.c_int32, C.c_int32, _I32, _I32]
+            L.kmc_tuning.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, _I32, _I32, _I32]
             L.kmc_destroy.argtypes = [vp]
             L.kmc_destroy.restype = None
             L.kmc_last_error.argtypes = []
@@ -196,15 +196,16 @@ def kmc_info(ctx):
     return dict(n_total=n.value, n_lys=nl.value, global_step=s.value)
 
 
-def kmc_tuning(ctx, warps=None, tile=None):
-    """Sets the launch shape (both given) or, with no arguments, returns it."""
-    w = C.c_int32()
-    t = C.c_int32()
+def kmc_tuning(ctx, warps=None, tile=None, chunk=0):
+    """Sets the launch shape (warps and tile given; 0 = autotune) or, with no
+    arguments, returns the shape in use as (warps, tile, chunk)."""
+    w, t, c = C.c_int32(), C.c_int32(), C.c_int32()
     if warps is None and tile is None:
-        _check(lib().kmc_tuning(ctx.handle, 0, 0, C.byref(w), C.byref(t)))
+        _check(lib().kmc_tuning(ctx.handle, -1, -1, -1, C.byref(w), C.byref(t), C.byref(c)))
     else:
-        _check(lib().kmc_tuning(ctx.handle, int(warps), int(tile), C.byref(w), C.byref(t)))
-    return int(w.value), int(t.value)
+        _check(lib().kmc_tuning(ctx.handle, int(warps), int(tile), int(chunk), C.byref(w),
+                                C.byref(t), C.byref(c)))
+    return int(w.value), int(t.value), int(c.value)
 
 
 def kmc_destroy(ctx):

@@ -80,15 +80,16 @@ def test_draws_are_bit_exact(prec):
         assert np.array_equal(g["u"], np.array(expect))
 
 
-@pytest.mark.parametrize("tile,warps", [(64, 4), (128, 8), (256, 16)])
-def test_fp64_step_parity(tile, warps):
+@pytest.mark.parametrize("tile,warps,chunk", [(64, 4, 0), (128, 8, 64), (32, 16, 128),
+                                              (64, 4, 192)])
+def test_fp64_step_parity(tile, warps, chunk):
     lyss = ragged_batch(2)
     rng = np.random.default_rng(3)
     m = np.concatenate([perturbed_moments(l.axis, rng) for l in lyss])
     Hs = np.array([0.012, -0.02, 0.0, 0.018, -0.005, 0.03])
     t_step = 1 / (1e5 * 200)
     ctx = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
-    kmc.kmc_tuning(ctx, warps, tile)
+    kmc.kmc_tuning(ctx, warps, tile, chunk)
     g = kmc.kmc_debug_step(ctx, Hs, t_step, 11, 1000, m)
     o = oracle_steps(lyss, m, Hs, t_step, 11, 1000)
     off = 0
@@ -112,6 +113,27 @@ def test_fp64_step_parity(tile, warps):
     assert np.max(np.abs(g["m_out"][same] - o["m_out"][same])) < 1e-12
     assert np.array_equal(g["flipped"][same], o["flipped"][same])
     assert np.array_equal(g["degenerate"], o["degenerate"])
+
+
+def test_fp32_shapes_agree_and_are_deterministic():
+    """Every launch shape (warps, tile, source split) gives the same FP32 fields
+    within FP32 rounding, and one shape run twice gives identical bits."""
+    lyss = ragged_batch(4)
+    rng = np.random.default_rng(8)
+    m = np.concatenate([perturbed_moments(l.axis, rng) for l in lyss])
+    Hs = np.full(len(lyss), 0.01)
+    ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+    outs = []
+    for shape in [(4, 64, 0), (8, 128, 0), (4, 32, 64), (16, 64, 128), (8, 64, 192)]:
+        kmc.kmc_tuning(ctx, *shape)
+        outs.append(kmc.kmc_debug_step(ctx, Hs, 5e-8, 2, 9, m))
+    again = kmc.kmc_debug_step(ctx, Hs, 5e-8, 2, 9, m)
+    for k in ("B_dip", "P", "m_out", "dE"):
+        assert np.array_equal(again[k], outs[-1][k])
+    rms = np.sqrt(np.mean(np.sum(outs[0]["B_dip"] ** 2, axis=1)))
+    for o in outs[1:]:
+        assert np.max(np.abs(o["B_dip"] - outs[0]["B_dip"])) < 2e-6 * rms
+        assert np.array_equal(o["u"], outs[0]["u"])
 
 
 def test_fp32_field_error_and_state():
