@@ -125,7 +125,8 @@ struct Prec<float> {
   static constexpr float two_pi = 6.28318530717958647692f;
   static constexpr float plane_tol = 1e-6f;   // |b x a| below this: plane from m
   static constexpr float newton_tol = 2e-9f;  // absolute, on the offset in a cell
-  static constexpr int newton_max = 24;
+  static constexpr int newton_max = 4;        // from the secant point: quadratic
+  __device__ static float div(float a, float b) { return __fdividef(a, b); }
   __device__ static float theta(int j) { return g_theta_f[j]; }
   __device__ static float2 sc(int j) { return g_sc_f[j]; }
   // sin and cos of 0 <= d <= 2 pi / 200 by their Taylor series (error < 1e-11)
@@ -141,6 +142,7 @@ struct Prec<double> {
   static constexpr double plane_tol = 1e-12;
   static constexpr double newton_tol = 1e-14;
   static constexpr int newton_max = 100;
+  __device__ static double div(double a, double b) { return a / b; }
   __device__ static double theta(int j) { return g_theta_d[j]; }
   __device__ static double2 sc(int j) { return g_sc_d[j]; }
   // Taylor series to d^9 / d^10: truncation below 1e-24 for d <= 2 pi / 200
@@ -171,11 +173,15 @@ struct Profile {
 };
 
 // Newton's method with bisection fallback for the root of de/dth inside grid
-// cell [theta_j, theta_j + h], as offset d from theta_j. dlo = de/dth at theta_j.
+// cell [theta_j, theta_j + h], as offset d from theta_j. dlo, dhi = de/dth at
+// theta_j and theta_j + h (opposite signs); the first iterate is the secant
+// point, so that two or three Newton steps reach the root.
 template <typename R>
 __device__ __forceinline__ R refine_in_cell(const Profile<R> &pf, R S0, R C0, R h, R dlo,
-                                            R &s_out, R &c_out) {
-  R lo = R(0), hi = h, x = R(0.5) * h;
+                                            R dhi, R &s_out, R &c_out) {
+  R lo = R(0), hi = h;
+  R x = (dlo != dhi) ? h * Prec<R>::div(dlo, dlo - dhi) : R(0.5) * h;
+  if (!(x > lo && x < hi)) x = R(0.5) * h;
   for (int it = 0; it < Prec<R>::newton_max; ++it) {
     R sd, cd;
     Prec<R>::sincos_small(x, sd, cd);
@@ -189,7 +195,7 @@ __device__ __forceinline__ R refine_in_cell(const Profile<R> &pf, R S0, R C0, R 
       hi = x;
     }
     const R dd = pf.d2(s, c);
-    R xn = (dd != R(0)) ? x - d / dd : R(0.5) * (lo + hi);
+    R xn = (dd != R(0)) ? x - Prec<R>::div(d, dd) : R(0.5) * (lo + hi);
     if (!(xn > lo && xn < hi)) xn = R(0.5) * (lo + hi);
     const bool done = fabs(xn - x) < Prec<R>::newton_tol || hi - lo < Prec<R>::newton_tol;
     x = xn;

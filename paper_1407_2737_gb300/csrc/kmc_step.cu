@@ -171,6 +171,7 @@ struct EpiShared {
   int cnt[kTargets];   // sign changes found by the scan
   int jq[kTargets][4];
   R dq[kTargets][4];   // derivative at the left node of each bracket
+  R dqh[kTargets][4];  // derivative at the right node
   R th[kTargets][4], en[kTargets][4], sq[kTargets][4], cq[kTargets][4], off[kTargets][4];
 };
 
@@ -179,42 +180,68 @@ __device__ __forceinline__ R profile_d1(R k2, R bc, R bs, R s, R c) {
   return s * fma(k2, c, bc) - bs * c;
 }
 
-// Scan of step iv for target t by one warp: lane l evaluates de/dth at grid
-// points j = l + 32 q (q = 0..6) and tests the cell (j, j+1), cyclically.
+// Grid points of step iv held by one lane during the scan: lane l owns the
+// consecutive points j = 7 l .. 7 l + 6 (lanes 0..27), lane 28 owns 196..199.
+constexpr int kScanPts = 7;
 template <typename R>
-__device__ __forceinline__ void warp_scan(EpiShared<R> &sm, int t, int lane) {
+struct ScanLane {
+  R s[kScanPts], c[kScanPts];  // sin and cos of the lane's grid points
+  int j0, npts;
+  __device__ void load(int lane) {
+    j0 = kScanPts * lane;
+    npts = max(0, min(kScanPts, kGrid - j0));
+#pragma unroll
+    for (int q = 0; q < kScanPts; ++q) {
+      const auto sc = Prec<R>::sc(min(j0 + q, kGrid - 1));
+      s[q] = sc.x;
+      c[q] = sc.y;
+    }
+  }
+};
+
+// Scan of step iv for target t by one warp: each lane evaluates de/dth at its
+// grid points and tests the cells (j, j+1) that start there, cyclically (the
+// cell after point 199 ends at point 0). Brackets are numbered in grid order
+// through a prefix sum over the lanes.
+template <typename R>
+__device__ __forceinline__ void warp_scan(EpiShared<R> &sm, const ScanLane<R> &g, int t,
+                                          int lane) {
   const R k2 = sm.k2[t], bc = sm.bc[t], bs = sm.bs[t];
-  R d[7];
+  R d[kScanPts];
 #pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    const int j = lane + 32 * q;
-    d[q] = R(0);
-    if (j < kGrid) {
-      const auto sc = Prec<R>::sc(j);
-      d[q] = profile_d1<R>(k2, bc, bs, sc.x, sc.y);
-    }
+  for (int q = 0; q < kScanPts; ++q) d[q] = profile_d1<R>(k2, bc, bs, g.s[q], g.c[q]);
+  // value at the first point of the next lane (the last lane wraps to point 0)
+  R nxt = __shfl_down_sync(0xffffffffu, d[0], 1);
+  const R d0 = __shfl_sync(0xffffffffu, d[0], 0);
+  if (g.j0 + g.npts == kGrid) nxt = d0;
+  unsigned chg = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPts; ++q) {
+    const R right = (q + 1 < g.npts) ? d[q < kScanPts - 1 ? q + 1 : q] : nxt;
+    if (q < g.npts && ((d[q] < R(0)) != (right < R(0)))) chg |= 1u << q;
   }
-  const R dfirst = __shfl_sync(0xffffffffu, d[0], 0);
-  int base = 0;
+  // exclusive prefix sum of the bracket counts over the lanes
+  const int mine = __popc(chg);
+  int incl = mine;
 #pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    const int j = lane + 32 * q;
-    R nx = __shfl_down_sync(0xffffffffu, d[q], 1);
-    const R w0 = __shfl_sync(0xffffffffu, d[q < 6 ? q + 1 : 0], 0);
-    if (lane == 31) nx = w0;
-    if (j == kGrid - 1) nx = dfirst;
-    const bool chg = (j < kGrid) && ((d[q] < R(0)) != (nx < R(0)));
-    const unsigned m = __ballot_sync(0xffffffffu, chg);
-    if (chg) {
-      const int slot = base + __popc(m & ((1u << lane) - 1u));
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  int slot = incl - mine;
+#pragma unroll
+  for (int q = 0; q < kScanPts; ++q) {
+    if (chg & (1u << q)) {
       if (slot < 4) {
-        sm.jq[t][slot] = j;
+        const R right = (q + 1 < g.npts) ? d[q < kScanPts - 1 ? q + 1 : q] : nxt;
+        sm.jq[t][slot] = g.j0 + q;
         sm.dq[t][slot] = d[q];
+        sm.dqh[t][slot] = right;
       }
+      ++slot;
     }
-    base += __popc(m);
   }
-  if (lane == 0) sm.cnt[t] = base;
+  if (lane == 31) sm.cnt[t] = incl;
 }
 
 // Newton refinement of bracket q of target t (one thread).
@@ -229,7 +256,7 @@ __device__ __forceinline__ void refine_bracket(EpiShared<R> &sm, int t, int q) {
   const auto sc = Prec<R>::sc(j);
   const R h = Prec<R>::theta(1) - Prec<R>::theta(0);
   R s, c;
-  const R off = refine_in_cell(pf, sc.x, sc.y, h, sm.dq[t][q], s, c);
+  const R off = refine_in_cell(pf, sc.x, sc.y, h, sm.dq[t][q], sm.dqh[t][q], s, c);
   R th = Prec<R>::theta(j) + off;
   if (th >= Prec<R>::two_pi) th -= Prec<R>::two_pi;
   sm.th[t][q] = th;
@@ -310,6 +337,16 @@ struct Decision {
   int nmin, flipped, near, bad;
 };
 
+// e^x for an exponent x held in FP64: x log2(e) = n + f exactly split into an
+// integer n and a fraction f in [0, 1); 2^f in FP32, then scaled by 2^n.
+__device__ __forceinline__ float exp_fp64_arg(double x) {
+  const double y = x * 1.4426950408889634073599;  // log2(e)
+  if (y < -160.0) return 0.0f;
+  const double n = floor(y);
+  const float r = exp2f(static_cast<float>(y - n));
+  return ldexpf(r, static_cast<int>(fmin(n, 200.0)));
+}
+
 // Steps v-vii for target t: basins, barrier (FP64 polish near the switching
 // field in the mixed path), Eqs. 3-5 in FP64, draw u < P. Returns (sin, cos)
 // of the new angle in the plane.
@@ -361,39 +398,48 @@ __device__ __forceinline__ Decision decide(const EpiShared<R> &sm, int t,
   const R e3 = fmin(sm.en[t][imax0], sm.en[t][imax1]);
   double dEa = static_cast<double>(e3 - sm.en[t][wa]);
   double dEb = static_cast<double>(e3 - sm.en[t][wb]);
-  if (MIXED && fmin(dEa, dEb) < 0.02 * static_cast<double>(sm.k[t])) {
-    // FP64 polish: one Newton step from each FP32 root, energies in FP64
+  if (MIXED && fmin(dEa, dEb) < 1e-3 * static_cast<double>(sm.k[t])) {
+    // Near the switching field E3 - E_a cancels: the energies of the two wells
+    // and of the lower maximum are taken again in FP64 at the FP32 roots (the
+    // energy is stationary there, so the root's FP32 error enters squared).
     Profile<double> pd;
     pd.k = static_cast<double>(sm.k[t]);
     pd.k2 = 2.0 * pd.k;
     pd.bc = static_cast<double>(st.bmag) * static_cast<double>(st.cphi);
     pd.bs = static_cast<double>(st.bmag) * static_cast<double>(st.sphi);
-    double e64[4];
-    for (int q = 0; q < 4; ++q) {
+    const int i3 = (sm.en[t][imax0] <= sm.en[t][imax1]) ? imax0 : imax1;
+    const int qs[3] = {wa, wb, i3};
+    double e64[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int q = qs[k];
       const double2 sc = g_sc_d[min(max(sm.jq[t][q], 0), kGrid - 1)];
-      double x = static_cast<double>(sm.off[t][q]), sd, cd;
-      Prec<double>::sincos_small(x, sd, cd);
-      double s = fma(sc.x, cd, sc.y * sd), c = fma(sc.y, cd, -sc.x * sd);
-      const double dd = pd.d2(s, c);
-      if (dd != 0.0) x -= pd.d1(s, c) / dd;
-      Prec<double>::sincos_small(x, sd, cd);
-      s = fma(sc.x, cd, sc.y * sd);
-      c = fma(sc.y, cd, -sc.x * sd);
-      e64[q] = pd.e(s, c);
+      double sd, cd;
+      Prec<double>::sincos_small(static_cast<double>(sm.off[t][q]), sd, cd);
+      e64[k] = pd.e(fma(sc.x, cd, sc.y * sd), fma(sc.y, cd, -sc.x * sd));
     }
-    const double e3d = fmin(e64[imax0], e64[imax1]);
-    dEa = e3d - e64[wa];
-    dEb = e3d - e64[wb];
+    dEa = e64[2] - e64[0];
+    dEb = e64[2] - e64[1];
   }
   o.dEa = dEa;
   o.dEb = dEb;
   int w = wa;
   if (!t_zero) {
-    // vi) Eqs. 3-5 with nu t = exp(ln(nu0 t_step) - beta dE)
-    const double ea = exp(lognu0t - beta * dEa);
-    const double eb = exp(lognu0t - beta * dEb);
-    const double sum = ea + eb;
-    const double P = (sum > 0.0) ? (ea / sum) * (-expm1(-sum)) : 0.0;
+    // vi) Eqs. 3-5 with nu t = exp(x), x = ln(nu0 t_step) - beta dE
+    double P;
+    if constexpr (MIXED) {
+      // the exponent x in FP64; e^x = 2^n 2^f with n integral and the
+      // fraction f in [0, 1) evaluated in FP32
+      const float ea = exp_fp64_arg(lognu0t - beta * dEa);
+      const float eb = exp_fp64_arg(lognu0t - beta * dEb);
+      const float sum = ea + eb;
+      P = (sum > 0.f) ? static_cast<double>((ea / sum) * (-expm1f(-sum))) : 0.0;
+    } else {
+      const double ea = exp(lognu0t - beta * dEa);
+      const double eb = exp(lognu0t - beta * dEb);
+      const double sum = ea + eb;
+      P = (sum > 0.0) ? (ea / sum) * (-expm1(-sum)) : 0.0;
+    }
     o.P = P;
     // vii) jump iff u < P
     o.near = fabs(u - P) < 1e-9;
@@ -407,28 +453,52 @@ __device__ __forceinline__ Decision decide(const EpiShared<R> &sm, int t,
   return o;
 }
 
-// Steps iii-vii for the block's targets; sm.h holds their dipolar fields.
-// V = float4 (mixed) or dbl4 (plain).
+// Per-target inputs of steps iii-vii that warp 0 loads (and the draw it makes)
+// before the pair loop, so that their latency hides behind it. Lanes past the
+// last target repeat the last target.
+template <typename V>
+struct TargetIn {
+  V ax4, m4;
+  double beta, vfrac, eacc, u;
+  int i, il;
+};
+
+template <typename V>
+__device__ __forceinline__ TargetIn<V> load_target(const StepArgs &a, const LysDev &L,
+                                                   const Item &it, long long step, int lane) {
+  TargetIn<V> p;
+  p.il = it.t0 + min(lane, it.nt - 1);
+  p.i = L.off + p.il;
+  p.ax4 = static_cast<const V *>(a.axis)[p.i];
+  p.m4 = static_cast<const V *>(a.m)[p.i];
+  p.beta = a.beta[p.i];
+  p.vfrac = a.vfrac[p.i];
+  p.eacc = a.e_acc[p.i];
+  p.u = kmc_uniform(a.seed, step, p.il, it.l);
+  return p;
+}
+
+// Steps iii-vii for the block's targets; sm.h holds their dipolar fields and
+// warp 0 holds their inputs in tin. V = float4 (mixed) or dbl4 (plain).
 template <typename V, bool MIXED>
 __device__ __forceinline__ void block_update(
     const StepArgs &a, const LysDev &L, const Item &it, long long step, int rec,
+    const TargetIn<V> &tin,
     EpiShared<typename std::conditional<MIXED, float, double>::type> &sm) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int nt = it.nt;
   const double bext = L.bmax * a.cos_k;
+  ScanLane<R> grid;
+  grid.load(lane);
   TargetState<R> st;
-  V m4;
-  int i = 0, il = 0;
+  V m4 = tin.m4;
+  const int i = tin.i, il = tin.il;
   // iii) working planes (warp 0, one target per lane)
   if (warp == 0) {
-    il = it.t0 + min(lane, nt - 1);
-    i = L.off + il;
-    const V ax4 = static_cast<const V *>(a.axis)[i];
-    m4 = static_cast<V *>(a.m)[i];
-    st = setup_plane<R>(ax4.x, ax4.y, ax4.z, m4.x, m4.y, m4.z, sm.h[0][lane], sm.h[1][lane],
-                        sm.h[2][lane] + static_cast<R>(bext));
+    st = setup_plane<R>(tin.ax4.x, tin.ax4.y, tin.ax4.z, m4.x, m4.y, m4.z, sm.h[0][lane],
+                        sm.h[1][lane], sm.h[2][lane] + static_cast<R>(bext));
     sm.k[lane] = static_cast<R>(L.k);
     sm.k2[lane] = R(2) * static_cast<R>(L.k);
     sm.bc[lane] = st.bmag * st.cphi;
@@ -436,7 +506,7 @@ __device__ __forceinline__ void block_update(
   }
   __syncthreads();
   // iv) scan: warps over targets, lanes over grid points
-  for (int t = warp; t < nt; t += nw) warp_scan<R>(sm, t, lane);
+  for (int t = warp; t < nt; t += nw) warp_scan<R>(sm, grid, t, lane);
   __syncthreads();
   // iv) Newton: one bracket per thread
   for (int x = threadIdx.x; x < 4 * nt; x += blockDim.x) {
@@ -447,11 +517,11 @@ __device__ __forceinline__ void block_update(
   if (warp != 0) return;
   // v-vii) decision and outputs (warp 0)
   const bool active = lane < nt;
-  const double u = kmc_uniform(a.seed, step, il, it.l);
+  const double u = tin.u;
   R s_new, c_new;
   // lanes past the last target repeat the last target (same state as st);
   // only targets < nt have scan results in shared memory
-  const Decision r = decide<R, MIXED>(sm, min(lane, nt - 1), st, a.beta[i], L.lognu0t,
+  const Decision r = decide<R, MIXED>(sm, min(lane, nt - 1), st, tin.beta, L.lognu0t,
                                       L.t_zero != 0, u, s_new, c_new);
   const R mx = fma(c_new, st.ax, s_new * st.ex);
   const R my = fma(c_new, st.ay, s_new * st.ey);
@@ -478,7 +548,7 @@ __device__ __forceinline__ void block_update(
       static_cast<dbl4 *>(a.src[par ^ 1])[i] = mu;
     }
     if (rec >= 0)
-      a.e_acc[i] += bext * (static_cast<double>(mz) - static_cast<double>(st.mz_old));
+      a.e_acc[i] = tin.eacc + bext * (static_cast<double>(mz) - static_cast<double>(st.mz_old));
     if (a.debug) {
       a.dbg.bdip[3 * i + 0] = static_cast<double>(sm.h[0][lane]);
       a.dbg.bdip[3 * i + 1] = static_cast<double>(sm.h[1][lane]);
@@ -492,7 +562,7 @@ __device__ __forceinline__ void block_update(
   }
   // loop record and counters: one atomic each per block
   if (rec >= 0) {
-    double c = active ? a.vfrac[i] * static_cast<double>(mz) : 0.0;
+    double c = active ? tin.vfrac * static_cast<double>(mz) : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if (lane == 0)
@@ -571,6 +641,8 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
   const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
 
   const float4 pi = static_cast<const float4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
+  TargetIn<float4> tin;
+  if (warp == 0) tin = load_target<float4>(a, L, it, step, lane);
   const f2 X = pk(pi.x, pi.x), Y = pk(pi.y, pi.y), Z = pk(pi.z, pi.z);
   float s6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, c6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int nrec = it.j1 - it.j0;
@@ -670,7 +742,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
     }
   }
   __syncthreads();
-  block_update<float4, true>(a, L, it, step, rec, sm);
+  block_update<float4, true>(a, L, it, step, rec, tin, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -692,6 +764,8 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
   const dbl4 *__restrict__ gmu = static_cast<const dbl4 *>(a.src[par]) + L.roff;
 
   const dbl4 pi = static_cast<const dbl4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
+  TargetIn<dbl4> tin;
+  if (warp == 0) tin = load_target<dbl4>(a, L, it, step, lane);
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const int nrec = it.j1 - it.j0;
   const int ntiles = (nrec + tile - 1) / tile;
@@ -758,7 +832,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
     for (int c = 0; c < 3; ++c) sm.h[c][lane] = 3.0 * tot[c] - tot[3 + c];
   }
   __syncthreads();
-  block_update<dbl4, false>(a, L, it, step, rec, sm);
+  block_update<dbl4, false>(a, L, it, step, rec, tin, sm);
 }
 
 // Ends a field period on the device: the next period starts S steps later.
