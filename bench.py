@@ -47,6 +47,24 @@ def fp32_peak_tflops():
     return SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+def max_over_ranks_of(x, world, device):
+    """The largest value of x over the ranks of the default process group
+    (the timed region of the slowest rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds_max, world):
+    """Whole-job throughput of independent replicas: every rank processes the
+    same units; the job takes as long as its slowest rank."""
+    return world * units_per_rank / seconds_max
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -171,6 +189,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison")
+    ap.add_argument("--shape", default="",
+                    help="pin the FP32 launch shape as warps,tile,chunk (default: autotuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -209,17 +229,15 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, world, "cuda")
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     # --- FP32-mixed, state resident in HBM ---------------------------------
     ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
     kmc.kmc_set_stream(ctx, stream.cuda_stream)
+    if args.shape:
+        kmc.kmc_tuning(ctx, *[int(x) for x in args.shape.split(",")])
     for _ in range(args.warmup):
         kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
                     run["seed"])
@@ -244,7 +262,7 @@ def main():
     kmc.kmc_sync(ctx)
     ms = [a.elapsed_time(b) for a, b in ev]
     t_total = max_over_ranks(sum(ms) / 1e3)
-    value = world * units_per_step * args.steps / t_total
+    value = job_throughput(units_per_step * args.steps, t_total, world)
     ms_per_step = 1e3 * t_total / args.steps
     sar32 = [kmc.kmc_read(ctx, kmc.KMC_READ_SAR, l)[0] for l in range(len(lyss))]
     launches_per_step = 1 + run["periods"] * (run["S"] + 1)
