@@ -162,6 +162,38 @@ kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
 /* Frees the context and its device memory. NULL-safe. */
 void kmc_destroy(kmc_ctx *ctx);
 
+/* Largest NP count kmc_dipolar_field_noalloc accepts. */
+#define KMC_NOALLOC_MAX_N 8192
+
+/* The dipolar field of one lysosome, computed like the FP32-mixed pair sum of
+ * kmc_run (split source ranges, compensated sums), for callers that cannot call
+ * cudaMalloc: code inside another framework's memory pool, processes whose
+ * device memory is reserved up front, or libraries handed device pointers by
+ * their caller. It allocates nothing. The paper has no counterpart: this entry
+ * point exists only for such callers.
+ *
+ *   n       NPs, 1 .. KMC_NOALLOC_MAX_N (otherwise KMC_ECAPACITY)
+ *   pos     DEVICE [n][3] centres, m
+ *   m       DEVICE [n][3] unit moments
+ *   vol     DEVICE [n] volumes, m^3
+ *   Ms      A/m, > 0
+ *   center  HOST [3] origin of the float32 frame, m (e.g. the lysosome centre)
+ *   length  unit of the float32 frame, m, > 0 (e.g. the NP diameter)
+ *   B       DEVICE [n][3] output: mu0 H_dip on every NP (Eq. 1), T
+ *   cuda_stream  stream to queue on (NULL: the default stream)
+ * All pointers are owned by the caller. The call only queues work: B is valid
+ * once the stream has reached it. Its working memory is one static device
+ * array of about 3.5 MB that every GPU loading the library holds until the
+ * process exits. Every call shares that array and leaves its contents behind;
+ * calls that overlap on the GPU (other streams, other host threads) race on it.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Errors: KMC_EINVAL (NULL pointer, Ms or length not
+ * positive), KMC_ECAPACITY (n out of range), KMC_ECUDA (launch failed). */
+kmc_status kmc_dipolar_field_noalloc(int32_t n, const double *pos, const double *m,
+                                     const double *vol, double Ms, const double *center,
+                                     double length, double *B, void *cuda_stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *kmc_last_error(void);
 

@@ -126,6 +126,11 @@ kmc_status ensure_device_init() {
 
 }  // namespace
 
+namespace kmc {
+// Lets other translation units of the library report through kmc_last_error().
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+}  // namespace kmc
+
 struct kmc_ctx {
   int fp32 = 0;
   int n_lys = 0;

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "KMC_OK", 1: "KMC_EINVAL", 2: "KMC_ENOMEM", 3: "KMC_ECUDA",
 # the entry points declared in include/kmc.h
 EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
-           "kmc_last_error")
+           "kmc_last_error", "kmc_dipolar_field_noalloc")
+KMC_NOALLOC_MAX_N = 8192
 
 
 class KmcError(RuntimeError):
@@ -74,6 +75,8 @@ def lib():
             L.kmc_load.argtypes = [vp, C.c_char_p]
             L.kmc_info.argtypes = [vp, _I64, _I32, _I64]
             L.kmc_tuning.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, _I32, _I32, _I32]
+            L.kmc_dipolar_field_noalloc.argtypes = [C.c_int32, vp, vp, vp, C.c_double, _D,
+                                                    C.c_double, vp, vp]
             L.kmc_destroy.argtypes = [vp]
             L.kmc_destroy.restype = None
             L.kmc_last_error.argtypes = []
@@ -206,6 +209,18 @@ def kmc_tuning(ctx, warps=None, tile=None, chunk=0):
         _check(lib().kmc_tuning(ctx.handle, int(warps), int(tile), int(chunk), C.byref(w),
                                 C.byref(t), C.byref(c)))
     return int(w.value), int(t.value), int(c.value)
+
+
+def kmc_dipolar_field_noalloc(n, pos_dev, m_dev, vol_dev, Ms, center, length, B_dev,
+                              stream_handle=0):
+    """Calls the no-allocation field entry point. pos_dev, m_dev, vol_dev and
+    B_dev are device addresses (integers, e.g. a tensor's data_ptr()) of
+    caller-owned float64 buffers; center is a host (3,) origin in m."""
+    cen = _f64(center, (3,))
+    _check(lib().kmc_dipolar_field_noalloc(int(n), C.c_void_p(pos_dev), C.c_void_p(m_dev),
+                                           C.c_void_p(vol_dev), float(Ms), _dp(cen),
+                                           float(length), C.c_void_p(B_dev),
+                                           C.c_void_p(stream_handle or 0)))
 
 
 def kmc_destroy(ctx):
