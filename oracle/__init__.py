@@ -95,7 +95,7 @@ def lib():
             L.kmc_oracle_run.argtypes = [C.POINTER(_Lys), C.c_int32, _D, C.c_double,
                                          C.c_double, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_uint64, C.c_int64, C.c_int32, _D, _D, _D,
-                                         _I64]
+                                         _D, _I64]
             L.kmc_oracle_run.restype = C.c_int32
             L.kmc_oracle_area.argtypes = [C.c_int32, _D, _D, C.c_int32]
             L.kmc_oracle_area.restype = C.c_double
@@ -104,6 +104,14 @@ def lib():
             L.kmc_oracle_mean_run.argtypes = [C.c_int32, _D, _D] + [C.c_double] * 6 + [
                 C.c_int32] * 3 + [_D]
             L.kmc_oracle_mean_run.restype = C.c_int32
+            L.kmc_oracle_local_concentration.argtypes = [C.c_int32, _D, _D, C.c_int32, _D]
+            L.kmc_oracle_local_concentration.restype = C.c_int32
+            L.kmc_oracle_local_concentration_at.argtypes = [C.c_int32, _D, _D, C.c_int32,
+                                                            C.c_int32, _I32, _D]
+            L.kmc_oracle_local_concentration_at.restype = C.c_int32
+            L.kmc_oracle_shell_profile.argtypes = [C.c_int32, _D, _D, _D, C.c_double,
+                                                   C.c_int32, C.c_int32, _D, _D, _D]
+            L.kmc_oracle_shell_profile.restype = C.c_double
             _lib = L
     return _lib
 
@@ -225,19 +233,20 @@ def initial_moments(axis):
 
 def run(lys, lys_index, mu0Hmax, f, S, periods, discard, seed, m=None, step0=0,
         nthreads=1):
-    """A whole kMC run of one lysosome; returns m, E_diss, loop_H, loop_M,
-    counters, area (J/m^3 per cycle) and sar (W/kg)."""
+    """A whole kMC run of one lysosome; returns m, E_diss, dHdip (Eq. 6, T),
+    loop_H, loop_M, counters, area (J/m^3 per cycle) and sar (W/kg)."""
     s, keep = _lys_struct(lys)
     n = s.n
     m = initial_moments(lys.axis) if m is None else _f64(m, (n, 3)).copy()
     nrec = max(0, S * (periods - discard))
     E = np.zeros(n)
+    dH = np.zeros(n)
     lH = np.zeros(max(nrec, 1))
     lM = np.zeros(max(nrec, 1))
     cnt = np.zeros(4, dtype=np.int64)
     rc = lib().kmc_oracle_run(C.byref(s), int(lys_index), _dp(m), float(mu0Hmax), float(f),
                               int(S), int(periods), int(discard), C.c_uint64(seed),
-                              C.c_int64(step0), int(nthreads), _dp(E), _dp(lH), _dp(lM),
+                              C.c_int64(step0), int(nthreads), _dp(E), _dp(dH), _dp(lH), _dp(lM),
                               cnt.ctypes.data_as(_I64))
     if rc != 0:
         raise RuntimeError("oracle run failed (%d)" % rc)
@@ -245,7 +254,7 @@ def run(lys, lys_index, mu0Hmax, f, S, periods, discard, seed, m=None, step0=0,
     area = lib().kmc_oracle_area(n, _dp(keep[2]), _dp(E), nper)
     rho = float(getattr(lys, "rho", 5200.0))
     del keep
-    return dict(m=m, E_diss=E, loop_H=lH[:nrec], loop_M=lM[:nrec],
+    return dict(m=m, E_diss=E, dHdip=dH, loop_H=lH[:nrec], loop_M=lM[:nrec],
                 counters=dict(flips=int(cnt[0]), near=int(cnt[1]), monostable=int(cnt[2]),
                               degenerate=int(cnt[3])),
                 area=float(area), sar=float(lib().kmc_oracle_sar(area, float(f), rho)))
@@ -275,3 +284,44 @@ def mean_run(axis, vol, Ms, Keff, T, tau0, mu0Hmax, f, S, periods, discard):
     if rc != 0:
         raise RuntimeError("oracle mean_run failed (%d)" % rc)
     return lM[:nrec]
+
+
+def local_concentration(pos, vol, N):
+    """Eq. 8: phi_N per NP from the distance to its N-th nearest neighbour."""
+    pos = _f64(pos, (-1, 3))
+    vol = _f64(vol, (-1,))
+    phi = np.zeros(len(vol))
+    rc = lib().kmc_oracle_local_concentration(len(vol), _dp(pos), _dp(vol), int(N), _dp(phi))
+    if rc != 0:
+        raise ValueError("oracle local_concentration failed (%d)" % rc)
+    return phi
+
+
+def local_concentration_at(pos, vol, N, idx):
+    """Eq. 8 at the listed NPs only."""
+    pos = _f64(pos, (-1, 3))
+    vol = _f64(vol, (-1,))
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    phi = np.zeros(len(idx))
+    rc = lib().kmc_oracle_local_concentration_at(len(vol), _dp(pos), _dp(vol), int(N), len(idx),
+                                                 idx.ctypes.data_as(_I32), _dp(phi))
+    if rc != 0:
+        raise ValueError("oracle local_concentration_at failed (%d)" % rc)
+    return phi
+
+
+def shell_profile(pos, vol, center, R, n_shells, values):
+    """Radial profile (Fig. 8): per shell the NP count and the volume-weighted
+    mean of each column of values ([n][n_val]); returns (count, mean, R used)."""
+    pos = _f64(pos, (-1, 3))
+    vol = _f64(vol, (-1,))
+    val = _f64(values, (len(vol), -1))
+    c = _f64(center, (3,))
+    count = np.zeros(int(n_shells))
+    mean = np.zeros((int(n_shells), val.shape[1]))
+    r = lib().kmc_oracle_shell_profile(len(vol), _dp(pos), _dp(vol), _dp(c), float(R),
+                                       int(n_shells), val.shape[1], _dp(val), _dp(count),
+                                       _dp(mean))
+    if r < 0:
+        raise ValueError("oracle shell_profile failed (%g)" % r)
+    return count, mean, float(r)

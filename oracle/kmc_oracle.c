@@ -47,6 +47,7 @@
 #endif
 
 #define TWO_PI 6.283185307179586476925286766559
+#define PI 3.14159265358979323846264338327950288
 #define ORACLE_MU0 (4.0e-7 * 3.14159265358979323846264338327950288)
 #define ORACLE_KB 1.380649e-23 /* J/K, exact in the 2019 SI */
 
@@ -358,7 +359,7 @@ int32_t kmc_oracle_step(const kmc_oracle_lysosome *lys, int32_t lys_index,
 int32_t kmc_oracle_run(const kmc_oracle_lysosome *lys, int32_t lys_index, double *m,
                        double mu0Hmax, double f, int32_t S, int32_t periods,
                        int32_t discard, uint64_t seed, int64_t step0, int32_t nthreads,
-                       double *E_diss, double *loop_H, double *loop_M,
+                       double *E_diss, double *dHdip, double *loop_H, double *loop_M,
                        int64_t *counters) {
   const int32_t n = lys->n;
   if (n < 0 || S <= 0 || periods < 0 || discard < 0 || f <= 0.0) return -3;
@@ -376,6 +377,13 @@ int32_t kmc_oracle_run(const kmc_oracle_lysosome *lys, int32_t lys_index, double
   for (int32_t i = 0; i < n; ++i) vsum += lys->vol[i];
   if (E_diss)
     for (int32_t i = 0; i < n; ++i) E_diss[i] = 0.0;
+  if (dHdip)
+    for (int32_t i = 0; i < n; ++i) dHdip[i] = 0.0;
+  /* Eq. 6 compares the dipolar field at the two extremes of the applied
+   * field: +mu0Hmax at step 0 of a period and -mu0Hmax at step S/2 (for odd
+   * S the first of the two most negative steps, (S-1)/2). */
+  const int32_t k_minus = S / 2;
+  int32_t n_rec_periods = 0;
   int64_t cnt[4] = {0, 0, 0, 0};
   int32_t rc = 0;
   int64_t rec = 0;
@@ -392,6 +400,14 @@ int32_t kmc_oracle_run(const kmc_oracle_lysosome *lys, int32_t lys_index, double
 #endif
       for (int32_t i = 0; i < n; ++i)
         dipolar_on(i, n, lys->pos, lys->vol, lys->Ms, m, &B[3 * i]);
+      /* Eq. 6: z component (the applied field's direction) of the dipolar
+       * field acting during the steps at +mu0Hmax and -mu0Hmax */
+      if (record && dHdip) {
+        if (k == 0)
+          for (int32_t i = 0; i < n; ++i) dHdip[i] += B[3 * i + 2];
+        if (k == k_minus)
+          for (int32_t i = 0; i < n; ++i) dHdip[i] -= B[3 * i + 2];
+      }
       /* iii)-vii) for every NP; all NPs see the start-of-step field */
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(nthreads) schedule(static)
@@ -427,7 +443,11 @@ int32_t kmc_oracle_run(const kmc_oracle_lysosome *lys, int32_t lys_index, double
         ++rec;
       }
     }
+    if (p >= discard) ++n_rec_periods;
   }
+  /* Eq. 6 averaged over the recorded periods */
+  if (dHdip && n_rec_periods > 0)
+    for (int32_t i = 0; i < n; ++i) dHdip[i] /= (double)n_rec_periods;
   if (counters) memcpy(counters, cnt, sizeof(cnt));
   free(B);
   free(mn);
@@ -447,6 +467,105 @@ double kmc_oracle_area(int32_t n, const double *vol, const double *E_diss,
 }
 
 double kmc_oracle_sar(double area, double f, double rho) { return area * f / rho; }
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 8 (Sec. III.5): local volume concentration around NP i from the
+ * distance r_N to its N-th nearest neighbour, phi_N = 3 N V / (4 pi r_N^3),
+ * V taken as the volume of NP i. Every distance is listed and sorted. */
+static int cmp_double(const void *a, const void *b) {
+  const double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+/* phi_N of NP i; d2 is scratch for n - 1 values */
+static double phi_of(int32_t i, int32_t n, const double *pos, const double *vol, int32_t N,
+                     double *d2) {
+  int32_t q = 0;
+  for (int32_t j = 0; j < n; ++j) {
+    if (j == i) continue;
+    const double dx = pos[3 * j + 0] - pos[3 * i + 0];
+    const double dy = pos[3 * j + 1] - pos[3 * i + 1];
+    const double dz = pos[3 * j + 2] - pos[3 * i + 2];
+    d2[q++] = (dx * dx + dy * dy) + dz * dz;
+  }
+  qsort(d2, (size_t)(n - 1), sizeof(double), cmp_double);
+  const double rN = sqrt(d2[N - 1]);
+  return (3.0 * (double)N * vol[i]) / (4.0 * PI * (rN * rN * rN));
+}
+
+int32_t kmc_oracle_local_concentration(int32_t n, const double *pos, const double *vol,
+                                       int32_t N, double *phi) {
+  if (n < 2 || N < 1 || N > n - 1) return -3;
+  double *d2 = (double *)malloc(sizeof(double) * (size_t)(n - 1));
+  if (!d2) return -2;
+  for (int32_t i = 0; i < n; ++i) phi[i] = phi_of(i, n, pos, vol, N, d2);
+  free(d2);
+  return 0;
+}
+
+int32_t kmc_oracle_local_concentration_at(int32_t n, const double *pos, const double *vol,
+                                          int32_t N, int32_t n_t, const int32_t *idx,
+                                          double *phi) {
+  if (n < 2 || N < 1 || N > n - 1 || n_t < 0) return -3;
+  for (int32_t t = 0; t < n_t; ++t)
+    if (idx[t] < 0 || idx[t] >= n) return -3;
+  double *d2 = (double *)malloc(sizeof(double) * (size_t)(n - 1));
+  if (!d2) return -2;
+  for (int32_t t = 0; t < n_t; ++t) phi[t] = phi_of(idx[t], n, pos, vol, N, d2);
+  free(d2);
+  return 0;
+}
+
+/* Radial profile (Sec. III.4, Fig. 8): NP i lies in shell
+ * s = floor(n_shells |r_i - c| / R), the last shell also taking |r_i - c| >= R.
+ * R <= 0 selects the radius of the smallest sphere about c that holds every
+ * NP whole, max_i (|r_i - c| + (3 V_i / 4 pi)^(1/3)). For each shell: count[s]
+ * NPs and, for each of the n_val per-NP columns of val ([n][n_val]), the
+ * volume-weighted mean sum V_i val_i / sum V_i in mean[s][n_val] (0 for an
+ * empty shell). Returns the radius used, or a negative value on bad input. */
+double kmc_oracle_shell_profile(int32_t n, const double *pos, const double *vol,
+                                const double center[3], double R, int32_t n_shells,
+                                int32_t n_val, const double *val, double *count,
+                                double *mean) {
+  if (n < 0 || n_shells < 1 || n_val < 0) return -1.0;
+  double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *vs = (double *)calloc((size_t)n_shells, sizeof(double));
+  if (!r || !vs) {
+    free(r);
+    free(vs);
+    return -2.0;
+  }
+  double Rmax = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    const double dx = pos[3 * i + 0] - center[0];
+    const double dy = pos[3 * i + 1] - center[1];
+    const double dz = pos[3 * i + 2] - center[2];
+    r[i] = sqrt((dx * dx + dy * dy) + dz * dz);
+    const double a = cbrt(3.0 * vol[i] / (4.0 * PI));
+    if (r[i] + a > Rmax) Rmax = r[i] + a;
+  }
+  if (R <= 0.0) R = Rmax;
+  for (int32_t s = 0; s < n_shells; ++s) {
+    count[s] = 0.0;
+    for (int32_t q = 0; q < n_val; ++q) mean[s * n_val + q] = 0.0;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t s = n_shells - 1;
+    if (R > 0.0) {
+      const double x = floor((double)n_shells * r[i] / R);
+      if (x < (double)(n_shells - 1)) s = (int32_t)x;
+    }
+    count[s] += 1.0;
+    vs[s] += vol[i];
+    for (int32_t q = 0; q < n_val; ++q) mean[s * n_val + q] += vol[i] * val[i * n_val + q];
+  }
+  for (int32_t s = 0; s < n_shells; ++s)
+    if (vs[s] > 0.0)
+      for (int32_t q = 0; q < n_val; ++q) mean[s * n_val + q] /= vs[s];
+  free(r);
+  free(vs);
+  return R;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Ref. [8] mode (Sec. II.3): probabilities instead of samples. The applied

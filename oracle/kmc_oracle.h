@@ -25,6 +25,11 @@
  *   per-NP split of the loop area (E_diss of one NP) .... parity unpinned:
  *                              only the lysosome total is fixed by the paper.
  *   mean_run (Ref. [8] mode) . pinned (two-state Boltzmann equilibrium)
+ *   run: dHdip (Eq. 6) ....... pinned (closed forms for a saturated pair,
+ *                              re-derivation from a stepped trajectory)
+ *   local_concentration ...... pinned (cubic lattices: neighbour shells in
+ *                              closed form)
+ *   shell_profile ............ pinned (hand-placed NPs with known shells)
  */
 #ifndef KMC_ORACLE_H
 #define KMC_ORACLE_H
@@ -110,13 +115,17 @@ int32_t kmc_oracle_step(const kmc_oracle_lysosome *lys, int32_t lys_index,
  *   E_diss [n]: sum over recorded steps of mu0 M_S V_i H_ext,k (m_z,new - m_z,old), J
  *   loop_H, loop_M [S*(periods-discard)]: mu0*H_ext,k (T) and the
  *   volume-weighted mean m_z after step k
+ *   dHdip [n]: Eq. 6 per NP, mu0 H_dip,z at the step of +mu0Hmax (step 0 of
+ *   a period) minus mu0 H_dip,z at the step of -mu0Hmax (step S/2; (S-1)/2
+ *   for odd S), both from the moments at the start of the step, averaged
+ *   over the recorded periods, T
  *   counters [4]: flips, near-threshold draws, monostable NP-steps,
  *   degenerate working planes.
  * nthreads > 1 runs the per-NP loops with OpenMP, as the paper did. */
 int32_t kmc_oracle_run(const kmc_oracle_lysosome *lys, int32_t lys_index, double *m,
                        double mu0Hmax, double f, int32_t S, int32_t periods,
                        int32_t discard, uint64_t seed, int64_t step0, int32_t nthreads,
-                       double *E_diss, double *loop_H, double *loop_M,
+                       double *E_diss, double *dHdip, double *loop_H, double *loop_M,
                        int64_t *counters);
 
 /* Hysteresis area A (J/m^3 per cycle) from the per-NP recorded energies, and
@@ -124,6 +133,27 @@ int32_t kmc_oracle_run(const kmc_oracle_lysosome *lys, int32_t lys_index, double
 double kmc_oracle_area(int32_t n, const double *vol, const double *E_diss,
                        int32_t n_periods);
 double kmc_oracle_sar(double area, double f, double rho);
+
+/* Eq. 8 (Sec. III.5): phi_N,i = 3 N V_i / (4 pi r_N^3) with r_N the distance
+ * from NP i to its N-th nearest neighbour. phi is [n]. Returns 0, or -3
+ * unless 1 <= N <= n - 1. */
+int32_t kmc_oracle_local_concentration(int32_t n, const double *pos, const double *vol,
+                                       int32_t N, double *phi);
+
+/* Eq. 8 at n_t listed NPs only (idx[t] in [0, n)); phi is [n_t]. */
+int32_t kmc_oracle_local_concentration_at(int32_t n, const double *pos, const double *vol,
+                                          int32_t N, int32_t n_t, const int32_t *idx,
+                                          double *phi);
+
+/* Radial profile (Sec. III.4, Fig. 8): n_shells shells of equal thickness
+ * R / n_shells about `center`; NP i goes to floor(n_shells |r_i - c| / R),
+ * clamped to the last shell. R <= 0 selects max_i (|r_i - c| + radius_i).
+ * count [n_shells]; mean [n_shells][n_val] = volume-weighted mean of each
+ * column of val [n][n_val] over the shell (0 if empty). Returns R used. */
+double kmc_oracle_shell_profile(int32_t n, const double *pos, const double *vol,
+                                const double center[3], double R, int32_t n_shells,
+                                int32_t n_val, const double *val, double *count,
+                                double *mean);
 
 /* The Ref. [8] program's mode used for validation (Sec. II.3): no sampling and
  * no interactions; each NP carries the probability of each well, moved with
