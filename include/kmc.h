@@ -88,9 +88,16 @@ enum {
   KMC_READ_AREA = 3,      /* [1] hysteresis area A, J/m^3 per cycle (Sec. III.2.a) */
   KMC_READ_SAR = 4,       /* [1] SAR = A f / rho, W/kg                             */
   KMC_READ_MOMENTS = 5,   /* [n][3] current unit moments                           */
-  KMC_READ_COUNTERS = 6   /* [4] over the last run: jumps, near-threshold draws
+  KMC_READ_COUNTERS = 6,  /* [4] over the last run: jumps, near-threshold draws
                              (|u - P| < 1e-9), NP-steps with one minimum, NP-steps
                              whose working plane needed the fallback               */
+  KMC_READ_DHDIP = 7      /* [n] Eq. 6 per NP, T: the dipolar field along z (the
+                             applied field's direction) during the step at
+                             +mu0 H_max (step 0 of a period) minus that during the
+                             step at -mu0 H_max (step S/2, (S-1)/2 for odd S), each
+                             from the moments at the start of the step, averaged
+                             over the recorded periods; > 0 where the dipolar
+                             field is parallel to the applied one (Sec. III.2.b) */
 };
 
 /* Creates a context holding n_lys lysosomes (copied to the device). Moments
@@ -158,6 +165,50 @@ kmc_status kmc_info(const kmc_ctx *ctx, int64_t *n_total, int32_t *n_lys,
  * may be NULL); call with warps = tile = chunk = -1 to only read it. */
 kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
                       int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out);
+
+/* Largest neighbour rank of kmc_local_concentration (the paper uses 20). */
+#define KMC_PHI_MAX_N 64
+
+/* Eq. 8 (Sec. III.5): the local volume concentration around each NP of
+ * lysosome `lys`, phi_N,i = 3 N V_i / (4 pi r_N^3) with r_N the distance from
+ * NP i to its N-th nearest neighbour in the lysosome. Computed on the device
+ * over all pairs in FP64; 1 <= N <= min(n - 1, KMC_PHI_MAX_N), else
+ * KMC_EINVAL. Writes phi[n] (host buffer of capacity cap; KMC_ECAPACITY and
+ * *written = n if too small). Synchronises the context's stream. */
+kmc_status kmc_local_concentration(kmc_ctx *ctx, int32_t lys, int32_t N, double *phi,
+                                   int64_t cap, int64_t *written);
+
+/* Radial profile of the last run (Sec. III.4, Fig. 8): the NPs of lysosome
+ * `lys` binned into n_shells shells of equal thickness R / n_shells about the
+ * lysosome's frame origin (kmc_lysosome.center, else the centroid of pos). NP
+ * i, at distance r_i from it, goes to shell floor(n_shells r_i / R), the last
+ * shell also taking r_i >= R. radius > 0 sets R; radius <= 0 takes the
+ * smallest sphere about the origin holding every NP whole,
+ * R = max_i (r_i + (3 V_i / 4 pi)^(1/3)). out [n_shells][4] (host, capacity
+ * cap): NP count, then volume-weighted means sum V_i x_i / sum V_i over the
+ * shell of x = the NP's hysteresis area (J/m^3 per cycle, KMC_READ_NP_ENERGY
+ * over V_i), its Delta_Hdip (T, KMC_READ_DHDIP) and its phi_N (Eq. 8; 0 when
+ * N = 0); 0 for an empty shell. *radius_used (may be NULL) receives R.
+ * KMC_ESTATE before the first kmc_run. */
+kmc_status kmc_shell_profile(kmc_ctx *ctx, int32_t lys, double radius, int32_t n_shells,
+                             int32_t N, double *out, int64_t cap, int64_t *written,
+                             double *radius_used);
+
+/* The Ref. [8] program's mode (Sec. II.3) on the device, for non-interacting
+ * NPs: no sampling and no dipolar field. Each NP carries the probability of
+ * each energy well; when the applied field (along z) moves the wells, the
+ * probability of an old well goes to the new minimum whose basin contains it,
+ * and Eqs. 3-5 relax the two occupations towards equilibrium over each step.
+ * Arguments as kmc_create (positions are not used) and kmc_run, without a
+ * seed; runs in FP64 on the device, one thread per NP. Writes the
+ * volume-weighted mean m_z after each recorded step of every lysosome,
+ * loop_M [n_lys][S * (periods - discard)] (host buffer of capacity cap;
+ * KMC_ECAPACITY and *written = the size needed if too small). Starts from
+ * m = +-easy axis with m_z >= 0, like kmc_create. Synchronous. */
+kmc_status kmc_mean_run(const kmc_lysosome *lys, int32_t n_lys, const double *mu0Hmax,
+                        int32_t n_amp, double f, int32_t steps_per_period, int32_t periods,
+                        int32_t discard_periods, double *loop_M, int64_t cap,
+                        int64_t *written);
 
 /* Frees the context and its device memory. NULL-safe. */
 void kmc_destroy(kmc_ctx *ctx);

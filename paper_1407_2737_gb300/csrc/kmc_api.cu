@@ -17,6 +17,7 @@
 
 #include "kmc.h"
 #include "kmc_launch.h"
+#include "kmc_local.h"
 
 using kmc::dbl4;
 using kmc::Item;
@@ -146,6 +147,12 @@ struct kmc_ctx {
   void *d_pos = nullptr, *d_axis = nullptr, *d_m = nullptr, *d_src[2] = {nullptr, nullptr};
   int *d_slot = nullptr;  // FP32: record * 2 + half of each NP
   double *d_beta = nullptr, *d_vfrac = nullptr, *d_eacc = nullptr;
+  double *d_dh = nullptr;     // [N] Eq. 6 accumulator (reduced field)
+  void *d_pos64 = nullptr;    // FP32 contexts: [N] dbl4 positions in FP64 (x, y, z, w)
+  double *d_phi = nullptr;    // [max n] scratch of kmc_local_concentration
+  std::vector<double> len;    // [n_lys] length unit L, m
+  std::vector<double> ctr;    // [n_lys][3] frame origin, m
+  std::vector<double> pos_si; // [N][3] positions as given, m
   long long *d_loop = nullptr;  // fixed point, units of 2^-62
   unsigned long long *d_cnt = nullptr;
   int32_t *d_err = nullptr;
@@ -159,7 +166,7 @@ struct kmc_ctx {
   size_t partial_cap = 0;  // items
   int32_t *d_arrivals = nullptr;
   size_t arrivals_cap = 0;
-  int items_chunk = -1;
+  Shape items_shape;  // shape the items were built for
   // debug outputs, allocated on first use
   double *d_dbg = nullptr;
   int32_t *d_dbg_flags = nullptr;
@@ -195,43 +202,85 @@ void drop_graph(kmc_ctx *c) {
   c->gexec = nullptr;
 }
 
-// Work items for source chunk `chunk` (0 = one item per 32 targets), largest
-// lysosomes first; the items of a target group are consecutive.
-std::vector<Item> build_items(const kmc_ctx *c, int chunk, int *n_groups) {
+// Work items for source chunk `chunk`, largest lysosomes first; the items of
+// a target group are consecutive.
+//
+// chunk = 0: one item per group of 32 targets. When the groups fit in one
+// wave (at most blocks_per_sm per SM) but do not fill the SMs evenly
+// (G = q P + r groups on P SMs), the r smallest groups are split into s parts
+// each and placed last, so that the blocks, which start in order, give every
+// SM q whole groups plus at most one part: the busiest SM then carries
+// q + 1/s group-loads instead of q + 1.
+std::vector<Item> build_items(const kmc_ctx *c, int chunk, int blocks_per_sm, int n_sms,
+                              int *n_groups) {
   std::vector<int> order(c->n_lys);
   for (int l = 0; l < c->n_lys; ++l) order[l] = l;
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return c->n[x] > c->n[y]; });
-  std::vector<Item> items;
-  int gid = 0;
+  struct Group {
+    int l, t0, nt, nrec;
+  };
+  std::vector<Group> groups;
   for (int l : order) {
     const int n = c->n[l];
     const int nrec = c->fp32 ? (n + 1) / 2 : n;
-    const int rchunk = chunk > 0 ? (c->fp32 ? chunk / 2 : chunk) : nrec;
-    const int S = std::max(1, (nrec + rchunk - 1) / rchunk);
-    for (int t0 = 0; t0 < n; t0 += kmc::kTargets, ++gid) {
-      for (int s = 0; s < S; ++s) {
-        Item it;
-        it.l = l;
-        it.t0 = t0;
-        it.nt = std::min(kmc::kTargets, n - t0);
-        it.gid = gid;
-        it.j0 = static_cast<int>(static_cast<long long>(s) * nrec / S);
-        it.j1 = static_cast<int>(static_cast<long long>(s + 1) * nrec / S);
-        it.split = s;
-        it.nsplit = S;
-        items.push_back(it);
+    for (int t0 = 0; t0 < n; t0 += kmc::kTargets)
+      groups.push_back({l, t0, std::min(kmc::kTargets, n - t0), nrec});
+  }
+  const int G = static_cast<int>(groups.size());
+  std::vector<int> parts(G, 1);
+  if (chunk > 0) {
+    for (int g = 0; g < G; ++g) {
+      const int rchunk = c->fp32 ? chunk / 2 : chunk;
+      parts[g] = std::max(1, (groups[g].nrec + rchunk - 1) / rchunk);
+    }
+  } else if (n_sms > 0 && G >= n_sms) {
+    const int q = G / n_sms, r = G % n_sms;
+    int best_s = 1;
+    double best = 1.0;  // extra load of the busiest SM without splitting
+    for (int s = 2; s <= 8 && r > 0; ++s) {
+      const int per_sm = (r * s + n_sms - 1) / n_sms;
+      if (q + per_sm > blocks_per_sm) break;
+      const double load = static_cast<double>(per_sm) / s;
+      if (load < best - 1e-9) {
+        best = load;
+        best_s = s;
       }
     }
+    for (int g = G - r; g < G && best_s > 1; ++g)
+      parts[g] = std::min(best_s, std::max(1, groups[g].nrec));
   }
-  *n_groups = gid;
+  std::vector<Item> items;
+  for (int g = 0; g < G; ++g) {
+    const Group &gr = groups[g];
+    const int S = parts[g];
+    for (int s = 0; s < S; ++s) {
+      Item it;
+      it.l = gr.l;
+      it.t0 = gr.t0;
+      it.nt = gr.nt;
+      it.gid = g;
+      it.j0 = static_cast<int>(static_cast<long long>(s) * gr.nrec / S);
+      it.j1 = static_cast<int>(static_cast<long long>(s + 1) * gr.nrec / S);
+      it.split = s;
+      it.nsplit = S;
+      items.push_back(it);
+    }
+  }
+  *n_groups = G;
   return items;
 }
 
-kmc_status set_items(kmc_ctx *c, int chunk) {
-  if (c->items_chunk == chunk && c->d_items) return KMC_OK;
+kmc_status set_items(kmc_ctx *c, const Shape &sh) {
+  if (c->items_shape.warps == sh.warps && c->items_shape.tile == sh.tile &&
+      c->items_shape.chunk == sh.chunk && c->d_items)
+    return KMC_OK;
+  int dev = 0, n_sms = 0, per_sm = 0;
+  KMC_CUDA(cudaGetDevice(&dev));
+  KMC_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+  KMC_CUDA(kmc::step_blocks_per_sm(c->fp32, sh.warps, sh.tile, &per_sm));
   int groups = 0;
-  const std::vector<Item> items = build_items(c, chunk, &groups);
+  const std::vector<Item> items = build_items(c, sh.chunk, per_sm, n_sms, &groups);
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   if (items.size() > c->items_cap) {
     if (c->d_items) cudaFree(c->d_items);
@@ -258,7 +307,7 @@ kmc_status set_items(kmc_ctx *c, int chunk) {
                       cudaMemcpyHostToDevice));
   KMC_CUDA(cudaMemset(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap));
   c->n_items = static_cast<int>(items.size());
-  c->items_chunk = chunk;
+  c->items_shape = sh;
   return KMC_OK;
 }
 
@@ -276,6 +325,7 @@ StepArgs base_args(kmc_ctx *c) {
   a.beta = c->d_beta;
   a.vfrac = c->d_vfrac;
   a.e_acc = c->d_eacc;
+  a.dh_acc = c->d_dh;
   a.loop_m = c->d_loop;
   a.counters = c->d_cnt;
   a.err = c->d_err;
@@ -335,7 +385,7 @@ bool shape_ok(const kmc_ctx *c, const Shape &s) {
 // Times one candidate shape on the current state (restored by the caller).
 // Returns milliseconds per step, or a negative value on error.
 float time_shape(kmc_ctx *c, const Shape &s) {
-  if (set_items(c, s.chunk) != KMC_OK) return -1.f;
+  if (set_items(c, s) != KMC_OK) return -1.f;
   StepArgs a = base_args(c);
   a.cos_k = 1.0;
   a.S = 1;
@@ -349,11 +399,13 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   float ms = -1.f;
   bool ok = true;
   for (int r = 0; r < 2 && ok; ++r)
-    ok = kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream) == cudaSuccess;
+    ok = kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true) ==
+         cudaSuccess;
   const int reps = 5;
   if (ok) ok = cudaEventRecord(e0, c->stream) == cudaSuccess;
   for (int r = 0; r < reps && ok; ++r)
-    ok = kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream) == cudaSuccess;
+    ok = kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true) ==
+         cudaSuccess;
   if (ok) ok = cudaEventRecord(e1, c->stream) == cudaSuccess;
   if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
   if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms /= reps;
@@ -371,7 +423,7 @@ kmc_status autotune(kmc_ctx *c) {
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       c->shape = it->second;
-      return set_items(c, c->shape.chunk);
+      return set_items(c, c->shape);
     }
   }
   // the timed launches advance a scratch copy of the state: save the moments
@@ -426,12 +478,12 @@ kmc_status autotune(kmc_ctx *c) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = bs;
   }
-  return set_items(c, bs.chunk);
+  return set_items(c, bs);
 }
 
 kmc_status ensure_shape(kmc_ctx *c) {
   if (c->shape.warps == 0) return autotune(c);
-  return set_items(c, c->shape.chunk);
+  return set_items(c, c->shape);
 }
 
 void free_ctx(kmc_ctx *c) {
@@ -439,6 +491,7 @@ void free_ctx(kmc_ctx *c) {
   drop_graph(c);
   void *ptrs[] = {c->d_lys,   c->d_pos,    c->d_axis,    c->d_m,        c->d_src[0],
                   c->d_src[1], c->d_slot,  c->d_beta,    c->d_vfrac,    c->d_eacc,
+                  c->d_dh,    c->d_pos64,  c->d_phi,
                   c->d_loop,  c->d_cnt,    c->d_err,     c->d_rs,       c->d_items,
                   c->d_partial, c->d_arrivals, c->d_dbg, c->d_dbg_flags};
   for (void *p : ptrs)
@@ -452,7 +505,8 @@ kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_p
                                const std::vector<unsigned char> &h_m,
                                const std::vector<unsigned char> &h_src,
                                const std::vector<int> &h_slot, const std::vector<double> &h_beta,
-                               const std::vector<double> &h_vfrac) {
+                               const std::vector<double> &h_vfrac,
+                               const std::vector<dbl4> &h_pos64) {
   const long long N = c->N;
   KMC_CUDA(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
   c->stream = c->own_stream;
@@ -467,6 +521,8 @@ kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_p
   KMC_TRY(dalloc(&c->d_beta, sizeof(double) * N));
   KMC_TRY(dalloc(&c->d_vfrac, sizeof(double) * N));
   KMC_TRY(dalloc(&c->d_eacc, sizeof(double) * N));
+  KMC_TRY(dalloc(&c->d_dh, sizeof(double) * N));
+  if (c->fp32) KMC_TRY(dalloc(&c->d_pos64, sizeof(dbl4) * N));
   KMC_TRY(dalloc(&c->d_cnt, sizeof(unsigned long long) * 4 * c->n_lys));
   KMC_TRY(dalloc(&c->d_err, sizeof(int32_t)));
   KMC_TRY(dalloc(&c->d_rs, sizeof(RunState)));
@@ -480,6 +536,9 @@ kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_p
   KMC_CUDA(cudaMemcpy(c->d_beta, h_beta.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
   KMC_CUDA(cudaMemcpy(c->d_vfrac, h_vfrac.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
   KMC_CUDA(cudaMemset(c->d_eacc, 0, sizeof(double) * N));
+  KMC_CUDA(cudaMemset(c->d_dh, 0, sizeof(double) * N));
+  if (c->fp32)
+    KMC_CUDA(cudaMemcpy(c->d_pos64, h_pos64.data(), sizeof(dbl4) * N, cudaMemcpyHostToDevice));
   KMC_CUDA(cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * 4 * c->n_lys));
   KMC_CUDA(cudaMemset(c->d_err, 0, sizeof(int32_t)));
   KMC_CUDA(cudaMemcpy(c->d_lys, c->h_lys.data(), sizeof(LysDev) * c->n_lys,
@@ -487,21 +546,8 @@ kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_p
   return KMC_OK;
 }
 
-}  // namespace
-
-// ===========================================================================
-extern "C" {
-
-const char *kmc_last_error(void) { return g_last_error.c_str(); }
-
-kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec,
-                      kmc_ctx **out) {
-  g_last_error.clear();
-  if (!out) return fail(KMC_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!lys || n_lys < 1) return fail(KMC_EINVAL, "need at least one lysosome");
-  if (prec != KMC_FP64_PLAIN && prec != KMC_FP32_MIXED)
-    return fail(KMC_EINVAL, "unknown precision %d", static_cast<int>(prec));
+// Checks the lysosome descriptions of kmc_create and kmc_mean_run; *N = NPs.
+kmc_status validate_lysosomes(const kmc_lysosome *lys, int32_t n_lys, long long *N_out) {
   long long N = 0;
   for (int l = 0; l < n_lys; ++l) {
     const kmc_lysosome &L = lys[l];
@@ -525,6 +571,27 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
     N += L.n;
     if (N > (1ll << 30)) return fail(KMC_EINVAL, "too many NPs");
   }
+  *N_out = N;
+  return KMC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *kmc_last_error(void) { return g_last_error.c_str(); }
+
+kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec,
+                      kmc_ctx **out) {
+  g_last_error.clear();
+  if (!out) return fail(KMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!lys || n_lys < 1) return fail(KMC_EINVAL, "need at least one lysosome");
+  if (prec != KMC_FP64_PLAIN && prec != KMC_FP32_MIXED)
+    return fail(KMC_EINVAL, "unknown precision %d", static_cast<int>(prec));
+  long long N = 0;
+  KMC_TRY(validate_lysosomes(lys, n_lys, &N));
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
@@ -545,7 +612,9 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
   std::vector<unsigned char> h_src((c->fp32 ? sizeof(SrcPair) : sizeof(dbl4)) * nrec);
   std::vector<int> h_slot(c->fp32 ? N : 0);
   std::vector<double> h_beta(N), h_vfrac(N);
+  std::vector<dbl4> h_pos64(c->fp32 ? N : 0);
   c->vol.resize(N);
+  c->pos_si.resize(3 * N);
   c->h_lys.resize(n_lys);
   SrcPair *src32 = reinterpret_cast<SrcPair *>(h_src.data());
   dbl4 *src64 = reinterpret_cast<dbl4 *>(h_src.data());
@@ -578,6 +647,10 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
     }
     c->vsum.push_back(vs);
     const double len = std::cbrt(6.0 * (vs / L.n) / kPi);  // diameter of the mean volume
+    c->len.push_back(len);
+    c->ctr.push_back(cx);
+    c->ctr.push_back(cy);
+    c->ctr.push_back(cz);
     const double w_scale = 1.0 / (4.0 * kPi * len * len * len);
     LysDev &D = c->h_lys[l];
     D.off = static_cast<int>(o);
@@ -601,6 +674,8 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
       const double x = (p[0] - cx) / len, y = (p[1] - cy) / len, z = (p[2] - cz) / len;
       const double w = L.vol[i] * w_scale;
       c->vol[o] = L.vol[i];
+      for (int q = 0; q < 3; ++q) c->pos_si[3 * o + q] = p[q];
+      if (c->fp32) h_pos64[o] = make4<dbl4>(x, y, z, w);
       h_beta[o] = L.T > 0 ? kMu0 * L.Ms * L.Ms * L.vol[i] / (kKB * L.T) : 0.0;
       h_vfrac[o] = L.vol[i] / vs;
       if (c->fp32) {
@@ -628,7 +703,8 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
     }
     r += c->fp32 ? (L.n + 1) / 2 : L.n;
   }
-  const kmc_status st = create_device_state(c, h_pos, h_axis, h_m, h_src, h_slot, h_beta, h_vfrac);
+  const kmc_status st =
+      create_device_state(c, h_pos, h_axis, h_m, h_src, h_slot, h_beta, h_vfrac, h_pos64);
   if (st != KMC_OK) {
     free_ctx(c);
     return st;
@@ -703,6 +779,7 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
   }
   KMC_CUDA(cudaMemsetAsync(c->d_loop, 0, sizeof(long long) * need, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_eacc, 0, sizeof(double) * c->N, c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_dh, 0, sizeof(double) * c->N, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long) * 4 * c->n_lys, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
@@ -726,7 +803,7 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
     for (int k = 0; k < S && ce == cudaSuccess; ++k) {
       a.k_local = k;
       a.cos_k = std::cos(2.0 * kPi * k / S);
-      ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, a, c->n_items, c->stream);
+      ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, a, c->n_items, c->stream, true);
     }
     if (ce == cudaSuccess) ce = kmc::launch_advance(c->d_rs, S, c->stream);
     const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
@@ -776,7 +853,8 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
   switch (what) {
     case KMC_READ_LOOP_H:
     case KMC_READ_LOOP_M: need = c->n_rec; break;
-    case KMC_READ_NP_ENERGY: need = n; break;
+    case KMC_READ_NP_ENERGY:
+    case KMC_READ_DHDIP: need = n; break;
     case KMC_READ_AREA:
     case KMC_READ_SAR: need = 1; break;
     case KMC_READ_MOMENTS: need = 3ll * n; break;
@@ -839,6 +917,13 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
           buf[3 * i + 2] = v.z;
         }
       }
+      break;
+    }
+    case KMC_READ_DHDIP: {
+      std::vector<double> d(n);
+      KMC_CUDA(cudaMemcpy(d.data(), c->d_dh + o, sizeof(double) * n, cudaMemcpyDeviceToHost));
+      const double unit = kMu0 * c->Ms[lys];  // tesla per unit of reduced field
+      for (int i = 0; i < n; ++i) buf[i] = nper > 0 ? unit * d[i] / nper : 0.0;
       break;
     }
     case KMC_READ_COUNTERS: {
@@ -988,6 +1073,202 @@ kmc_status kmc_load(kmc_ctx *c, const char *path) {
   KMC_CUDA(cudaMemcpy(c->d_m, raw.data(), raw.size(), cudaMemcpyHostToDevice));
   c->step_global = hdr2[1];
   c->have_run = false;
+  return KMC_OK;
+}
+
+kmc_status kmc_local_concentration(kmc_ctx *c, int32_t lys, int32_t N, double *phi, int64_t cap,
+                                   int64_t *written) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (written) *written = 0;
+  if (lys < 0 || lys >= c->n_lys) return fail(KMC_EINVAL, "lysosome %d out of range", lys);
+  const int n = c->n[lys];
+  if (N < 1 || N > n - 1 || N > kmc::kPhiMaxN)
+    return fail(KMC_EINVAL, "neighbour rank N = %d outside 1..min(n - 1 = %d, %d)", N, n - 1,
+                kmc::kPhiMaxN);
+  if (cap < 0 || (cap > 0 && !phi)) return fail(KMC_EINVAL, "bad output buffer");
+  if (written) *written = n;
+  if (cap < n) return fail(KMC_ECAPACITY, "output needs %d elements", n);
+  KMC_TRY(check_device_error(c));
+  if (!c->d_phi) {
+    int max_n = 0;
+    for (int x : c->n) max_n = std::max(max_n, x);
+    KMC_TRY(dalloc(&c->d_phi, sizeof(double) * max_n));
+  }
+  const dbl4 *pos = static_cast<const dbl4 *>(c->fp32 ? c->d_pos64 : c->d_pos) + c->off[lys];
+  KMC_CUDA(kmc::launch_local_concentration(pos, n, N, c->d_phi, c->stream));
+  KMC_CUDA(cudaMemcpyAsync(phi, c->d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  return KMC_OK;
+}
+
+kmc_status kmc_shell_profile(kmc_ctx *c, int32_t lys, double radius, int32_t n_shells, int32_t N,
+                             double *out, int64_t cap, int64_t *written, double *radius_used) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (written) *written = 0;
+  if (lys < 0 || lys >= c->n_lys) return fail(KMC_EINVAL, "lysosome %d out of range", lys);
+  if (n_shells < 1 || !is_finite(radius)) return fail(KMC_EINVAL, "need n_shells >= 1, finite radius");
+  if (cap < 0 || (cap > 0 && !out)) return fail(KMC_EINVAL, "bad output buffer");
+  if (!c->have_run) return fail(KMC_ESTATE, "no run has been made on this context");
+  const int n = c->n[lys], o = c->off[lys];
+  const int64_t need = 4ll * n_shells;
+  if (written) *written = need;
+  if (cap < need) return fail(KMC_ECAPACITY, "output needs %lld elements", (long long)need);
+  std::vector<double> area(n), dh(n), phi(n, 0.0);
+  int64_t got = 0;
+  KMC_TRY(kmc_read(c, KMC_READ_NP_ENERGY, lys, area.data(), n, &got));
+  KMC_TRY(kmc_read(c, KMC_READ_DHDIP, lys, dh.data(), n, &got));
+  if (N > 0) KMC_TRY(kmc_local_concentration(c, lys, N, phi.data(), n, &got));
+  // per-NP area (J/m^3 per cycle) from the energy per period
+  for (int i = 0; i < n; ++i) area[i] /= c->vol[o + i];
+  // radii about the frame origin, in the order of operations of the definition
+  const double *ctr = &c->ctr[3 * lys];
+  std::vector<double> r(n);
+  double rmax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double *p = &c->pos_si[3 * (o + i)];
+    const double dx = p[0] - ctr[0], dy = p[1] - ctr[1], dz = p[2] - ctr[2];
+    const double sq = dx * dx + dy * dy;
+    r[i] = std::sqrt(sq + dz * dz);
+    const double a = std::cbrt(3.0 * c->vol[o + i] / (4.0 * kPi));
+    rmax = std::max(rmax, r[i] + a);
+  }
+  const double R = radius > 0.0 ? radius : rmax;
+  std::vector<double> vs(n_shells, 0.0);
+  for (int64_t q = 0; q < need; ++q) out[q] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    int sh = n_shells - 1;
+    if (R > 0.0) {
+      const double x = std::floor(static_cast<double>(n_shells) * r[i] / R);
+      if (x < static_cast<double>(n_shells - 1)) sh = static_cast<int>(x);
+    }
+    const double V = c->vol[o + i];
+    double *row = out + 4 * sh;
+    row[0] += 1.0;
+    row[1] += V * area[i];
+    row[2] += V * dh[i];
+    row[3] += V * phi[i];
+    vs[sh] += V;
+  }
+  for (int sh = 0; sh < n_shells; ++sh)
+    if (vs[sh] > 0.0)
+      for (int q = 1; q < 4; ++q) out[4 * sh + q] /= vs[sh];
+  if (radius_used) *radius_used = R;
+  return KMC_OK;
+}
+
+kmc_status kmc_mean_run(const kmc_lysosome *lys, int32_t n_lys, const double *mu0Hmax,
+                        int32_t n_amp, double f, int32_t S, int32_t periods, int32_t discard,
+                        double *loop_M, int64_t cap, int64_t *written) {
+  g_last_error.clear();
+  if (written) *written = 0;
+  if (!lys || n_lys < 1) return fail(KMC_EINVAL, "need at least one lysosome");
+  long long N = 0;
+  KMC_TRY(validate_lysosomes(lys, n_lys, &N));
+  if (!mu0Hmax || (n_amp != 1 && n_amp != n_lys))
+    return fail(KMC_EINVAL, "need 1 or n_lys = %d amplitudes", n_lys);
+  for (int q = 0; q < n_amp; ++q)
+    if (!is_finite(mu0Hmax[q])) return fail(KMC_EINVAL, "non-finite field amplitude");
+  if (!(f > 0) || !is_finite(f)) return fail(KMC_EINVAL, "f must be > 0");
+  if (S < 1) return fail(KMC_EINVAL, "steps_per_period must be >= 1");
+  if (periods < 0 || discard < 0 || discard > periods)
+    return fail(KMC_EINVAL, "need 0 <= discard_periods <= periods");
+  const long long n_rec = static_cast<long long>(S) * (periods - discard);
+  if (n_rec > (1ll << 28)) return fail(KMC_EINVAL, "too many recorded steps");
+  if (cap < 0 || (cap > 0 && !loop_M)) return fail(KMC_EINVAL, "bad output buffer");
+  const long long need = n_rec * n_lys;
+  if (written) *written = need;
+  if (cap < need) return fail(KMC_ECAPACITY, "output needs %lld elements", need);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(KMC_ECUDA, "no CUDA device available");
+  }
+  KMC_TRY(ensure_device_init());
+  const double t_step = 1.0 / (f * S);
+  std::vector<kmc::MeanLysDev> hl(n_lys);
+  std::vector<kmc::MeanItem> items;
+  std::vector<dbl4> axis(N);
+  std::vector<double> beta(N), vfrac(N), cosk(S);
+  for (int k = 0; k < S; ++k) cosk[k] = std::cos(2.0 * kPi * k / S);
+  long long o = 0;
+  for (int l = 0; l < n_lys; ++l) {
+    const kmc_lysosome &L = lys[l];
+    double vs = 0.0;
+    for (int i = 0; i < L.n; ++i) vs += L.vol[i];
+    kmc::MeanLysDev &D = hl[l];
+    D.off = static_cast<int>(o);
+    D.n = L.n;
+    D.t_zero = L.T == 0.0;
+    D.pad = 0;
+    D.k = L.Keff / (kMu0 * L.Ms * L.Ms);
+    D.bmax = mu0Hmax[n_amp == 1 ? 0 : l] / (kMu0 * L.Ms);
+    D.lognu0t = std::log(t_step / L.tau0);
+    for (int t0 = 0; t0 < L.n; t0 += kmc::kTargets)
+      items.push_back({l, t0, std::min(kmc::kTargets, L.n - t0), 0});
+    for (int i = 0; i < L.n; ++i, ++o) {
+      const double *a = &L.axis[3 * i];
+      const double an = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      axis[o] = make4<dbl4>(a[0] / an, a[1] / an, a[2] / an, 0.0);
+      beta[o] = L.T > 0 ? kMu0 * L.Ms * L.Ms * L.vol[i] / (kKB * L.T) : 0.0;
+      vfrac[o] = L.vol[i] / vs;
+    }
+  }
+  // device copies, freed on every path out
+  struct Buffers {
+    void *p[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t st = nullptr;
+    ~Buffers() {
+      if (st) cudaStreamSynchronize(st);
+      for (void *q : p)
+        if (q) cudaFree(q);
+      if (st) cudaStreamDestroy(st);
+    }
+  } b;
+  KMC_CUDA(cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking));
+  const size_t nl = static_cast<size_t>(std::max(need, 1ll));
+  KMC_TRY(dalloc(reinterpret_cast<kmc::MeanLysDev **>(&b.p[0]), sizeof(kmc::MeanLysDev) * n_lys));
+  KMC_TRY(dalloc(reinterpret_cast<kmc::MeanItem **>(&b.p[1]), sizeof(kmc::MeanItem) * items.size()));
+  KMC_TRY(dalloc(reinterpret_cast<dbl4 **>(&b.p[2]), sizeof(dbl4) * N));
+  KMC_TRY(dalloc(reinterpret_cast<double **>(&b.p[3]), sizeof(double) * 2 * N));
+  KMC_TRY(dalloc(reinterpret_cast<double **>(&b.p[4]), sizeof(double) * S));
+  KMC_TRY(dalloc(reinterpret_cast<long long **>(&b.p[5]), sizeof(long long) * nl));
+  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&b.p[6]), sizeof(int32_t)));
+  double *d_bv = static_cast<double *>(b.p[3]);
+  KMC_CUDA(cudaMemcpyAsync(b.p[0], hl.data(), sizeof(kmc::MeanLysDev) * n_lys,
+                           cudaMemcpyHostToDevice, b.st));
+  KMC_CUDA(cudaMemcpyAsync(b.p[1], items.data(), sizeof(kmc::MeanItem) * items.size(),
+                           cudaMemcpyHostToDevice, b.st));
+  KMC_CUDA(cudaMemcpyAsync(b.p[2], axis.data(), sizeof(dbl4) * N, cudaMemcpyHostToDevice, b.st));
+  KMC_CUDA(cudaMemcpyAsync(d_bv, beta.data(), sizeof(double) * N, cudaMemcpyHostToDevice, b.st));
+  KMC_CUDA(cudaMemcpyAsync(d_bv + N, vfrac.data(), sizeof(double) * N, cudaMemcpyHostToDevice,
+                           b.st));
+  KMC_CUDA(cudaMemcpyAsync(b.p[4], cosk.data(), sizeof(double) * S, cudaMemcpyHostToDevice, b.st));
+  KMC_CUDA(cudaMemsetAsync(b.p[5], 0, sizeof(long long) * nl, b.st));
+  KMC_CUDA(cudaMemsetAsync(b.p[6], 0, sizeof(int32_t), b.st));
+  kmc::MeanArgs a;
+  a.items = static_cast<const kmc::MeanItem *>(b.p[1]);
+  a.n_items = static_cast<int32_t>(items.size());
+  a.S = S;
+  a.periods = periods;
+  a.discard = discard;
+  a.n_rec = static_cast<int32_t>(std::max(n_rec, 1ll));
+  a.lys = static_cast<const kmc::MeanLysDev *>(b.p[0]);
+  a.axis = static_cast<const dbl4 *>(b.p[2]);
+  a.beta = d_bv;
+  a.vfrac = d_bv + N;
+  a.cos_k = static_cast<const double *>(b.p[4]);
+  a.loop = static_cast<long long *>(b.p[5]);
+  a.err = static_cast<int32_t *>(b.p[6]);
+  KMC_CUDA(kmc::launch_mean(a, b.st));
+  std::vector<long long> fx(nl);
+  int32_t err = 0;
+  KMC_CUDA(cudaMemcpyAsync(fx.data(), b.p[5], sizeof(long long) * nl, cudaMemcpyDeviceToHost,
+                           b.st));
+  KMC_CUDA(cudaMemcpyAsync(&err, b.p[6], sizeof(int32_t), cudaMemcpyDeviceToHost, b.st));
+  KMC_CUDA(cudaStreamSynchronize(b.st));
+  if (err & kmc::kErrExtrema)
+    return fail(KMC_ESTATE, "an energy profile had more than two minima or maxima");
+  for (long long q = 0; q < need; ++q) loop_M[q] = static_cast<double>(fx[q]) / kmc::kLoopScale;
   return KMC_OK;
 }
 

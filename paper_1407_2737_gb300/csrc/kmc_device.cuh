@@ -4,6 +4,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "kmc_types.h"
 
 namespace kmc {
@@ -15,6 +17,7 @@ __device__ float g_theta_f[kGrid];
 __device__ float2 g_sc_f[kGrid];
 __device__ double g_theta_d[kGrid];
 __device__ double2 g_sc_d[kGrid];
+
 
 // ---------------------------------------------------------------------------
 // Shared-memory staging by bulk asynchronous copies (TMA engine).
@@ -68,6 +71,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Programmatic dependent launch. A step kernel launched with programmatic
+// stream serialisation may start while the previous step is still running;
+// grid_dependency_wait() returns once that grid has completed and its memory
+// is visible (at once when there is no such dependency), so every read of
+// state the previous step writes comes after it. grid_launch_dependents(),
+// once every block has called it or exited, lets the next step's grid launch
+// while this one drains.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Waits for phase `parity` of `bar` for at most ~2 s; returns false (and sets
@@ -156,6 +174,21 @@ struct Prec<double> {
                         1.0 / 24.0),
                 -0.5),
             1.0);
+  }
+};
+
+// Copy of the grid of step iv in shared memory, filled by every block at its
+// start (the pair loop hides the loads); the scan reads one node per warp
+// (a broadcast), Newton one node per thread.
+template <typename R>
+struct GridTables {
+  typename std::conditional<std::is_same<R, float>::value, float2, double2>::type sc[kGrid];
+  R th[kGrid];
+  __device__ void load() {
+    for (int j = threadIdx.x; j < kGrid; j += blockDim.x) {
+      sc[j] = Prec<R>::sc(j);
+      th[j] = Prec<R>::theta(j);
+    }
   }
 };
 

@@ -12,9 +12,17 @@ namespace kmc {
 size_t step_smem_bytes(int prec_fp32, int warps, int tile);
 
 // One time step of every work item (lysosome, 32 targets) on stream st.
-// warps in {4, 8, 16}; tile = sources per staged tile.
+// warps in {4, 8, 16}; tile = sources per staged tile. With pdl the launch
+// may overlap the tail of the previous kernel on st (programmatic dependent
+// launch); the kernel waits for that kernel before it reads any state.
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
-                        cudaStream_t st);
+                        cudaStream_t st, bool pdl = false);
+
+// Blocks of the step kernel of this shape that fit on one SM at once.
+cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int *blocks);
+
+// The Ref. [8] mode over all items of a (one warp per item).
+cudaError_t launch_mean(const MeanArgs &a, cudaStream_t st);
 
 // Advances the device run state by one field period of S steps.
 cudaError_t launch_advance(RunState *rs, int S, cudaStream_t st);

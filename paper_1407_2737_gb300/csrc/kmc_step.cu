@@ -26,8 +26,9 @@
 //
 // Steps iii-vii are shared by the whole block: warp 0 sets up the working
 // plane of each target, all warps scan the 200-point energy-derivative grid
-// (lanes over grid points), all threads run Newton's method (one root per
-// thread), and warp 0 takes the decision (basins, barrier, rates, draw).
+// (lanes over targets, warps over segments of the grid), all threads run
+// Newton's method (one root per thread), and warp 0 takes the decision
+// (basins, barrier, rates, draw).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -35,6 +36,7 @@
 
 #include "kmc_device.cuh"
 #include "kmc_launch.h"
+#include "kmc_mean.cuh"
 
 namespace kmc {
 
@@ -169,9 +171,14 @@ struct EpiShared {
   R h[3][kTargets];    // combined dipolar field
   R k2[kTargets], k[kTargets], bc[kTargets], bs[kTargets];  // profile of Eq. 2
   int cnt[kTargets];   // sign changes found by the scan
+  // brackets as the scan finds them (any order): left node, derivative at the
+  // left and at the right node
+  int ju[kTargets][4];
+  R du[kTargets][4], duh[kTargets][4];
+  // brackets in grid order after Newton: left node, derivative there, root,
+  // energy, sin and cos of the root, offset of the root from the left node
   int jq[kTargets][4];
-  R dq[kTargets][4];   // derivative at the left node of each bracket
-  R dqh[kTargets][4];  // derivative at the right node
+  R dq[kTargets][4];
   R th[kTargets][4], en[kTargets][4], sq[kTargets][4], cq[kTargets][4], off[kTargets][4];
 };
 
@@ -180,90 +187,67 @@ __device__ __forceinline__ R profile_d1(R k2, R bc, R bs, R s, R c) {
   return s * fma(k2, c, bc) - bs * c;
 }
 
-// Grid points of step iv held by one lane during the scan: lane l owns the
-// consecutive points j = 7 l .. 7 l + 6 (lanes 0..27), lane 28 owns 196..199.
-constexpr int kScanPts = 7;
+// Scan of step iv: lane = target, warp w = the w-th of nw contiguous segments
+// of the 200 nodes. Each lane evaluates de/dth at its segment's nodes and at
+// the node after it (cyclically: the cell after node 199 ends at node 0), and
+// records every sign change in a free slot of its target (shared-memory
+// counter, at most 4 kept). All lanes of a warp read the same node, a
+// shared-memory broadcast.
 template <typename R>
-struct ScanLane {
-  R s[kScanPts], c[kScanPts];  // sin and cos of the lane's grid points
-  int j0, npts;
-  __device__ void load(int lane) {
-    j0 = kScanPts * lane;
-    npts = max(0, min(kScanPts, kGrid - j0));
-#pragma unroll
-    for (int q = 0; q < kScanPts; ++q) {
-      const auto sc = Prec<R>::sc(min(j0 + q, kGrid - 1));
-      s[q] = sc.x;
-      c[q] = sc.y;
-    }
-  }
-};
-
-// Scan of step iv for target t by one warp: each lane evaluates de/dth at its
-// grid points and tests the cells (j, j+1) that start there, cyclically (the
-// cell after point 199 ends at point 0). Brackets are numbered in grid order
-// through a prefix sum over the lanes.
-template <typename R>
-__device__ __forceinline__ void warp_scan(EpiShared<R> &sm, const ScanLane<R> &g, int t,
-                                          int lane) {
-  const R k2 = sm.k2[t], bc = sm.bc[t], bs = sm.bs[t];
-  R d[kScanPts];
-#pragma unroll
-  for (int q = 0; q < kScanPts; ++q) d[q] = profile_d1<R>(k2, bc, bs, g.s[q], g.c[q]);
-  // value at the first point of the next lane (the last lane wraps to point 0)
-  R nxt = __shfl_down_sync(0xffffffffu, d[0], 1);
-  const R d0 = __shfl_sync(0xffffffffu, d[0], 0);
-  if (g.j0 + g.npts == kGrid) nxt = d0;
-  unsigned chg = 0;
-#pragma unroll
-  for (int q = 0; q < kScanPts; ++q) {
-    const R right = (q + 1 < g.npts) ? d[q < kScanPts - 1 ? q + 1 : q] : nxt;
-    if (q < g.npts && ((d[q] < R(0)) != (right < R(0)))) chg |= 1u << q;
-  }
-  // exclusive prefix sum of the bracket counts over the lanes
-  const int mine = __popc(chg);
-  int incl = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  int slot = incl - mine;
-#pragma unroll
-  for (int q = 0; q < kScanPts; ++q) {
-    if (chg & (1u << q)) {
+__device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<R> &tab,
+                                             int warp, int nw, int lane, int nt) {
+  const int seg = (kGrid + nw - 1) / nw;
+  const int j0 = warp * seg, j1 = min(kGrid, j0 + seg);
+  if (lane >= nt || j0 >= kGrid) return;
+  const R k2 = sm.k2[lane], bc = sm.bc[lane], bs = sm.bs[lane];
+  auto d1 = [&](int j) {
+    const auto sc = tab.sc[j];
+    return profile_d1<R>(k2, bc, bs, sc.x, sc.y);
+  };
+  R left = d1(j0);
+#pragma unroll 5
+  for (int j = j0; j < j1; ++j) {
+    const R right = d1(j + 1 < kGrid ? j + 1 : 0);
+    if ((left < R(0)) != (right < R(0))) {
+      const int slot = atomicAdd(&sm.cnt[lane], 1);
       if (slot < 4) {
-        const R right = (q + 1 < g.npts) ? d[q < kScanPts - 1 ? q + 1 : q] : nxt;
-        sm.jq[t][slot] = g.j0 + q;
-        sm.dq[t][slot] = d[q];
-        sm.dqh[t][slot] = right;
+        sm.ju[lane][slot] = j;
+        sm.du[lane][slot] = left;
+        sm.duh[lane][slot] = right;
       }
-      ++slot;
     }
+    left = right;
   }
-  if (lane == 31) sm.cnt[t] = incl;
 }
 
-// Newton refinement of bracket q of target t (one thread).
+// Newton refinement of bracket q (of nb) of target t (one thread); the result
+// goes to the bracket's rank in grid order.
 template <typename R>
-__device__ __forceinline__ void refine_bracket(EpiShared<R> &sm, int t, int q) {
+__device__ __forceinline__ void refine_bracket(EpiShared<R> &sm, const GridTables<R> &tab, int t,
+                                               int q, int nb) {
   Profile<R> pf;
   pf.k2 = sm.k2[t];
   pf.k = sm.k[t];
   pf.bc = sm.bc[t];
   pf.bs = sm.bs[t];
-  const int j = min(max(sm.jq[t][q], 0), kGrid - 1);
-  const auto sc = Prec<R>::sc(j);
-  const R h = Prec<R>::theta(1) - Prec<R>::theta(0);
+  const int ju = sm.ju[t][q];
+  int rank = 0;
+  for (int p = 0; p < nb; ++p) rank += sm.ju[t][p] < ju;
+  const int j = min(max(ju, 0), kGrid - 1);
+  const auto sc = tab.sc[j];
+  const R h = tab.th[1] - tab.th[0];
   R s, c;
-  const R off = refine_in_cell(pf, sc.x, sc.y, h, sm.dq[t][q], sm.dqh[t][q], s, c);
-  R th = Prec<R>::theta(j) + off;
+  const R dl = sm.du[t][q];
+  const R off = refine_in_cell(pf, sc.x, sc.y, h, dl, sm.duh[t][q], s, c);
+  R th = tab.th[j] + off;
   if (th >= Prec<R>::two_pi) th -= Prec<R>::two_pi;
-  sm.th[t][q] = th;
-  sm.off[t][q] = off;
-  sm.sq[t][q] = s;
-  sm.cq[t][q] = c;
-  sm.en[t][q] = pf.e(s, c);
+  sm.jq[t][rank] = ju;
+  sm.dq[t][rank] = dl;
+  sm.th[t][rank] = th;
+  sm.off[t][rank] = off;
+  sm.sq[t][rank] = s;
+  sm.cq[t][rank] = c;
+  sm.en[t][rank] = pf.e(s, c);
 }
 
 // Per-target values warp 0 keeps in registers between the stages.
@@ -484,14 +468,13 @@ template <typename V, bool MIXED>
 __device__ __forceinline__ void block_update(
     const StepArgs &a, const LysDev &L, const Item &it, long long step, int rec,
     const TargetIn<V> &tin,
-    EpiShared<typename std::conditional<MIXED, float, double>::type> &sm) {
+    EpiShared<typename std::conditional<MIXED, float, double>::type> &sm,
+    const GridTables<typename std::conditional<MIXED, float, double>::type> &tab) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   const int nt = it.nt;
   const double bext = L.bmax * a.cos_k;
-  ScanLane<R> grid;
-  grid.load(lane);
   TargetState<R> st;
   V m4 = tin.m4;
   const int i = tin.i, il = tin.il;
@@ -503,15 +486,17 @@ __device__ __forceinline__ void block_update(
     sm.k2[lane] = R(2) * static_cast<R>(L.k);
     sm.bc[lane] = st.bmag * st.cphi;
     sm.bs[lane] = st.bmag * st.sphi;
+    sm.cnt[lane] = 0;
   }
   __syncthreads();
-  // iv) scan: warps over targets, lanes over grid points
-  for (int t = warp; t < nt; t += nw) warp_scan<R>(sm, grid, t, lane);
+  // iv) scan: lanes over targets, warps over segments of the grid
+  segment_scan<R>(sm, tab, warp, nw, lane, nt);
   __syncthreads();
   // iv) Newton: one bracket per thread
   for (int x = threadIdx.x; x < 4 * nt; x += blockDim.x) {
     const int t = x >> 2, q = x & 3;
-    if (q < min(sm.cnt[t], 4)) refine_bracket<R>(sm, t, q);
+    const int nb = min(sm.cnt[t], 4);
+    if (q < nb) refine_bracket<R>(sm, tab, t, q, nb);
   }
   __syncthreads();
   if (warp != 0) return;
@@ -549,6 +534,15 @@ __device__ __forceinline__ void block_update(
     }
     if (rec >= 0)
       a.e_acc[i] = tin.eacc + bext * (static_cast<double>(mz) - static_cast<double>(st.mz_old));
+    // Eq. 6: the dipolar field along the applied field at its two extremes
+    const bool at_max = a.k_local == 0, at_min = a.k_local == a.S / 2;
+    if (rec >= 0 && (at_max || at_min)) {
+      const double hz = static_cast<double>(sm.h[2][lane]);
+      double d = a.dh_acc[i];
+      if (at_max) d += hz;
+      if (at_min) d -= hz;
+      a.dh_acc[i] = d;
+    }
     if (a.debug) {
       a.dbg.bdip[3 * i + 0] = static_cast<double>(sm.h[0][lane]);
       a.dbg.bdip[3 * i + 1] = static_cast<double>(sm.h[1][lane]);
@@ -631,16 +625,20 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *dyn = smem + 16;
   __shared__ int s_last;
+  __shared__ GridTables<float> tab;
+  tab.load();
   const Item it = a.items[blockIdx.x];
   const LysDev L = a.lys[it.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // items, lysosome constants and positions do not change during a run
+  const float4 pi = static_cast<const float4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
+  grid_dependency_wait();
   const long long step = a.rs->step_base + a.k_local;
   const int per = a.rs->period;
   const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
   const int par = static_cast<int>(step & 1);
   const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
 
-  const float4 pi = static_cast<const float4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
   TargetIn<float4> tin;
   if (warp == 0) tin = load_target<float4>(a, L, it, step, lane);
   const f2 X = pk(pi.x, pi.x), Y = pk(pi.y, pi.y), Z = pk(pi.z, pi.z);
@@ -742,7 +740,10 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
     }
   }
   __syncthreads();
-  block_update<float4, true>(a, L, it, step, rec, tin, sm);
+  block_update<float4, true>(a, L, it, step, rec, tin, sm, tab);
+  // the next step's blocks may now be scheduled; triggering earlier lets them
+  // take the slots of early-finishing blocks and unbalances the next step
+  grid_launch_dependents();
 }
 
 // ---------------------------------------------------------------------------
@@ -753,9 +754,14 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *dyn = smem + 16;
   __shared__ int s_last;
+  __shared__ GridTables<double> tab;
+  tab.load();
   const Item it = a.items[blockIdx.x];
   const LysDev L = a.lys[it.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // items, lysosome constants and positions do not change during a run
+  const dbl4 pi = static_cast<const dbl4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
+  grid_dependency_wait();
   const long long step = a.rs->step_base + a.k_local;
   const int per = a.rs->period;
   const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
@@ -763,7 +769,6 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
   const dbl4 *__restrict__ gpos = static_cast<const dbl4 *>(a.src_pos) + L.roff;
   const dbl4 *__restrict__ gmu = static_cast<const dbl4 *>(a.src[par]) + L.roff;
 
-  const dbl4 pi = static_cast<const dbl4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
   TargetIn<dbl4> tin;
   if (warp == 0) tin = load_target<dbl4>(a, L, it, step, lane);
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -832,7 +837,10 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
     for (int c = 0; c < 3; ++c) sm.h[c][lane] = 3.0 * tot[c] - tot[3 + c];
   }
   __syncthreads();
-  block_update<dbl4, false>(a, L, it, step, rec, tin, sm);
+  block_update<dbl4, false>(a, L, it, step, rec, tin, sm, tab);
+  // the next step's blocks may now be scheduled; triggering earlier lets them
+  // take the slots of early-finishing blocks and unbalances the next step
+  grid_launch_dependents();
 }
 
 // Ends a field period on the device: the next period starts S steps later.
@@ -851,34 +859,86 @@ size_t step_smem_bytes(int prec_fp32, int warps, int tile) {
   return 16 + (stage > epi ? stage : epi);
 }
 
+// Launches kernel k over n_items blocks; with pdl the launch carries the
+// programmatic stream serialisation attribute.
+template <typename K>
+static cudaError_t launch_items(K kernel, const StepArgs &a, int n_items, int threads,
+                                size_t smem, int tile, cudaStream_t st, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(n_items));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, a, tile);
+}
+
 template <int NW>
-static cudaError_t launch_f32(const StepArgs &a, int n_items, int tile, cudaStream_t st) {
-  kmc_step_f32<NW><<<n_items, NW * 32, step_smem_bytes(1, NW, tile), st>>>(a, tile);
-  return cudaGetLastError();
+static cudaError_t launch_f32(const StepArgs &a, int n_items, int tile, cudaStream_t st,
+                              bool pdl) {
+  return launch_items(kmc_step_f32<NW>, a, n_items, NW * 32, step_smem_bytes(1, NW, tile), tile,
+                      st, pdl);
 }
 template <int NW>
-static cudaError_t launch_f64(const StepArgs &a, int n_items, int tile, cudaStream_t st) {
-  kmc_step_f64<NW><<<n_items, NW * 32, step_smem_bytes(0, NW, tile), st>>>(a, tile);
-  return cudaGetLastError();
+static cudaError_t launch_f64(const StepArgs &a, int n_items, int tile, cudaStream_t st,
+                              bool pdl) {
+  return launch_items(kmc_step_f64<NW>, a, n_items, NW * 32, step_smem_bytes(0, NW, tile), tile,
+                      st, pdl);
 }
 
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool pdl) {
   if (n_items <= 0) return cudaSuccess;
   if (prec_fp32) {
     switch (warps) {
-      case 4: return launch_f32<4>(a, n_items, tile, st);
-      case 8: return launch_f32<8>(a, n_items, tile, st);
-      case 16: return launch_f32<16>(a, n_items, tile, st);
+      case 4: return launch_f32<4>(a, n_items, tile, st, pdl);
+      case 8: return launch_f32<8>(a, n_items, tile, st, pdl);
+      case 16: return launch_f32<16>(a, n_items, tile, st, pdl);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (warps) {
-    case 4: return launch_f64<4>(a, n_items, tile, st);
-    case 8: return launch_f64<8>(a, n_items, tile, st);
-    case 16: return launch_f64<16>(a, n_items, tile, st);
+    case 4: return launch_f64<4>(a, n_items, tile, st, pdl);
+    case 8: return launch_f64<8>(a, n_items, tile, st, pdl);
+    case 16: return launch_f64<16>(a, n_items, tile, st, pdl);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <typename K>
+static cudaError_t occupancy(K kernel, int threads, size_t smem, int *blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, threads, smem);
+}
+
+cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int *blocks) {
+  *blocks = 0;
+  const size_t smem = step_smem_bytes(prec_fp32, warps, tile);
+  const int th = warps * 32;
+  if (prec_fp32) {
+    switch (warps) {
+      case 4: return occupancy(kmc_step_f32<4>, th, smem, blocks);
+      case 8: return occupancy(kmc_step_f32<8>, th, smem, blocks);
+      case 16: return occupancy(kmc_step_f32<16>, th, smem, blocks);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (warps) {
+    case 4: return occupancy(kmc_step_f64<4>, th, smem, blocks);
+    case 8: return occupancy(kmc_step_f64<8>, th, smem, blocks);
+    case 16: return occupancy(kmc_step_f64<16>, th, smem, blocks);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_mean(const MeanArgs &a, cudaStream_t st) {
+  if (a.n_items <= 0) return cudaSuccess;
+  const int blocks = (a.n_items + kMeanWarps - 1) / kMeanWarps;
+  kmc_mean_kernel<<<blocks, kMeanWarps * 32, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_advance(RunState *rs, int S, cudaStream_t st) {
@@ -908,6 +968,7 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_sc_f, sc_f, sizeof(sc_f));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_theta_d, th_d, sizeof(th_d));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_sc_d, sc_d, sizeof(sc_d));
+
   // kernel attributes are set here, never inside a stream capture
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<8>);

@@ -84,6 +84,8 @@ struct StepArgs {
   const double *beta;       // [N] mu0 M_S^2 V_i / (k_B T)
   const double *vfrac;      // [N] V_i / sum of V over the lysosome
   double *e_acc;            // [N] sum_k b_k (m_z,k+1 - m_z,k) over recorded steps
+  double *dh_acc;           // [N] Eq. 6: sum over recorded periods of b_dip,z at
+                            // step 0 (+b_max) minus b_dip,z at step S/2 (-b_max)
   long long *loop_m;        // [n_lys][n_rec] volume-weighted mean m_z in fixed point
                             // (units of 2^-62): integer sums do not depend on the
                             // order in which blocks add, so runs are reproducible
@@ -101,6 +103,33 @@ struct StepArgs {
   DebugOut dbg;
   int32_t debug;
   int32_t pad;
+};
+
+// Ref. [8] mode (kmc_mean.cuh): per lysosome, per work item, arguments.
+struct MeanLysDev {
+  int32_t off, n;   // first NP, NPs
+  int32_t t_zero;   // T = 0: no relaxation (the wells are only followed)
+  int32_t pad;
+  double k;         // K_eff / (mu0 M_S^2)
+  double bmax;      // mu0 H_max / (mu0 M_S)
+  double lognu0t;   // ln(t_step / tau0)
+};
+
+struct MeanItem {   // 32 NPs of one lysosome, one warp
+  int32_t l, t0, nt, pad;
+};
+
+struct MeanArgs {
+  const MeanItem *items;
+  int32_t n_items;
+  int32_t S, periods, discard, n_rec;
+  const MeanLysDev *lys;
+  const dbl4 *axis;      // [N] unit easy axes
+  const double *beta;    // [N] mu0 M_S^2 V_i / (k_B T)
+  const double *vfrac;   // [N] V_i / sum V over the lysosome
+  const double *cos_k;   // [S] cos(2 pi k / S)
+  long long *loop;       // [n_lys][n_rec] volume-weighted <m_z>, units of 2^-62
+  int32_t *err;
 };
 
 // Error bits written to the device error word.

@@ -21,7 +21,7 @@ KMC_OK, KMC_EINVAL, KMC_ENOMEM, KMC_ECUDA, KMC_ETIMEOUT, KMC_ESTATE, KMC_ECAPACI
     KMC_EIO = range(8)
 KMC_FP64_PLAIN, KMC_FP32_MIXED = 0, 1
 (KMC_READ_LOOP_H, KMC_READ_LOOP_M, KMC_READ_NP_ENERGY, KMC_READ_AREA, KMC_READ_SAR,
- KMC_READ_MOMENTS, KMC_READ_COUNTERS) = range(7)
+ KMC_READ_MOMENTS, KMC_READ_COUNTERS, KMC_READ_DHDIP) = range(8)
 
 STATUS_NAMES = {0: "KMC_OK", 1: "KMC_EINVAL", 2: "KMC_ENOMEM", 3: "KMC_ECUDA",
                 4: "KMC_ETIMEOUT", 5: "KMC_ESTATE", 6: "KMC_ECAPACITY", 7: "KMC_EIO"}
@@ -29,8 +29,10 @@ STATUS_NAMES = {0: "KMC_OK", 1: "KMC_EINVAL", 2: "KMC_ENOMEM", 3: "KMC_ECUDA",
 # the entry points declared in include/kmc.h
 EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
-           "kmc_last_error", "kmc_dipolar_field_noalloc")
+           "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
+           "kmc_shell_profile", "kmc_mean_run")
 KMC_NOALLOC_MAX_N = 8192
+KMC_PHI_MAX_N = 64
 
 
 class KmcError(RuntimeError):
@@ -77,6 +79,13 @@ def lib():
             L.kmc_tuning.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, _I32, _I32, _I32]
             L.kmc_dipolar_field_noalloc.argtypes = [C.c_int32, vp, vp, vp, C.c_double, _D,
                                                     C.c_double, vp, vp]
+            L.kmc_local_concentration.argtypes = [vp, C.c_int32, C.c_int32, _D, C.c_int64,
+                                                  _I64]
+            L.kmc_shell_profile.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, _D,
+                                            C.c_int64, _I64, _D]
+            L.kmc_mean_run.argtypes = [C.POINTER(kmc_lysosome), C.c_int32, _D, C.c_int32,
+                                       C.c_double, C.c_int32, C.c_int32, C.c_int32, _D,
+                                       C.c_int64, _I64]
             L.kmc_destroy.argtypes = [vp]
             L.kmc_destroy.restype = None
             L.kmc_last_error.argtypes = []
@@ -140,6 +149,30 @@ def kmc_create(lysosomes, precision=KMC_FP32_MIXED, center=None):
     h = C.c_void_p()
     _check(L.kmc_create(arr, len(lysosomes), int(precision), C.byref(h)))
     return Context(h.value, [int(np.asarray(ly.vol).shape[0]) for ly in lysosomes])
+
+
+def kmc_mean_run(lysosomes, mu0Hmax, f, steps_per_period, periods, discard_periods):
+    """Ref. [8] mode on the device: returns [n_lys][S * (periods - discard)]
+    volume-weighted mean m_z after each recorded step."""
+    keep = []
+    arr = (kmc_lysosome * len(lysosomes))()
+    for q, ly in enumerate(lysosomes):
+        pos = _f64(ly.pos, (-1, 3))
+        axis = _f64(ly.axis, (-1, 3))
+        vol = _f64(ly.vol, (-1,))
+        keep += [pos, axis, vol]
+        arr[q] = kmc_lysosome(len(vol), _dp(pos), _dp(axis), _dp(vol), None, float(ly.Ms),
+                              float(ly.Keff), float(ly.T), float(ly.tau0),
+                              float(getattr(ly, "rho", 5200.0)))
+    H = _f64(np.atleast_1d(mu0Hmax), (-1,))
+    n_rec = int(steps_per_period) * (int(periods) - int(discard_periods))
+    out = np.zeros(max(n_rec * len(lysosomes), 1))
+    n = C.c_int64(0)
+    _check(lib().kmc_mean_run(arr, len(lysosomes), _dp(H), len(H), float(f),
+                              int(steps_per_period), int(periods), int(discard_periods),
+                              _dp(out), len(out), C.byref(n)))
+    del keep
+    return out[:int(n.value)].reshape(len(lysosomes), -1)
 
 
 def kmc_set_stream(ctx, stream_handle):
@@ -221,6 +254,32 @@ def kmc_dipolar_field_noalloc(n, pos_dev, m_dev, vol_dev, Ms, center, length, B_
                                            C.c_void_p(vol_dev), float(Ms), _dp(cen),
                                            float(length), C.c_void_p(B_dev),
                                            C.c_void_p(stream_handle or 0)))
+
+
+def kmc_local_concentration(ctx, lys, N):
+    """Eq. 8: phi_N of every NP of lysosome `lys` (computed on the device)."""
+    n = C.c_int64(0)
+    L = lib()
+    st = L.kmc_local_concentration(ctx.handle, int(lys), int(N), None, 0, C.byref(n))
+    if st not in (KMC_OK, KMC_ECAPACITY):
+        _check(st)
+    buf = np.zeros(max(int(n.value), 1))
+    _check(L.kmc_local_concentration(ctx.handle, int(lys), int(N), _dp(buf), len(buf),
+                                     C.byref(n)))
+    return buf[:int(n.value)]
+
+
+def kmc_shell_profile(ctx, lys, radius, n_shells, N):
+    """Radial profile of the last run: dict of per-shell count, area (J/m^3 per
+    cycle), dHdip (T) and phi_N, and the radius R used (m)."""
+    out = np.zeros(4 * int(n_shells))
+    n = C.c_int64(0)
+    R = C.c_double(0.0)
+    _check(lib().kmc_shell_profile(ctx.handle, int(lys), float(radius), int(n_shells), int(N),
+                                   _dp(out), len(out), C.byref(n), C.byref(R)))
+    t = out.reshape(-1, 4)
+    return dict(count=t[:, 0].copy(), area=t[:, 1].copy(), dHdip=t[:, 2].copy(),
+                phi=t[:, 3].copy(), radius=float(R.value))
 
 
 def kmc_destroy(ctx):
