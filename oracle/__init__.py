@@ -112,6 +112,11 @@ def lib():
             L.kmc_oracle_shell_profile.argtypes = [C.c_int32, _D, _D, _D, C.c_double,
                                                    C.c_int32, C.c_int32, _D, _D, _D]
             L.kmc_oracle_shell_profile.restype = C.c_double
+            L.kmc_oracle_regen_axes.argtypes = [C.c_int32, C.c_uint64, C.c_uint32, C.c_int32, _D]
+            L.kmc_oracle_regen_axes.restype = None
+            L.kmc_oracle_regen_positions.argtypes = [C.c_int32, _D, C.c_double, C.c_uint64,
+                                                     C.c_uint32, C.c_int32, _D]
+            L.kmc_oracle_regen_positions.restype = None
             _lib = L
     return _lib
 
@@ -325,3 +330,20 @@ def shell_profile(pos, vol, center, R, n_shells, values):
     if r < 0:
         raise ValueError("oracle shell_profile failed (%g)" % r)
     return count, mean, float(r)
+
+
+def regen_axes(n, seed, loop, lys=0):
+    """Fresh easy axes for loop `loop` (Sec. II.4), uniform on the sphere."""
+    axis = np.zeros((int(n), 3))
+    lib().kmc_oracle_regen_axes(int(n), C.c_uint64(seed), C.c_uint32(loop), int(lys), _dp(axis))
+    return axis
+
+
+def regen_positions(nodes, disorder, seed, loop, lys=0):
+    """Fresh positions around the nodes (Sec. II.4): a uniform direction and a
+    distance uniform on [0, disorder]."""
+    nodes = _f64(nodes, (-1, 3))
+    pos = np.zeros_like(nodes)
+    lib().kmc_oracle_regen_positions(len(nodes), _dp(nodes), float(disorder), C.c_uint64(seed),
+                                     C.c_uint32(loop), int(lys), _dp(pos))
+    return pos

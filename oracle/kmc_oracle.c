@@ -95,6 +95,54 @@ double kmc_oracle_uniform(uint64_t seed, int64_t step, int32_t np, int32_t lys) 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sample regeneration between loops (Sec. II.4). Two 53-bit uniforms per
+ * Philox call, from words (w0, w1) and (w2, w3) like kmc_oracle_uniform, with
+ * counter (loop, 0x80000000 | sub, NP, lys): the set top bit of word 1 keeps
+ * these counters apart from the kMC draws (word 1 = high half of a step index,
+ * below 2^31). */
+static void regen_uniforms(uint64_t seed, uint32_t loop, uint32_t sub, int32_t np,
+                           int32_t lys, double u[2]) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const uint32_t ctr[4] = {loop, 0x80000000u | sub, (uint32_t)np, (uint32_t)lys};
+  uint32_t w[4];
+  kmc_oracle_philox4x32_10(ctr, key, w);
+  u[0] = (double)(((uint64_t)w[0] << 21) ^ (uint64_t)(w[1] >> 11)) * (1.0 / 9007199254740992.0);
+  u[1] = (double)(((uint64_t)w[2] << 21) ^ (uint64_t)(w[3] >> 11)) * (1.0 / 9007199254740992.0);
+}
+
+/* A direction uniform on the sphere from two uniforms: z uniform on [-1, 1]
+ * (Archimedes) and the azimuth uniform on [0, 2 pi). */
+static void sphere_point(const double u[2], double out[3]) {
+  const double z = 1.0 - 2.0 * u[0];
+  const double ph = TWO_PI * u[1];
+  const double r2 = 1.0 - z * z;
+  const double r = r2 > 0.0 ? sqrt(r2) : 0.0;
+  out[0] = r * cos(ph);
+  out[1] = r * sin(ph);
+  out[2] = z;
+}
+
+void kmc_oracle_regen_axes(int32_t n, uint64_t seed, uint32_t loop, int32_t lys, double *axis) {
+  for (int32_t i = 0; i < n; ++i) {
+    double u[2];
+    regen_uniforms(seed, loop, 0u, i, lys, u);
+    sphere_point(u, &axis[3 * i]);
+  }
+}
+
+void kmc_oracle_regen_positions(int32_t n, const double *nodes, double disorder, uint64_t seed,
+                                uint32_t loop, int32_t lys, double *pos) {
+  for (int32_t i = 0; i < n; ++i) {
+    double u[2], v[2], dir[3];
+    regen_uniforms(seed, loop, 1u, i, lys, u);
+    regen_uniforms(seed, loop, 2u, i, lys, v);
+    sphere_point(u, dir);
+    const double rho = disorder * v[0];  /* distance uniform on [0, disorder] */
+    for (int q = 0; q < 3; ++q) pos[3 * i + q] = nodes[3 * i + q] + rho * dir[q];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Eq. 1: mu0 H_dip,i = sum_{j != i} (mu0 M_S V_j / 4 pi)
  *                      [3 (m_j . e_ij) e_ij - m_j] / r_ij^3. */
 static void dipolar_on(int32_t i, int32_t n, const double *pos, const double *vol,

@@ -30,6 +30,10 @@
  *   local_concentration ...... pinned (cubic lattices: neighbour shells in
  *                              closed form)
  *   shell_profile ............ pinned (hand-placed NPs with known shells)
+ *   regen_axes, regen_positions  pinned (moments of the uniform sphere
+ *                              distribution, KS tests of z, azimuth and
+ *                              displacement length, no overlap at maximal
+ *                              disorder by brute force)
  */
 #ifndef KMC_ORACLE_H
 #define KMC_ORACLE_H
@@ -75,6 +79,18 @@ void kmc_oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
  * key = (seed low, seed high), counter = (step low, step high, np, lys),
  * u = ((w0 << 21) ^ (w1 >> 11)) * 2^-53 from output words w0, w1. */
 double kmc_oracle_uniform(uint64_t seed, int64_t step, int32_t np, int32_t lys);
+
+/* Sample regeneration between loops (Sec. II.4): between loops the paper
+ * draws fresh easy axes and, around fixed mean positions (the nodes of a cubic
+ * lattice), fresh positions. Draws: Philox4x32-10, key (seed lo, seed hi),
+ * counter (loop, 0x80000000 | sub, NP, lys), two 53-bit uniforms per call as
+ * in kmc_oracle_uniform. Axes (sub 0): uniform on the sphere, z = 1 - 2 u0,
+ * azimuth 2 pi u1. Positions: node + rho e with e uniform on the sphere from
+ * sub 1 and rho = disorder * (first uniform of sub 2), uniform on
+ * [0, disorder] as the paper states it. axis, pos are [n][3]. */
+void kmc_oracle_regen_axes(int32_t n, uint64_t seed, uint32_t loop, int32_t lys, double *axis);
+void kmc_oracle_regen_positions(int32_t n, const double *nodes, double disorder, uint64_t seed,
+                                uint32_t loop, int32_t lys, double *pos);
 
 /* Eq. 1: mu0*H_dip on every NP from the moments of all the others, exact sum
  * over j != i with per-source volume V_j. B is [n][3] in tesla. */

@@ -9,6 +9,9 @@ without overlap, with random easy axes. This module builds such inputs:
   sphere of radius R - d/2, each kept iff it lies at least d from every centre
   kept before it;
 * easy axes uniform on the unit sphere;
+* or, the paper's own choice (Sec. II.4), the nodes of a simple-cubic lattice
+  of cell a = d (pi / 6c)^(1/3) nearest the centre, as mean positions for
+  the disorder drawn loop by loop (at most (a - d)/2, so no two overlap);
 * centres snapped to the float32 grid in units of d about the lysosome centre
   (the origin), so that the float32 copy held by the GPU path is the same
   geometry as the float64 copy held by the oracle (a shift of at most 3e-8 d
@@ -125,6 +128,40 @@ def make_lysosome(n, d, c, Ms=1e6, Keff=1.3e4, T=300.0, tau0=1e-10, seed=0,
     return Lysosome(pos=pos, axis=axis, vol=vol, Ms=float(Ms), Keff=float(Keff),
                     T=float(T), tau0=float(tau0), rho=float(rho), d=float(d),
                     radius=float(R), c=float(c))
+
+
+def lattice_spacing(d, c):
+    """Edge of the simple-cubic cell holding one sphere of diameter d at volume
+    concentration c: a^3 c = pi d^3 / 6."""
+    return d * (math.pi / (6.0 * c)) ** (1.0 / 3.0)
+
+
+def max_disorder(d, c):
+    """Largest displacement that keeps two neighbouring NPs of a simple-cubic
+    lattice from overlapping: each may move (a - d) / 2 towards the other
+    (Sec. II.4: the disorder is as large as possible without overlap)."""
+    return 0.5 * (lattice_spacing(d, c) - d)
+
+
+def lattice_nodes_lysosome(n, d, c, Ms=1e6, Keff=1.3e4, T=300.0, tau0=1e-10, seed=0,
+                           rho=5200.0):
+    """The paper's own placement (Sec. II.4): the n nodes of the simple-cubic
+    lattice of spacing lattice_spacing(d, c) nearest the centre (a node sits
+    at the origin; ties by grid order), random easy axes. The nodes are the
+    mean positions around which the disorder is drawn, loop by loop."""
+    if not 0.0 < c < math.pi / 6.0:
+        raise ValueError("a simple-cubic lattice holds at most pi/6 of the volume")
+    a = lattice_spacing(d, c)
+    h = int(math.ceil((0.75 * n / math.pi) ** (1.0 / 3.0))) + 2
+    g = np.arange(-h, h + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    p = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float64)
+    r2 = np.einsum("ij,ij->i", p, p)
+    pos = p[np.argsort(r2, kind="stable")[:n]] * a
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return Lysosome(pos=pos, axis=random_axes(n, rng), vol=np.full(n, sphere_volume(d)),
+                    Ms=float(Ms), Keff=float(Keff), T=float(T), tau0=float(tau0), rho=float(rho),
+                    d=float(d), radius=float(lysosome_radius(n, d, c)), c=float(c))
 
 
 def lattice_lysosome(n_side, spacing, d, Ms=1e6, Keff=1.3e4, T=300.0, tau0=1e-10):

@@ -3,6 +3,7 @@ inside a sphere, Sec. II.1 / III.1)."""
 import math
 
 import numpy as np
+import pytest
 from scipy.spatial.distance import pdist
 
 from paper_1407_2737_gb300 import inputs
@@ -34,3 +35,20 @@ def test_batched_workload_shape():
     assert np.all((ns >= 200) & (ns <= 10000))
     assert len(run["mu0Hmax"]) == 16
     assert np.all((run["mu0Hmax"] >= 0.010) & (run["mu0Hmax"] <= 0.080))
+
+
+def test_lattice_nodes_lysosome():
+    # the n simple-cubic nodes of cell a = d (pi / 6c)^(1/3) nearest the centre
+    d, c, n = 14e-9, 0.1, 2000
+    lys = inputs.lattice_nodes_lysosome(n, d, c, seed=3)
+    a = inputs.lattice_spacing(d, c)
+    assert lys.n == n
+    assert a ** 3 * c == pytest.approx(math.pi * d ** 3 / 6, rel=1e-12)
+    g = lys.pos / a
+    np.testing.assert_allclose(g, np.round(g), atol=1e-9)
+    assert len({tuple(x) for x in np.round(g).astype(int)}) == n
+    r = np.linalg.norm(lys.pos, axis=1)
+    # every node left out lies no nearer than the farthest one kept
+    assert r.max() == pytest.approx(lys.radius, rel=0.05)
+    assert inputs.max_disorder(d, c) == pytest.approx(0.5 * (a - d), rel=1e-12)
+    np.testing.assert_allclose(np.linalg.norm(lys.axis, axis=1), 1.0, atol=1e-12)
