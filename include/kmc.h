@@ -91,13 +91,17 @@ enum {
   KMC_READ_COUNTERS = 6,  /* [4] over the last run: jumps, near-threshold draws
                              (|u - P| < 1e-9), NP-steps with one minimum, NP-steps
                              whose working plane needed the fallback               */
-  KMC_READ_DHDIP = 7      /* [n] Eq. 6 per NP, T: the dipolar field along z (the
+  KMC_READ_DHDIP = 7,     /* [n] Eq. 6 per NP, T: the dipolar field along z (the
                              applied field's direction) during the step at
                              +mu0 H_max (step 0 of a period) minus that during the
                              step at -mu0 H_max (step S/2, (S-1)/2 for odd S), each
                              from the moments at the start of the step, averaged
                              over the recorded periods; > 0 where the dipolar
                              field is parallel to the applied one (Sec. III.2.b) */
+  KMC_READ_POSITIONS = 8, /* [n][3] current NP centres, m (those given to
+                             kmc_create until kmc_regenerate moves them)     */
+  KMC_READ_AXES = 9,      /* [n][3] current unit easy axes (FP32 contexts: as
+                             held in float32)                                */
 };
 
 /* Creates a context holding n_lys lysosomes (copied to the device). Moments
@@ -209,6 +213,29 @@ kmc_status kmc_mean_run(const kmc_lysosome *lys, int32_t n_lys, const double *mu
                         int32_t n_amp, double f, int32_t steps_per_period, int32_t periods,
                         int32_t discard_periods, double *loop_M, int64_t cap,
                         int64_t *written);
+
+/* What kmc_regenerate redraws (bit mask). */
+enum { KMC_REGEN_AXES = 1, KMC_REGEN_POSITIONS = 2 };
+
+/* Sample regeneration between loops (Sec. II.4), on the device: the paper
+ * averages loops over fresh easy axes and, around fixed mean positions (the
+ * nodes of a cubic lattice), fresh positions. For lysosome `lys` (-1: all):
+ *   KMC_REGEN_AXES       easy axes uniform on the sphere;
+ *   KMC_REGEN_POSITIONS  position = mean position + rho e, e uniform on the
+ *                        sphere, rho uniform on [0, disorder] (m); the mean
+ *                        positions are those given to kmc_create;
+ * then every moment of the lysosome restarts along its axis with m_z >= 0.
+ * Draws: Philox4x32-10, key (seed lo, seed hi), counter (loop, 0x80000000 |
+ * sub, NP, lysosome) with sub 0 for the axis and 1, 2 for the displacement;
+ * two 53-bit uniforms per call from words (0, 1) and (2, 3) as for the kMC
+ * draw; z = 1 - 2 u0 and azimuth 2 pi u1 give a point on the sphere. The
+ * result is what kmc_create would build from the drawn axes and positions;
+ * the global step counter carries on. A checkpoint (kmc_save) does not hold
+ * the geometry: after kmc_load, call kmc_regenerate again with the same
+ * arguments. Errors: KMC_EINVAL (lys out of range, bad mask, disorder < 0 or
+ * not finite). Synchronises the context's stream. */
+kmc_status kmc_regenerate(kmc_ctx *ctx, int32_t lys, int32_t what, double disorder,
+                          uint64_t seed, uint32_t loop);
 
 /* Frees the context and its device memory. NULL-safe. */
 void kmc_destroy(kmc_ctx *ctx);

@@ -69,7 +69,8 @@ V make4(double x, double y, double z, double w) {
   return v;
 }
 
-// Source moments w_i m_i of every NP into the source buffer of parity par.
+// Source records (FP32: positions and w_i m_i; FP64: w_i m_i) of every NP into
+// the source buffer of parity par.
 __global__ void sources_f32(const float4 *__restrict__ pos, const float4 *__restrict__ m,
                             const int *__restrict__ slot, SrcPair *__restrict__ src, long long n) {
   const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
@@ -77,6 +78,9 @@ __global__ void sources_f32(const float4 *__restrict__ pos, const float4 *__rest
   const float4 p = pos[i], q = m[i];
   const int s = slot[i];
   SrcPair &r = src[s >> 1];
+  r.x[s & 1] = p.x;
+  r.y[s & 1] = p.y;
+  r.z[s & 1] = p.z;
   r.mx[s & 1] = p.w * q.x;
   r.my[s & 1] = p.w * q.y;
   r.mz[s & 1] = p.w * q.z;
@@ -152,7 +156,9 @@ struct kmc_ctx {
   double *d_phi = nullptr;    // [max n] scratch of kmc_local_concentration
   std::vector<double> len;    // [n_lys] length unit L, m
   std::vector<double> ctr;    // [n_lys][3] frame origin, m
-  std::vector<double> pos_si; // [N][3] positions as given, m
+  std::vector<double> pos_si; // [N][3] current positions, m
+  double *d_nodes = nullptr;  // [N][3] positions given at creation (mean positions), m
+  double *d_possi = nullptr;  // [N][3] positions written by kmc_regenerate, m
   long long *d_loop = nullptr;  // fixed point, units of 2^-62
   unsigned long long *d_cnt = nullptr;
   int32_t *d_err = nullptr;
@@ -491,7 +497,7 @@ void free_ctx(kmc_ctx *c) {
   drop_graph(c);
   void *ptrs[] = {c->d_lys,   c->d_pos,    c->d_axis,    c->d_m,        c->d_src[0],
                   c->d_src[1], c->d_slot,  c->d_beta,    c->d_vfrac,    c->d_eacc,
-                  c->d_dh,    c->d_pos64,  c->d_phi,
+                  c->d_dh,    c->d_pos64,  c->d_phi,     c->d_nodes,    c->d_possi,
                   c->d_loop,  c->d_cnt,    c->d_err,     c->d_rs,       c->d_items,
                   c->d_partial, c->d_arrivals, c->d_dbg, c->d_dbg_flags};
   for (void *p : ptrs)
@@ -855,13 +861,16 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
     case KMC_READ_LOOP_M: need = c->n_rec; break;
     case KMC_READ_NP_ENERGY:
     case KMC_READ_DHDIP: need = n; break;
+    case KMC_READ_POSITIONS:
+    case KMC_READ_AXES: need = 3ll * n; break;
     case KMC_READ_AREA:
     case KMC_READ_SAR: need = 1; break;
     case KMC_READ_MOMENTS: need = 3ll * n; break;
     case KMC_READ_COUNTERS: need = 4; break;
     default: return fail(KMC_EINVAL, "unknown output %d", what);
   }
-  if (what != KMC_READ_MOMENTS && !c->have_run)
+  if (what != KMC_READ_MOMENTS && what != KMC_READ_POSITIONS && what != KMC_READ_AXES &&
+      !c->have_run)
     return fail(KMC_ESTATE, "no run has been made on this context");
   if (written) *written = need;
   if (cap < need) return fail(KMC_ECAPACITY, "output needs %lld elements", (long long)need);
@@ -900,9 +909,14 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
       if (what == KMC_READ_SAR) buf[0] = area * c->f / c->rho[lys];
       break;
     }
+    case KMC_READ_POSITIONS:
+      for (int64_t q = 0; q < 3ll * n; ++q) buf[q] = c->pos_si[3ll * o + q];
+      break;
+    case KMC_READ_AXES:
     case KMC_READ_MOMENTS: {
       std::vector<unsigned char> raw(c->vbytes * n);
-      KMC_CUDA(cudaMemcpy(raw.data(), static_cast<unsigned char *>(c->d_m) + c->vbytes * o,
+      const void *src = what == KMC_READ_AXES ? c->d_axis : c->d_m;
+      KMC_CUDA(cudaMemcpy(raw.data(), static_cast<const unsigned char *>(src) + c->vbytes * o,
                           raw.size(), cudaMemcpyDeviceToHost));
       for (int i = 0; i < n; ++i) {
         if (c->fp32) {
@@ -1269,6 +1283,58 @@ kmc_status kmc_mean_run(const kmc_lysosome *lys, int32_t n_lys, const double *mu
   if (err & kmc::kErrExtrema)
     return fail(KMC_ESTATE, "an energy profile had more than two minima or maxima");
   for (long long q = 0; q < need; ++q) loop_M[q] = static_cast<double>(fx[q]) / kmc::kLoopScale;
+  return KMC_OK;
+}
+
+kmc_status kmc_regenerate(kmc_ctx *c, int32_t lys, int32_t what, double disorder, uint64_t seed,
+                          uint32_t loop) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (lys < -1 || lys >= c->n_lys) return fail(KMC_EINVAL, "lysosome %d out of range", lys);
+  if (what < 1 || what > (KMC_REGEN_AXES | KMC_REGEN_POSITIONS))
+    return fail(KMC_EINVAL, "what must combine KMC_REGEN_AXES and KMC_REGEN_POSITIONS");
+  if ((what & KMC_REGEN_POSITIONS) && !(disorder >= 0 && is_finite(disorder)))
+    return fail(KMC_EINVAL, "disorder must be finite and >= 0");
+  KMC_TRY(check_device_error(c));
+  if (!c->d_nodes) {  // the mean positions: those given at creation
+    KMC_TRY(dalloc(&c->d_nodes, sizeof(double) * 3 * c->N));
+    KMC_TRY(dalloc(&c->d_possi, sizeof(double) * 3 * c->N));
+    KMC_CUDA(cudaMemcpy(c->d_nodes, c->pos_si.data(), sizeof(double) * 3 * c->N,
+                        cudaMemcpyHostToDevice));
+    KMC_CUDA(cudaMemcpy(c->d_possi, c->pos_si.data(), sizeof(double) * 3 * c->N,
+                        cudaMemcpyHostToDevice));
+  }
+  const int l0 = lys < 0 ? 0 : lys, l1 = lys < 0 ? c->n_lys : lys + 1;
+  for (int l = l0; l < l1; ++l) {
+    kmc::RegenArgs a;
+    a.off = c->off[l];
+    a.n = c->n[l];
+    a.lys = l;
+    a.what = what;
+    a.loop = loop;
+    a.fp32 = c->fp32;
+    a.seed = seed;
+    a.disorder = disorder;
+    a.len = c->len[l];
+    a.cx = c->ctr[3 * l];
+    a.cy = c->ctr[3 * l + 1];
+    a.cz = c->ctr[3 * l + 2];
+    a.nodes = c->d_nodes;
+    a.pos = c->d_pos;
+    a.axis = c->d_axis;
+    a.m = c->d_m;
+    a.pos64 = c->d_pos64;
+    a.pos_si = c->d_possi;
+    KMC_CUDA(kmc::launch_regen(a, c->stream));
+  }
+  KMC_TRY(refresh_sources(c, 0));
+  KMC_TRY(refresh_sources(c, 1));
+  if (what & KMC_REGEN_POSITIONS) {
+    const size_t o = 3ull * c->off[l0];
+    const size_t cnt = 3ull * (c->off[l1 - 1] + c->n[l1 - 1]) - o;
+    KMC_CUDA(cudaMemcpyAsync(c->pos_si.data() + o, c->d_possi + o, sizeof(double) * cnt,
+                             cudaMemcpyDeviceToHost, c->stream));
+  }
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
   return KMC_OK;
 }
 

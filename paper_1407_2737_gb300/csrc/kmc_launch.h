@@ -24,6 +24,9 @@ cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int *blocks);
 // The Ref. [8] mode over all items of a (one warp per item).
 cudaError_t launch_mean(const MeanArgs &a, cudaStream_t st);
 
+// Redraws the axes and/or positions of one lysosome (a.off .. a.off + a.n).
+cudaError_t launch_regen(const RegenArgs &a, cudaStream_t st);
+
 // Advances the device run state by one field period of S steps.
 cudaError_t launch_advance(RunState *rs, int S, cudaStream_t st);
 

@@ -37,6 +37,7 @@
 #include "kmc_device.cuh"
 #include "kmc_launch.h"
 #include "kmc_mean.cuh"
+#include "kmc_regen.cuh"
 
 namespace kmc {
 
@@ -188,35 +189,44 @@ __device__ __forceinline__ R profile_d1(R k2, R bc, R bs, R s, R c) {
 }
 
 // Scan of step iv: lane = target, warp w = the w-th of nw contiguous segments
-// of the 200 nodes. Each lane evaluates de/dth at its segment's nodes and at
-// the node after it (cyclically: the cell after node 199 ends at node 0), and
-// records every sign change in a free slot of its target (shared-memory
-// counter, at most 4 kept). All lanes of a warp read the same node, a
-// shared-memory broadcast.
+// of the 200 nodes (nw >= 4, so a segment holds at most 50). A first pass
+// evaluates de/dth at the segment's nodes and at the node after it (cyclically:
+// the cell after node 199 ends at node 0) and keeps only their signs, as a bit
+// mask, so that its loads and arithmetic pipeline freely; a second pass visits
+// the sign changes (at most four per target) and records each in a free slot of
+// its target (shared-memory counter). All lanes of a warp read the same node,
+// a shared-memory broadcast.
+constexpr int kMaxSeg = 50;
 template <typename R>
 __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<R> &tab,
                                              int warp, int nw, int lane, int nt) {
   const int seg = (kGrid + nw - 1) / nw;
-  const int j0 = warp * seg, j1 = min(kGrid, j0 + seg);
-  if (lane >= nt || j0 >= kGrid) return;
+  const int j0 = warp * seg, len = min(kGrid, j0 + seg) - j0;
+  if (lane >= nt || len <= 0) return;
   const R k2 = sm.k2[lane], bc = sm.bc[lane], bs = sm.bs[lane];
   auto d1 = [&](int j) {
     const auto sc = tab.sc[j];
     return profile_d1<R>(k2, bc, bs, sc.x, sc.y);
   };
-  R left = d1(j0);
-#pragma unroll 5
-  for (int j = j0; j < j1; ++j) {
-    const R right = d1(j + 1 < kGrid ? j + 1 : 0);
-    if ((left < R(0)) != (right < R(0))) {
-      const int slot = atomicAdd(&sm.cnt[lane], 1);
-      if (slot < 4) {
-        sm.ju[lane][slot] = j;
-        sm.du[lane][slot] = left;
-        sm.duh[lane][slot] = right;
-      }
+  unsigned long long neg = 0;  // bit q: de/dth < 0 at node j0 + q (q = len: the next node)
+#pragma unroll
+  for (int q = 0; q <= kMaxSeg; ++q) {
+    if (q <= len) {
+      const int j = j0 + q;
+      neg |= static_cast<unsigned long long>(d1(j < kGrid ? j : 0) < R(0)) << q;
     }
-    left = right;
+  }
+  unsigned long long chg = (neg ^ (neg >> 1)) & ((1ull << len) - 1);
+  while (chg) {
+    const int q = __ffsll(static_cast<long long>(chg)) - 1;
+    chg &= chg - 1;
+    const int j = j0 + q;
+    const int slot = atomicAdd(&sm.cnt[lane], 1);
+    if (slot < 4) {
+      sm.ju[lane][slot] = j;
+      sm.du[lane][slot] = d1(j);
+      sm.duh[lane][slot] = d1(j + 1 < kGrid ? j + 1 : 0);
+    }
   }
 }
 
@@ -938,6 +948,12 @@ cudaError_t launch_mean(const MeanArgs &a, cudaStream_t st) {
   if (a.n_items <= 0) return cudaSuccess;
   const int blocks = (a.n_items + kMeanWarps - 1) / kMeanWarps;
   kmc_mean_kernel<<<blocks, kMeanWarps * 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_regen(const RegenArgs &a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  kmc_regen_kernel<<<(a.n + 127) / 128, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -132,6 +132,21 @@ struct MeanArgs {
   int32_t *err;
 };
 
+// Sample regeneration between loops (kmc_regen.cuh), one lysosome per launch.
+enum : int32_t { kRegenAxes = 1, kRegenPositions = 2 };
+struct RegenArgs {
+  int32_t off, n, lys, what;
+  uint32_t loop;
+  int32_t fp32;
+  unsigned long long seed;
+  double disorder;        // largest displacement, m
+  double len, cx, cy, cz; // length unit and frame origin of the lysosome, m
+  const double *nodes;    // [N][3] mean positions (those given at creation), m
+  void *pos, *axis, *m;   // float4 / dbl4 per NP, as built at creation
+  void *pos64;            // FP32 contexts: [N] dbl4 positions in FP64
+  double *pos_si;         // [N][3] out: the new positions, m
+};
+
 // Error bits written to the device error word.
 enum : int32_t {
   kErrTimeout = 1,     // an mbarrier wait gave up

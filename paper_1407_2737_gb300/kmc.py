@@ -21,7 +21,9 @@ KMC_OK, KMC_EINVAL, KMC_ENOMEM, KMC_ECUDA, KMC_ETIMEOUT, KMC_ESTATE, KMC_ECAPACI
     KMC_EIO = range(8)
 KMC_FP64_PLAIN, KMC_FP32_MIXED = 0, 1
 (KMC_READ_LOOP_H, KMC_READ_LOOP_M, KMC_READ_NP_ENERGY, KMC_READ_AREA, KMC_READ_SAR,
- KMC_READ_MOMENTS, KMC_READ_COUNTERS, KMC_READ_DHDIP) = range(8)
+ KMC_READ_MOMENTS, KMC_READ_COUNTERS, KMC_READ_DHDIP, KMC_READ_POSITIONS,
+ KMC_READ_AXES) = range(10)
+KMC_REGEN_AXES, KMC_REGEN_POSITIONS = 1, 2
 
 STATUS_NAMES = {0: "KMC_OK", 1: "KMC_EINVAL", 2: "KMC_ENOMEM", 3: "KMC_ECUDA",
                 4: "KMC_ETIMEOUT", 5: "KMC_ESTATE", 6: "KMC_ECAPACITY", 7: "KMC_EIO"}
@@ -30,7 +32,7 @@ STATUS_NAMES = {0: "KMC_OK", 1: "KMC_EINVAL", 2: "KMC_ENOMEM", 3: "KMC_ECUDA",
 EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
-           "kmc_shell_profile", "kmc_mean_run")
+           "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate")
 KMC_NOALLOC_MAX_N = 8192
 KMC_PHI_MAX_N = 64
 
@@ -86,6 +88,8 @@ def lib():
             L.kmc_mean_run.argtypes = [C.POINTER(kmc_lysosome), C.c_int32, _D, C.c_int32,
                                        C.c_double, C.c_int32, C.c_int32, C.c_int32, _D,
                                        C.c_int64, _I64]
+            L.kmc_regenerate.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.c_uint64,
+                                         C.c_uint32]
             L.kmc_destroy.argtypes = [vp]
             L.kmc_destroy.restype = None
             L.kmc_last_error.argtypes = []
@@ -175,6 +179,12 @@ def kmc_mean_run(lysosomes, mu0Hmax, f, steps_per_period, periods, discard_perio
     return out[:int(n.value)].reshape(len(lysosomes), -1)
 
 
+def kmc_regenerate(ctx, lys, what, disorder, seed, loop):
+    """Redraw axes and/or positions of lysosome `lys` (-1: all) on the device."""
+    _check(lib().kmc_regenerate(ctx.handle, int(lys), int(what), float(disorder),
+                                C.c_uint64(int(seed)), C.c_uint32(int(loop))))
+
+
 def kmc_set_stream(ctx, stream_handle):
     _check(lib().kmc_set_stream(ctx.handle, C.c_void_p(stream_handle or 0)))
 
@@ -198,7 +208,9 @@ def kmc_read(ctx, what, lys=0):
     buf = np.zeros(max(int(n.value), 1))
     _check(L.kmc_read(ctx.handle, int(what), int(lys), _dp(buf), len(buf), C.byref(n)))
     out = buf[:int(n.value)]
-    return out.reshape(-1, 3) if what == KMC_READ_MOMENTS else out
+    if what in (KMC_READ_MOMENTS, KMC_READ_POSITIONS, KMC_READ_AXES):
+        return out.reshape(-1, 3)
+    return out
 
 
 def kmc_debug_step(ctx, mu0Hext, t_step, seed, step, m_in):
