@@ -101,14 +101,17 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
 // ---------------------------------------------------------------------------
 // Pair loops over one staged tile. MASK: the tile holds some of the block's
 // own targets, so the self term (r2 = 0; distinct NPs are never coincident)
-// is dropped.
+// is dropped. The FP32 loop is a function of its own (not inlined) so that
+// its register allocation and schedule do not depend on the rest of the
+// kernel (measured: inlined, the loop lost 7 % of its throughput when the
+// update code after it changed).
 
 struct AccF32 {
   f2 ax, ay, az, bx, by, bz;  // packed partial sums (even / odd sources)
 };
 
 template <bool MASK>
-__device__ __forceinline__ void pair_tile_f32(const ulonglong2 *__restrict__ sp, int cnt,
+__device__ __noinline__ void pair_tile_f32(const ulonglong2 *__restrict__ sp, int cnt,
                                               int first, int stride, f2 X, f2 Y, f2 Z,
                                               AccF32 &acc) {
 #pragma unroll 2
@@ -208,13 +211,22 @@ __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<
     const auto sc = tab.sc[j];
     return profile_d1<R>(k2, bc, bs, sc.x, sc.y);
   };
-  unsigned long long neg = 0;  // bit q: de/dth < 0 at node j0 + q (q = len: the next node)
+  // bit q: de/dth < 0 at node j0 + q (q = len: the next node). Batches of 13
+  // independent evaluations keep about 40 registers in flight: a fully
+  // unrolled pass would hold 51 table entries and, inside this kernel's
+  // register budget, the compiler serialises it (measured 4x slower).
+  constexpr int kBatch = 13;
+  unsigned long long neg = 0;
+#pragma unroll 1
+  for (int q0 = 0; q0 <= len; q0 += kBatch) {
+    unsigned bits = 0;
 #pragma unroll
-  for (int q = 0; q <= kMaxSeg; ++q) {
-    if (q <= len) {
-      const int j = j0 + q;
-      neg |= static_cast<unsigned long long>(d1(j < kGrid ? j : 0) < R(0)) << q;
+    for (int u = 0; u < kBatch; ++u) {
+      int j = j0 + q0 + u;
+      j = j < kGrid ? j : j - kGrid;  // q0 + u <= kMaxSeg + kBatch - 1: one wrap at most
+      bits |= static_cast<unsigned>(d1(j) < R(0)) << u;
     }
+    neg |= static_cast<unsigned long long>(bits) << q0;
   }
   unsigned long long chg = (neg ^ (neg >> 1)) & ((1ull << len) - 1);
   while (chg) {
