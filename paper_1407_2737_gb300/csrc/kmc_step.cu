@@ -111,9 +111,10 @@ struct AccF32 {
 };
 
 template <bool MASK>
-__device__ __noinline__ void pair_tile_f32(const ulonglong2 *__restrict__ sp, int cnt,
-                                              int first, int stride, f2 X, f2 Y, f2 Z,
-                                              AccF32 &acc) {
+__device__ __noinline__ AccF32 pair_tile_f32(const ulonglong2 *__restrict__ sp, int cnt,
+                                              int first, int stride, f2 X, f2 Y, f2 Z) {
+  AccF32 acc;
+  acc.ax = acc.ay = acc.az = acc.bx = acc.by = acc.bz = 0ull;
 #pragma unroll 2
   for (int r = first; r < cnt; r += stride) {
     const ulonglong2 a = sp[3 * r];      // x0 x1 | y0 y1
@@ -140,6 +141,7 @@ __device__ __noinline__ void pair_tile_f32(const ulonglong2 *__restrict__ sp, in
     acc.by = fma2(q3, c.x, acc.by);
     acc.bz = fma2(q3, c.y, acc.bz);
   }
+  return acc;
 }
 
 __device__ __forceinline__ void pair_tile_f64(const dbl4 *__restrict__ sp,
@@ -681,13 +683,9 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
     const bool mask = (r0 <= own1) && (own0 < r0 + cnt);
-    AccF32 acc;
-    acc.ax = acc.ay = acc.az = acc.bx = acc.by = acc.bz = 0ull;
     const ulonglong2 *sp = buf + static_cast<size_t>(b) * tile * 3;
-    if (mask)
-      pair_tile_f32<true>(sp, cnt, warp, NW, X, Y, Z, acc);
-    else
-      pair_tile_f32<false>(sp, cnt, warp, NW, X, Y, Z, acc);
+    const AccF32 acc = mask ? pair_tile_f32<true>(sp, cnt, warp, NW, X, Y, Z)
+                            : pair_tile_f32<false>(sp, cnt, warp, NW, X, Y, Z);
     kahan_add(s6[0], c6[0], hsum(acc.ax));
     kahan_add(s6[1], c6[1], hsum(acc.ay));
     kahan_add(s6[2], c6[2], hsum(acc.az));
