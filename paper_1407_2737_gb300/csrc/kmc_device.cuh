@@ -192,6 +192,18 @@ struct GridTables {
   }
 };
 
+// de/dth of Eq. 2 at (sin, cos) = (s, c): s (2k c + b cos phi) - b sin phi c,
+// with its roundings spelled out so that every evaluation at a node gives the
+// same bits wherever the compiler places it (the scan tests the sign of values
+// that can sit within rounding of zero, and evaluates each node twice).
+__device__ __forceinline__ float profile_d1(float k2, float bc, float bs, float s, float c) {
+  return __fmaf_rn(s, __fmaf_rn(k2, c, bc), -__fmul_rn(bs, c));
+}
+__device__ __forceinline__ double profile_d1(double k2, double bc, double bs, double s,
+                                             double c) {
+  return __fma_rn(s, __fma_rn(k2, c, bc), -__dmul_rn(bs, c));
+}
+
 // Eq. 2 in a working plane: e = k sin^2 th - b cos(th - phi);
 // de/dth = 2k s c + b (s cos phi - c sin phi); d2e = 2k (c^2 - s^2) + b (c cos phi + s sin phi).
 template <typename R>
@@ -200,7 +212,7 @@ struct Profile {
   R k;
   R bc;  // b cos phi
   R bs;  // b sin phi
-  __device__ R d1(R s, R c) const { return s * fma(k2, c, bc) - bs * c; }
+  __device__ R d1(R s, R c) const { return profile_d1(k2, bc, bs, s, c); }
   __device__ R d2(R s, R c) const { return k2 * (c * c - s * s) + fma(bc, c, bs * s); }
   __device__ R e(R s, R c) const { return k * s * s - fma(bc, c, bs * s); }
 };

@@ -188,10 +188,6 @@ struct EpiShared {
   R th[kTargets][4], en[kTargets][4], sq[kTargets][4], cq[kTargets][4], off[kTargets][4];
 };
 
-template <typename R>
-__device__ __forceinline__ R profile_d1(R k2, R bc, R bs, R s, R c) {
-  return s * fma(k2, c, bc) - bs * c;
-}
 
 // Scan of step iv: lane = target, warp w = the w-th of nw contiguous segments
 // of the 200 nodes (nw >= 4, so a segment holds at most 50). A first pass
@@ -211,7 +207,7 @@ __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<
   const R k2 = sm.k2[lane], bc = sm.bc[lane], bs = sm.bs[lane];
   auto d1 = [&](int j) {
     const auto sc = tab.sc[j];
-    return profile_d1<R>(k2, bc, bs, sc.x, sc.y);
+    return profile_d1(k2, bc, bs, sc.x, sc.y);
   };
   // bit q: de/dth < 0 at node j0 + q (q = len: the next node). Batches of 13
   // independent evaluations keep about 40 registers in flight: a fully
@@ -242,6 +238,36 @@ __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<
       sm.duh[lane][slot] = d1(j + 1 < kGrid ? j + 1 : 0);
     }
   }
+}
+
+// FP32 rounding can flip the sign of de/dth at a node where it nearly vanishes
+// (a near-double root just before a well disappears), which adds two sign
+// changes. A target whose FP32 scan counts more than four is scanned again by
+// one thread with the profile evaluated in FP64 at every node, and those
+// brackets (at most four, in grid order) replace the FP32 ones. Kept out of
+// line: inlined, this rarely taken FP64 code cost the pair loop 7 %.
+__device__ __noinline__ void rescan_fp64(EpiShared<float> &sm, int t) {
+  const double k2 = sm.k2[t], bc = sm.bc[t], bs = sm.bs[t];
+  auto d1 = [&](int j) {
+    const double2 sc = g_sc_d[j];
+    return profile_d1(k2, bc, bs, sc.x, sc.y);
+  };
+  const double d_first = d1(0);
+  double left = d_first;
+  int cnt = 0;
+  for (int j = 0; j < kGrid; ++j) {
+    const double right = (j + 1 < kGrid) ? d1(j + 1) : d_first;
+    if ((left < 0.0) != (right < 0.0)) {
+      if (cnt < 4) {
+        sm.ju[t][cnt] = j;
+        sm.du[t][cnt] = static_cast<float>(left);
+        sm.duh[t][cnt] = static_cast<float>(right);
+      }
+      ++cnt;
+    }
+    left = right;
+  }
+  sm.cnt[t] = cnt;
 }
 
 // Newton refinement of bracket q (of nb) of target t (one thread); the result
@@ -516,6 +542,13 @@ __device__ __forceinline__ void block_update(
   // iv) scan: lanes over targets, warps over segments of the grid
   segment_scan<R>(sm, tab, warp, nw, lane, nt);
   __syncthreads();
+  if constexpr (MIXED) {
+    const bool noisy = warp == 0 && lane < nt && sm.cnt[lane] > 4;
+    if (__syncthreads_or(noisy)) {
+      if (noisy) rescan_fp64(sm, lane);
+      __syncthreads();
+    }
+  }
   // iv) Newton: one bracket per thread
   for (int x = threadIdx.x; x < 4 * nt; x += blockDim.x) {
     const int t = x >> 2, q = x & 3;
