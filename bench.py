@@ -39,6 +39,9 @@ WORKLOAD = ("single lysosome N=2000 x 8 seeds, d=14 nm, Keff=2e4 J/m^3, Ms=1e6 A
             "c=10%, T=300 K, tau0=1e-10 s, mu0Hmax=20 mT, f=100 kHz, "
             "200 steps/period x 20 periods (5 discarded)")
 FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
+# DRAM bytes (read + write) of one launch of the step kernel at this workload in
+# the 4-warp, 256-record shape, from one ncu capture of the committed kernel
+STEP_DRAM_BYTES = 1.629e6
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -334,11 +337,14 @@ def main():
             "pair_interactions_per_s": world * pairs_per_launch * n_steps * args.steps / t_total,
             "sar_W_per_g": float(np.mean(sar32)) / 1e3,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": STEP_DRAM_BYTES if warps == 4 and tile == 256 else None,
                          "kernel": "kmc_step_f32<%d>" % warps,
                          "note": "FP32 pipe: 30 flops per ordered pair; launch time = timed "
                                  "region / step launches (includes graph gaps); peak = "
-                                 "152 SM x 128 lanes x 2 x 2070 MHz"},
+                                 "152 SM x 128 lanes x 2 x 2070 MHz (nominal; FFMA chains "
+                                 "measured 74.6 TFLOP/s); traffic = ncu DRAM bytes of one "
+                                 "launch of this shape"},
             "fp64_plain": fp64,
             "e2e": {"value": world * units_per_step * args.steps / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
