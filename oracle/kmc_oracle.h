@@ -22,8 +22,10 @@
  *   np_update, step, run .... pinned (Fig. 1b example, Neel statistics,
  *                              two-state equilibrium, T = 0 Stoner-Wohlfarth
  *                              limits, A/K_eff = 2)
- *   per-NP split of the loop area (E_diss of one NP) .... parity unpinned:
- *                              only the lysosome total is fixed by the paper.
+ *   per-NP split of the loop area (E_diss of one NP): pinned for isolated NPs
+ *                              (discrete square Stoner-Wohlfarth loops); for
+ *                              interacting NPs parity unpinned: only the
+ *                              lysosome total is fixed by the paper.
  *   mean_run (Ref. [8] mode) . pinned (two-state Boltzmann equilibrium)
  *   run: dHdip (Eq. 6) ....... pinned (closed forms for a saturated pair,
  *                              re-derivation from a stepped trajectory)

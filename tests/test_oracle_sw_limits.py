@@ -85,3 +85,29 @@ def test_sar_conversion(golden_dir):
     v = read_paper_values(golden_dir)
     s = oracle.sar(v["sar_area_J_m3"], v["sar_f_Hz"], v["sar_rho_kg_m3"])  # W/kg
     assert abs(s / 1000.0 - v["sar_W_per_g"]) < 0.5
+
+
+def test_per_np_energy_of_isolated_square_loops():
+    # The per-NP split of the loop area (reading 12) in the limit where every
+    # reading agrees: isolated NPs, axes along +-z, T = 0. Each moment starts at
+    # m_z = +1, drops to -1 at the first step of the descending half whose field
+    # lies beyond -H_K and returns at the first ascending step beyond +H_K, so
+    # per period E_i = mu0 M_S V (H_up * 2 + H_down * (-2)) with those two field
+    # samples.
+    K = 1.3e4
+    BK = 2 * K / MS
+    lys = _far_apart([[0, 0, 1.0], [0, 0, -1.0], [0, 0, 1.0]], 16e-9, Keff=K, T=0.0,
+                     tau0=1e-10)
+    S, periods, discard = 400, 3, 1
+    Hmax = 1.72 * BK  # every sample at least 1 % away from +-H_K
+    out = oracle.run(lys, 0, Hmax, 1e5, S, periods, discard, seed=0)
+    H, M = out["loop_H"][:S], out["loop_M"][:S]
+    # no field sample sits where the grid could miss the vanishing well
+    assert np.all(np.abs(np.abs(H) / BK - 1) > 1e-3)
+    k_down = np.where(M < 0)[0][0]
+    k_up = k_down + np.where(M[k_down:] > 0)[0][0]
+    assert H[k_down] < -BK and H[k_down - 1] >= -BK
+    assert H[k_up] > BK and H[k_up - 1] <= BK
+    E = MS * lys.vol * 2.0 * (H[k_up] - H[k_down])
+    nper = periods - discard
+    np.testing.assert_allclose(out["E_diss"] / nper, E, rtol=1e-12)
