@@ -237,6 +237,15 @@ enum { KMC_REGEN_AXES = 1, KMC_REGEN_POSITIONS = 2 };
 kmc_status kmc_regenerate(kmc_ctx *ctx, int32_t lys, int32_t what, double disorder,
                           uint64_t seed, uint32_t loop);
 
+/* Failure-detection test hook (FP64 contexts). Launches one step whose every
+ * staged copy waits for 16 bytes more than it delivers, so each block's bounded
+ * wait runs out (after 1 ms instead of 2 s) and reports through the device
+ * error word; no kernel faults, traps or hangs, and the blocks stop before
+ * writing any state. Returns what such a stall returns, KMC_ETIMEOUT, then
+ * clears the error so the context stays usable (the next kmc_run proceeds as
+ * if the call had not been made). KMC_EINVAL on an FP32 context. */
+kmc_status kmc_debug_stall(kmc_ctx *ctx);
+
 /* Frees the context and its device memory. NULL-safe. */
 void kmc_destroy(kmc_ctx *ctx);
 

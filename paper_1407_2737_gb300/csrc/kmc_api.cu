@@ -1338,6 +1338,29 @@ kmc_status kmc_regenerate(kmc_ctx *c, int32_t lys, int32_t what, double disorder
   return KMC_OK;
 }
 
+kmc_status kmc_debug_stall(kmc_ctx *c) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (c->fp32) return fail(KMC_EINVAL, "the stall hook runs on FP64 contexts");
+  KMC_TRY(check_device_error(c));
+  KMC_TRY(ensure_shape(c));
+  RunState rs{c->step_global, -1, 0};
+  KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  StepArgs a = base_args(c);
+  a.S = 1;
+  a.n_rec = 1;
+  a.cos_k = 1.0;
+  a.stall_tx = 16;
+  a.stall_wait_ns = 1000000ull;  // 1 ms
+  KMC_CUDA(kmc::launch_step(c->fp32, c->shape.warps, c->shape.tile, a, c->n_items, c->stream));
+  const kmc_status st = check_device_error(c);  // KMC_ETIMEOUT when the waits ran out
+  // the blocks stopped before any write: clear the flag, the context stays usable
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  return st == KMC_OK ? fail(KMC_ESTATE, "the stalled waits did not run out") : st;
+}
+
 kmc_status kmc_info(const kmc_ctx *c, int64_t *n_total, int32_t *n_lys, int64_t *global_step) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (n_total) *n_total = c->N;

@@ -88,15 +88,15 @@ __device__ __forceinline__ void grid_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Waits for phase `parity` of `bar` for at most ~2 s; returns false (and sets
-// the error word) if the copy never completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  int32_t *err) {
+// Waits for phase `parity` of `bar` for at most limit_ns (2 s); returns false
+// (and sets the error word) if the copy never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int32_t *err,
+                                                  unsigned long long limit_ns = 2000000000ull) {
   for (int i = 0; i < 64; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > 2000000000ull) {
+    if (global_ns() - t0 > limit_ns) {
       atomicOr(err, kErrTimeout);
       return false;
     }

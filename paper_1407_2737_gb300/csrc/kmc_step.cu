@@ -642,7 +642,8 @@ __device__ __forceinline__ void block_update(
 // never landed (error word set); the decision is block-uniform.
 template <typename Issue, typename Body>
 __device__ __forceinline__ bool staged_loop(int ntiles, uint64_t *bar, int32_t *err,
-                                            Issue issue, Body body) {
+                                            Issue issue, Body body,
+                                            unsigned long long limit_ns = 2000000000ull) {
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -655,7 +656,7 @@ __device__ __forceinline__ bool staged_loop(int ntiles, uint64_t *bar, int32_t *
   }
   for (int t = 0; t < ntiles; ++t) {
     const int b = t & 1;
-    const bool ok = mbar_wait_bounded(&bar[b], (t >> 1) & 1, err);
+    const bool ok = mbar_wait_bounded(&bar[b], (t >> 1) & 1, err, limit_ns);
     if (ok) body(b, t);
     // every warp is done with buffer b; a failed wait anywhere stops all
     if (!__syncthreads_and(ok)) return false;
@@ -834,7 +835,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
     const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(dbl4);
-    mbar_expect_tx(&bar[b], 2 * bytes);
+    mbar_expect_tx(&bar[b], 2 * bytes + a.stall_tx);
     bulk_g2s(spos + b * tile, gpos + r0, bytes, &bar[b]);
     bulk_g2s(smu + b * tile, gmu + r0, bytes, &bar[b]);
   };
@@ -843,7 +844,9 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
     const int cnt = min(tile, it.j1 - r0);
     pair_tile_f64(spos + b * tile, smu + b * tile, cnt, warp, NW, pi.x, pi.y, pi.z, acc);
   };
-  if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
+  if (!staged_loop(ntiles, bar, a.err, issue, body,
+                   a.stall_tx ? a.stall_wait_ns : 2000000000ull))
+    return;
 
   double *wp = reinterpret_cast<double *>(dyn);  // [NW][6][32]
 #pragma unroll

@@ -103,6 +103,12 @@ struct StepArgs {
   DebugOut dbg;
   int32_t debug;
   int32_t pad;
+  // failure-detection test hook (FP64 kernel): every tile's expected byte
+  // count exceeds its copies by stall_tx, so its wait can only run out, after
+  // stall_wait_ns; 0 in every production launch
+  uint32_t stall_tx;
+  uint32_t pad2;
+  unsigned long long stall_wait_ns;
 };
 
 // Ref. [8] mode (kmc_mean.cuh): per lysosome, per work item, arguments.

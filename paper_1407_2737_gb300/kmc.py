@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "KMC_OK", 1: "KMC_EINVAL", 2: "KMC_ENOMEM", 3: "KMC_ECUDA",
 EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
-           "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate")
+           "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall")
 KMC_NOALLOC_MAX_N = 8192
 KMC_PHI_MAX_N = 64
 
@@ -90,6 +90,7 @@ def lib():
                                        C.c_int64, _I64]
             L.kmc_regenerate.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.c_uint64,
                                          C.c_uint32]
+            L.kmc_debug_stall.argtypes = [vp]
             L.kmc_destroy.argtypes = [vp]
             L.kmc_destroy.restype = None
             L.kmc_last_error.argtypes = []
@@ -183,6 +184,12 @@ def kmc_regenerate(ctx, lys, what, disorder, seed, loop):
     """Redraw axes and/or positions of lysosome `lys` (-1: all) on the device."""
     _check(lib().kmc_regenerate(ctx.handle, int(lys), int(what), float(disorder),
                                 C.c_uint64(int(seed)), C.c_uint32(int(loop))))
+
+
+def kmc_debug_stall(ctx):
+    """Failure-detection hook: raises KmcError(KMC_ETIMEOUT) when the stalled
+    waits run out as designed."""
+    _check(lib().kmc_debug_stall(ctx.handle))
 
 
 def kmc_set_stream(ctx, stream_handle):
