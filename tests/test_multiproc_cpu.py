@@ -45,3 +45,47 @@ def test_two_ranks_gloo():
         assert t == 2.0                     # slowest rank's time
         assert value == 2 * 6.4e7 / 2.0      # all units over that time
         assert (r, w) == (rank, world)
+
+
+def _failing_worker(rank, world, port, out):
+    import datetime
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    import bench
+    if rank == 1:
+        out[rank] = "raised"
+        raise RuntimeError("rank 1 fails before the timing reduction")
+    try:
+        bench.max_over_ranks_of(1.0, world, "cpu")
+        out[rank] = "no error"
+    except Exception as e:  # the lost peer surfaces as an error, not a hang
+        out[rank] = "error: " + type(e).__name__
+
+
+def test_a_failed_rank_ends_the_others_collective():
+    # failure injected on the host: one rank raises, the survivor's next
+    # collective ends with an error within the process-group timeout
+    world = 2
+    ctx = mp.get_context("spawn")
+    with mp.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_failing_worker, args=(r, world, port, out))
+                 for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+        alive = [p.is_alive() for p in procs]
+        for p in procs:
+            if p.is_alive():
+                p.kill()
+        res = dict(out)
+    assert not any(alive)
+    assert procs[1].exitcode != 0
+    assert res.get(1) == "raised"
+    assert res.get(0, "").startswith("error")
