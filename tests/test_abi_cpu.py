@@ -66,3 +66,12 @@ def test_no_device_is_an_error_not_a_fallback(L):
     with pytest.raises(kmc.KmcError) as e:
         kmc.kmc_create([lys])
     assert e.value.status == kmc.KMC_ECUDA
+
+
+def test_header_constants_match_the_binding():
+    text = "".join(open(os.path.join(ROOT, "include", fn)).read()
+                   for fn in sorted(os.listdir(os.path.join(ROOT, "include"))) if fn.endswith(".h"))
+    defs = re.findall(r"#define\s+(KMC_\w+)\s+(\d+)", text)
+    assert len(defs) >= 2
+    for name, value in defs:
+        assert getattr(kmc, name) == int(value), name
