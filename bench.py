@@ -39,9 +39,10 @@ WORKLOAD = ("single lysosome N=2000 x 8 seeds, d=14 nm, Keff=2e4 J/m^3, Ms=1e6 A
             "c=10%, T=300 K, tau0=1e-10 s, mu0Hmax=20 mT, f=100 kHz, "
             "200 steps/period x 20 periods (5 discarded)")
 FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
-# DRAM bytes (read + write) of one launch of the step kernel at this workload in
-# the 4-warp, 256-record shape, from one ncu capture of the committed kernel
-STEP_DRAM_BYTES = 1.629e6
+# DRAM bytes (read + write) of one kMC step at this workload (8 chains, one
+# launch each), by launch shape (warps, tile, chunk): 8 x the mean over 16
+# serialised ncu captures of the committed kernel
+STEP_DRAM_BYTES = {(4, 256, 512): 2.186e6, (4, 256, 1024): 2.153e6}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -268,8 +269,11 @@ def main():
     value = job_throughput(units_per_step * args.steps, t_total, world)
     ms_per_step = 1e3 * t_total / args.steps
     sar32 = [kmc.kmc_read(ctx, kmc.KMC_READ_SAR, l)[0] for l in range(len(lyss))]
-    launches_per_step = 1 + run["periods"] * (run["S"] + 1)
-    # roofline of the fused step kernel: one launch per kMC step
+    # one step = one step-kernel launch per chain (equal lysosomes: one chain
+    # each, up to KMC_MAX_CHAINS), run concurrently; one period advance
+    chains = min(len(lyss), kmc.KMC_MAX_CHAINS)
+    launches_per_step = 1 + run["periods"] * (run["S"] * chains + 1)
+    # roofline of the fused step kernel over one kMC step (all chains' launches)
     launch_s = t_total / (args.steps * n_steps)
     achieved = FLOPS_PER_PAIR * pairs_per_launch / launch_s / 1e12
     peak = fp32_peak_tflops()
@@ -331,20 +335,22 @@ def main():
             "dtype": "f32-mixed", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "KMC_FP32_MIXED",
                        "kmc_steps_per_bench_step": n_steps, "particles": n_np,
-                       "launch": {"warps": warps, "tile": tile, "chunk": chunk},
+                       "launch": {"warps": warps, "tile": tile, "chunk": chunk,
+                                  "chains": chains},
                        "l2": "256 MB buffer written between timed steps (state < L2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "pair_interactions_per_s": world * pairs_per_launch * n_steps * args.steps / t_total,
             "sar_W_per_g": float(np.mean(sar32)) / 1e3,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": STEP_DRAM_BYTES if warps == 4 and tile == 256 else None,
+                         "traffic": STEP_DRAM_BYTES.get((warps, tile, chunk)),
                          "kernel": "kmc_step_f32<%d>" % warps,
-                         "note": "FP32 pipe: 30 flops per ordered pair; launch time = timed "
-                                 "region / step launches (includes graph gaps); peak = "
-                                 "152 SM x 128 lanes x 2 x 2070 MHz (nominal; FFMA chains "
-                                 "measured 74.6 TFLOP/s); traffic = ncu DRAM bytes of one "
-                                 "launch of this shape"},
+                         "note": "FP32 pipe: 30 flops per ordered pair; a kMC step is one "
+                                 "launch per chain, the chains' launches concurrent; step "
+                                 "time = timed region / kMC steps (includes graph gaps); "
+                                 "peak = 152 SM x 128 lanes x 2 x 2070 MHz (nominal; FFMA "
+                                 "chains measured 74.6 TFLOP/s); traffic = ncu DRAM bytes of "
+                                 "one kMC step (all chains) at this shape"},
             "fp64_plain": fp64,
             "e2e": {"value": world * units_per_step * args.steps / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -122,7 +122,12 @@ kmc_status kmc_set_stream(kmc_ctx *ctx, void *cuda_stream);
  * Moments and the global step counter carry over between runs; the loop,
  * energy and counter outputs are those of the latest run. The draw of NP i of
  * lysosome l at global step s is Philox4x32-10 with key (seed low, seed high)
- * and counter (s low, s high, i, l). */
+ * and counter (s low, s high, i, l). Lysosomes do not interact, so a batch
+ * advances as up to KMC_MAX_CHAINS independent chains of step kernels (sets of
+ * whole lysosomes of about equal work; min(n_lys, KMC_MAX_CHAINS) chains when
+ * the lysosomes are of one size), joined once per period; each lysosome's
+ * results are those it gets alone under the same launch shape, bit for bit. */
+#define KMC_MAX_CHAINS 8
 kmc_status kmc_run(kmc_ctx *ctx, const double *mu0Hmax, int32_t n_amp, double f,
                    int32_t steps_per_period, int32_t periods, int32_t discard_periods,
                    uint64_t seed);

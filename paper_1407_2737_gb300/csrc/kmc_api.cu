@@ -31,6 +31,11 @@ namespace {
 constexpr double kMu0 = 4.0e-7 * 3.14159265358979323846;
 constexpr double kKB = 1.380649e-23;
 constexpr double kPi = 3.14159265358979323846;
+// Lysosomes are independent: a run advances up to kMaxChains disjoint sets of
+// them as parallel branches of the period graph, each branch one step kernel
+// per step, so one set's update phase overlaps the pair sums of the others
+// instead of every step ending in a device-wide barrier.
+constexpr int kMaxChains = KMC_MAX_CHAINS;
 
 thread_local std::string g_last_error;
 
@@ -173,6 +178,9 @@ struct kmc_ctx {
   int32_t *d_arrivals = nullptr;
   size_t arrivals_cap = 0;
   Shape items_shape;  // shape the items were built for
+  std::vector<int> chain_cut;  // chain q runs items chain_cut[q] .. chain_cut[q + 1] - 1
+  cudaStream_t chain_st[kMaxChains] = {};  // branches 1.. of the period graph
+  cudaEvent_t chain_ev[kMaxChains] = {};   // [0] fork, [q] join of branch q
   // debug outputs, allocated on first use
   double *d_dbg = nullptr;
   int32_t *d_dbg_flags = nullptr;
@@ -286,7 +294,11 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   KMC_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
   KMC_CUDA(kmc::step_blocks_per_sm(c->fp32, sh.warps, sh.tile, &per_sm));
   int groups = 0;
-  const std::vector<Item> items = build_items(c, sh.chunk, per_sm, n_sms, &groups);
+  // with several chains the lysosomes' kernels interleave on the SMs, and the
+  // split that evens out one device-wide wave does not apply
+  const int chains = std::min(c->n_lys, kMaxChains);
+  const std::vector<Item> items =
+      build_items(c, sh.chunk, per_sm, chains > 1 ? 0 : n_sms, &groups);
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   if (items.size() > c->items_cap) {
     if (c->d_items) cudaFree(c->d_items);
@@ -314,6 +326,19 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   KMC_CUDA(cudaMemset(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap));
   c->n_items = static_cast<int>(items.size());
   c->items_shape = sh;
+  // chains: cut the item list (lysosome by lysosome, largest first) at
+  // lysosome boundaries into runs of about equal source-record counts
+  long long total = 0, acc = 0;
+  for (const Item &it : items) total += it.j1 - it.j0;
+  c->chain_cut.assign(1, 0);
+  for (size_t u = 0; u < items.size(); ++u) {
+    acc += items[u].j1 - items[u].j0;
+    const bool boundary = u + 1 == items.size() || items[u + 1].l != items[u].l;
+    const long long q = static_cast<long long>(c->chain_cut.size());
+    if (boundary && q < chains && acc * chains >= total * q)
+      c->chain_cut.push_back(static_cast<int>(u + 1));
+  }
+  if (c->chain_cut.back() != c->n_items) c->chain_cut.push_back(c->n_items);
   return KMC_OK;
 }
 
@@ -388,6 +413,64 @@ bool shape_ok(const kmc_ctx *c, const Shape &s) {
   return true;
 }
 
+// Captures `steps` step launches of shape sh as a graph: the chains of the
+// current items as parallel branches (fork on c->stream, join back onto it),
+// step k of a run when `period` (k_local = k, then the period advance), else
+// `steps` repeats of one unrecorded step.
+kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int steps, bool period,
+                         cudaGraphExec_t *out) {
+  *out = nullptr;
+  const int n_chains = static_cast<int>(c->chain_cut.size()) - 1;
+  for (int q = 0; q < n_chains; ++q) {
+    if (q > 0 && !c->chain_st[q])
+      KMC_CUDA(cudaStreamCreateWithFlags(&c->chain_st[q], cudaStreamNonBlocking));
+    if (!c->chain_ev[q])
+      KMC_CUDA(cudaEventCreateWithFlags(&c->chain_ev[q], cudaEventDisableTiming));
+  }
+  cudaGraph_t g = nullptr;
+  KMC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaSuccess;
+  // fork: branch 0 stays on the capturing stream, branches 1.. wait for it
+  if (n_chains > 1) ce = cudaEventRecord(c->chain_ev[0], c->stream);
+  for (int q = 1; q < n_chains && ce == cudaSuccess; ++q)
+    ce = cudaStreamWaitEvent(c->chain_st[q], c->chain_ev[0], 0);
+  const bool split = c->partial_cap >= static_cast<size_t>(c->n_items);
+  for (int q = 0; q < n_chains && ce == cudaSuccess; ++q) {
+    cudaStream_t st = q == 0 ? c->stream : c->chain_st[q];
+    const int u0 = c->chain_cut[q];
+    StepArgs b = a;
+    b.items = c->d_items + u0;
+    if (split) b.partial = c->d_partial + static_cast<size_t>(u0) * 12 * kmc::kTargets;
+    for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
+      if (period) {
+        b.k_local = k;
+        b.cos_k = std::cos(2.0 * kPi * k / steps);
+      }
+      ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, b, c->chain_cut[q + 1] - u0, st, true);
+    }
+  }
+  // join, then the period advance
+  for (int q = 1; q < n_chains && ce == cudaSuccess; ++q) {
+    ce = cudaEventRecord(c->chain_ev[q], c->chain_st[q]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(c->stream, c->chain_ev[q], 0);
+  }
+  if (ce == cudaSuccess && period) ce = kmc::launch_advance(c->d_rs, steps, c->stream);
+  const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+  if (ce != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(KMC_ECUDA, "graph capture failed: %s",
+                cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+  }
+  const cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    *out = nullptr;
+    return fail(KMC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+  }
+  return KMC_OK;
+}
+
 // Times one candidate shape on the current state (restored by the caller).
 // Returns milliseconds per step, or a negative value on error.
 float time_shape(kmc_ctx *c, const Shape &s) {
@@ -396,27 +479,40 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   a.cos_k = 1.0;
   a.S = 1;
   a.n_rec = 1;
+  // several chains share the SMs, so a shape is timed the way a run executes
+  // it: a graph of a few steps of every chain
+  const bool chained = c->chain_cut.size() > 2;
+  double pairs = 0.0;  // per step; short steps are timed over more of them
+  for (int x : c->n) pairs += static_cast<double>(x) * x;
+  const int graph_steps = pairs < 2e8 ? 8 : 2;
+  cudaGraphExec_t gx = nullptr;
+  if (chained && capture_steps(c, a, s, graph_steps, false, &gx) != KMC_OK) return -1.f;
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
-  if (cudaEventCreate(&e1) != cudaSuccess) {
-    cudaEventDestroy(e0);
+  if (cudaEventCreate(&e0) != cudaSuccess) {
+    if (gx) cudaGraphExecDestroy(gx);
     return -1.f;
   }
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    if (gx) cudaGraphExecDestroy(gx);
+    return -1.f;
+  }
+  auto one = [&]() {
+    return gx ? cudaGraphLaunch(gx, c->stream)
+              : kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true);
+  };
   float ms = -1.f;
   bool ok = true;
-  for (int r = 0; r < 2 && ok; ++r)
-    ok = kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true) ==
-         cudaSuccess;
-  const int reps = 5;
+  for (int r = 0; r < 2 && ok; ++r) ok = one() == cudaSuccess;
+  const int reps = gx ? 3 : 5;
   if (ok) ok = cudaEventRecord(e0, c->stream) == cudaSuccess;
-  for (int r = 0; r < reps && ok; ++r)
-    ok = kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true) ==
-         cudaSuccess;
+  for (int r = 0; r < reps && ok; ++r) ok = one() == cudaSuccess;
   if (ok) ok = cudaEventRecord(e1, c->stream) == cudaSuccess;
   if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
-  if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms /= reps;
+  if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms /= reps * (gx ? graph_steps : 1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (gx) cudaGraphExecDestroy(gx);
   return ok ? ms : -1.f;
 }
 
@@ -502,6 +598,10 @@ void free_ctx(kmc_ctx *c) {
                   c->d_partial, c->d_arrivals, c->d_dbg, c->d_dbg_flags};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  for (int q = 0; q < kMaxChains; ++q) {
+    if (c->chain_st[q]) cudaStreamDestroy(c->chain_st[q]);
+    if (c->chain_ev[q]) cudaEventDestroy(c->chain_ev[q]);
+  }
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
@@ -803,28 +903,7 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
     a.S = S;
     a.discard = discard;
     a.n_rec = static_cast<int>(std::max(n_rec, 1ll));
-    cudaGraph_t g = nullptr;
-    KMC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaSuccess;
-    for (int k = 0; k < S && ce == cudaSuccess; ++k) {
-      a.k_local = k;
-      a.cos_k = std::cos(2.0 * kPi * k / S);
-      ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, a, c->n_items, c->stream, true);
-    }
-    if (ce == cudaSuccess) ce = kmc::launch_advance(c->d_rs, S, c->stream);
-    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
-    if (ce != cudaSuccess || ee != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      return fail(KMC_ECUDA, "graph capture failed: %s",
-                  cudaGetErrorString(ce != cudaSuccess ? ce : ee));
-    }
-    const cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
-    cudaGraphDestroy(g);
-    if (ie != cudaSuccess) {
-      c->gexec = nullptr;
-      return fail(KMC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
-    }
+    KMC_TRY(capture_steps(c, a, sh, S, true, &c->gexec));
     c->g_S = S;
     c->g_discard = discard;
     c->g_nrec = static_cast<int>(n_rec);

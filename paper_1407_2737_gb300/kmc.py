@@ -34,6 +34,7 @@ EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
            "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall")
 KMC_NOALLOC_MAX_N = 8192
+KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
 KMC_PHI_MAX_N = 64
 
 

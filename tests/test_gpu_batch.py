@@ -35,3 +35,23 @@ def test_batched_lysosomes_each_at_its_own_amplitude():
     flips = sum(kmc.kmc_read(ctx, kmc.KMC_READ_COUNTERS, l)[0] for l in range(len(lyss)))
     assert flips > 0
     kmc.kmc_destroy(ctx)
+
+
+def test_a_lysosome_in_a_chained_batch_matches_it_alone():
+    """A batch runs its lysosomes as parallel chains of step kernels; each
+    lysosome's trajectory is the one it has alone (same index 0, same shape)."""
+    a = inputs.make_lysosome(100, 12e-9, 0.05, seed=21)
+    others = [inputs.make_lysosome(333, 14e-9, 0.08, seed=22),
+              inputs.make_lysosome(57, 10e-9, 0.05, seed=23),
+              inputs.make_lysosome(250, 12e-9, 0.05, seed=24)]
+    out = []
+    for lyss in ([a], [a] + others):
+        ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+        kmc.kmc_tuning(ctx, 4, 64, 0)
+        kmc.kmc_run(ctx, 0.02, 1e5, 40, 3, 1, 9)
+        out.append([kmc.kmc_read(ctx, w, 0) for w in (kmc.KMC_READ_LOOP_M, kmc.KMC_READ_MOMENTS,
+                                                       kmc.KMC_READ_NP_ENERGY,
+                                                       kmc.KMC_READ_COUNTERS)])
+        kmc.kmc_destroy(ctx)
+    for x, y in zip(*out):
+        assert np.array_equal(x, y)
