@@ -482,9 +482,12 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   // several chains share the SMs, so a shape is timed the way a run executes
   // it: a graph of a few steps of every chain
   const bool chained = c->chain_cut.size() > 2;
-  double pairs = 0.0;  // per step; short steps are timed over more of them
+  // per step; short steps are timed over more of them, so that the chains
+  // reach their steady interleaving (a short graph favours small blocks,
+  // which fill and drain the SMs faster at the graph's ends)
+  double pairs = 0.0;
   for (int x : c->n) pairs += static_cast<double>(x) * x;
-  const int graph_steps = pairs < 2e8 ? 8 : 2;
+  const int graph_steps = pairs < 2e8 ? 32 : 2;
   cudaGraphExec_t gx = nullptr;
   if (chained && capture_steps(c, a, s, graph_steps, false, &gx) != KMC_OK) return -1.f;
   cudaEvent_t e0, e1;
@@ -504,7 +507,7 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   float ms = -1.f;
   bool ok = true;
   for (int r = 0; r < 2 && ok; ++r) ok = one() == cudaSuccess;
-  const int reps = gx ? 3 : 5;
+  const int reps = gx ? 2 : 5;
   if (ok) ok = cudaEventRecord(e0, c->stream) == cudaSuccess;
   for (int r = 0; r < reps && ok; ++r) ok = one() == cudaSuccess;
   if (ok) ok = cudaEventRecord(e1, c->stream) == cudaSuccess;
