@@ -289,6 +289,8 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   if (c->items_shape.warps == sh.warps && c->items_shape.tile == sh.tile &&
       c->items_shape.chunk == sh.chunk && c->d_items)
     return KMC_OK;
+  // until the rebuild completes, no shape's items are valid
+  c->items_shape = Shape();
   int dev = 0, n_sms = 0, per_sm = 0;
   KMC_CUDA(cudaGetDevice(&dev));
   KMC_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -300,8 +302,12 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   const std::vector<Item> items =
       build_items(c, sh.chunk, per_sm, chains > 1 ? 0 : n_sms, &groups);
   KMC_CUDA(cudaStreamSynchronize(c->stream));
+  // a failed allocation leaves the buffer empty (null, capacity 0), so a
+  // later call allocates again instead of using a stale capacity
   if (items.size() > c->items_cap) {
     if (c->d_items) cudaFree(c->d_items);
+    c->d_items = nullptr;
+    c->items_cap = 0;
     KMC_TRY(dalloc(&c->d_items, sizeof(Item) * items.size()));
     c->items_cap = items.size();
     drop_graph(c);
@@ -311,12 +317,16 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   const size_t need_partial = split ? items.size() : 1;
   if (need_partial > c->partial_cap) {
     if (c->d_partial) cudaFree(c->d_partial);
+    c->d_partial = nullptr;
+    c->partial_cap = 0;
     KMC_TRY(dalloc(&c->d_partial, sizeof(float) * 12 * kmc::kTargets * need_partial));
     c->partial_cap = need_partial;
     drop_graph(c);
   }
   if (static_cast<size_t>(groups) > c->arrivals_cap) {
     if (c->d_arrivals) cudaFree(c->d_arrivals);
+    c->d_arrivals = nullptr;
+    c->arrivals_cap = 0;
     KMC_TRY(dalloc(&c->d_arrivals, sizeof(int32_t) * groups));
     c->arrivals_cap = groups;
     drop_graph(c);
