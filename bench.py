@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -83,7 +84,9 @@ class Clocks:
 
     def __init__(self, device_uuid=None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        # raw samples (the JSON line carries their summary): KMC_CLOCKS_DIR, else a temp dir
+        out = os.environ.get("KMC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, "clocks_%d.csv" % os.getpid())
         self.uuid = device_uuid
 
     def __enter__(self):

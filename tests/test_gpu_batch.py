@@ -1,4 +1,4 @@
-"""A batch shaped like the paper's survey workload (lognormal NP counts, d, K_eff,
+"""A batch shaped like the paper's batched workload (lognormal NP counts, d, K_eff,
 concentration and field amplitude drawn per lysosome) through one context, with
 each lysosome at its own amplitude.
 
