@@ -16,6 +16,14 @@ same seeds, the roofline of the fused step kernel (FP32 pipe) and the FP64
 oracle timed on the host cores (cpu_baseline).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--config c0|c1|c2|c3|c4]
+
+--config picks another of the paper-shaped workloads for the same measurement
+(c1, the 8 x 2000-NP workload above, is the default and the headline line):
+c0 one 100-NP lysosome; c2 one 8000-NP lysosome at 5 % and 40 mT; c3 512
+lysosomes of lognormal size, each with its own parameters and amplitude; c4 one
+50 000-NP lysosome. c3 and c4 time a bounded number of periods per bench step,
+stated in the line's config; their FP64 and oracle legs run bounded samples.
 """
 from __future__ import annotations
 
@@ -39,6 +47,21 @@ UNIT = "particle-steps/s"
 WORKLOAD = ("single lysosome N=2000 x 8 seeds, d=14 nm, Keff=2e4 J/m^3, Ms=1e6 A/m, "
             "c=10%, T=300 K, tau0=1e-10 s, mu0Hmax=20 mT, f=100 kHz, "
             "200 steps/period x 20 periods (5 discarded)")
+# the other workloads: (description, periods and discarded periods timed per
+# bench step, or None for the whole run; kMC steps of the FP64 and oracle samples)
+CONFIGS = {
+    "c0": ("single lysosome N=100, d=12 nm, Keff=1.3e4 J/m^3, Ms=1e6 A/m, c=5%, T=300 K, "
+           "tau0=1e-10 s, mu0Hmax=20 mT, f=100 kHz, 200 steps/period x 20 periods "
+           "(5 discarded)", None, None),
+    "c1": (WORKLOAD, None, None),
+    "c2": ("single lysosome N=8000, d=12 nm, Keff=1.3e4 J/m^3, c=5%, mu0Hmax=40 mT, "
+           "f=100 kHz, 500 steps/period x 20 periods (5 discarded)", None, None),
+    "c3": ("512 lysosomes, N lognormal (median 1500, sigma_ln 0.5, clipped to [200, 10000]), "
+           "d~U[8,20] nm, Keff~U[1e4,5e4] J/m^3, c~U[1,20]%, mu0Hmax~U{10..80} mT, "
+           "f=100 kHz, 200 steps/period", (4, 1), 200),
+    "c4": ("single lysosome N=50000, d=16 nm, Keff=3e4 J/m^3, c=10%, mu0Hmax=40 mT, "
+           "f=100 kHz, 500 steps/period", (2, 1), 50),
+}
 FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
 # DRAM bytes (read + write) of one kMC step at this workload (8 chains, one
 # launch each), by launch shape (warps, tile, chunk): 8 x the mean over 16
@@ -134,25 +157,39 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(lys, run, budget_s=10.0):
-    """The FP64 oracle, as it stands, on the host cores: one period of the
-    2000-NP lysosome (one of the 8 streams), repeated up to ~budget_s."""
+def cpu_oracle_sample(lys, run, budget_s=10.0, chunk=None):
+    """The FP64 oracle, as it stands, on the host cores: runs of `chunk` steps
+    (default one period) of the first lysosome, repeated up to ~budget_s."""
     import oracle
     threads = os.cpu_count() or 1
+    S = int(chunk or run["S"])
+    H = float(np.atleast_1d(run["mu0Hmax"])[0])
     done_steps, t0 = 0, time.perf_counter()
     m = None
     while True:
-        out = oracle.run(lys, 0, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"], m=m,
+        out = oracle.run(lys, 0, H, run["f"], S, 1, 0, run["seed"], m=m,
                          step0=done_steps, nthreads=threads)
         m = out["m"]
-        done_steps += run["S"]
+        done_steps += S
         el = time.perf_counter() - t0
-        if el > budget_s or el * (done_steps + run["S"]) / done_steps > 3 * budget_s:
+        if el > budget_s or el * (done_steps + S) / done_steps > 3 * budget_s:
             break
     value = lys.n * done_steps / el
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d steps (%d periods of %d) of one 2000-NP stream, %.1f s" % (
-                done_steps, done_steps // run["S"], run["S"], el)}
+            "sample": "%d steps (%d runs of %d) of one %d-NP stream, %.1f s" % (
+                done_steps, done_steps // S, S, lys.n, el)}
+
+
+def workload_of(inputs, name):
+    """Lysosomes and run parameters of workload `name` (seed 0), with the
+    bounded periods of a bench step where the workload has them."""
+    lyss, run = {"c0": inputs.config_small, "c1": inputs.config_single2000,
+                 "c2": inputs.config_sweep8000, "c3": inputs.config_batched,
+                 "c4": inputs.config_large50000}[name](seed=0)
+    bounded = CONFIGS[name][1]
+    if bounded:
+        run["periods"], run["discard"] = bounded
+    return lyss, run
 
 
 def run_reference(args):
@@ -160,28 +197,31 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1407_2737_gb300 import inputs
-    lyss, run = inputs.config_single2000(replicas=8, seed=0)
+    workload = CONFIGS[args.config][0]
+    lyss, run = workload_of(inputs, args.config)
     import oracle
     oracle.build()
     threads = os.cpu_count() or 1
+    S = max(1, min(run["S"], int(5e9 / lyss[0].n ** 2)))
+    H = float(np.atleast_1d(run["mu0Hmax"])[0])
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.run(lyss[0], k % 8, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"],
-                   nthreads=threads)
+        oracle.run(lyss[0], k % len(lyss), H, run["f"], S, 1, 0, run["seed"], nthreads=threads)
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
-    units = lyss[0].n * run["S"]
+    units = lyss[0].n * S
     value = units * len(times) / sum(times)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "one 200-step period of one 2000-NP "
-                       "stream per step (FP64 oracle, OpenMP over NPs)"},
+            "config": {"workload": workload, "name": args.config,
+                       "sample": "%d steps of one %d-NP stream per step (FP64 oracle, OpenMP "
+                       "over NPs)" % (S, lyss[0].n)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "one 200-step period of one 2000-NP stream per step"},
+                             "sample": "%d steps of one %d-NP stream per step" % (S, lyss[0].n)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -198,6 +238,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison")
     ap.add_argument("--shape", default="",
                     help="pin the FP32 launch shape as warps,tile,chunk (default: autotuned)")
+    ap.add_argument("--config", default="c1", choices=sorted(CONFIGS),
+                    help="workload (default c1, the headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -219,7 +261,8 @@ def main():
     if world > 1:
         dist.barrier()
 
-    lyss, run = inputs.config_single2000(replicas=8, seed=0)
+    workload, bounded, fp64_steps = CONFIGS[args.config]
+    lyss, run = workload_of(inputs, args.config)
     n_steps = run["S"] * run["periods"]
     n_np = sum(l.n for l in lyss)
     units_per_step = n_np * n_steps
@@ -299,36 +342,48 @@ def main():
             e2e_times.append(time.perf_counter() - t0)
     e2e_t = max_over_ranks(sum(e2e_times))
     n_rec = run["S"] * (run["periods"] - run["discard"])
-    h2d = sum(l.n * 7 * 8 for l in lyss) + 8 * 3
+    h2d = sum(l.n * 7 * 8 for l in lyss) + 8 * 3 + 8 * int(np.size(run["mu0Hmax"]))
     d2h = sum(8 + 8 * n_rec + 8 * l.n for l in lyss)
 
-    # --- FP64-plain GPU path: bounded sample + full-run SAR on the same seeds
+    # --- FP64-plain GPU path: the whole run on the same seeds (SAR compared),
+    # or for the long workloads a bounded sample of fp64_steps steps (rate only)
     fp64 = None
     if not args.no_fp64:
+        S64, per64, dis64 = ((run["S"], run["periods"], run["discard"]) if not fp64_steps
+                             else (fp64_steps, 1, 0))
         c64 = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
         kmc.kmc_set_stream(c64, stream.cuda_stream)
-        kmc.kmc_run(c64, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"])  # tune
+        kmc.kmc_run(c64, run["mu0Hmax"], run["f"], S64, 1, 0, run["seed"])  # tune
         kmc.kmc_destroy(c64)
         c64 = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
         kmc.kmc_set_stream(c64, stream.cuda_stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        kmc.kmc_run(c64, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
-                    run["seed"])
+        kmc.kmc_run(c64, run["mu0Hmax"], run["f"], S64, per64, dis64, run["seed"])
         e1.record(stream)
         kmc.kmc_sync(c64)
         t64 = e0.elapsed_time(e1) / 1e3
-        sar64 = [kmc.kmc_read(c64, kmc.KMC_READ_SAR, l)[0] for l in range(len(lyss))]
+        units64 = n_np * S64 * per64
+        fp64 = {"value": units64 / t64, "unit": UNIT,
+                "ms_per_step": 1e3 * t64 * units_per_step / units64,
+                "speedup_fp32_mixed": float(value / world / (units64 / t64))}
+        if not fp64_steps:
+            sar64 = [kmc.kmc_read(c64, kmc.KMC_READ_SAR, l)[0] for l in range(len(lyss))]
+            rel = abs(np.mean(sar32) - np.mean(sar64)) / abs(np.mean(sar64))
+            fp64.update({"sar_W_per_g": float(np.mean(sar64)) / 1e3,
+                         "sar_rel_err_fp32_vs_fp64": float(rel),
+                         "sar_note": "same seeds; the two paths' trajectories part after a "
+                                     "few periods, so this is one sample of run-to-run "
+                                     "noise; the 1 % bound is tested over 32 seeds"})
+        else:
+            fp64["sample"] = "%d steps of the whole workload (rate only)" % (units64 // n_np)
         kmc.kmc_destroy(c64)
-        rel = abs(np.mean(sar32) - np.mean(sar64)) / abs(np.mean(sar64))
-        fp64 = {"value": units_per_step / t64, "unit": UNIT, "ms_per_step": 1e3 * t64,
-                "sar_W_per_g": float(np.mean(sar64)) / 1e3,
-                "sar_rel_err_fp32_vs_fp64": float(rel),
-                "speedup_fp32_mixed": float(value / world / (units_per_step / t64))}
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu and args.gpus == 1:
-        cpu = cpu_oracle_sample(lyss[0], run)
+        # oracle runs of at most ~5e9 pair evaluations each
+        cpu = cpu_oracle_sample(lyss[0], run,
+                                chunk=max(1, min(run["S"], int(5e9 / lyss[0].n ** 2))))
 
     if rank == 0:
         line = {
@@ -336,7 +391,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-mixed", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "KMC_FP32_MIXED",
+            "config": {"workload": workload, "name": args.config,
+                       "bench_step": ("whole run" if not bounded else
+                                      "%d periods (%d discarded) of the workload" % bounded),
+                       "precision": "KMC_FP32_MIXED",
                        "kmc_steps_per_bench_step": n_steps, "particles": n_np,
                        "launch": {"warps": warps, "tile": tile, "chunk": chunk,
                                   "chains": chains},
@@ -346,7 +404,8 @@ def main():
             "sar_W_per_g": float(np.mean(sar32)) / 1e3,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": STEP_DRAM_BYTES.get((warps, tile, chunk)),
+                         "traffic": (STEP_DRAM_BYTES.get((warps, tile, chunk))
+                                     if args.config == "c1" else None),
                          "kernel": "kmc_step_f32<%d>" % warps,
                          "note": "FP32 pipe: 30 flops per ordered pair; a kMC step is one "
                                  "launch per chain, the chains' launches concurrent; step "
