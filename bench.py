@@ -16,7 +16,7 @@ same seeds, the roofline of the fused step kernel (FP32 pipe) and the FP64
 oracle timed on the host cores (cpu_baseline).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--config c0|c1|c2|c3|c4]
+                    [--config c0|c1|c2|c3|c4] [--row f1|f2|f4]
 
 --config picks another of the paper-shaped workloads for the same measurement
 (c1, the 8 x 2000-NP workload above, is the default and the headline line):
@@ -24,6 +24,11 @@ c0 one 100-NP lysosome; c2 one 8000-NP lysosome at 5 % and 40 mT; c3 512
 lysosomes of lognormal size, each with its own parameters and amplitude; c4 one
 50 000-NP lysosome. c3 and c4 time a bounded number of periods per bench step,
 stated in the line's config; their FP64 and oracle legs run bounded samples.
+
+--row measures one of the outputs built on top of the step instead, with its
+own metric: f1 the local concentration phi_N of Eq. 8 (N = 10) on the 50 000-NP
+lysosome, f2 the regeneration of axes and positions between loops on the same
+lysosome, f4 the Ref. [8] mean-magnetisation mode on the 8 x 2000-NP workload.
 """
 from __future__ import annotations
 
@@ -68,6 +73,8 @@ FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA =
 # serialised ncu captures of the committed kernel
 STEP_DRAM_BYTES = {(4, 256, 512): 2.186e6, (4, 256, 1024): 2.153e6}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (FMA = 2 flops)
+HBM_GBS = 6771.5             # measured copy bandwidth of the GB300s
 
 
 def fp32_peak_tflops():
@@ -192,6 +199,140 @@ def workload_of(inputs, name):
     return lyss, run
 
 
+def run_row(args):
+    """One JSON line for an output built on top of the step (see the module
+    docstring), timed with CUDA events around the entry point on the context's
+    stream (wall clock for the mean mode, which owns its stream), beside the
+    oracle's routine for the same output on a bounded sample."""
+    import torch
+    import oracle
+    from paper_1407_2737_gb300 import build as kbuild
+    from paper_1407_2737_gb300 import inputs, kmc
+    kbuild.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    threads = os.cpu_count() or 1
+
+    def events(fn):
+        times = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1) / 1e3)
+        return sum(times) / len(times)
+
+    if args.row in ("f1", "f2"):
+        (lys,), _ = inputs.config_large50000(seed=0)
+        n = lys.n
+        t0 = time.perf_counter()
+        ctx = kmc.kmc_create([lys], kmc.KMC_FP32_MIXED, center=np.zeros(3))
+        kmc.kmc_set_stream(ctx, stream.cuda_stream)
+        t_create = time.perf_counter() - t0
+    if args.row == "f1":
+        N = 10
+        t = events(lambda k: kmc.kmc_local_concentration(ctx, 0, N))
+        pairs = n * (n - 1)
+        value = pairs / t
+        idx = np.arange(0, n, max(1, n // 64))
+        t0 = time.perf_counter()
+        oracle.local_concentration_at(lys.pos, lys.vol, N, idx)
+        tc = time.perf_counter() - t0
+        line = {"metric": "pair distances/s, local concentration phi_N (Eq. 8, N = 10)",
+                "value": value, "unit": "pairs/s", "ms_per_step": 1e3 * t,
+                "dtype": "f64", "config": {"workload": CONFIGS["c4"][0], "row": "f1",
+                                           "step": "phi_N of all 50 000 NPs (all pairs)"},
+                "roofline": {"bound": "alu", "achieved": 8 * value / 1e12,
+                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": 8 * value / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                             "kernel": "local_concentration_kernel",
+                             "note": "8 FP64 instructions per pair, none an FMA, so a full "
+                                     "FP64 pipe gives 50 % of the FMA peak"},
+                "e2e": {"value": pairs / (t + t_create), "unit": "pairs/s",
+                        "h2d_bytes_per_step": n * 7 * 8, "d2h_bytes_per_step": n * 8},
+                "gpu_launches": args.steps,
+                "cpu_baseline": {"value": len(idx) * (n - 1) / tc, "unit": "pairs/s",
+                                 "cores": 1, "kind": "oracle",
+                                 "sample": "phi_N of %d NPs against all %d (%.1f s)" % (
+                                     len(idx), n, tc)}}
+    elif args.row == "f2":
+        what = kmc.KMC_REGEN_AXES | kmc.KMC_REGEN_POSITIONS
+        disorder = 0.5 * 16e-9
+        t = events(lambda k: kmc.kmc_regenerate(ctx, 0, what, disorder, 11, k + 1))
+        value = n / t
+        bytes_np = 120  # nodes in, SI and frame positions, FP64 copy, axis, moment out
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 2.0:
+            oracle.regen_axes(n, 11, reps + 1)
+            oracle.regen_positions(lys.pos, disorder, 11, reps + 1)
+            reps += 1
+        tc = (time.perf_counter() - t0) / reps
+        line = {"metric": "NP regenerations/s (axes and positions between loops)",
+                "value": value, "unit": "NPs/s", "ms_per_step": 1e3 * t, "dtype": "f64",
+                "config": {"workload": CONFIGS["c4"][0], "row": "f2",
+                           "step": "new axes and positions for all 50 000 NPs, then the "
+                                   "host copy of the positions"},
+                "roofline": {"bound": "hbm", "achieved": bytes_np * value / 1e9, "peak": HBM_GBS,
+                             "unit": "GB/s", "frac": bytes_np * value / 1e9 / HBM_GBS,
+                             "traffic": None, "kernel": "kmc_regen_kernel",
+                             "note": "120 B per NP; the timed call includes the 1.2 MB "
+                                     "copy of the positions to the host"},
+                "e2e": {"value": value, "unit": "NPs/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": n * 24},
+                "gpu_launches": args.steps,
+                "cpu_baseline": {"value": n / tc, "unit": "NPs/s", "cores": 1, "kind": "oracle",
+                                 "sample": "%d regenerations of all %d NPs" % (reps, n)}}
+    else:  # f4
+        lyss, run = inputs.config_single2000(replicas=8, seed=0)
+        n_np = sum(l.n for l in lyss)
+        steps = run["S"] * run["periods"]
+        times = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kmc.kmc_mean_run(lyss, run["mu0Hmax"], run["f"], run["S"], run["periods"],
+                             run["discard"])
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        t = sum(times) / len(times)
+        value = n_np * steps / t
+        flops = 1000  # the 200-node scan alone: 200 x (2 FMA + 1 MUL) in FP64
+        t0 = time.perf_counter()
+        l0 = lyss[0]
+        oracle.mean_run(l0.axis, l0.vol, l0.Ms, l0.Keff, l0.T, l0.tau0, run["mu0Hmax"], run["f"],
+                        run["S"], 2, 0)
+        tc = time.perf_counter() - t0
+        line = {"metric": "particle-steps/s, Ref. [8] mean-magnetisation mode",
+                "value": value, "unit": "particle-steps/s", "ms_per_step": 1e3 * t,
+                "dtype": "f64", "config": {"workload": WORKLOAD, "row": "f4",
+                                           "step": "one whole mean-mode run of the workload"},
+                "roofline": {"bound": "alu", "achieved": flops * value / 1e12,
+                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": flops * value / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                             "kernel": "kmc_mean_kernel",
+                             "note": "algorithmic flops = the scan only (1000 per NP-step); one "
+                                     "thread per NP runs the whole run, latency-bound"},
+                "e2e": {"value": value, "unit": "particle-steps/s",
+                        "h2d_bytes_per_step": n_np * 5 * 8, "d2h_bytes_per_step":
+                        8 * len(lyss) * run["S"] * (run["periods"] - run["discard"])},
+                "gpu_launches": args.steps,
+                "cpu_baseline": {"value": l0.n * run["S"] * 2 / tc, "unit": "particle-steps/s",
+                                 "cores": 1, "kind": "oracle",
+                                 "sample": "2 periods of one 2000-NP lysosome (%.1f s)" % tc}}
+    line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                 "data": "synthetic"})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -238,13 +379,19 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison")
     ap.add_argument("--shape", default="",
                     help="pin the FP32 launch shape as warps,tile,chunk (default: autotuned)")
+    ap.add_argument("--shape64", default="",
+                    help="pin the FP64-plain launch shape as warps,tile,chunk (default: autotuned)")
     ap.add_argument("--config", default="c1", choices=sorted(CONFIGS),
                     help="workload (default c1, the headline line)")
+    ap.add_argument("--row", default="", choices=["", "f1", "f2", "f4"],
+                    help="measure an output built on the step instead (see above)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.row:
+        return run_row(args)
 
     import torch
     import torch.distributed as dist
@@ -351,22 +498,29 @@ def main():
     if not args.no_fp64:
         S64, per64, dis64 = ((run["S"], run["periods"], run["discard"]) if not fp64_steps
                              else (fp64_steps, 1, 0))
+        shape64 = [int(x) for x in args.shape64.split(",")] if args.shape64 else None
         c64 = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
         kmc.kmc_set_stream(c64, stream.cuda_stream)
+        if shape64:
+            kmc.kmc_tuning(c64, *shape64)
         kmc.kmc_run(c64, run["mu0Hmax"], run["f"], S64, 1, 0, run["seed"])  # tune
         kmc.kmc_destroy(c64)
         c64 = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
         kmc.kmc_set_stream(c64, stream.cuda_stream)
+        if shape64:
+            kmc.kmc_tuning(c64, *shape64)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         kmc.kmc_run(c64, run["mu0Hmax"], run["f"], S64, per64, dis64, run["seed"])
         e1.record(stream)
         kmc.kmc_sync(c64)
         t64 = e0.elapsed_time(e1) / 1e3
+        w64, tl64, ch64 = kmc.kmc_tuning(c64)
         units64 = n_np * S64 * per64
         fp64 = {"value": units64 / t64, "unit": UNIT,
                 "ms_per_step": 1e3 * t64 * units_per_step / units64,
-                "speedup_fp32_mixed": float(value / world / (units64 / t64))}
+                "speedup_fp32_mixed": float(value / world / (units64 / t64)),
+                "launch": {"warps": w64, "tile": tl64, "chunk": ch64}}
         if not fp64_steps:
             sar64 = [kmc.kmc_read(c64, kmc.KMC_READ_SAR, l)[0] for l in range(len(lyss))]
             rel = abs(np.mean(sar32) - np.mean(sar64)) / abs(np.mean(sar64))
