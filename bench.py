@@ -283,7 +283,8 @@ def run_row(args):
                              "unit": "GB/s", "frac": bytes_np * value / 1e9 / HBM_GBS,
                              "traffic": None, "kernel": "kmc_regen_kernel",
                              "note": "120 B per NP; the timed call includes the 1.2 MB "
-                                     "copy of the positions to the host"},
+                                     "copy of the positions to the host; the kernel alone "
+                                     "(~21 us) is bound by FP64 sampling arithmetic, not HBM"},
                 "e2e": {"value": value, "unit": "NPs/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": n * 24},
                 "gpu_launches": args.steps,
@@ -317,8 +318,10 @@ def run_row(args):
                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": flops * value / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
                              "kernel": "kmc_mean_kernel",
-                             "note": "algorithmic flops = the scan only (1000 per NP-step); one "
-                                     "thread per NP runs the whole run, latency-bound"},
+                             "note": "algorithmic flops count the 200-node scan only (1000 per "
+                                     "NP-step); one thread per NP runs the whole run and the "
+                                     "FP64 pipe is ~80 % busy with the Newton steps' FP64 "
+                                     "divisions, the exponentials and the sines (ncu)"},
                 "e2e": {"value": value, "unit": "particle-steps/s",
                         "h2d_bytes_per_step": n_np * 5 * 8, "d2h_bytes_per_step":
                         8 * len(lyss) * run["S"] * (run["periods"] - run["discard"])},
