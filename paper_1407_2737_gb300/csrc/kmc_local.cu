@@ -18,7 +18,9 @@ namespace kmc {
 
 namespace {
 
-constexpr int kPhiThreads = 128;
+// one warp per block: many small blocks spread the targets evenly over the SMs
+// (50 000 NPs: 46.9 ms against 50.9 ms with 128-thread blocks)
+constexpr int kPhiThreads = 32;
 constexpr int kPhiTile = 512;
 
 __global__ void __launch_bounds__(kPhiThreads)
