@@ -117,6 +117,12 @@ def lib():
             L.kmc_oracle_regen_positions.argtypes = [C.c_int32, _D, C.c_double, C.c_uint64,
                                                      C.c_uint32, C.c_int32, _D]
             L.kmc_oracle_regen_positions.restype = None
+            L.kmc_oracle_rsa_candidate.argtypes = [C.c_double, C.c_double, C.c_uint64,
+                                                   C.c_uint32, C.c_int64, C.c_int32, _D]
+            L.kmc_oracle_rsa_candidate.restype = None
+            L.kmc_oracle_rsa.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_uint64,
+                                         C.c_uint32, C.c_int32, C.c_int64, _D]
+            L.kmc_oracle_rsa.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -330,6 +336,28 @@ def shell_profile(pos, vol, center, R, n_shells, values):
     if r < 0:
         raise ValueError("oracle shell_profile failed (%g)" % r)
     return count, mean, float(r)
+
+
+def rsa_candidate(radius, d, seed, loop, c, lys=0):
+    """Candidate c of the RSA stream: a point uniform in the ball of radius
+    radius - d/2 (m)."""
+    out = np.zeros(3)
+    lib().kmc_oracle_rsa_candidate(float(radius), float(d), C.c_uint64(seed), C.c_uint32(loop),
+                                   C.c_int64(c), int(lys), _dp(out))
+    return out
+
+
+def rsa(n, radius, d, seed, loop, lys=0, max_candidates=None):
+    """Random sequential addition of n spheres of diameter d in the sphere of
+    the given radius, from the candidate stream; returns (positions [n][3],
+    candidates used). Raises if max_candidates (default 1000 n) run out."""
+    pos = np.zeros((int(n), 3))
+    cap = int(max_candidates if max_candidates is not None else 1000 * max(int(n), 1))
+    used = lib().kmc_oracle_rsa(int(n), float(radius), float(d), C.c_uint64(seed), C.c_uint32(loop),
+                                int(lys), C.c_int64(cap), _dp(pos))
+    if used < 0:
+        raise RuntimeError("RSA ran out of candidates")
+    return pos, int(used)
 
 
 def regen_axes(n, seed, loop, lys=0):

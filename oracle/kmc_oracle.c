@@ -122,6 +122,45 @@ static void sphere_point(const double u[2], double out[3]) {
   out[2] = z;
 }
 
+/* RSA candidate c: direction from sub 3, radius (R - d/2) max(u0, u1, u2)
+ * from subs 4 and 5 (the maximum of three uniforms has density 3 x^2, the
+ * radial density of a uniform ball). */
+void kmc_oracle_rsa_candidate(double radius, double d, uint64_t seed, uint32_t loop, int64_t c,
+                              int32_t lys, double out[3]) {
+  double u[2], v[2], w[2], e[3];
+  regen_uniforms(seed, loop, 3u, (int32_t)(uint32_t)c, lys, u);
+  regen_uniforms(seed, loop, 4u, (int32_t)(uint32_t)c, lys, v);
+  regen_uniforms(seed, loop, 5u, (int32_t)(uint32_t)c, lys, w);
+  sphere_point(u, e);
+  double x = v[0] > v[1] ? v[0] : v[1];
+  if (w[0] > x) x = w[0];
+  const double r = (radius - 0.5 * d) * x;
+  for (int q = 0; q < 3; ++q) out[q] = r * e[q];
+}
+
+int64_t kmc_oracle_rsa(int32_t n, double radius, double d, uint64_t seed, uint32_t loop,
+                       int32_t lys, int64_t max_candidates, double *pos) {
+  const double d2 = d * d;
+  int32_t kept = 0;
+  int64_t c = 0;
+  while (kept < n) {
+    if (c >= max_candidates) return -1;
+    double p[3];
+    kmc_oracle_rsa_candidate(radius, d, seed, loop, c, lys, p);
+    ++c;
+    int ok = 1;
+    for (int32_t j = 0; j < kept && ok; ++j) {
+      const double dx = p[0] - pos[3 * j], dy = p[1] - pos[3 * j + 1], dz = p[2] - pos[3 * j + 2];
+      if ((dx * dx + dy * dy) + dz * dz < d2) ok = 0;
+    }
+    if (ok) {
+      for (int q = 0; q < 3; ++q) pos[3 * kept + q] = p[q];
+      ++kept;
+    }
+  }
+  return c;
+}
+
 void kmc_oracle_regen_axes(int32_t n, uint64_t seed, uint32_t loop, int32_t lys, double *axis) {
   for (int32_t i = 0; i < n; ++i) {
     double u[2];

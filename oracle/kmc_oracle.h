@@ -36,6 +36,10 @@
  *                              distribution, KS tests of z, azimuth and
  *                              displacement length, no overlap at maximal
  *                              disorder by brute force)
+ *   rsa_candidate, rsa ....... pinned (candidates uniform in the ball: KS of
+ *                              the radius and the direction; every accept and
+ *                              reject re-derived by brute force; the dilute
+ *                              limit keeps the first n candidates)
  */
 #ifndef KMC_ORACLE_H
 #define KMC_ORACLE_H
@@ -93,6 +97,20 @@ double kmc_oracle_uniform(uint64_t seed, int64_t step, int32_t np, int32_t lys);
 void kmc_oracle_regen_axes(int32_t n, uint64_t seed, uint32_t loop, int32_t lys, double *axis);
 void kmc_oracle_regen_positions(int32_t n, const double *nodes, double disorder, uint64_t seed,
                                 uint32_t loop, int32_t lys, double *pos);
+
+/* Random sequential addition (Sec. II.4 names it as the alternative to the
+ * lattice; the configs place lysosomes by it): candidate c is a point uniform
+ * in the ball of radius R - d/2 about the origin, with direction from sub 3
+ * (as the axes) and radius (R - d/2) * max(u0, u1, u2), whose density grows as
+ * r^2, from sub 4 (u0, u1) and sub 5 (u0); NP slot of the counter = c.
+ * Candidates are taken in order c = 0, 1, ...; one is kept iff its squared
+ * distance to every kept one is at least d^2, until n are kept. Returns the
+ * number of candidates used, or -1 if max_candidates ran out first (pos then
+ * holds the ones kept so far). pos is [n][3], m, about the lysosome centre. */
+void kmc_oracle_rsa_candidate(double radius, double d, uint64_t seed, uint32_t loop, int64_t c,
+                              int32_t lys, double out[3]);
+int64_t kmc_oracle_rsa(int32_t n, double radius, double d, uint64_t seed, uint32_t loop,
+                       int32_t lys, int64_t max_candidates, double *pos);
 
 /* Eq. 1: mu0*H_dip on every NP from the moments of all the others, exact sum
  * over j != i with per-source volume V_j. B is [n][3] in tesla. */
