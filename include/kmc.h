@@ -242,6 +242,24 @@ enum { KMC_REGEN_AXES = 1, KMC_REGEN_POSITIONS = 2 };
 kmc_status kmc_regenerate(kmc_ctx *ctx, int32_t lys, int32_t what, double disorder,
                           uint64_t seed, uint32_t loop);
 
+/* Random sequential addition (Sec. II.4; the alternative to the lattice) of
+ * the NPs of lysosome `lys` on the device: spheres of `diameter` (m) placed
+ * one after another at candidate centres uniform in the ball of radius
+ * radius - diameter/2 (m) about the lysosome's centre, each kept iff no kept
+ * sphere lies closer than `diameter`, until every NP has a place; NP i takes
+ * the i-th kept centre. Candidate c comes from Philox4x32-10, key (seed lo,
+ * seed hi), counter (loop, 0x80000000 | sub, c, lys): direction from sub 3 as
+ * for the axes, radius (radius - diameter/2) max(u0, u1, u2) from subs 4 and
+ * 5. The kept centres are exactly those of the sequential rule, taken batch
+ * by batch. Then, as kmc_regenerate does, the NP arrays follow the new
+ * positions and the moments restart along the axes. max_candidates (<= 0:
+ * 1000 n) bounds the candidates; KMC_ESTATE if they run out (positions left
+ * unchanged). *candidates_used (may be NULL) = candidates consumed.
+ * KMC_EINVAL unless 0 < diameter < 2 radius. */
+kmc_status kmc_regenerate_rsa(kmc_ctx *ctx, int32_t lys, double radius, double diameter,
+                              uint64_t seed, uint32_t loop, int64_t max_candidates,
+                              int64_t *candidates_used);
+
 /* Failure-detection test hook (FP64 contexts). Launches one step whose every
  * staged copy waits for 16 bytes more than it delivers, so each block's bounded
  * wait runs out (after 1 ms instead of 2 s) and reports through the device

@@ -1378,6 +1378,111 @@ kmc_status kmc_mean_run(const kmc_lysosome *lys, int32_t n_lys, const double *mu
   return KMC_OK;
 }
 
+kmc_status kmc_regenerate_rsa(kmc_ctx *c, int32_t lys, double radius, double diameter,
+                              uint64_t seed, uint32_t loop, int64_t max_candidates,
+                              int64_t *candidates_used) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (candidates_used) *candidates_used = 0;
+  if (lys < 0 || lys >= c->n_lys) return fail(KMC_EINVAL, "lysosome %d out of range", lys);
+  if (!(diameter > 0.0) || !is_finite(diameter) || !is_finite(radius) ||
+      !(radius > 0.5 * diameter))
+    return fail(KMC_EINVAL, "need 0 < diameter < 2 radius, both finite");
+  const int n = c->n[lys];
+  const long long cap = max_candidates > 0 ? max_candidates : 1000ll * n;
+  KMC_TRY(check_device_error(c));
+  if (!c->d_nodes) {  // the mean positions: those given at creation
+    KMC_TRY(dalloc(&c->d_nodes, sizeof(double) * 3 * c->N));
+    KMC_TRY(dalloc(&c->d_possi, sizeof(double) * 3 * c->N));
+    KMC_CUDA(cudaMemcpy(c->d_nodes, c->pos_si.data(), sizeof(double) * 3 * c->N,
+                        cudaMemcpyHostToDevice));
+    KMC_CUDA(cudaMemcpy(c->d_possi, c->pos_si.data(), sizeof(double) * 3 * c->N,
+                        cudaMemcpyHostToDevice));
+  }
+  // scratch, freed on every return
+  const int B = static_cast<int>(std::min<long long>(4096, std::max<long long>(256, 2ll * n)));
+  struct Scratch {
+    void *p[8] = {};
+    ~Scratch() {
+      for (void *q : p)
+        if (q) cudaFree(q);
+    }
+  } sc;
+  KMC_TRY(dalloc(reinterpret_cast<double **>(&sc.p[0]), sizeof(double) * 3 * n));
+  KMC_TRY(dalloc(reinterpret_cast<double **>(&sc.p[1]), sizeof(double) * 3 * B));
+  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[2]), sizeof(int32_t) * B));
+  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[3]), sizeof(int32_t) * B));
+  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[4]), sizeof(int32_t) * B * kmc::kRsaMaxConf));
+  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[5]), sizeof(int32_t) * B));
+  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[6]), sizeof(int32_t)));
+  KMC_TRY(dalloc(reinterpret_cast<long long **>(&sc.p[7]), sizeof(long long)));
+  KMC_CUDA(cudaMemsetAsync(sc.p[6], 0, sizeof(int32_t), c->stream));
+  kmc::RsaArgs a;
+  a.Rb = radius - 0.5 * diameter;
+  a.d2 = diameter * diameter;
+  a.seed = seed;
+  a.loop = loop;
+  a.lys = lys;
+  a.B = B;
+  a.n = n;
+  a.pos = static_cast<double *>(sc.p[0]);
+  a.cand = static_cast<double *>(sc.p[1]);
+  a.clear = static_cast<int32_t *>(sc.p[2]);
+  a.nconf = static_cast<int32_t *>(sc.p[3]);
+  a.conf = static_cast<int32_t *>(sc.p[4]);
+  a.acc = static_cast<int32_t *>(sc.p[5]);
+  a.kept = static_cast<int32_t *>(sc.p[6]);
+  a.used = static_cast<long long *>(sc.p[7]);
+  int32_t kept = 0;
+  long long c0 = 0;
+  while (kept < n) {
+    if (c0 >= cap)
+      return fail(KMC_ESTATE, "random sequential addition placed %d of %d spheres in %lld "
+                  "candidates (packing too dense for this radius)", kept, n, cap);
+    a.c0 = c0;
+    a.B = static_cast<int>(std::min<long long>(B, cap - c0));
+    KMC_CUDA(kmc::launch_rsa_batch(a, c->stream));
+    KMC_CUDA(cudaMemcpyAsync(&kept, a.kept, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    KMC_CUDA(cudaStreamSynchronize(c->stream));
+    c0 += a.B;
+  }
+  long long used = 0;
+  KMC_CUDA(cudaMemcpy(&used, a.used, sizeof(long long), cudaMemcpyDeviceToHost));
+  // the kept centres become the lysosome's positions (absolute, m), then the
+  // NP arrays follow them and the moments restart along the axes
+  std::vector<double> p(3ull * n);
+  KMC_CUDA(cudaMemcpy(p.data(), a.pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+  const size_t o = 3ull * c->off[lys];
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < 3; ++q) c->pos_si[o + 3 * i + q] = c->ctr[3 * lys + q] + p[3 * i + q];
+  KMC_CUDA(cudaMemcpyAsync(c->d_possi + o, c->pos_si.data() + o, sizeof(double) * 3 * n,
+                           cudaMemcpyHostToDevice, c->stream));
+  kmc::RegenArgs r;
+  r.off = c->off[lys];
+  r.n = n;
+  r.lys = lys;
+  r.what = kmc::kRegenGiven;
+  r.loop = loop;
+  r.fp32 = c->fp32;
+  r.seed = seed;
+  r.disorder = 0.0;
+  r.len = c->len[lys];
+  r.cx = c->ctr[3 * lys];
+  r.cy = c->ctr[3 * lys + 1];
+  r.cz = c->ctr[3 * lys + 2];
+  r.nodes = c->d_nodes;
+  r.pos = c->d_pos;
+  r.axis = c->d_axis;
+  r.m = c->d_m;
+  r.pos64 = c->d_pos64;
+  r.pos_si = c->d_possi;
+  KMC_CUDA(kmc::launch_regen(r, c->stream));
+  KMC_TRY(refresh_sources(c, 0));
+  KMC_TRY(refresh_sources(c, 1));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  if (candidates_used) *candidates_used = used;
+  return KMC_OK;
+}
+
 kmc_status kmc_regenerate(kmc_ctx *c, int32_t lys, int32_t what, double disorder, uint64_t seed,
                           uint32_t loop) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");

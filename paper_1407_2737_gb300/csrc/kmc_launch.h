@@ -27,6 +27,10 @@ cudaError_t launch_mean(const MeanArgs &a, cudaStream_t st);
 // Redraws the axes and/or positions of one lysosome (a.off .. a.off + a.n).
 cudaError_t launch_regen(const RegenArgs &a, cudaStream_t st);
 
+// One batch of the random sequential addition (RsaArgs): candidates, their
+// checks against the kept spheres, then the in-order pass that keeps them.
+cudaError_t launch_rsa_batch(const RsaArgs &a, cudaStream_t st);
+
 // Advances the device run state by one field period of S steps.
 cudaError_t launch_advance(RunState *rs, int S, cudaStream_t st);
 

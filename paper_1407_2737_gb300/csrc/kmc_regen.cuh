@@ -10,7 +10,10 @@
 // the kMC draw from words (0, 1) and (2, 3).
 //   axes (sub 0): uniform on the sphere, z = 1 - 2 u0, azimuth 2 pi u1;
 //   positions: node + rho e, e uniform on the sphere from sub 1 and
-//     rho = disorder * (first uniform of sub 2), uniform on [0, disorder].
+//     rho = disorder * (first uniform of sub 2), uniform on [0, disorder];
+//   random sequential addition: candidate c (NP slot of the counter = c) is
+//     uniform in the ball of centres, direction from sub 3 and radius
+//     Rb max(u0, u1, u2) from subs 4 and 5.
 // The NP's arrays are then rewritten as creation builds them (unit axis,
 // position in the lysosome's frame, moment along the axis with m_z >= 0).
 #pragma once
@@ -28,14 +31,17 @@ __device__ __forceinline__ void regen_uniforms(unsigned long long seed, uint32_t
                              static_cast<unsigned long long>(w.w >> 11)) * 0x1.0p-53;
 }
 
+// Uniform point on the unit sphere. Roundings are spelled out so that no
+// product is fused into a subtraction: near the poles 1 - z^2 cancels, and a
+// fused form would differ from the plain one by many ulps.
 __device__ __forceinline__ void sphere_point(const double u[2], double &x, double &y, double &z) {
-  z = 1.0 - 2.0 * u[0];
-  const double r2 = 1.0 - z * z;
+  z = __dsub_rn(1.0, __dmul_rn(2.0, u[0]));
+  const double r2 = __dsub_rn(1.0, __dmul_rn(z, z));
   const double r = r2 > 0.0 ? sqrt(r2) : 0.0;
   double s, c;
-  sincos(Prec<double>::two_pi * u[1], &s, &c);
-  x = r * c;
-  y = r * s;
+  sincos(__dmul_rn(Prec<double>::two_pi, u[1]), &s, &c);
+  x = __dmul_rn(r, c);
+  y = __dmul_rn(r, s);
 }
 
 __global__ void kmc_regen_kernel(const RegenArgs a) {
@@ -63,17 +69,25 @@ __global__ void kmc_regen_kernel(const RegenArgs a) {
     ay = v.y;
     az = v.z;
   }
-  if (a.what & kRegenPositions) {
-    double u[2], v[2], ex, ey, ez;
-    regen_uniforms(a.seed, a.loop, 1u, i, a.lys, u);
-    regen_uniforms(a.seed, a.loop, 2u, i, a.lys, v);
-    sphere_point(u, ex, ey, ez);
-    const double rho = a.disorder * v[0];
-    const double px = a.nodes[3 * g] + rho * ex, py = a.nodes[3 * g + 1] + rho * ey,
-                 pz = a.nodes[3 * g + 2] + rho * ez;
-    a.pos_si[3 * g] = px;
-    a.pos_si[3 * g + 1] = py;
-    a.pos_si[3 * g + 2] = pz;
+  if (a.what & (kRegenPositions | kRegenGiven)) {
+    double px, py, pz;
+    if (a.what & kRegenPositions) {
+      double u[2], v[2], ex, ey, ez;
+      regen_uniforms(a.seed, a.loop, 1u, i, a.lys, u);
+      regen_uniforms(a.seed, a.loop, 2u, i, a.lys, v);
+      sphere_point(u, ex, ey, ez);
+      const double rho = __dmul_rn(a.disorder, v[0]);
+      px = __dadd_rn(a.nodes[3 * g], __dmul_rn(rho, ex));
+      py = __dadd_rn(a.nodes[3 * g + 1], __dmul_rn(rho, ey));
+      pz = __dadd_rn(a.nodes[3 * g + 2], __dmul_rn(rho, ez));
+      a.pos_si[3 * g] = px;
+      a.pos_si[3 * g + 1] = py;
+      a.pos_si[3 * g + 2] = pz;
+    } else {
+      px = a.pos_si[3 * g];
+      py = a.pos_si[3 * g + 1];
+      pz = a.pos_si[3 * g + 2];
+    }
     const double x = (px - a.cx) / a.len, y = (py - a.cy) / a.len, z = (pz - a.cz) / a.len;
     if (a.fp32) {
       float4 &p4 = static_cast<float4 *>(a.pos)[g];
@@ -109,6 +123,88 @@ __global__ void kmc_regen_kernel(const RegenArgs a) {
     v.z = sgn * az;
     static_cast<dbl4 *>(a.m)[g] = v;
   }
+}
+
+// Candidate c of the random sequential addition, about the lysosome centre.
+__device__ __forceinline__ void rsa_candidate(double Rb, unsigned long long seed, uint32_t loop,
+                                              long long c, int lys, double *p) {
+  double u[2], v[2], w[2], ex, ey, ez;
+  const int slot = static_cast<int>(static_cast<uint32_t>(c));
+  regen_uniforms(seed, loop, 3u, slot, lys, u);
+  regen_uniforms(seed, loop, 4u, slot, lys, v);
+  regen_uniforms(seed, loop, 5u, slot, lys, w);
+  sphere_point(u, ex, ey, ez);
+  double x = v[0] > v[1] ? v[0] : v[1];
+  if (w[0] > x) x = w[0];
+  const double r = __dmul_rn(Rb, x);
+  p[0] = __dmul_rn(r, ex);
+  p[1] = __dmul_rn(r, ey);
+  p[2] = __dmul_rn(r, ez);
+}
+
+// Squared distance, rounded as the definition reads it.
+__device__ __forceinline__ double rsa_d2(const double *p, const double *q) {
+  const double dx = __dsub_rn(p[0], q[0]), dy = __dsub_rn(p[1], q[1]), dz = __dsub_rn(p[2], q[2]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__global__ void rsa_candidates_kernel(const RsaArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < a.B) rsa_candidate(a.Rb, a.seed, a.loop, a.c0 + k, a.lys, a.cand + 3 * k);
+}
+
+// Block k: does candidate k clear every sphere kept by earlier batches, and
+// which earlier candidates of this batch lie closer than d.
+__global__ void rsa_check_kernel(const RsaArgs a) {
+  __shared__ int s_nconf;
+  const int k = blockIdx.x;
+  const int kept = *a.kept;
+  const double *p = a.cand + 3 * k;
+  bool clash = false;
+  for (int j = threadIdx.x; j < kept && !clash; j += blockDim.x)
+    clash = rsa_d2(p, a.pos + 3 * j) < a.d2;
+  if (threadIdx.x == 0) s_nconf = 0;
+  clash = __syncthreads_or(clash);
+  if (!clash) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
+      if (rsa_d2(p, a.cand + 3 * j) < a.d2) {
+        const int q = atomicAdd(&s_nconf, 1);
+        if (q < kRsaMaxConf) a.conf[k * kRsaMaxConf + q] = j;
+      }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.clear[k] = clash ? 0 : 1;
+    a.nconf[k] = s_nconf;
+  }
+}
+
+// One thread walks the batch in candidate order: a candidate that cleared the
+// earlier batches is kept unless a candidate kept earlier in this batch lies
+// closer than d. That is the sequential rule, candidate by candidate.
+__global__ void rsa_resolve_kernel(const RsaArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int kept = *a.kept;
+  for (int k = 0; k < a.B && kept < a.n; ++k) {
+    bool ok = a.clear[k] != 0;
+    if (ok) {
+      const int nc = a.nconf[k];
+      if (nc <= kRsaMaxConf) {
+        for (int q = 0; q < nc && ok; ++q) ok = a.acc[a.conf[k * kRsaMaxConf + q]] == 0;
+      } else {
+        for (int j = 0; j < k && ok; ++j)
+          ok = !(a.acc[j] && rsa_d2(a.cand + 3 * k, a.cand + 3 * j) < a.d2);
+      }
+    }
+    a.acc[k] = ok ? 1 : 0;
+    if (ok) {
+      a.pos[3 * kept] = a.cand[3 * k];
+      a.pos[3 * kept + 1] = a.cand[3 * k + 1];
+      a.pos[3 * kept + 2] = a.cand[3 * k + 2];
+      if (++kept == a.n) *a.used = a.c0 + k + 1;
+    }
+  }
+  *a.kept = kept;
 }
 
 }  // namespace kmc

@@ -1003,6 +1003,14 @@ cudaError_t launch_regen(const RegenArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_rsa_batch(const RsaArgs &a, cudaStream_t st) {
+  if (a.B <= 0) return cudaSuccess;
+  rsa_candidates_kernel<<<(a.B + 127) / 128, 128, 0, st>>>(a);
+  rsa_check_kernel<<<a.B, 128, 0, st>>>(a);
+  rsa_resolve_kernel<<<1, 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_advance(RunState *rs, int S, cudaStream_t st) {
   kmc_advance_kernel<<<1, 1, 0, st>>>(rs, S);
   return cudaGetLastError();

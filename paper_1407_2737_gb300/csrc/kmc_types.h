@@ -139,7 +139,32 @@ struct MeanArgs {
 };
 
 // Sample regeneration between loops (kmc_regen.cuh), one lysosome per launch.
-enum : int32_t { kRegenAxes = 1, kRegenPositions = 2 };
+// kRegenGiven: positions already written to pos_si (random sequential
+// addition); the kernel only brings the NP's other arrays in line with them
+enum : int32_t { kRegenAxes = 1, kRegenPositions = 2, kRegenGiven = 4 };
+
+// Random sequential addition on the device, one batch of B candidates
+// (candidate indices c0 .. c0 + B - 1). The batch keeps, in candidate order,
+// each candidate that clears every sphere kept before it, until n are kept.
+constexpr int kRsaMaxConf = 16;  // listed conflicts per candidate; more: checked in full
+struct RsaArgs {
+  double Rb;                   // radius of the ball of centres, R - d/2, m
+  double d2;                   // d^2, m^2
+  unsigned long long seed;
+  uint32_t loop;
+  int32_t lys;
+  long long c0;                // first candidate of the batch
+  int32_t B;                   // candidates in the batch
+  int32_t n;                   // spheres to keep
+  int32_t *kept;               // [1] spheres kept so far (updated by the batch)
+  long long *used;             // [1] candidates used when the n-th was kept
+  double *pos;                 // [n][3] kept centres, m, about the lysosome centre
+  double *cand;                // [B][3] scratch
+  int32_t *clear;              // [B] 1 if the candidate clears the earlier batches' spheres
+  int32_t *nconf;              // [B] earlier candidates of the batch closer than d
+  int32_t *conf;               // [B][kRsaMaxConf] their indices
+  int32_t *acc;                // [B] 1 if kept
+};
 struct RegenArgs {
   int32_t off, n, lys, what;
   uint32_t loop;

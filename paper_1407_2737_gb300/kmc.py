@@ -32,7 +32,8 @@ STATUS_NAMES = {0: "KMC_OK", 1: "KMC_EINVAL", 2: "KMC_ENOMEM", 3: "KMC_ECUDA",
 EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
-           "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall")
+           "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall",
+           "kmc_regenerate_rsa")
 KMC_NOALLOC_MAX_N = 8192
 KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
 KMC_PHI_MAX_N = 64
@@ -92,6 +93,8 @@ def lib():
             L.kmc_regenerate.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.c_uint64,
                                          C.c_uint32]
             L.kmc_debug_stall.argtypes = [vp]
+            L.kmc_regenerate_rsa.argtypes = [vp, C.c_int32, C.c_double, C.c_double, C.c_uint64,
+                                             C.c_uint32, C.c_int64, _I64]
             L.kmc_destroy.argtypes = [vp]
             L.kmc_destroy.restype = None
             L.kmc_last_error.argtypes = []
@@ -185,6 +188,16 @@ def kmc_regenerate(ctx, lys, what, disorder, seed, loop):
     """Redraw axes and/or positions of lysosome `lys` (-1: all) on the device."""
     _check(lib().kmc_regenerate(ctx.handle, int(lys), int(what), float(disorder),
                                 C.c_uint64(int(seed)), C.c_uint32(int(loop))))
+
+
+def kmc_regenerate_rsa(ctx, lys, radius, diameter, seed, loop, max_candidates=0):
+    """Random sequential addition of lysosome `lys` on the device; returns the
+    number of candidates used."""
+    used = C.c_int64(0)
+    _check(lib().kmc_regenerate_rsa(ctx.handle, int(lys), float(radius), float(diameter),
+                                    C.c_uint64(int(seed)), C.c_uint32(int(loop)),
+                                    int(max_candidates), C.byref(used)))
+    return int(used.value)
 
 
 def kmc_debug_stall(ctx):

@@ -109,3 +109,67 @@ def test_regenerate_errors():
             kmc.kmc_regenerate(ctx, args[0], args[1], args[2], 1, 0)
         assert e.value.status == kmc.KMC_EINVAL
     kmc.kmc_destroy(ctx)
+
+
+# --- random sequential addition on the device ---------------------------------
+
+@pytest.mark.parametrize("prec", [kmc.KMC_FP64_PLAIN, kmc.KMC_FP32_MIXED])
+def test_rsa_matches_the_oracle(prec):
+    """Same candidate stream, same sequential rule: the same candidates are kept
+    (candidate count exact), positions to the last bits of sin and cos."""
+    lyss = [inputs.make_lysosome(150, 12e-9, 0.05, seed=5),
+            inputs.make_lysosome(2000, 14e-9, 0.10, seed=6)]
+    ctx = kmc.kmc_create(lyss, prec, center=np.zeros(3))
+    for lys, R, d, seed, loop in [(0, 60e-9, 12e-9, 9, 1), (1, inputs.lysosome_radius(2000, 14e-9, 0.1),
+                                                             14e-9, 21, 3)]:
+        used = kmc.kmc_regenerate_rsa(ctx, lys, R, d, seed, loop)
+        o, ou = oracle.rsa(lyss[lys].n, R, d, seed, loop, lys)
+        assert used == ou and used > lyss[lys].n
+        np.testing.assert_allclose(kmc.kmc_read(ctx, kmc.KMC_READ_POSITIONS, lys), o,
+                                   rtol=0, atol=1e-15 * R)
+    # the moments restart along the axes, and a run on the new positions goes through
+    m = kmc.kmc_read(ctx, kmc.KMC_READ_MOMENTS, 1)
+    ax = kmc.kmc_read(ctx, kmc.KMC_READ_AXES, 1)
+    np.testing.assert_allclose(np.abs(np.sum(m * ax, axis=1)), 1.0, atol=2e-6)
+    assert np.all(m[:, 2] >= -1e-7)
+    kmc.kmc_run(ctx, 0.02, 1e5, 40, 2, 1, 7)
+    assert np.all(np.isfinite(kmc.kmc_read(ctx, kmc.KMC_READ_LOOP_M, 1)))
+    kmc.kmc_destroy(ctx)
+
+
+def test_rsa_packing_at_20000():
+    spatial = pytest.importorskip("scipy.spatial")
+    n, d, c = 20000, 12e-9, 0.10
+    R = inputs.lysosome_radius(n, d, c)
+    # n NPs far apart at creation; the addition gives them their places
+    lys = inputs.Lysosome(pos=np.zeros((n, 3)) + np.arange(n)[:, None] * 1e-6,
+                          axis=inputs.random_axes(n, np.random.default_rng(2)),
+                          vol=np.full(n, inputs.sphere_volume(d)), Ms=1e6, Keff=1.3e4, T=300.0,
+                          tau0=1e-10, d=d)
+    ctx = kmc.kmc_create([lys], kmc.KMC_FP32_MIXED, center=np.zeros(3))
+    used = kmc.kmc_regenerate_rsa(ctx, 0, R, d, 4, 1)
+    p = kmc.kmc_read(ctx, kmc.KMC_READ_POSITIONS, 0)
+    kmc.kmc_destroy(ctx)
+    assert used >= n
+    assert np.linalg.norm(p, axis=1).max() <= (R - d / 2) * (1 + 1e-12)
+    dmin, _ = spatial.cKDTree(p).query(p, k=2)
+    assert dmin[:, 1].min() >= d * (1 - 1e-12)
+
+
+def test_rsa_rejects_bad_arguments_and_reports_a_packing_too_dense():
+    lys = inputs.make_lysosome(300, 12e-9, 0.05, seed=3)
+    ctx = kmc.kmc_create([lys], kmc.KMC_FP64_PLAIN, center=np.zeros(3))
+    before = kmc.kmc_read(ctx, kmc.KMC_READ_POSITIONS, 0)
+    for R, d in [(10e-9, 30e-9), (1e-7, 0.0), (float("nan"), 1e-8)]:
+        with pytest.raises(kmc.KmcError) as e:
+            kmc.kmc_regenerate_rsa(ctx, 0, R, d, 1, 1)
+        assert e.value.status == kmc.KMC_EINVAL
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.kmc_regenerate_rsa(ctx, 1, 1e-7, 1e-8, 1, 1)
+    assert e.value.status == kmc.KMC_EINVAL
+    # 300 spheres of 12 nm cannot fit in a 40 nm sphere
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.kmc_regenerate_rsa(ctx, 0, 40e-9, 12e-9, 1, 1, max_candidates=20000)
+    assert e.value.status == kmc.KMC_ESTATE
+    assert np.array_equal(kmc.kmc_read(ctx, kmc.KMC_READ_POSITIONS, 0), before)
+    kmc.kmc_destroy(ctx)
