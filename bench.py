@@ -28,7 +28,8 @@ stated in the line's config; their FP64 and oracle legs run bounded samples.
 --row measures one of the outputs built on top of the step instead, with its
 own metric: f1 the local concentration phi_N of Eq. 8 (N = 10) on the 50 000-NP
 lysosome, f2 the regeneration of axes and positions between loops on the same
-lysosome, f4 the Ref. [8] mean-magnetisation mode on the 8 x 2000-NP workload.
+lysosome (lattice and disorder), f2r its random sequential addition, f4 the Ref.
+[8] mean-magnetisation mode on the 8 x 2000-NP workload.
 """
 from __future__ import annotations
 
@@ -228,7 +229,7 @@ def run_row(args):
                 times.append(e0.elapsed_time(e1) / 1e3)
         return sum(times) / len(times)
 
-    if args.row in ("f1", "f2"):
+    if args.row in ("f1", "f2", "f2r"):
         (lys,), _ = inputs.config_large50000(seed=0)
         n = lys.n
         t0 = time.perf_counter()
@@ -290,6 +291,43 @@ def run_row(args):
                 "gpu_launches": args.steps,
                 "cpu_baseline": {"value": n / tc, "unit": "NPs/s", "cores": 1, "kind": "oracle",
                                  "sample": "%d regenerations of all %d NPs" % (reps, n)}}
+    elif args.row == "f2r":
+        d, R = 16e-9, inputs.lysosome_radius(n, 16e-9, 0.10)
+        used = []
+        t = events(lambda k: used.append(kmc.kmc_regenerate_rsa(ctx, 0, R, d, 11, k + 1)))
+        value = n / t
+        # distance checks: each candidate against the spheres kept before it,
+        # about used * n / 2, at 8 FP64 flops each (no FMA)
+        flops = 8.0 * used[-1] * n / 2
+        (l1,), _ = inputs.config_single2000(replicas=1, seed=0)
+        R1 = inputs.lysosome_radius(l1.n, 14e-9, 0.10)
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 2.0:
+            oracle.rsa(l1.n, R1, 14e-9, 11, reps + 1)
+            reps += 1
+        tc = (time.perf_counter() - t0) / reps
+        line = {"metric": "NPs placed/s, random sequential addition (10 % volume fraction)",
+                "value": value, "unit": "NPs/s", "ms_per_step": 1e3 * t, "dtype": "f64",
+                "config": {"workload": CONFIGS["c4"][0], "row": "f2r",
+                           "step": "all 50 000 NPs placed anew (%d candidates), then the NP "
+                                   "arrays rebuilt" % used[-1]},
+                "roofline": {"bound": "alu", "achieved": flops / t / 1e12,
+                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                             "kernel": "rsa_check_kernel",
+                             "note": "8 FP64 flops per distance check, used * n / 2 checks; "
+                                     "sequential by definition: batches of candidates checked "
+                                     "in parallel, then kept in order by one thread"},
+                "e2e": {"value": value, "unit": "NPs/s", "h2d_bytes_per_step": n * 24,
+                        "d2h_bytes_per_step": n * 24},
+                # batches of 2048 candidates, three kernels each; then the regeneration
+                # kernel and the two source refreshes
+                "gpu_launches": args.steps * (3 * -(-used[-1] // 2048) + 3),
+                "cpu_baseline": {"value": l1.n / tc, "unit": "NPs/s", "cores": 1,
+                                 "kind": "oracle",
+                                 "sample": "the 2000-NP lysosome (cost grows as n^2), "
+                                           "%d runs" % reps}}
     else:  # f4
         lyss, run = inputs.config_single2000(replicas=8, seed=0)
         n_np = sum(l.n for l in lyss)
@@ -386,7 +424,7 @@ def main():
                     help="pin the FP64-plain launch shape as warps,tile,chunk (default: autotuned)")
     ap.add_argument("--config", default="c1", choices=sorted(CONFIGS),
                     help="workload (default c1, the headline line)")
-    ap.add_argument("--row", default="", choices=["", "f1", "f2", "f4"],
+    ap.add_argument("--row", default="", choices=["", "f1", "f2", "f2r", "f4"],
                     help="measure an output built on the step instead (see above)")
     args = ap.parse_args()
     if args.warmup < 3:

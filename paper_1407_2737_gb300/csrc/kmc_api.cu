@@ -1399,9 +1399,10 @@ kmc_status kmc_regenerate_rsa(kmc_ctx *c, int32_t lys, double radius, double dia
                         cudaMemcpyHostToDevice));
   }
   // scratch, freed on every return
-  const int B = static_cast<int>(std::min<long long>(4096, std::max<long long>(256, 2ll * n)));
+  const int B = static_cast<int>(
+      std::min<long long>(kmc::kRsaMaxBatch, std::max<long long>(256, 2ll * n)));
   struct Scratch {
-    void *p[8] = {};
+    void *p[7] = {};
     ~Scratch() {
       for (void *q : p)
         if (q) cudaFree(q);
@@ -1412,10 +1413,9 @@ kmc_status kmc_regenerate_rsa(kmc_ctx *c, int32_t lys, double radius, double dia
   KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[2]), sizeof(int32_t) * B));
   KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[3]), sizeof(int32_t) * B));
   KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[4]), sizeof(int32_t) * B * kmc::kRsaMaxConf));
-  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[5]), sizeof(int32_t) * B));
-  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[6]), sizeof(int32_t)));
-  KMC_TRY(dalloc(reinterpret_cast<long long **>(&sc.p[7]), sizeof(long long)));
-  KMC_CUDA(cudaMemsetAsync(sc.p[6], 0, sizeof(int32_t), c->stream));
+  KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[5]), sizeof(int32_t)));
+  KMC_TRY(dalloc(reinterpret_cast<long long **>(&sc.p[6]), sizeof(long long)));
+  KMC_CUDA(cudaMemsetAsync(sc.p[5], 0, sizeof(int32_t), c->stream));
   kmc::RsaArgs a;
   a.Rb = radius - 0.5 * diameter;
   a.d2 = diameter * diameter;
@@ -1429,9 +1429,8 @@ kmc_status kmc_regenerate_rsa(kmc_ctx *c, int32_t lys, double radius, double dia
   a.clear = static_cast<int32_t *>(sc.p[2]);
   a.nconf = static_cast<int32_t *>(sc.p[3]);
   a.conf = static_cast<int32_t *>(sc.p[4]);
-  a.acc = static_cast<int32_t *>(sc.p[5]);
-  a.kept = static_cast<int32_t *>(sc.p[6]);
-  a.used = static_cast<long long *>(sc.p[7]);
+  a.kept = static_cast<int32_t *>(sc.p[5]);
+  a.used = static_cast<long long *>(sc.p[6]);
   int32_t kept = 0;
   long long c0 = 0;
   while (kept < n) {

@@ -179,32 +179,57 @@ __global__ void rsa_check_kernel(const RsaArgs a) {
   }
 }
 
-// One thread walks the batch in candidate order: a candidate that cleared the
-// earlier batches is kept unless a candidate kept earlier in this batch lies
-// closer than d. That is the sequential rule, candidate by candidate.
+// The batch in candidate order: a candidate that cleared the earlier batches
+// is kept unless a candidate kept earlier in this batch lies closer than d.
+// That is the sequential rule, candidate by candidate. The walk is one thread
+// on shared-memory copies (dynamic shared memory: rsa_resolve_smem(B) bytes);
+// the kept centres are then copied out by the whole block.
+__host__ __device__ constexpr size_t rsa_resolve_smem(int B) {
+  return static_cast<size_t>(B) * (3 + kRsaMaxConf) * sizeof(int32_t);
+}
+
 __global__ void rsa_resolve_kernel(const RsaArgs a) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int kept = *a.kept;
-  for (int k = 0; k < a.B && kept < a.n; ++k) {
-    bool ok = a.clear[k] != 0;
-    if (ok) {
-      const int nc = a.nconf[k];
-      if (nc <= kRsaMaxConf) {
-        for (int q = 0; q < nc && ok; ++q) ok = a.acc[a.conf[k * kRsaMaxConf + q]] == 0;
-      } else {
-        for (int j = 0; j < k && ok; ++j)
-          ok = !(a.acc[j] && rsa_d2(a.cand + 3 * k, a.cand + 3 * j) < a.d2);
+  extern __shared__ int32_t rsa_sm[];
+  int32_t *s_clear = rsa_sm, *s_nconf = rsa_sm + a.B, *s_slot = rsa_sm + 2 * a.B;
+  int32_t *s_conf = rsa_sm + 3 * a.B;
+  __shared__ int32_t s_kept;
+  for (int k = threadIdx.x; k < a.B; k += blockDim.x) {
+    s_clear[k] = a.clear[k];
+    s_nconf[k] = a.nconf[k];
+    s_slot[k] = -1;
+  }
+  for (int q = threadIdx.x; q < a.B * kRsaMaxConf; q += blockDim.x) s_conf[q] = a.conf[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int kept = *a.kept;
+    for (int k = 0; k < a.B && kept < a.n; ++k) {
+      bool ok = s_clear[k] != 0;
+      if (ok) {
+        const int nc = s_nconf[k];
+        if (nc <= kRsaMaxConf) {
+          for (int q = 0; q < nc && ok; ++q) ok = s_slot[s_conf[k * kRsaMaxConf + q]] < 0;
+        } else {
+          for (int j = 0; j < k && ok; ++j)
+            ok = !(s_slot[j] >= 0 && rsa_d2(a.cand + 3 * k, a.cand + 3 * j) < a.d2);
+        }
+      }
+      if (ok) {
+        s_slot[k] = kept;
+        if (++kept == a.n) *a.used = a.c0 + k + 1;
       }
     }
-    a.acc[k] = ok ? 1 : 0;
-    if (ok) {
-      a.pos[3 * kept] = a.cand[3 * k];
-      a.pos[3 * kept + 1] = a.cand[3 * k + 1];
-      a.pos[3 * kept + 2] = a.cand[3 * k + 2];
-      if (++kept == a.n) *a.used = a.c0 + k + 1;
+    s_kept = kept;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < a.B; k += blockDim.x) {
+    const int sl = s_slot[k];
+    if (sl >= 0) {
+      a.pos[3 * sl] = a.cand[3 * k];
+      a.pos[3 * sl + 1] = a.cand[3 * k + 1];
+      a.pos[3 * sl + 2] = a.cand[3 * k + 2];
     }
   }
-  *a.kept = kept;
+  if (threadIdx.x == 0) *a.kept = s_kept;
 }
 
 }  // namespace kmc

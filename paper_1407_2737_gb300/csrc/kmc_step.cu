@@ -1007,7 +1007,7 @@ cudaError_t launch_rsa_batch(const RsaArgs &a, cudaStream_t st) {
   if (a.B <= 0) return cudaSuccess;
   rsa_candidates_kernel<<<(a.B + 127) / 128, 128, 0, st>>>(a);
   rsa_check_kernel<<<a.B, 128, 0, st>>>(a);
-  rsa_resolve_kernel<<<1, 32, 0, st>>>(a);
+  rsa_resolve_kernel<<<1, 1024, rsa_resolve_smem(a.B), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1046,6 +1046,9 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<16>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rsa_resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(rsa_resolve_smem(kRsaMaxBatch)));
   return e;
 }
 

@@ -146,7 +146,7 @@ enum : int32_t { kRegenAxes = 1, kRegenPositions = 2, kRegenGiven = 4 };
 // Random sequential addition on the device, one batch of B candidates
 // (candidate indices c0 .. c0 + B - 1). The batch keeps, in candidate order,
 // each candidate that clears every sphere kept before it, until n are kept.
-constexpr int kRsaMaxConf = 16;  // listed conflicts per candidate; more: checked in full
+constexpr int kRsaMaxConf = 8;  // listed conflicts per candidate; more: checked in full
 struct RsaArgs {
   double Rb;                   // radius of the ball of centres, R - d/2, m
   double d2;                   // d^2, m^2
@@ -163,8 +163,8 @@ struct RsaArgs {
   int32_t *clear;              // [B] 1 if the candidate clears the earlier batches' spheres
   int32_t *nconf;              // [B] earlier candidates of the batch closer than d
   int32_t *conf;               // [B][kRsaMaxConf] their indices
-  int32_t *acc;                // [B] 1 if kept
 };
+constexpr int kRsaMaxBatch = 2048;  // candidates per batch at most
 struct RegenArgs {
   int32_t off, n, lys, what;
   uint32_t loop;
