@@ -297,7 +297,8 @@ def run_row(args):
         t = events(lambda k: used.append(kmc.kmc_regenerate_rsa(ctx, 0, R, d, 11, k + 1)))
         value = n / t
         # distance checks: each candidate against the spheres kept before it,
-        # about used * n / 2, at 8 FP64 flops each (no FMA)
+        # about used * n / 2, at 8 flops each (an FP32 pre-screen; FP64 only
+        # within the rounding margin around d)
         flops = 8.0 * used[-1] * n / 2
         (l1,), _ = inputs.config_single2000(replicas=1, seed=0)
         R1 = inputs.lysosome_radius(l1.n, 14e-9, 0.10)
@@ -313,12 +314,13 @@ def run_row(args):
                            "step": "all 50 000 NPs placed anew (%d candidates), then the NP "
                                    "arrays rebuilt" % used[-1]},
                 "roofline": {"bound": "alu", "achieved": flops / t / 1e12,
-                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": flops / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                             "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
+                             "frac": flops / t / 1e12 / fp32_peak_tflops(), "traffic": None,
                              "kernel": "rsa_check_kernel",
-                             "note": "8 FP64 flops per distance check, used * n / 2 checks; "
+                             "note": "8 FP32 flops per distance check, used * n / 2 checks; "
                                      "sequential by definition: batches of candidates checked "
-                                     "in parallel, then kept in order by one thread"},
+                                     "in parallel, then kept in order by one thread, whose walk "
+                                     "and the per-batch launches bound the placement"},
                 "e2e": {"value": value, "unit": "NPs/s", "h2d_bytes_per_step": n * 24,
                         "d2h_bytes_per_step": n * 24},
                 # batches of 2048 candidates, three kernels each; then the regeneration

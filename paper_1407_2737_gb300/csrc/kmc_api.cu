@@ -1402,7 +1402,7 @@ kmc_status kmc_regenerate_rsa(kmc_ctx *c, int32_t lys, double radius, double dia
   const int B = static_cast<int>(
       std::min<long long>(kmc::kRsaMaxBatch, std::max<long long>(256, 2ll * n)));
   struct Scratch {
-    void *p[7] = {};
+    void *p[8] = {};
     ~Scratch() {
       for (void *q : p)
         if (q) cudaFree(q);
@@ -1415,6 +1415,7 @@ kmc_status kmc_regenerate_rsa(kmc_ctx *c, int32_t lys, double radius, double dia
   KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[4]), sizeof(int32_t) * B * kmc::kRsaMaxConf));
   KMC_TRY(dalloc(reinterpret_cast<int32_t **>(&sc.p[5]), sizeof(int32_t)));
   KMC_TRY(dalloc(reinterpret_cast<long long **>(&sc.p[6]), sizeof(long long)));
+  KMC_TRY(dalloc(reinterpret_cast<float4 **>(&sc.p[7]), sizeof(float4) * n));
   KMC_CUDA(cudaMemsetAsync(sc.p[5], 0, sizeof(int32_t), c->stream));
   kmc::RsaArgs a;
   a.Rb = radius - 0.5 * diameter;
@@ -1431,6 +1432,18 @@ kmc_status kmc_regenerate_rsa(kmc_ctx *c, int32_t lys, double radius, double dia
   a.conf = static_cast<int32_t *>(sc.p[4]);
   a.kept = static_cast<int32_t *>(sc.p[5]);
   a.used = static_cast<long long *>(sc.p[6]);
+  a.posf = static_cast<float4 *>(sc.p[7]);
+  // FP32 pre-screen: with centres within Rb of the origin, converting them
+  // to FP32 (error <= u Rb per coordinate, u = 2^-24) and forming the squared
+  // distance D^2 in FP32 errs by at most 4 sqrt(3) u Rb D + 5 u D^2; the
+  // margin 2M = 32 u (Rb d + d^2) is over four times that at D = d, and the
+  // error grows more slowly than |D^2 - d^2| away from it
+  {
+    const double u = 0x1.0p-24;
+    const double M = 16.0 * u * (a.Rb * diameter + a.d2);
+    a.d2_lo = static_cast<float>(std::max(0.0, a.d2 - 2.0 * M));
+    a.d2_hi = static_cast<float>(a.d2 + 2.0 * M);
+  }
   int32_t kept = 0;
   long long c0 = 0;
   while (kept < n) {

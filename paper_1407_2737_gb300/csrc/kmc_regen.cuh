@@ -154,15 +154,27 @@ __global__ void rsa_candidates_kernel(const RsaArgs a) {
 }
 
 // Block k: does candidate k clear every sphere kept by earlier batches, and
-// which earlier candidates of this batch lie closer than d.
+// which earlier candidates of this batch lie closer than d. Against the kept
+// spheres an FP32 squared distance settles the pair unless it falls within
+// the margin [d2_lo, d2_hi] around d^2, which bounds the FP32 error for
+// centres inside the ball; there the FP64 test of the definition decides.
 __global__ void rsa_check_kernel(const RsaArgs a) {
   __shared__ int s_nconf;
   const int k = blockIdx.x;
   const int kept = *a.kept;
   const double *p = a.cand + 3 * k;
+  const float px = static_cast<float>(p[0]), py = static_cast<float>(p[1]),
+              pz = static_cast<float>(p[2]);
   bool clash = false;
-  for (int j = threadIdx.x; j < kept && !clash; j += blockDim.x)
-    clash = rsa_d2(p, a.pos + 3 * j) < a.d2;
+  for (int j = threadIdx.x; j < kept && !clash; j += blockDim.x) {
+    const float4 q = a.posf[j];
+    const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+    const float d2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    if (d2f < a.d2_lo)
+      clash = true;
+    else if (d2f <= a.d2_hi)
+      clash = rsa_d2(p, a.pos + 3 * j) < a.d2;
+  }
   if (threadIdx.x == 0) s_nconf = 0;
   clash = __syncthreads_or(clash);
   if (!clash) {
@@ -224,9 +236,12 @@ __global__ void rsa_resolve_kernel(const RsaArgs a) {
   for (int k = threadIdx.x; k < a.B; k += blockDim.x) {
     const int sl = s_slot[k];
     if (sl >= 0) {
-      a.pos[3 * sl] = a.cand[3 * k];
-      a.pos[3 * sl + 1] = a.cand[3 * k + 1];
-      a.pos[3 * sl + 2] = a.cand[3 * k + 2];
+      const double x = a.cand[3 * k], y = a.cand[3 * k + 1], z = a.cand[3 * k + 2];
+      a.pos[3 * sl] = x;
+      a.pos[3 * sl + 1] = y;
+      a.pos[3 * sl + 2] = z;
+      a.posf[sl] = make_float4(static_cast<float>(x), static_cast<float>(y),
+                               static_cast<float>(z), 0.0f);
     }
   }
   if (threadIdx.x == 0) *a.kept = s_kept;

@@ -159,6 +159,9 @@ struct RsaArgs {
   int32_t *kept;               // [1] spheres kept so far (updated by the batch)
   long long *used;             // [1] candidates used when the n-th was kept
   double *pos;                 // [n][3] kept centres, m, about the lysosome centre
+  float4 *posf;                // [n] the same in FP32 (x, y, z, 0), for the pre-screen
+  float d2_lo, d2_hi;          // FP32 squared distances below d2_lo clash and above d2_hi
+                               // clear for certain; in between the FP64 test decides
   double *cand;                // [B][3] scratch
   int32_t *clear;              // [B] 1 if the candidate clears the earlier batches' spheres
   int32_t *nconf;              // [B] earlier candidates of the batch closer than d
