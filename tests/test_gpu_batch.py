@@ -89,3 +89,48 @@ def test_fp64_chained_batch_flip_for_flip():
                                    rtol=0, atol=1e-11 * scale)
     kmc.kmc_destroy(ctx)
     assert compared >= 2
+
+
+def _batch4():
+    return [inputs.make_lysosome(n, 12e-9, 0.05, seed=60 + q) for q, n in enumerate([180, 90, 333, 45])]
+
+
+def test_chained_batch_on_a_caller_stream_gives_the_same_bits():
+    torch = pytest.importorskip("torch")
+    out = []
+    for use_stream in (False, True):
+        ctx = kmc.kmc_create(_batch4(), kmc.KMC_FP32_MIXED, center=np.zeros(3))
+        kmc.kmc_tuning(ctx, 4, 64, 0)
+        st = torch.cuda.Stream() if use_stream else None
+        if st is not None:
+            kmc.kmc_set_stream(ctx, st.cuda_stream)
+        kmc.kmc_run(ctx, [0.02, 0.03, 0.025, 0.015], 1e5, 40, 3, 1, 2)
+        out.append([kmc.kmc_read(ctx, w, l) for l in range(4)
+                    for w in (kmc.KMC_READ_LOOP_M, kmc.KMC_READ_MOMENTS, kmc.KMC_READ_COUNTERS)])
+        kmc.kmc_destroy(ctx)
+    for x, y in zip(*out):
+        assert np.array_equal(x, y)
+
+
+def test_chained_batch_checkpoint_resume_is_bit_identical(tmp_path):
+    H = [0.02, 0.03, 0.025, 0.015]
+    for prec in (kmc.KMC_FP64_PLAIN, kmc.KMC_FP32_MIXED):
+        a = kmc.kmc_create(_batch4(), prec, center=np.zeros(3))
+        kmc.kmc_run(a, H, 1e5, 40, 3, 0, 8)
+        kmc.kmc_run(a, H, 1e5, 40, 2, 0, 8)
+        ref = [kmc.kmc_read(a, w, l) for l in range(4)
+               for w in (kmc.KMC_READ_MOMENTS, kmc.KMC_READ_LOOP_M)]
+        kmc.kmc_destroy(a)
+        b = kmc.kmc_create(_batch4(), prec, center=np.zeros(3))
+        kmc.kmc_run(b, H, 1e5, 40, 3, 0, 8)
+        p = str(tmp_path / ("batch%d.bin" % prec))
+        kmc.kmc_save(b, p)
+        kmc.kmc_destroy(b)
+        c = kmc.kmc_create(_batch4(), prec, center=np.zeros(3))
+        kmc.kmc_load(c, p)
+        kmc.kmc_run(c, H, 1e5, 40, 2, 0, 8)
+        got = [kmc.kmc_read(c, w, l) for l in range(4)
+               for w in (kmc.KMC_READ_MOMENTS, kmc.KMC_READ_LOOP_M)]
+        kmc.kmc_destroy(c)
+        for x, y in zip(ref, got):
+            assert np.array_equal(x, y)
