@@ -250,11 +250,12 @@ def run_row(args):
                 "dtype": "f64", "config": {"workload": CONFIGS["c4"][0], "row": "f1",
                                            "step": "phi_N of all 50 000 NPs (all pairs)"},
                 "roofline": {"bound": "alu", "achieved": 8 * value / 1e12,
-                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": 8 * value / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                             "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
+                             "frac": 8 * value / 1e12 / fp32_peak_tflops(), "traffic": None,
                              "kernel": "local_concentration_kernel",
-                             "note": "8 FP64 instructions per pair, none an FMA, so a full "
-                                     "FP64 pipe gives 50 % of the FMA peak"},
+                             "note": "an FP32 pre-screen per pair (8 flops), FP64 only for "
+                                     "the pairs that can enter the N-nearest list; one warp "
+                                     "per 32 targets leaves ~9 warps per SM (latency-bound)"},
                 "e2e": {"value": pairs / (t + t_create), "unit": "pairs/s",
                         "h2d_bytes_per_step": n * 7 * 8, "d2h_bytes_per_step": n * 8},
                 "gpu_launches": args.steps,

@@ -159,6 +159,7 @@ struct kmc_ctx {
   double *d_dh = nullptr;     // [N] Eq. 6 accumulator (reduced field)
   void *d_pos64 = nullptr;    // FP32 contexts: [N] dbl4 positions in FP64 (x, y, z, w)
   double *d_phi = nullptr;    // [max n] scratch of kmc_local_concentration
+  float4 *d_phif = nullptr;   // [max n] its FP32 copy of the positions
   std::vector<double> len;    // [n_lys] length unit L, m
   std::vector<double> ctr;    // [n_lys][3] frame origin, m
   std::vector<double> pos_si; // [N][3] current positions, m
@@ -606,7 +607,7 @@ void free_ctx(kmc_ctx *c) {
   drop_graph(c);
   void *ptrs[] = {c->d_lys,   c->d_pos,    c->d_axis,    c->d_m,        c->d_src[0],
                   c->d_src[1], c->d_slot,  c->d_beta,    c->d_vfrac,    c->d_eacc,
-                  c->d_dh,    c->d_pos64,  c->d_phi,     c->d_nodes,    c->d_possi,
+                  c->d_dh,    c->d_pos64,  c->d_phi,     c->d_nodes,    c->d_possi, c->d_phif,
                   c->d_loop,  c->d_cnt,    c->d_err,     c->d_rs,       c->d_items,
                   c->d_partial, c->d_arrivals, c->d_dbg, c->d_dbg_flags};
   for (void *p : ptrs)
@@ -1200,8 +1201,23 @@ kmc_status kmc_local_concentration(kmc_ctx *c, int32_t lys, int32_t N, double *p
     for (int x : c->n) max_n = std::max(max_n, x);
     KMC_TRY(dalloc(&c->d_phi, sizeof(double) * max_n));
   }
+  if (!c->d_phif) {
+    int max_n = 0;
+    for (int x : c->n) max_n = std::max(max_n, x);
+    KMC_TRY(dalloc(&c->d_phif, sizeof(float4) * max_n));
+  }
   const dbl4 *pos = static_cast<const dbl4 *>(c->fp32 ? c->d_pos64 : c->d_pos) + c->off[lys];
-  KMC_CUDA(kmc::launch_local_concentration(pos, n, N, c->d_phi, c->stream));
+  // largest distance from the frame origin, in units of L (with a little
+  // slack for the rounding of the device's frame coordinates)
+  double rmax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double *q = &c->pos_si[3ull * (c->off[lys] + i)];
+    const double dx = q[0] - c->ctr[3 * lys], dy = q[1] - c->ctr[3 * lys + 1],
+                 dz = q[2] - c->ctr[3 * lys + 2];
+    rmax = std::max(rmax, std::sqrt(dx * dx + dy * dy + dz * dz));
+  }
+  rmax = 1.01 * rmax / c->len[lys];
+  KMC_CUDA(kmc::launch_local_concentration(pos, n, N, rmax, c->d_phif, c->d_phi, c->stream));
   KMC_CUDA(cudaMemcpyAsync(phi, c->d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   return KMC_OK;

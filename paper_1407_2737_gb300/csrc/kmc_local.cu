@@ -2,13 +2,20 @@
 // device: for every NP i of one lysosome, r_N = distance to its N-th nearest
 // neighbour and phi_N,i = 3 N V_i / (4 pi r_N^3).
 //
-// One thread per target NP, all pairs in FP64 (N^2 work, like the dipolar sum
-// but run once per geometry). Source positions are staged through shared
-// memory tile by tile; each thread keeps the N smallest squared distances seen
+// One thread per target NP, all pairs (N^2 work, like the dipolar sum but run
+// once per geometry). FP32 copies of the source positions are staged through
+// shared memory tile by tile; each thread keeps the N smallest squared FP64 distances seen
 // so far in ascending order and inserts a new one only when it is below the
 // current N-th (the N-th order statistic does not depend on how ties between
 // equal distances are broken). Squared distances are formed as
 // (dx^2 + dy^2) + dz^2 without contraction, the order the oracle uses.
+//
+// An FP32 pre-screen skips a pair whose FP32 squared distance exceeds the
+// current N-th by more than a bound on the FP32 error: with coordinates of
+// magnitude at most rmax (converted to FP32 with error <= u rmax, u = 2^-24),
+// the FP32 value errs by at most 4 sqrt(3) u rmax D + 5 u D^2, and the
+// margin is 64 u (rmax sqrt(thr) + thr). Every pair that could enter the list
+// is still formed in FP64 as above, so phi is unchanged bit for bit.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -19,25 +26,43 @@ namespace kmc {
 namespace {
 
 // one warp per block: many small blocks spread the targets evenly over the SMs
-// (50 000 NPs: 46.9 ms against 50.9 ms with 128-thread blocks)
+// (50 000 NPs, before the FP32 pre-screen: 46.9 ms against 50.9 ms with
+// 128-thread blocks; splitting a target's sources over 4 warps was slower,
+// since each warp's threshold then tightens on a quarter of them)
 constexpr int kPhiThreads = 32;
 constexpr int kPhiTile = 512;
 
+__device__ __forceinline__ float screen_limit(double thr, double rmax) {
+  if (!(thr < INFINITY)) return INFINITY;
+  const double u = 0x1.0p-24;
+  return static_cast<float>(thr + 64.0 * u * (rmax * sqrt(thr) + thr));
+}
+
+// FP32 copy of the positions, made once per call.
+__global__ void positions_f32_kernel(const dbl4 *__restrict__ pos, int n, float4 *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n)
+    out[i] = make_float4(static_cast<float>(pos[i].x), static_cast<float>(pos[i].y),
+                         static_cast<float>(pos[i].z), 0.0f);
+}
+
 __global__ void __launch_bounds__(kPhiThreads)
-    local_concentration_kernel(const dbl4 *__restrict__ pos, int n, int N,
-                               double *__restrict__ phi) {
-  __shared__ double sx[kPhiTile], sy[kPhiTile], sz[kPhiTile];
+    local_concentration_kernel(const dbl4 *__restrict__ pos, const float4 *__restrict__ posf,
+                               int n, int N, double rmax, double *__restrict__ phi) {
+  __shared__ float sx[kPhiTile], sy[kPhiTile], sz[kPhiTile];
   const int i = blockIdx.x * kPhiThreads + threadIdx.x;
   const bool active = i < n;
   const dbl4 p = pos[active ? i : 0];
+  const float4 pf = posf[active ? i : 0];
   double best[kPhiMaxN];
   for (int q = 0; q < N; ++q) best[q] = INFINITY;
   double thr = INFINITY;  // best[N - 1]
+  float lim = INFINITY;   // FP32 squared distances above it cannot enter the list
   for (int t0 = 0; t0 < n; t0 += kPhiTile) {
     const int cnt = min(kPhiTile, n - t0);
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += kPhiThreads) {
-      const dbl4 s = pos[t0 + j];
+      const float4 s = posf[t0 + j];
       sx[j] = s.x;
       sy[j] = s.y;
       sz[j] = s.z;
@@ -45,9 +70,13 @@ __global__ void __launch_bounds__(kPhiThreads)
     __syncthreads();
     if (!active) continue;
     for (int j = 0; j < cnt; ++j) {
-      const double dx = __dsub_rn(sx[j], p.x);
-      const double dy = __dsub_rn(sy[j], p.y);
-      const double dz = __dsub_rn(sz[j], p.z);
+      const float dxf = sx[j] - pf.x, dyf = sy[j] - pf.y, dzf = sz[j] - pf.z;
+      if (fmaf(dzf, dzf, fmaf(dyf, dyf, dxf * dxf)) > lim) continue;
+      // a pair that could enter the list: its distance as the oracle forms it
+      const dbl4 s = pos[t0 + j];
+      const double dx = __dsub_rn(s.x, p.x);
+      const double dy = __dsub_rn(s.y, p.y);
+      const double dz = __dsub_rn(s.z, p.z);
       const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
       if (d2 < thr && t0 + j != i) {
         int k = N - 1;
@@ -57,6 +86,7 @@ __global__ void __launch_bounds__(kPhiThreads)
         }
         best[k] = d2;
         thr = best[N - 1];
+        lim = screen_limit(thr, rmax);
       }
     }
   }
@@ -68,11 +98,12 @@ __global__ void __launch_bounds__(kPhiThreads)
 
 }  // namespace
 
-cudaError_t launch_local_concentration(const dbl4 *pos, int n, int N, double *phi,
-                                       cudaStream_t st) {
+cudaError_t launch_local_concentration(const dbl4 *pos, int n, int N, double rmax,
+                                       float4 *posf, double *phi, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  positions_f32_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, n, posf);
   const int blocks = (n + kPhiThreads - 1) / kPhiThreads;
-  local_concentration_kernel<<<blocks, kPhiThreads, 0, st>>>(pos, n, N, phi);
+  local_concentration_kernel<<<blocks, kPhiThreads, 0, st>>>(pos, posf, n, N, rmax, phi);
   return cudaGetLastError();
 }
 

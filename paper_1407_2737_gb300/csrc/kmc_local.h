@@ -13,8 +13,9 @@ constexpr int kPhiMaxN = 64;
 // phi[i] = 3 N w_i / r_N^3 for the n NPs of pos (one lysosome; x, y, z in units
 // of the length L, w = V_i / (4 pi L^3)), with r_N the distance to the N-th
 // nearest other NP: Eq. 8 with V_i = 4 pi L^3 w_i. Requires 1 <= N <= n - 1,
-// N <= kPhiMaxN.
-cudaError_t launch_local_concentration(const dbl4 *pos, int n, int N, double *phi,
-                                       cudaStream_t st);
+// N <= kPhiMaxN. rmax bounds the distance of every position from the origin
+// (it sets the margin of the FP32 pre-screen); posf is [n] scratch.
+cudaError_t launch_local_concentration(const dbl4 *pos, int n, int N, double rmax,
+                                       float4 *posf, double *phi, cudaStream_t st);
 
 }  // namespace kmc
