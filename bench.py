@@ -422,7 +422,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison")
     ap.add_argument("--shape", default="",
-                    help="pin the FP32 launch shape as warps,tile,chunk (default: autotuned)")
+                    help="pin the FP32 launch shape as warps,tile,chunk[,targets per lane] "
+                         "(default: autotuned)")
     ap.add_argument("--shape64", default="",
                     help="pin the FP64-plain launch shape as warps,tile,chunk (default: autotuned)")
     ap.add_argument("--config", default="c1", choices=sorted(CONFIGS),
@@ -478,12 +479,16 @@ def main():
     ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
     kmc.kmc_set_stream(ctx, stream.cuda_stream)
     if args.shape:
-        kmc.kmc_tuning(ctx, *[int(x) for x in args.shape.split(",")])
+        sh = [int(x) for x in args.shape.split(",")]
+        if len(sh) == 4:
+            kmc.kmc_targets_per_lane(ctx, sh[3])
+        kmc.kmc_tuning(ctx, *sh[:3])
     for _ in range(args.warmup):
         kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
                     run["seed"])
     kmc.kmc_sync(ctx)
     warps, tile, chunk = kmc.kmc_tuning(ctx)
+    tpl = kmc.kmc_targets_per_lane(ctx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     uuid = None
@@ -595,7 +600,7 @@ def main():
                        "precision": "KMC_FP32_MIXED",
                        "kmc_steps_per_bench_step": n_steps, "particles": n_np,
                        "launch": {"warps": warps, "tile": tile, "chunk": chunk,
-                                  "chains": chains},
+                                  "targets_per_lane": tpl, "chains": chains},
                        "l2": "256 MB buffer written between timed steps (state < L2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "pair_interactions_per_s": world * pairs_per_launch * n_steps * args.steps / t_total,

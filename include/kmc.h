@@ -175,6 +175,15 @@ kmc_status kmc_info(const kmc_ctx *ctx, int64_t *n_total, int32_t *n_lys,
 kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
                       int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out);
 
+/* Targets per lane of the FP32 step kernel: 1 (a block takes 32 targets, one
+ * per lane) or 2 (64 targets, two per lane, so that each staged source record
+ * feeds two independent chains; FP32 contexts only, KMC_EINVAL on FP64). The
+ * two give the same bits at the same warps, tile and chunk. 0 (the default)
+ * lets the autotuner choose; a pinned value also applies to a shape set by
+ * kmc_tuning. The value in use (0 before the first tuning) is returned
+ * through tpl_out (may be NULL); tpl = -1 only reads it. */
+kmc_status kmc_targets_per_lane(kmc_ctx *ctx, int32_t tpl, int32_t *tpl_out);
+
 /* Largest neighbour rank of kmc_local_concentration (the paper uses 20). */
 #define KMC_PHI_MAX_N 64
 

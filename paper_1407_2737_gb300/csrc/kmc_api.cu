@@ -106,14 +106,19 @@ __global__ void sources_f64(const dbl4 *__restrict__ pos, const dbl4 *__restrict
 
 struct Shape {
   int warps = 0, tile = 0, chunk = 0;
+  int tpl = 1;  // targets per lane: 2 runs 64-target groups (FP32 two-target kernel)
+  bool operator==(const Shape &o) const {
+    return warps == o.warps && tile == o.tile && chunk == o.chunk && tpl == o.tpl;
+  }
 };
 
 struct TuneKey {
   int prec;
   long long N;
-  int n_lys, max_n;
+  int n_lys, max_n, tpl_mode;
   bool operator<(const TuneKey &o) const {
-    return std::tie(prec, N, n_lys, max_n) < std::tie(o.prec, o.N, o.n_lys, o.max_n);
+    return std::tie(prec, N, n_lys, max_n, tpl_mode) <
+           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode);
   }
 };
 std::mutex g_tune_mu;
@@ -180,6 +185,7 @@ struct kmc_ctx {
   size_t arrivals_cap = 0;
   Shape items_shape;  // shape the items were built for
   std::vector<int> chain_cut;  // chain q runs items chain_cut[q] .. chain_cut[q + 1] - 1
+  int tpl_mode = 0;            // targets per lane: 0 = the autotuner's choice, else 1 or 2
   cudaStream_t chain_st[kMaxChains] = {};  // branches 1.. of the period graph
   cudaEvent_t chain_ev[kMaxChains] = {};   // [0] fork, [q] join of branch q
   // debug outputs, allocated on first use
@@ -227,7 +233,8 @@ void drop_graph(kmc_ctx *c) {
 // SM q whole groups plus at most one part: the busiest SM then carries
 // q + 1/s group-loads instead of q + 1.
 std::vector<Item> build_items(const kmc_ctx *c, int chunk, int blocks_per_sm, int n_sms,
-                              int *n_groups) {
+                              int *n_groups, int tpl) {
+  const int gsize = kmc::kTargets * tpl;  // targets per group
   std::vector<int> order(c->n_lys);
   for (int l = 0; l < c->n_lys; ++l) order[l] = l;
   std::stable_sort(order.begin(), order.end(),
@@ -239,8 +246,7 @@ std::vector<Item> build_items(const kmc_ctx *c, int chunk, int blocks_per_sm, in
   for (int l : order) {
     const int n = c->n[l];
     const int nrec = c->fp32 ? (n + 1) / 2 : n;
-    for (int t0 = 0; t0 < n; t0 += kmc::kTargets)
-      groups.push_back({l, t0, std::min(kmc::kTargets, n - t0), nrec});
+    for (int t0 = 0; t0 < n; t0 += gsize) groups.push_back({l, t0, std::min(gsize, n - t0), nrec});
   }
   const int G = static_cast<int>(groups.size());
   std::vector<int> parts(G, 1);
@@ -287,21 +293,19 @@ std::vector<Item> build_items(const kmc_ctx *c, int chunk, int blocks_per_sm, in
 }
 
 kmc_status set_items(kmc_ctx *c, const Shape &sh) {
-  if (c->items_shape.warps == sh.warps && c->items_shape.tile == sh.tile &&
-      c->items_shape.chunk == sh.chunk && c->d_items)
-    return KMC_OK;
+  if (c->items_shape == sh && c->d_items) return KMC_OK;
   // until the rebuild completes, no shape's items are valid
   c->items_shape = Shape();
   int dev = 0, n_sms = 0, per_sm = 0;
   KMC_CUDA(cudaGetDevice(&dev));
   KMC_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
-  KMC_CUDA(kmc::step_blocks_per_sm(c->fp32, sh.warps, sh.tile, &per_sm));
+  KMC_CUDA(kmc::step_blocks_per_sm(c->fp32, sh.warps, sh.tile, sh.tpl, &per_sm));
   int groups = 0;
   // with several chains the lysosomes' kernels interleave on the SMs, and the
   // split that evens out one device-wide wave does not apply
   const int chains = std::min(c->n_lys, kMaxChains);
   const std::vector<Item> items =
-      build_items(c, sh.chunk, per_sm, chains > 1 ? 0 : n_sms, &groups);
+      build_items(c, sh.chunk, per_sm, chains > 1 ? 0 : n_sms, &groups, sh.tpl);
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   // a failed allocation leaves the buffer empty (null, capacity 0), so a
   // later call allocates again instead of using a stale capacity
@@ -320,7 +324,7 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
     if (c->d_partial) cudaFree(c->d_partial);
     c->d_partial = nullptr;
     c->partial_cap = 0;
-    KMC_TRY(dalloc(&c->d_partial, sizeof(float) * 12 * kmc::kTargets * need_partial));
+    KMC_TRY(dalloc(&c->d_partial, sizeof(float) * 12 * kmc::kTargets * 2 * need_partial));
     c->partial_cap = need_partial;
     drop_graph(c);
   }
@@ -451,13 +455,14 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
     const int u0 = c->chain_cut[q];
     StepArgs b = a;
     b.items = c->d_items + u0;
-    if (split) b.partial = c->d_partial + static_cast<size_t>(u0) * 12 * kmc::kTargets;
+    if (split) b.partial = c->d_partial + static_cast<size_t>(u0) * 12 * kmc::kTargets * sh.tpl;
     for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
       if (period) {
         b.k_local = k;
         b.cos_k = std::cos(2.0 * kPi * k / steps);
       }
-      ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, b, c->chain_cut[q + 1] - u0, st, true);
+      ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, b, c->chain_cut[q + 1] - u0, st, true,
+                            sh.tpl);
     }
   }
   // join, then the period advance
@@ -513,7 +518,7 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   }
   auto one = [&]() {
     return gx ? cudaGraphLaunch(gx, c->stream)
-              : kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true);
+              : kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true, s.tpl);
   };
   float ms = -1.f;
   bool ok = true;
@@ -533,7 +538,7 @@ float time_shape(kmc_ctx *c, const Shape &s) {
 kmc_status autotune(kmc_ctx *c) {
   int max_n = 0;
   for (int x : c->n) max_n = std::max(max_n, x);
-  const TuneKey key{c->fp32, c->N, c->n_lys, max_n};
+  const TuneKey key{c->fp32, c->N, c->n_lys, max_n, c->tpl_mode};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -561,26 +566,32 @@ kmc_status autotune(kmc_ctx *c) {
   bs.warps = 4;
   bs.tile = 64;
   bs.chunk = 0;
+  bs.tpl = c->tpl_mode == 2 ? 2 : 1;
   const int warps_c[] = {4, 8};
-  const int tiles_f32[] = {64, 128, 256};
-  const int tiles_f64[] = {32, 64, 128};
+  const int tiles_f32[] = {64, 128, 256, 512};
+  const int tiles_f64[] = {32, 64, 128, 128};  // (the FP64 list has three distinct tiles)
   const int chunks[] = {0, 256, 512, 1024, 2048, 4096, 8192};
   for (int w : warps_c) {
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < (c->fp32 ? 4 : 3); ++q) {
       const int t = c->fp32 ? tiles_f32[q] : tiles_f64[q];
       if (t > max_tile(c->fp32, w)) continue;
       if ((c->fp32 ? 2 : 1) * t > 2 * std::max(max_n, 64) && q > 0) continue;
       for (int ch : chunks) {
         if (ch > 0 && ch >= max_n) continue;
         if (ch > 0 && ch < (c->fp32 ? 2 : 1) * t) continue;
-        Shape s;
-        s.warps = w;
-        s.tile = t;
-        s.chunk = ch;
-        const float ms = time_shape(c, s);
-        if (ms > 0.f && ms < best) {
-          best = ms;
-          bs = s;
+        for (int tpl = 1; tpl <= 2; ++tpl) {
+          if (c->tpl_mode != 0 && tpl != c->tpl_mode) continue;
+          if (tpl == 2 && !c->fp32) continue;
+          Shape s;
+          s.warps = w;
+          s.tile = t;
+          s.chunk = ch;
+          s.tpl = tpl;
+          const float ms = time_shape(c, s);
+          if (ms > 0.f && ms < best) {
+            best = ms;
+            bs = s;
+          }
         }
       }
     }
@@ -840,6 +851,20 @@ kmc_status kmc_set_stream(kmc_ctx *c, void *cuda_stream) {
   return KMC_OK;
 }
 
+kmc_status kmc_targets_per_lane(kmc_ctx *c, int32_t tpl, int32_t *tpl_out) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (tpl != -1) {
+    if (tpl < 0 || tpl > 2) return fail(KMC_EINVAL, "targets per lane: 0 (autotuned), 1 or 2");
+    if (tpl == 2 && !c->fp32)
+      return fail(KMC_EINVAL, "two targets per lane run on FP32 contexts");
+    c->tpl_mode = tpl;
+    // a pinned choice applies to the shape in use; 0 leaves it to the autotuner
+    if (tpl != 0 && c->shape.warps != 0) c->shape.tpl = tpl;
+  }
+  if (tpl_out) *tpl_out = c->tpl_mode != 0 ? c->tpl_mode : (c->shape.warps ? c->shape.tpl : 0);
+  return KMC_OK;
+}
+
 kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
                       int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
@@ -852,6 +877,7 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
     s.warps = warps;
     s.tile = tile;
     s.chunk = chunk;
+    s.tpl = c->tpl_mode == 2 ? 2 : 1;
     if (!shape_ok(c, s))
       return fail(KMC_EINVAL,
                   "bad shape: warps in {4, 8, 16}, tile a power of two in [32, %d], chunk a "
@@ -909,8 +935,7 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
   // one field period (S step launches + the period advance) as a CUDA graph
   const Shape &sh = c->shape;
   if (!c->gexec || c->g_S != S || c->g_discard != discard || c->g_nrec != n_rec ||
-      c->g_shape.warps != sh.warps || c->g_shape.tile != sh.tile ||
-      c->g_shape.chunk != sh.chunk || c->g_seed != seed) {
+      !(c->g_shape == sh) || c->g_seed != seed) {
     drop_graph(c);
     StepArgs a = base_args(c);
     a.seed = seed;
@@ -1093,7 +1118,8 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
   a.dbg.P = c->d_dbg + 5 * N;
   a.dbg.u = c->d_dbg + 6 * N;
   a.dbg.flags = c->d_dbg_flags;
-  KMC_CUDA(kmc::launch_step(c->fp32, c->shape.warps, c->shape.tile, a, c->n_items, c->stream));
+  KMC_CUDA(kmc::launch_step(c->fp32, c->shape.warps, c->shape.tile, a, c->n_items, c->stream,
+                            false, c->shape.tpl));
   KMC_TRY(check_device_error(c));
   std::vector<double> h(7 * N);
   std::vector<int32_t> hf(N);

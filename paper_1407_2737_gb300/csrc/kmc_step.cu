@@ -801,6 +801,226 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
 }
 
 // ---------------------------------------------------------------------------
+// FP32-mixed step with two targets per lane: the block takes a group of 64
+// targets, lane t holding targets t0 + t and t0 + 32 + t, so that every staged
+// source record feeds two independent chains. Each target's sums are formed by
+// the same packed operations over the same records as in kmc_step_f32, and the
+// warps and source parts are combined in the same order, so the fields, and
+// hence the whole step, are the same bits. The two halves then run steps
+// iii-vii one after the other with the same update code.
+struct AccF32x2 {
+  AccF32 a, b;  // first and second target of the lane
+};
+
+template <bool MASK>
+__device__ __noinline__ AccF32x2 pair_tile_f32_2t(const ulonglong2 *__restrict__ sp, int cnt,
+                                                   int first, int stride, f2 X0, f2 Y0, f2 Z0,
+                                                   f2 X1, f2 Y1, f2 Z1) {
+  AccF32x2 acc;
+  acc.a.ax = acc.a.ay = acc.a.az = acc.a.bx = acc.a.by = acc.a.bz = 0ull;
+  acc.b = acc.a;
+  // the two targets already give two independent chains; unrolling further
+  // took 158 registers (3 blocks per SM) and ran slower than this (128)
+#pragma unroll 1
+  for (int r = first; r < cnt; r += stride) {
+    const ulonglong2 a = sp[3 * r];      // x0 x1 | y0 y1
+    const ulonglong2 b = sp[3 * r + 1];  // z0 z1 | mx0 mx1
+    const ulonglong2 c = sp[3 * r + 2];  // my0 my1 | mz0 mz1
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const f2 X = h ? X1 : X0, Y = h ? Y1 : Y0, Z = h ? Z1 : Z0;
+      AccF32 &A = h ? acc.b : acc.a;
+      const f2 dx = sub2(a.x, X), dy = sub2(a.y, Y), dz = sub2(b.x, Z);
+      const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+      float r2l, r2h;
+      upk(r2, r2l, r2h);
+      float il = rsqrt_approx(r2l), ih = rsqrt_approx(r2h);
+      if (MASK) {
+        il = (r2l > 0.0f) ? il : 0.0f;
+        ih = (r2h > 0.0f) ? ih : 0.0f;
+      }
+      const f2 q = pk(il, ih);
+      const f2 q2 = mul2(q, q);
+      const f2 q3 = mul2(q, q2);
+      const f2 md = fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx)));
+      const f2 s = mul2(mul2(md, q2), q3);
+      A.ax = fma2(s, dx, A.ax);
+      A.ay = fma2(s, dy, A.ay);
+      A.az = fma2(s, dz, A.az);
+      A.bx = fma2(q3, b.y, A.bx);
+      A.by = fma2(q3, c.x, A.by);
+      A.bz = fma2(q3, c.y, A.bz);
+    }
+  }
+  return acc;
+}
+
+// Dynamic shared memory of the two-target kernel after its pair loop: the
+// warps' (sum, -error) pairs of both halves, then the update state.
+constexpr size_t epi_bytes_t2(int warps) {
+  return static_cast<size_t>(warps) * 24 * kTargets * sizeof(float) + sizeof(EpiShared<float>) + 64;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int tile) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *dyn = smem + 16;
+  __shared__ int s_last;
+  __shared__ GridTables<float> tab;
+  __shared__ float s_h1[12][kTargets];  // second half's (sum, error) while the first updates
+  tab.load();
+  const Item it = a.items[blockIdx.x];
+  const LysDev L = a.lys[it.l];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt0 = min(it.nt, kTargets), nt1 = it.nt - nt0;
+  const float4 *pos = static_cast<const float4 *>(a.pos);
+  const float4 pi0 = pos[L.off + it.t0 + min(lane, nt0 - 1)];
+  const float4 pi1 = nt1 > 0 ? pos[L.off + it.t0 + kTargets + min(lane, nt1 - 1)] : pi0;
+  grid_dependency_wait();
+  const long long step = a.rs->step_base + a.k_local;
+  const int per = a.rs->period;
+  const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
+  const int par = static_cast<int>(step & 1);
+  const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
+
+  Item h0 = it;
+  h0.nt = nt0;
+  TargetIn<float4> tin;
+  if (warp == 0) tin = load_target<float4>(a, L, h0, step, lane);
+  const f2 X0 = pk(pi0.x, pi0.x), Y0 = pk(pi0.y, pi0.y), Z0 = pk(pi0.z, pi0.z);
+  const f2 X1 = pk(pi1.x, pi1.x), Y1 = pk(pi1.y, pi1.y), Z1 = pk(pi1.z, pi1.z);
+  float s12[12], c12[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) s12[c] = c12[c] = 0.f;
+  const int nrec = it.j1 - it.j0;
+  const int ntiles = (nrec + tile - 1) / tile;
+  const int own0 = it.t0 >> 1, own1 = (it.t0 + it.nt - 1) >> 1;  // records holding targets
+  ulonglong2 *buf = reinterpret_cast<ulonglong2 *>(dyn);          // [2][tile][3]
+  auto issue = [&](int t) {
+    const int b = t & 1;
+    const int r0 = it.j0 + t * tile;
+    const int cnt = min(tile, it.j1 - r0);
+    const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
+    mbar_expect_tx(&bar[b], bytes);
+    bulk_g2s(buf + static_cast<size_t>(b) * tile * 3, gsrc + r0, bytes, &bar[b]);
+  };
+  auto body = [&](int b, int t) {
+    const int r0 = it.j0 + t * tile;
+    const int cnt = min(tile, it.j1 - r0);
+    const bool mask = (r0 <= own1) && (own0 < r0 + cnt);
+    const ulonglong2 *sp = buf + static_cast<size_t>(b) * tile * 3;
+    const AccF32x2 acc = mask ? pair_tile_f32_2t<true>(sp, cnt, warp, NW, X0, Y0, Z0, X1, Y1, Z1)
+                              : pair_tile_f32_2t<false>(sp, cnt, warp, NW, X0, Y0, Z0, X1, Y1, Z1);
+    kahan_add(s12[0], c12[0], hsum(acc.a.ax));
+    kahan_add(s12[1], c12[1], hsum(acc.a.ay));
+    kahan_add(s12[2], c12[2], hsum(acc.a.az));
+    kahan_add(s12[3], c12[3], hsum(acc.a.bx));
+    kahan_add(s12[4], c12[4], hsum(acc.a.by));
+    kahan_add(s12[5], c12[5], hsum(acc.a.bz));
+    kahan_add(s12[6], c12[6], hsum(acc.b.ax));
+    kahan_add(s12[7], c12[7], hsum(acc.b.ay));
+    kahan_add(s12[8], c12[8], hsum(acc.b.az));
+    kahan_add(s12[9], c12[9], hsum(acc.b.bx));
+    kahan_add(s12[10], c12[10], hsum(acc.b.by));
+    kahan_add(s12[11], c12[11], hsum(acc.b.bz));
+  };
+  if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
+
+  // cross-warp combine in a fixed order, per half as in kmc_step_f32
+  float *wp = reinterpret_cast<float *>(dyn);  // [NW][24][32]: 12 sums, then 12 errors
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    wp[(warp * 24 + c) * 32 + lane] = s12[c];
+    wp[(warp * 24 + 12 + c) * 32 + lane] = -c12[c];
+  }
+  __syncthreads();
+  EpiShared<float> &sm =
+      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 24 * 32 * 4);
+  float hi[12], lo[12];
+  if (warp == 0) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      float s = 0.f, e = 0.f;
+      for (int w = 0; w < NW; ++w) {
+        neumaier_add(s, e, wp[(w * 24 + c) * 32 + lane]);
+        e += wp[(w * 24 + 12 + c) * 32 + lane];
+      }
+      hi[c] = s;
+      lo[c] = e;
+    }
+    if (it.nsplit > 1) {
+      float *part = a.partial + static_cast<size_t>(blockIdx.x) * 24 * 32;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        __stcg(part + c * 32 + lane, hi[c]);
+        __stcg(part + (12 + c) * 32 + lane, lo[c]);
+      }
+      __threadfence();
+    }
+  }
+  if (it.nsplit > 1) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
+    __syncthreads();
+    if (!s_last) return;  // another item of the group finishes the step
+    __threadfence();
+    if (warp == 0) {
+      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * 24 * 32;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        float s = 0.f, e = 0.f;
+        for (int q = 0; q < it.nsplit; ++q) {
+          neumaier_add(s, e, __ldcg(base + (q * 24 + c) * 32 + lane));
+          e += __ldcg(base + (q * 24 + 12 + c) * 32 + lane);
+        }
+        hi[c] = s;
+        lo[c] = e;
+      }
+      if (lane == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
+    }
+  }
+  if (warp == 0) {
+    // b_dip = 3A - B of the first half; the second half's sums wait in shared memory
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float s = 0.f, e = 0.f;
+      neumaier_add(s, e, 3.0f * hi[c]);
+      neumaier_add(s, e, -hi[3 + c]);
+      neumaier_add(s, e, 3.0f * lo[c] - lo[3 + c]);
+      sm.h[c][lane] = s + e;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      s_h1[c][lane] = hi[6 + c];
+      s_h1[6 + c][lane] = lo[6 + c];
+    }
+  }
+  __syncthreads();
+  block_update<float4, true>(a, L, h0, step, rec, tin, sm, tab);
+  if (nt1 > 0) {
+    __syncthreads();
+    Item h1 = it;
+    h1.t0 = it.t0 + kTargets;
+    h1.nt = nt1;
+    if (warp == 0) {
+      tin = load_target<float4>(a, L, h1, step, lane);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float s = 0.f, e = 0.f;
+        neumaier_add(s, e, 3.0f * s_h1[c][lane]);
+        neumaier_add(s, e, -s_h1[3 + c][lane]);
+        neumaier_add(s, e, 3.0f * s_h1[6 + c][lane] - s_h1[9 + c][lane]);
+        sm.h[c][lane] = s + e;
+      }
+    }
+    __syncthreads();
+    block_update<float4, true>(a, L, h1, step, rec, tin, sm, tab);
+  }
+  grid_launch_dependents();
+}
+
+// ---------------------------------------------------------------------------
 // FP64-plain step kernel (same structure, scalar FP64 pair loop).
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int tile) {
@@ -908,10 +1128,11 @@ __global__ void kmc_advance_kernel(RunState *rs, int S) {
 // ---------------------------------------------------------------------------
 // Host side of the launches.
 
-size_t step_smem_bytes(int prec_fp32, int warps, int tile) {
+size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl) {
   const size_t stage = prec_fp32 ? 2 * static_cast<size_t>(tile) * sizeof(SrcPair)
                                  : 4 * static_cast<size_t>(tile) * sizeof(dbl4);
-  const size_t epi = prec_fp32 ? epi_bytes<float>(warps) : epi_bytes<double>(warps);
+  const size_t epi = !prec_fp32 ? epi_bytes<double>(warps)
+                                : (tpl == 2 ? epi_bytes_t2(warps) : epi_bytes<float>(warps));
   return 16 + (stage > epi ? stage : epi);
 }
 
@@ -935,28 +1156,32 @@ static cudaError_t launch_items(K kernel, const StepArgs &a, int n_items, int th
 
 template <int NW>
 static cudaError_t launch_f32(const StepArgs &a, int n_items, int tile, cudaStream_t st,
-                              bool pdl) {
-  return launch_items(kmc_step_f32<NW>, a, n_items, NW * 32, step_smem_bytes(1, NW, tile), tile,
+                              bool pdl, int tpl) {
+  if (tpl == 2)
+    return launch_items(kmc_step_f32_t2<NW>, a, n_items, NW * 32, step_smem_bytes(1, NW, tile, 2),
+                        tile, st, pdl);
+  return launch_items(kmc_step_f32<NW>, a, n_items, NW * 32, step_smem_bytes(1, NW, tile, 1), tile,
                       st, pdl);
 }
 template <int NW>
 static cudaError_t launch_f64(const StepArgs &a, int n_items, int tile, cudaStream_t st,
                               bool pdl) {
-  return launch_items(kmc_step_f64<NW>, a, n_items, NW * 32, step_smem_bytes(0, NW, tile), tile,
-                      st, pdl);
+  return launch_items(kmc_step_f64<NW>, a, n_items, NW * 32, step_smem_bytes(0, NW, tile, 1),
+                      tile, st, pdl);
 }
 
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
-                        cudaStream_t st, bool pdl) {
+                        cudaStream_t st, bool pdl, int tpl) {
   if (n_items <= 0) return cudaSuccess;
   if (prec_fp32) {
     switch (warps) {
-      case 4: return launch_f32<4>(a, n_items, tile, st, pdl);
-      case 8: return launch_f32<8>(a, n_items, tile, st, pdl);
-      case 16: return launch_f32<16>(a, n_items, tile, st, pdl);
+      case 4: return launch_f32<4>(a, n_items, tile, st, pdl, tpl);
+      case 8: return launch_f32<8>(a, n_items, tile, st, pdl, tpl);
+      case 16: return launch_f32<16>(a, n_items, tile, st, pdl, tpl);
       default: return cudaErrorInvalidValue;
     }
   }
+  if (tpl != 1) return cudaErrorInvalidValue;
   switch (warps) {
     case 4: return launch_f64<4>(a, n_items, tile, st, pdl);
     case 8: return launch_f64<8>(a, n_items, tile, st, pdl);
@@ -970,10 +1195,18 @@ static cudaError_t occupancy(K kernel, int threads, size_t smem, int *blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, threads, smem);
 }
 
-cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int *blocks) {
+cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int *blocks) {
   *blocks = 0;
-  const size_t smem = step_smem_bytes(prec_fp32, warps, tile);
+  const size_t smem = step_smem_bytes(prec_fp32, warps, tile, tpl);
   const int th = warps * 32;
+  if (prec_fp32 && tpl == 2) {
+    switch (warps) {
+      case 4: return occupancy(kmc_step_f32_t2<4>, th, smem, blocks);
+      case 8: return occupancy(kmc_step_f32_t2<8>, th, smem, blocks);
+      case 16: return occupancy(kmc_step_f32_t2<16>, th, smem, blocks);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (prec_fp32) {
     switch (warps) {
       case 4: return occupancy(kmc_step_f32<4>, th, smem, blocks);
@@ -1043,6 +1276,9 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<16>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_t2<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_t2<8>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_t2<16>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<16>);

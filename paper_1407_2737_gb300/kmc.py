@@ -33,7 +33,7 @@ EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
            "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall",
-           "kmc_regenerate_rsa")
+           "kmc_regenerate_rsa", "kmc_targets_per_lane")
 KMC_NOALLOC_MAX_N = 8192
 KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
 KMC_PHI_MAX_N = 64
@@ -93,6 +93,7 @@ def lib():
             L.kmc_regenerate.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.c_uint64,
                                          C.c_uint32]
             L.kmc_debug_stall.argtypes = [vp]
+            L.kmc_targets_per_lane.argtypes = [vp, C.c_int32, _I32]
             L.kmc_regenerate_rsa.argtypes = [vp, C.c_int32, C.c_double, C.c_double, C.c_uint64,
                                              C.c_uint32, C.c_int64, _I64]
             L.kmc_destroy.argtypes = [vp]
@@ -198,6 +199,14 @@ def kmc_regenerate_rsa(ctx, lys, radius, diameter, seed, loop, max_candidates=0)
                                     C.c_uint64(int(seed)), C.c_uint32(int(loop)),
                                     int(max_candidates), C.byref(used)))
     return int(used.value)
+
+
+def kmc_targets_per_lane(ctx, tpl=None):
+    """Pins the FP32 kernel's targets per lane (1 or 2; 0 = autotuned) or, with
+    no argument, returns the value in use."""
+    t = C.c_int32()
+    _check(lib().kmc_targets_per_lane(ctx.handle, -1 if tpl is None else int(tpl), C.byref(t)))
+    return int(t.value)
 
 
 def kmc_debug_stall(ctx):

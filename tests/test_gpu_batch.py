@@ -134,3 +134,31 @@ def test_chained_batch_checkpoint_resume_is_bit_identical(tmp_path):
         kmc.kmc_destroy(c)
         for x, y in zip(ref, got):
             assert np.array_equal(x, y)
+
+
+def test_two_targets_per_lane_give_the_same_bits():
+    """The two-target kernel (64-target groups, two per lane) forms every
+    target's sums with the same operations in the same order as the one-target
+    kernel and runs the same update: identical outputs at the same shape."""
+    lyss = [inputs.make_lysosome(n, 12e-9, 0.05, seed=70 + q) for q, n in enumerate([700, 97, 33, 1])]
+    for shape in [(4, 64, 0), (4, 128, 256), (8, 64, 128)]:
+        out = []
+        for tpl in (1, 2):
+            ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+            kmc.kmc_targets_per_lane(ctx, tpl)
+            kmc.kmc_tuning(ctx, *shape)
+            assert kmc.kmc_targets_per_lane(ctx) == tpl
+            kmc.kmc_run(ctx, [0.02, 0.03, 0.025, 0.01], 1e5, 40, 3, 1, 3)
+            out.append([kmc.kmc_read(ctx, w, l) for l in range(len(lyss))
+                        for w in (kmc.KMC_READ_LOOP_M, kmc.KMC_READ_MOMENTS,
+                                  kmc.KMC_READ_NP_ENERGY, kmc.KMC_READ_DHDIP,
+                                  kmc.KMC_READ_COUNTERS)])
+            kmc.kmc_destroy(ctx)
+        for x, y in zip(*out):
+            assert np.array_equal(x, y), shape
+    lys64 = inputs.make_lysosome(40, 12e-9, 0.05, seed=1)
+    ctx = kmc.kmc_create([lys64], kmc.KMC_FP64_PLAIN, center=np.zeros(3))
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.kmc_targets_per_lane(ctx, 2)
+    assert e.value.status == kmc.KMC_EINVAL
+    kmc.kmc_destroy(ctx)
