@@ -69,10 +69,10 @@ CONFIGS = {
            "f=100 kHz, 500 steps/period", (2, 1), 50),
 }
 FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
-# DRAM bytes (read + write) of one kMC step at this workload (8 chains, one
-# launch each), by launch shape (warps, tile, chunk): 8 x the mean over 16
-# serialised ncu captures of the committed kernel
-STEP_DRAM_BYTES = {(4, 256, 512): 2.186e6, (4, 256, 1024): 2.153e6}
+# DRAM bytes (read + write) of one kMC step, by (workload, warps, tile, chunk,
+# targets per lane), from serialised ncu captures of the committed kernel. c1:
+# 8 chains, one launch each: 8 x the mean over 16 launches. c4: one launch.
+STEP_DRAM_BYTES = {("c1", 4, 256, 512, 1): 2.186e6, ("c1", 4, 256, 1024, 1): 2.153e6}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (FMA = 2 flops)
 HBM_GBS = 6771.5             # measured copy bandwidth of the GB300s
@@ -607,9 +607,10 @@ def main():
             "sar_W_per_g": float(np.mean(sar32)) / 1e3,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": (STEP_DRAM_BYTES.get((warps, tile, chunk))
-                                     if args.config == "c1" else None),
-                         "kernel": "kmc_step_f32<%d>" % warps,
+                         "traffic": STEP_DRAM_BYTES.get((args.config, warps, tile, chunk,
+                                                         tpl)),
+                         "kernel": ("kmc_step_f32_t2<%d>" if tpl == 2 else
+                                    "kmc_step_f32<%d>") % warps,
                          "note": "FP32 pipe: 30 flops per ordered pair; a kMC step is one "
                                  "launch per chain, the chains' launches concurrent; step "
                                  "time = timed region / kMC steps (includes graph gaps); "

@@ -302,7 +302,7 @@ void kmc_destroy(kmc_ctx *ctx);
  *   cuda_stream  stream to queue on (NULL: the default stream)
  * All pointers are owned by the caller. The call only queues work: B is valid
  * once the stream has reached it. Its working memory is one static device
- * array of about 3.5 MB that every GPU loading the library holds until the
+ * array of about 2 MB that every GPU loading the library holds until the
  * process exits. Every call shares that array and leaves its contents behind;
  * calls that overlap on the GPU (other streams, other host threads) race on it.
  * The first call on each device looks up the array's device address

@@ -86,9 +86,7 @@ __global__ void sources_f32(const float4 *__restrict__ pos, const float4 *__rest
   r.x[s & 1] = p.x;
   r.y[s & 1] = p.y;
   r.z[s & 1] = p.z;
-  r.mx[s & 1] = p.w * q.x;
-  r.my[s & 1] = p.w * q.y;
-  r.mz[s & 1] = p.w * q.z;
+  kmc::set_source_moment(r, s & 1, p.w, q.x, q.y, q.z);
 }
 
 __global__ void sources_f64(const dbl4 *__restrict__ pos, const dbl4 *__restrict__ m,
@@ -455,7 +453,10 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
     const int u0 = c->chain_cut[q];
     StepArgs b = a;
     b.items = c->d_items + u0;
-    if (split) b.partial = c->d_partial + static_cast<size_t>(u0) * 12 * kmc::kTargets * sh.tpl;
+    // an item's partials: (sum, error) of 3 FP32 or 6 FP64 (two floats each) components
+    // per target
+    if (split)
+      b.partial = c->d_partial + static_cast<size_t>(u0) * (c->fp32 ? 6 : 12) * kmc::kTargets * sh.tpl;
     for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
       if (period) {
         b.k_local = k;
@@ -794,7 +795,8 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
     if (c->fp32 && (L.n & 1)) {  // padding NP of the last record: far away, no moment
       SrcPair &pad = src32[r + L.n / 2];
       pad.x[1] = pad.y[1] = pad.z[1] = kmc::kPadCoord;
-      pad.mx[1] = pad.my[1] = pad.mz[1] = 0.0f;
+      kmc::set_source_moment(pad, 1, 0.0f, 0.0f, 0.0f, 0.0f);
+      pad.pad[0] = pad.pad[1] = 0.0f;
     }
     for (int i = 0; i < L.n; ++i, ++o) {
       const double *p = &L.pos[3 * i];
@@ -821,9 +823,8 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
         rec.x[h] = pf.x;
         rec.y[h] = pf.y;
         rec.z[h] = pf.z;
-        rec.mx[h] = pf.w * mf.x;
-        rec.my[h] = pf.w * mf.y;
-        rec.mz[h] = pf.w * mf.z;
+        kmc::set_source_moment(rec, h, pf.w, mf.x, mf.y, mf.z);
+        rec.pad[h] = 0.0f;
         h_slot[o] = static_cast<int>(2 * (r + i / 2) + h);
       } else {
         reinterpret_cast<dbl4 *>(h_pos.data())[o] = make4<dbl4>(x, y, z, w);

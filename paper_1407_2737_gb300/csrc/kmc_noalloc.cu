@@ -10,7 +10,7 @@
 // per-item partial sums, per-group arrival counters) in one file-scope static
 // device array, so that no call allocates or frees anything.
 //
-// The array is fixed at kNoallocBytes (3.5 MB, for up to KMC_NOALLOC_MAX_N NPs);
+// The array is fixed at kNoallocBytes (2.0 MB, for up to KMC_NOALLOC_MAX_N NPs);
 // every GPU that loads the library holds it until the process exits. All calls
 // share it: calls that overlap on the GPU (different streams, or host threads)
 // race on it and must be serialised by the caller.
@@ -42,7 +42,7 @@ constexpr int kTile = 128;                                      // records per s
 constexpr int kWarps = 4;
 constexpr size_t kRecBytes = sizeof(SrcPair) * kMaxRec;
 constexpr size_t kTgtBytes = sizeof(float4) * kMaxN;
-constexpr size_t kPartBytes = sizeof(float) * 12 * 32 * kMaxItems;
+constexpr size_t kPartBytes = sizeof(float) * 6 * 32 * kMaxItems;  // (sum, error) x 3
 constexpr size_t kCntBytes = sizeof(int) * kGroups;
 constexpr size_t kNoallocBytes = kRecBytes + kTgtBytes + kPartBytes + kCntBytes;
 
@@ -134,9 +134,10 @@ __global__ void noalloc_pack(unsigned char *scratch, int n, const double *__rest
   if (i >= n + (n & 1)) return;
   SrcPair &r = sc_rec(scratch)[i >> 1];
   const int h = i & 1;
+  r.pad[h] = 0.0f;
   if (i == n) {  // padding NP of an odd count: far away, no moment
     r.x[h] = r.y[h] = r.z[h] = kmc::kPadCoord;
-    r.mx[h] = r.my[h] = r.mz[h] = 0.0f;
+    kmc::set_source_moment(r, h, 0.0f, 0.0f, 0.0f, 0.0f);
     return;
   }
   const float x = static_cast<float>((pos[3 * i] - cx) * inv_len);
@@ -146,18 +147,21 @@ __global__ void noalloc_pack(unsigned char *scratch, int n, const double *__rest
   r.x[h] = x;
   r.y[h] = y;
   r.z[h] = z;
-  r.mx[h] = static_cast<float>(w * m[3 * i]);
-  r.my[h] = static_cast<float>(w * m[3 * i + 1]);
-  r.mz[h] = static_cast<float>(w * m[3 * i + 2]);
+  kmc::set_source_moment(r, h, w, static_cast<float>(m[3 * i]), static_cast<float>(m[3 * i + 1]),
+                         static_cast<float>(m[3 * i + 2]));
   sc_tgt(scratch)[i] = make_float4(x, y, z, w);
 }
 
+// The pair terms of Eq. 1 in the form of kmc::SrcPair: per component,
+// q^3 (u d + n) with u = (t.d) q^2.
 template <bool MASK>
 __device__ __forceinline__ void pairs(const ulonglong2 *__restrict__ sp, int cnt, int first,
-                                      f2 X, f2 Y, f2 Z, f2 (&acc)[6]) {
+                                      f2 X, f2 Y, f2 Z, f2 (&acc)[3]) {
 #pragma unroll 2
   for (int r = first; r < cnt; r += kWarps) {
-    const ulonglong2 a = sp[3 * r], b = sp[3 * r + 1], c = sp[3 * r + 2];
+    const ulonglong2 *p = sp + kmc::kRecU2 * r;
+    const ulonglong2 a = p[0], b = p[1], c = p[2], d = p[3];
+    const f2 e = reinterpret_cast<const f2 *>(p + 4)[0];
     const f2 dx = sub2(a.x, X), dy = sub2(a.y, Y), dz = sub2(b.x, Z);
     const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     float r2l, r2h;
@@ -170,14 +174,10 @@ __device__ __forceinline__ void pairs(const ulonglong2 *__restrict__ sp, int cnt
     const f2 q = pk(il, ih);
     const f2 q2 = mul2(q, q);
     const f2 q3 = mul2(q, q2);
-    const f2 md = fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx)));
-    const f2 s = mul2(mul2(md, q2), q3);
-    acc[0] = fma2(s, dx, acc[0]);
-    acc[1] = fma2(s, dy, acc[1]);
-    acc[2] = fma2(s, dz, acc[2]);
-    acc[3] = fma2(q3, b.y, acc[3]);
-    acc[4] = fma2(q3, c.x, acc[4]);
-    acc[5] = fma2(q3, c.y, acc[5]);
+    const f2 u = mul2(fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx))), q2);
+    acc[0] = fma2(q3, fma2(u, dx, d.x), acc[0]);
+    acc[1] = fma2(q3, fma2(u, dy, d.y), acc[1]);
+    acc[2] = fma2(q3, fma2(u, dz, e), acc[2]);
   }
 }
 
@@ -186,8 +186,8 @@ __device__ __forceinline__ void pairs(const ulonglong2 *__restrict__ sp, int cnt
 __global__ void __launch_bounds__(kWarps * 32)
     noalloc_field(unsigned char *scratch, int n, int nsplit, double bunit,
                   double *__restrict__ B) {
-  __shared__ __align__(128) ulonglong2 buf[2][kTile * 3];
-  __shared__ float wp[kWarps][12][32];
+  __shared__ __align__(128) ulonglong2 buf[2][kTile * kmc::kRecU2];
+  __shared__ float wp[kWarps][6][32];
   __shared__ uint64_t bar[2];
   __shared__ int s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kWarps * 32)
   const int own0 = t0 >> 1, own1 = (t0 + nt - 1) >> 1;
   const float4 p = sc_tgt(scratch)[t0 + min(lane, nt - 1)];
   const f2 X = pk(p.x, p.x), Y = pk(p.y, p.y), Z = pk(p.z, p.z);
-  float s6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, c6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float s3[3] = {0.f, 0.f, 0.f}, c3[3] = {0.f, 0.f, 0.f};
   const SrcPair *src = sc_rec(scratch);
   const int ntiles = (j1 - j0 + kTile - 1) / kTile;
   const uint32_t b0 = static_cast<uint32_t>(__cvta_generic_to_shared(&bar[0]));
@@ -251,13 +251,13 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
     if (ok) {
       const int r0 = j0 + t * kTile, cnt = min(kTile, j1 - r0);
-      f2 acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+      f2 acc[3] = {0ull, 0ull, 0ull};
       if (r0 <= own1 && own0 < r0 + cnt)
         pairs<true>(buf[t & 1], cnt, warp, X, Y, Z, acc);
       else
         pairs<false>(buf[t & 1], cnt, warp, X, Y, Z, acc);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) kahan_add(s6[c], c6[c], hsum(acc[c]));
+      for (int c = 0; c < 3; ++c) kahan_add(s3[c], c3[c], hsum(acc[c]));
     }
     if (!__syncthreads_and(ok)) return;  // B is left unwritten
     if (threadIdx.x == 0 && t + 2 < ntiles) {
@@ -266,29 +266,29 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
   }
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    wp[warp][c][lane] = s6[c];
-    wp[warp][6 + c][lane] = -c6[c];
+  for (int c = 0; c < 3; ++c) {
+    wp[warp][c][lane] = s3[c];
+    wp[warp][3 + c][lane] = -c3[c];
   }
   __syncthreads();
-  float hi[6], lo[6];
+  float hi[3], lo[3];
   if (warp == 0) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < 3; ++c) {
       float s = 0.f, e = 0.f;
       for (int w = 0; w < kWarps; ++w) {
         neumaier_add(s, e, wp[w][c][lane]);
-        e += wp[w][6 + c][lane];
+        e += wp[w][3 + c][lane];
       }
       hi[c] = s;
       lo[c] = e;
     }
     if (nsplit > 1) {
-      float *part = sc_part(scratch) + static_cast<size_t>(blockIdx.x) * 12 * 32;
+      float *part = sc_part(scratch) + static_cast<size_t>(blockIdx.x) * 6 * 32;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
+      for (int c = 0; c < 3; ++c) {
         __stcg(part + c * 32 + lane, hi[c]);
-        __stcg(part + (6 + c) * 32 + lane, lo[c]);
+        __stcg(part + (3 + c) * 32 + lane, lo[c]);
       }
       __threadfence();
     }
@@ -300,13 +300,13 @@ __global__ void __launch_bounds__(kWarps * 32)
     if (!s_last) return;
     __threadfence();
     if (warp == 0) {
-      const float *base = sc_part(scratch) + static_cast<size_t>(blockIdx.x - split) * 12 * 32;
+      const float *base = sc_part(scratch) + static_cast<size_t>(blockIdx.x - split) * 6 * 32;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
+      for (int c = 0; c < 3; ++c) {
         float s = 0.f, e = 0.f;
         for (int q = 0; q < nsplit; ++q) {
-          neumaier_add(s, e, __ldcg(base + (q * 12 + c) * 32 + lane));
-          e += __ldcg(base + (q * 12 + 6 + c) * 32 + lane);
+          neumaier_add(s, e, __ldcg(base + (q * 6 + c) * 32 + lane));
+          e += __ldcg(base + (q * 6 + 3 + c) * 32 + lane);
         }
         hi[c] = s;
         lo[c] = e;
@@ -316,13 +316,7 @@ __global__ void __launch_bounds__(kWarps * 32)
   }
   if (warp == 0 && lane < nt) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float s = 0.f, e = 0.f;
-      neumaier_add(s, e, 3.0f * hi[c]);
-      neumaier_add(s, e, -hi[3 + c]);
-      neumaier_add(s, e, 3.0f * lo[c] - lo[3 + c]);
-      B[3 * (t0 + lane) + c] = bunit * static_cast<double>(s + e);
-    }
+    for (int c = 0; c < 3; ++c) B[3 * (t0 + lane) + c] = bunit * static_cast<double>(hi[c] + lo[c]);
   }
 }
 

@@ -107,39 +107,56 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
 // update code after it changed).
 
 struct AccF32 {
-  f2 ax, ay, az, bx, by, bz;  // packed partial sums (even / odd sources)
+  f2 x, y, z;  // packed partial sums of the field (even / odd sources)
 };
+
+// One source record against the lane's target (X, Y, Z): the pair terms of
+// both sources, 18 packed instructions and two rsqrt (see SrcPair).
+template <bool MASK>
+__device__ __forceinline__ void pair_record(const ulonglong2 &a, const ulonglong2 &b,
+                                            const ulonglong2 &c, const ulonglong2 &d, f2 e,
+                                            f2 X, f2 Y, f2 Z, AccF32 &acc) {
+  const f2 dx = sub2(a.x, X), dy = sub2(a.y, Y), dz = sub2(b.x, Z);
+  const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+  float r2l, r2h;
+  upk(r2, r2l, r2h);
+  float il = rsqrt_approx(r2l), ih = rsqrt_approx(r2h);
+  if (MASK) {
+    il = (r2l > 0.0f) ? il : 0.0f;
+    ih = (r2h > 0.0f) ? ih : 0.0f;
+  }
+  const f2 q = pk(il, ih);
+  const f2 q2 = mul2(q, q);
+  const f2 q3 = mul2(q, q2);
+  const f2 u = mul2(fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx))), q2);
+  acc.x = fma2(q3, fma2(u, dx, d.x), acc.x);
+  acc.y = fma2(q3, fma2(u, dy, d.y), acc.y);
+  acc.z = fma2(q3, fma2(u, dz, e), acc.z);
+}
+
+// Record r of a staged tile: x | y, z | tx, ty | tz, nx | ny, nz | padding.
+__device__ __forceinline__ void load_record(const ulonglong2 *__restrict__ sp, int r,
+                                            ulonglong2 &a, ulonglong2 &b, ulonglong2 &c,
+                                            ulonglong2 &d, f2 &e) {
+  const ulonglong2 *p = sp + kRecU2 * r;
+  a = p[0];
+  b = p[1];
+  c = p[2];
+  d = p[3];
+  e = reinterpret_cast<const f2 *>(p + 4)[0];
+}
 
 template <bool MASK>
 __device__ __noinline__ AccF32 pair_tile_f32(const ulonglong2 *__restrict__ sp, int cnt,
                                               int first, int stride, f2 X, f2 Y, f2 Z) {
   AccF32 acc;
-  acc.ax = acc.ay = acc.az = acc.bx = acc.by = acc.bz = 0ull;
+  acc.x = acc.y = acc.z = 0ull;
 #pragma unroll 2
   for (int r = first; r < cnt; r += stride) {
-    const ulonglong2 a = sp[3 * r];      // x0 x1 | y0 y1
-    const ulonglong2 b = sp[3 * r + 1];  // z0 z1 | mx0 mx1
-    const ulonglong2 c = sp[3 * r + 2];  // my0 my1 | mz0 mz1
-    const f2 dx = sub2(a.x, X), dy = sub2(a.y, Y), dz = sub2(b.x, Z);
-    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-    float r2l, r2h;
-    upk(r2, r2l, r2h);
-    float il = rsqrt_approx(r2l), ih = rsqrt_approx(r2h);
-    if (MASK) {
-      il = (r2l > 0.0f) ? il : 0.0f;
-      ih = (r2h > 0.0f) ? ih : 0.0f;
-    }
-    const f2 q = pk(il, ih);
-    const f2 q2 = mul2(q, q);
-    const f2 q3 = mul2(q, q2);
-    const f2 md = fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx)));
-    const f2 s = mul2(mul2(md, q2), q3);
-    acc.ax = fma2(s, dx, acc.ax);
-    acc.ay = fma2(s, dy, acc.ay);
-    acc.az = fma2(s, dz, acc.az);
-    acc.bx = fma2(q3, b.y, acc.bx);
-    acc.by = fma2(q3, c.x, acc.by);
-    acc.bz = fma2(q3, c.y, acc.bz);
+    ulonglong2 a, b, c, d;
+    f2 e;
+    load_record(sp, r, a, b, c, d, e);
+    pair_record<MASK>(a, b, c, d, e, X, Y, Z, acc);
   }
   return acc;
 }
@@ -577,10 +594,7 @@ __device__ __forceinline__ void block_update(
     const R w = static_cast<const V *>(a.pos)[i].w;
     if constexpr (MIXED) {
       SrcPair *rec_out = static_cast<SrcPair *>(a.src[par ^ 1]) + L.roff + (il >> 1);
-      const int hf = il & 1;
-      rec_out->mx[hf] = w * mx;
-      rec_out->my[hf] = w * my;
-      rec_out->mz[hf] = w * mz;
+      set_source_moment(*rec_out, il & 1, w, mx, my, mz);
     } else {
       dbl4 mu;
       mu.x = w * mx;
@@ -672,8 +686,13 @@ __device__ __forceinline__ bool staged_loop(int ntiles, uint64_t *bar, int32_t *
 // update state.
 template <typename R>
 constexpr size_t epi_bytes(int warps) {
-  return static_cast<size_t>(warps) * 12 * kTargets * sizeof(float) + sizeof(EpiShared<R>) + 64;
+  return static_cast<size_t>(warps) * (sizeof(R) == 4 ? 6 : 12) * kTargets * sizeof(float) +
+         sizeof(EpiShared<R>) + 64;
 }
+
+// Split partials of one FP32 item of 32 targets: (sum, error) of 3 components.
+// The buffer is sized for the FP64 kernel's 6 doubles per target.
+constexpr int kPartF32 = 6 * kTargets;
 
 // ---------------------------------------------------------------------------
 // FP32-mixed step kernel.
@@ -700,63 +719,60 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
   TargetIn<float4> tin;
   if (warp == 0) tin = load_target<float4>(a, L, it, step, lane);
   const f2 X = pk(pi.x, pi.x), Y = pk(pi.y, pi.y), Z = pk(pi.z, pi.z);
-  float s6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, c6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float s3[3] = {0.f, 0.f, 0.f}, c3[3] = {0.f, 0.f, 0.f};
   const int nrec = it.j1 - it.j0;
   const int ntiles = (nrec + tile - 1) / tile;
   const int own0 = it.t0 >> 1, own1 = (it.t0 + it.nt - 1) >> 1;  // records holding targets
-  ulonglong2 *buf = reinterpret_cast<ulonglong2 *>(dyn);          // [2][tile][3]
+  ulonglong2 *buf = reinterpret_cast<ulonglong2 *>(dyn);          // [2][tile][kRecU2]
   auto issue = [&](int t) {
     const int b = t & 1;
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
     const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
     mbar_expect_tx(&bar[b], bytes);
-    bulk_g2s(buf + static_cast<size_t>(b) * tile * 3, gsrc + r0, bytes, &bar[b]);
+    bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
   };
   auto body = [&](int b, int t) {
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
     const bool mask = (r0 <= own1) && (own0 < r0 + cnt);
-    const ulonglong2 *sp = buf + static_cast<size_t>(b) * tile * 3;
+    const ulonglong2 *sp = buf + static_cast<size_t>(b) * tile * kRecU2;
     const AccF32 acc = mask ? pair_tile_f32<true>(sp, cnt, warp, NW, X, Y, Z)
                             : pair_tile_f32<false>(sp, cnt, warp, NW, X, Y, Z);
-    kahan_add(s6[0], c6[0], hsum(acc.ax));
-    kahan_add(s6[1], c6[1], hsum(acc.ay));
-    kahan_add(s6[2], c6[2], hsum(acc.az));
-    kahan_add(s6[3], c6[3], hsum(acc.bx));
-    kahan_add(s6[4], c6[4], hsum(acc.by));
-    kahan_add(s6[5], c6[5], hsum(acc.bz));
+    kahan_add(s3[0], c3[0], hsum(acc.x));
+    kahan_add(s3[1], c3[1], hsum(acc.y));
+    kahan_add(s3[2], c3[2], hsum(acc.z));
   };
   if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
 
   // cross-warp combine in a fixed order: value = hi + lo per component
-  float *wp = reinterpret_cast<float *>(dyn);  // [NW][12][32]
+  float *wp = reinterpret_cast<float *>(dyn);  // [NW][6][32]
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    wp[(warp * 12 + c) * 32 + lane] = s6[c];
-    wp[(warp * 12 + 6 + c) * 32 + lane] = -c6[c];  // Kahan keeps minus the error
+  for (int c = 0; c < 3; ++c) {
+    wp[(warp * 6 + c) * 32 + lane] = s3[c];
+    wp[(warp * 6 + 3 + c) * 32 + lane] = -c3[c];  // Kahan keeps minus the error
   }
   __syncthreads();
   EpiShared<float> &sm =
-      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 12 * 32 * 4);
-  float hi[6], lo[6];
+      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 6 * 32 * 4);
+  float hi[3], lo[3];
   if (warp == 0) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < 3; ++c) {
       float s = 0.f, e = 0.f;
       for (int w = 0; w < NW; ++w) {
-        neumaier_add(s, e, wp[(w * 12 + c) * 32 + lane]);
-        e += wp[(w * 12 + 6 + c) * 32 + lane];
+        neumaier_add(s, e, wp[(w * 6 + c) * 32 + lane]);
+        e += wp[(w * 6 + 3 + c) * 32 + lane];
       }
       hi[c] = s;
       lo[c] = e;
     }
     if (it.nsplit > 1) {
-      float *part = a.partial + static_cast<size_t>(blockIdx.x) * 12 * 32;
+      float *part = a.partial + static_cast<size_t>(blockIdx.x) * kPartF32;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
+      for (int c = 0; c < 3; ++c) {
         __stcg(part + c * 32 + lane, hi[c]);
-        __stcg(part + (6 + c) * 32 + lane, lo[c]);
+        __stcg(part + (3 + c) * 32 + lane, lo[c]);
       }
       __threadfence();
     }
@@ -768,13 +784,13 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
     if (!s_last) return;  // another item of the group finishes the step
     __threadfence();
     if (warp == 0) {
-      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * 12 * 32;
+      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * kPartF32;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
+      for (int c = 0; c < 3; ++c) {
         float s = 0.f, e = 0.f;
         for (int q = 0; q < it.nsplit; ++q) {
-          neumaier_add(s, e, __ldcg(base + (q * 12 + c) * 32 + lane));
-          e += __ldcg(base + (q * 12 + 6 + c) * 32 + lane);
+          neumaier_add(s, e, __ldcg(base + q * kPartF32 + c * 32 + lane));
+          e += __ldcg(base + q * kPartF32 + (3 + c) * 32 + lane);
         }
         hi[c] = s;
         lo[c] = e;
@@ -783,15 +799,8 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
     }
   }
   if (warp == 0) {
-    // b_dip = 3A - B, compensation terms added last
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float s = 0.f, e = 0.f;
-      neumaier_add(s, e, 3.0f * hi[c]);
-      neumaier_add(s, e, -hi[3 + c]);
-      neumaier_add(s, e, 3.0f * lo[c] - lo[3 + c]);
-      sm.h[c][lane] = s + e;
-    }
+    for (int c = 0; c < 3; ++c) sm.h[c][lane] = hi[c] + lo[c];  // compensation added last
   }
   __syncthreads();
   block_update<float4, true>(a, L, it, step, rec, tin, sm, tab);
@@ -817,40 +826,16 @@ __device__ __noinline__ AccF32x2 pair_tile_f32_2t(const ulonglong2 *__restrict__
                                                    int first, int stride, f2 X0, f2 Y0, f2 Z0,
                                                    f2 X1, f2 Y1, f2 Z1) {
   AccF32x2 acc;
-  acc.a.ax = acc.a.ay = acc.a.az = acc.a.bx = acc.a.by = acc.a.bz = 0ull;
+  acc.a.x = acc.a.y = acc.a.z = 0ull;
   acc.b = acc.a;
-  // the two targets already give two independent chains; unrolling further
-  // took 158 registers (3 blocks per SM) and ran slower than this (128)
+  // the two targets already give two independent chains
 #pragma unroll 1
   for (int r = first; r < cnt; r += stride) {
-    const ulonglong2 a = sp[3 * r];      // x0 x1 | y0 y1
-    const ulonglong2 b = sp[3 * r + 1];  // z0 z1 | mx0 mx1
-    const ulonglong2 c = sp[3 * r + 2];  // my0 my1 | mz0 mz1
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const f2 X = h ? X1 : X0, Y = h ? Y1 : Y0, Z = h ? Z1 : Z0;
-      AccF32 &A = h ? acc.b : acc.a;
-      const f2 dx = sub2(a.x, X), dy = sub2(a.y, Y), dz = sub2(b.x, Z);
-      const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-      float r2l, r2h;
-      upk(r2, r2l, r2h);
-      float il = rsqrt_approx(r2l), ih = rsqrt_approx(r2h);
-      if (MASK) {
-        il = (r2l > 0.0f) ? il : 0.0f;
-        ih = (r2h > 0.0f) ? ih : 0.0f;
-      }
-      const f2 q = pk(il, ih);
-      const f2 q2 = mul2(q, q);
-      const f2 q3 = mul2(q, q2);
-      const f2 md = fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx)));
-      const f2 s = mul2(mul2(md, q2), q3);
-      A.ax = fma2(s, dx, A.ax);
-      A.ay = fma2(s, dy, A.ay);
-      A.az = fma2(s, dz, A.az);
-      A.bx = fma2(q3, b.y, A.bx);
-      A.by = fma2(q3, c.x, A.by);
-      A.bz = fma2(q3, c.y, A.bz);
-    }
+    ulonglong2 a, b, c, d;
+    f2 e;
+    load_record(sp, r, a, b, c, d, e);
+    pair_record<MASK>(a, b, c, d, e, X0, Y0, Z0, acc.a);
+    pair_record<MASK>(a, b, c, d, e, X1, Y1, Z1, acc.b);
   }
   return acc;
 }
@@ -858,7 +843,7 @@ __device__ __noinline__ AccF32x2 pair_tile_f32_2t(const ulonglong2 *__restrict__
 // Dynamic shared memory of the two-target kernel after its pair loop: the
 // warps' (sum, -error) pairs of both halves, then the update state.
 constexpr size_t epi_bytes_t2(int warps) {
-  return static_cast<size_t>(warps) * 24 * kTargets * sizeof(float) + sizeof(EpiShared<float>) + 64;
+  return static_cast<size_t>(warps) * 12 * kTargets * sizeof(float) + sizeof(EpiShared<float>) + 64;
 }
 
 template <int NW>
@@ -868,7 +853,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
   unsigned char *dyn = smem + 16;
   __shared__ int s_last;
   __shared__ GridTables<float> tab;
-  __shared__ float s_h1[12][kTargets];  // second half's (sum, error) while the first updates
+  __shared__ float s_h1[3][kTargets];  // second half's field while the first updates
   tab.load();
   const Item it = a.items[blockIdx.x];
   const LysDev L = a.lys[it.l];
@@ -890,71 +875,69 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
   if (warp == 0) tin = load_target<float4>(a, L, h0, step, lane);
   const f2 X0 = pk(pi0.x, pi0.x), Y0 = pk(pi0.y, pi0.y), Z0 = pk(pi0.z, pi0.z);
   const f2 X1 = pk(pi1.x, pi1.x), Y1 = pk(pi1.y, pi1.y), Z1 = pk(pi1.z, pi1.z);
-  float s12[12], c12[12];
+  float s6[6], c6[6];
 #pragma unroll
-  for (int c = 0; c < 12; ++c) s12[c] = c12[c] = 0.f;
+  for (int c = 0; c < 6; ++c) s6[c] = c6[c] = 0.f;
   const int nrec = it.j1 - it.j0;
   const int ntiles = (nrec + tile - 1) / tile;
   const int own0 = it.t0 >> 1, own1 = (it.t0 + it.nt - 1) >> 1;  // records holding targets
-  ulonglong2 *buf = reinterpret_cast<ulonglong2 *>(dyn);          // [2][tile][3]
+  ulonglong2 *buf = reinterpret_cast<ulonglong2 *>(dyn);          // [2][tile][kRecU2]
   auto issue = [&](int t) {
     const int b = t & 1;
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
     const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
     mbar_expect_tx(&bar[b], bytes);
-    bulk_g2s(buf + static_cast<size_t>(b) * tile * 3, gsrc + r0, bytes, &bar[b]);
+    bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
   };
   auto body = [&](int b, int t) {
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
     const bool mask = (r0 <= own1) && (own0 < r0 + cnt);
-    const ulonglong2 *sp = buf + static_cast<size_t>(b) * tile * 3;
+    const ulonglong2 *sp = buf + static_cast<size_t>(b) * tile * kRecU2;
     const AccF32x2 acc = mask ? pair_tile_f32_2t<true>(sp, cnt, warp, NW, X0, Y0, Z0, X1, Y1, Z1)
                               : pair_tile_f32_2t<false>(sp, cnt, warp, NW, X0, Y0, Z0, X1, Y1, Z1);
-    kahan_add(s12[0], c12[0], hsum(acc.a.ax));
-    kahan_add(s12[1], c12[1], hsum(acc.a.ay));
-    kahan_add(s12[2], c12[2], hsum(acc.a.az));
-    kahan_add(s12[3], c12[3], hsum(acc.a.bx));
-    kahan_add(s12[4], c12[4], hsum(acc.a.by));
-    kahan_add(s12[5], c12[5], hsum(acc.a.bz));
-    kahan_add(s12[6], c12[6], hsum(acc.b.ax));
-    kahan_add(s12[7], c12[7], hsum(acc.b.ay));
-    kahan_add(s12[8], c12[8], hsum(acc.b.az));
-    kahan_add(s12[9], c12[9], hsum(acc.b.bx));
-    kahan_add(s12[10], c12[10], hsum(acc.b.by));
-    kahan_add(s12[11], c12[11], hsum(acc.b.bz));
+    kahan_add(s6[0], c6[0], hsum(acc.a.x));
+    kahan_add(s6[1], c6[1], hsum(acc.a.y));
+    kahan_add(s6[2], c6[2], hsum(acc.a.z));
+    kahan_add(s6[3], c6[3], hsum(acc.b.x));
+    kahan_add(s6[4], c6[4], hsum(acc.b.y));
+    kahan_add(s6[5], c6[5], hsum(acc.b.z));
   };
   if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
 
   // cross-warp combine in a fixed order, per half as in kmc_step_f32
-  float *wp = reinterpret_cast<float *>(dyn);  // [NW][24][32]: 12 sums, then 12 errors
+  float *wp = reinterpret_cast<float *>(dyn);  // [NW][12][32]: 6 sums, then 6 errors
 #pragma unroll
-  for (int c = 0; c < 12; ++c) {
-    wp[(warp * 24 + c) * 32 + lane] = s12[c];
-    wp[(warp * 24 + 12 + c) * 32 + lane] = -c12[c];
+  for (int c = 0; c < 6; ++c) {
+    wp[(warp * 12 + c) * 32 + lane] = s6[c];
+    wp[(warp * 12 + 6 + c) * 32 + lane] = -c6[c];
   }
   __syncthreads();
   EpiShared<float> &sm =
-      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 24 * 32 * 4);
-  float hi[12], lo[12];
+      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 12 * 32 * 4);
+  // hi[0..2], lo[0..2]: first half; hi[3..5], lo[3..5]: second half
+  float hi[6], lo[6];
   if (warp == 0) {
 #pragma unroll
-    for (int c = 0; c < 12; ++c) {
+    for (int c = 0; c < 6; ++c) {
       float s = 0.f, e = 0.f;
       for (int w = 0; w < NW; ++w) {
-        neumaier_add(s, e, wp[(w * 24 + c) * 32 + lane]);
-        e += wp[(w * 24 + 12 + c) * 32 + lane];
+        neumaier_add(s, e, wp[(w * 12 + c) * 32 + lane]);
+        e += wp[(w * 12 + 6 + c) * 32 + lane];
       }
       hi[c] = s;
       lo[c] = e;
     }
     if (it.nsplit > 1) {
-      float *part = a.partial + static_cast<size_t>(blockIdx.x) * 24 * 32;
+      // the two halves' partials, each laid out as kmc_step_f32's
+      float *part = a.partial + static_cast<size_t>(blockIdx.x) * 2 * kPartF32;
 #pragma unroll
-      for (int c = 0; c < 12; ++c) {
+      for (int c = 0; c < 3; ++c) {
         __stcg(part + c * 32 + lane, hi[c]);
-        __stcg(part + (12 + c) * 32 + lane, lo[c]);
+        __stcg(part + (3 + c) * 32 + lane, lo[c]);
+        __stcg(part + kPartF32 + c * 32 + lane, hi[3 + c]);
+        __stcg(part + kPartF32 + (3 + c) * 32 + lane, lo[3 + c]);
       }
       __threadfence();
     }
@@ -966,13 +949,14 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
     if (!s_last) return;  // another item of the group finishes the step
     __threadfence();
     if (warp == 0) {
-      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * 24 * 32;
+      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * 2 * kPartF32;
 #pragma unroll
-      for (int c = 0; c < 12; ++c) {
+      for (int c = 0; c < 6; ++c) {
+        const int o = (c < 3 ? 0 : kPartF32) + (c % 3) * 32 + lane;
         float s = 0.f, e = 0.f;
         for (int q = 0; q < it.nsplit; ++q) {
-          neumaier_add(s, e, __ldcg(base + (q * 24 + c) * 32 + lane));
-          e += __ldcg(base + (q * 24 + 12 + c) * 32 + lane);
+          neumaier_add(s, e, __ldcg(base + q * 2 * kPartF32 + o));
+          e += __ldcg(base + q * 2 * kPartF32 + o + 3 * 32);
         }
         hi[c] = s;
         lo[c] = e;
@@ -981,19 +965,11 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
     }
   }
   if (warp == 0) {
-    // b_dip = 3A - B of the first half; the second half's sums wait in shared memory
+    // the first half's field; the second half's waits in shared memory
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float s = 0.f, e = 0.f;
-      neumaier_add(s, e, 3.0f * hi[c]);
-      neumaier_add(s, e, -hi[3 + c]);
-      neumaier_add(s, e, 3.0f * lo[c] - lo[3 + c]);
-      sm.h[c][lane] = s + e;
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      s_h1[c][lane] = hi[6 + c];
-      s_h1[6 + c][lane] = lo[6 + c];
+      sm.h[c][lane] = hi[c] + lo[c];
+      s_h1[c][lane] = hi[3 + c] + lo[3 + c];
     }
   }
   __syncthreads();
@@ -1006,13 +982,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
     if (warp == 0) {
       tin = load_target<float4>(a, L, h1, step, lane);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float s = 0.f, e = 0.f;
-        neumaier_add(s, e, 3.0f * s_h1[c][lane]);
-        neumaier_add(s, e, -s_h1[3 + c][lane]);
-        neumaier_add(s, e, 3.0f * s_h1[6 + c][lane] - s_h1[9 + c][lane]);
-        sm.h[c][lane] = s + e;
-      }
+      for (int c = 0; c < 3; ++c) sm.h[c][lane] = s_h1[c][lane];
     }
     __syncthreads();
     block_update<float4, true>(a, L, h1, step, rec, tin, sm, tab);

@@ -21,14 +21,37 @@ struct __align__(32) dbl4 {  // FP64 record: x, y, z and a fourth value
 };
 
 // FP32 source record: two NPs (even, odd) interleaved so that each 8-byte
-// pair of lanes feeds one packed f32x2 instruction. 48 bytes, three 16-byte
-// shared-memory loads. A lysosome with an odd NP count ends with a padding NP
-// far away (x = y = z = 1e4 L) whose moment is zero.
+// pair of lanes feeds one packed f32x2 instruction. Per NP j: its position,
+// t_j = 3 w_j m_j and n_j = -w_j m_j. With d = r_j - r_i and q = 1/|d|, the
+// pair term of Eq. 1, w_j (3 (m_j.d) d / |d|^5 - m_j / |d|^3), is then
+// q^3 (u d + n_j) with u = (t_j.d) q^2: three multiply-adds per component and
+// one sum per component instead of separate sums of the two terms. 80 bytes:
+// five 16-byte shared-memory loads, the last 8 bytes padding. A lysosome with
+// an odd NP count ends with a padding NP far away (x = y = z = 1e4 L) whose
+// moment is zero.
 struct __align__(16) SrcPair {
   float x[2], y[2];
-  float z[2], mx[2];
-  float my[2], mz[2];
+  float z[2], tx[2];
+  float ty[2], tz[2];
+  float nx[2], ny[2];
+  float nz[2], pad[2];
 };
+constexpr int kRecU2 = 5;  // 16-byte words per SrcPair
+static_assert(sizeof(SrcPair) == 16 * kRecU2, "SrcPair is five 16-byte words");
+
+// Moment part of a source record from w and the unit moment (every writer
+// uses this, so that records rebuilt from the state match the ones the step
+// wrote, bit for bit).
+__host__ __device__ inline void set_source_moment(SrcPair &r, int h, float w, float mx,
+                                                  float my, float mz) {
+  const float wx = w * mx, wy = w * my, wz = w * mz;
+  r.tx[h] = 3.0f * wx;
+  r.ty[h] = 3.0f * wy;
+  r.tz[h] = 3.0f * wz;
+  r.nx[h] = -wx;
+  r.ny[h] = -wy;
+  r.nz[h] = -wz;
+}
 
 constexpr int kGrid = 200;   // scan points of step iv (Sec. II.1)
 constexpr int kTargets = 32; // target NPs per work item (one per lane of a warp)
