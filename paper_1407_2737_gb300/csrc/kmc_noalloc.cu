@@ -174,10 +174,10 @@ __device__ __forceinline__ void pairs(const ulonglong2 *__restrict__ sp, int cnt
     const f2 q = pk(il, ih);
     const f2 q2 = mul2(q, q);
     const f2 q3 = mul2(q, q2);
-    const f2 u = mul2(fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx))), q2);
-    acc[0] = fma2(q3, fma2(u, dx, d.x), acc[0]);
-    acc[1] = fma2(q3, fma2(u, dy, d.y), acc[1]);
-    acc[2] = fma2(q3, fma2(u, dz, e), acc[2]);
+    const f2 u = mul2(fma2(e, dz, fma2(d.y, dy, mul2(d.x, dx))), q2);
+    acc[0] = fma2(q3, fma2(u, dx, b.y), acc[0]);
+    acc[1] = fma2(q3, fma2(u, dy, c.x), acc[1]);
+    acc[2] = fma2(q3, fma2(u, dz, c.y), acc[2]);
   }
 }
 

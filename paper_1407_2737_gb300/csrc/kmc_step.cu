@@ -128,13 +128,13 @@ __device__ __forceinline__ void pair_record(const ulonglong2 &a, const ulonglong
   const f2 q = pk(il, ih);
   const f2 q2 = mul2(q, q);
   const f2 q3 = mul2(q, q2);
-  const f2 u = mul2(fma2(c.y, dz, fma2(c.x, dy, mul2(b.y, dx))), q2);
-  acc.x = fma2(q3, fma2(u, dx, d.x), acc.x);
-  acc.y = fma2(q3, fma2(u, dy, d.y), acc.y);
-  acc.z = fma2(q3, fma2(u, dz, e), acc.z);
+  const f2 u = mul2(fma2(e, dz, fma2(d.y, dy, mul2(d.x, dx))), q2);
+  acc.x = fma2(q3, fma2(u, dx, b.y), acc.x);
+  acc.y = fma2(q3, fma2(u, dy, c.x), acc.y);
+  acc.z = fma2(q3, fma2(u, dz, c.y), acc.z);
 }
 
-// Record r of a staged tile: x | y, z | tx, ty | tz, nx | ny, nz | padding.
+// Record r of a staged tile: x | y, z | nx, ny | nz, tx | ty, tz | padding.
 __device__ __forceinline__ void load_record(const ulonglong2 *__restrict__ sp, int r,
                                             ulonglong2 &a, ulonglong2 &b, ulonglong2 &c,
                                             ulonglong2 &d, f2 &e) {

@@ -26,15 +26,16 @@ struct __align__(32) dbl4 {  // FP64 record: x, y, z and a fourth value
 // pair term of Eq. 1, w_j (3 (m_j.d) d / |d|^5 - m_j / |d|^3), is then
 // q^3 (u d + n_j) with u = (t_j.d) q^2: three multiply-adds per component and
 // one sum per component instead of separate sums of the two terms. 80 bytes:
-// five 16-byte shared-memory loads, the last 8 bytes padding. A lysosome with
+// five 16-byte shared-memory loads, the last 8 bytes padding. n sits before t:
+// this order ran 1-4 % faster than t before n (same instructions). A lysosome with
 // an odd NP count ends with a padding NP far away (x = y = z = 1e4 L) whose
 // moment is zero.
 struct __align__(16) SrcPair {
   float x[2], y[2];
-  float z[2], tx[2];
-  float ty[2], tz[2];
-  float nx[2], ny[2];
-  float nz[2], pad[2];
+  float z[2], nx[2];
+  float ny[2], nz[2];
+  float tx[2], ty[2];
+  float tz[2], pad[2];
 };
 constexpr int kRecU2 = 5;  // 16-byte words per SrcPair
 static_assert(sizeof(SrcPair) == 16 * kRecU2, "SrcPair is five 16-byte words");
