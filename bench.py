@@ -71,8 +71,9 @@ CONFIGS = {
 FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
 # DRAM bytes (read + write) of one kMC step, by (workload, warps, tile, chunk,
 # targets per lane), from serialised ncu captures of the committed kernel. c1:
-# 8 chains, one launch each: 8 x the mean over 16 launches. c4: one launch.
-STEP_DRAM_BYTES = {("c1", 4, 256, 1024, 1): 2.364e6}
+# 8 chains, one launch each: 8 x the mean over 16 launches. c4: one launch per
+# step, the mean over 2.
+STEP_DRAM_BYTES = {("c1", 4, 256, 1024, 1): 2.365e6, ("c4", 4, 256, 4096, 2): 6.06e6}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (FMA = 2 flops)
 HBM_GBS = 6771.5             # measured copy bandwidth of the GB300s
