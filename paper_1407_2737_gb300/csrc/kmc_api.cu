@@ -74,7 +74,7 @@ V make4(double x, double y, double z, double w) {
   return v;
 }
 
-// Source records (FP32: positions and w_i m_i; FP64: w_i m_i) of every NP into
+// Source records (FP32: positions, 3 w_i m_i and -w_i m_i; FP64: w_i m_i) of every NP into
 // the source buffer of parity par.
 __global__ void sources_f32(const float4 *__restrict__ pos, const float4 *__restrict__ m,
                             const int *__restrict__ slot, SrcPair *__restrict__ src, long long n) {

@@ -5,19 +5,22 @@
 // moments of the start of the step from one ping-pong buffer and writes the
 // new ones to the other.
 //
-// Work item = one block of NW warps: 32 target NPs of one lysosome against a
-// contiguous range of that lysosome's sources. Sources are staged in shared
+// Work item = one block of NW warps: 32 target NPs of one lysosome (64 in the
+// two-targets-per-lane kernel) against a contiguous range of that lysosome's
+// sources. Sources are staged in shared
 // memory, tile by tile, by bulk asynchronous copies (cp.async.bulk, double
 // buffered, completion on an mbarrier). Warp w takes every NW-th source record
 // of a tile for the same 32 targets (one per lane), so every shared-memory
 // load is a broadcast.
 //
 // FP32-mixed pair term (Eq. 1 in reduced units) on two sources at once with
-// packed f32x2 instructions: d = r_j - r_i; r2 = |d|^2; q = rsqrt(r2) per
-// half; q3 = q^3; s = (mu_j . d) q^2 q3; A += s d; B += q3 mu_j; b_dip = 3A - B.
-// That is 19 packed instructions and 2 reciprocal square roots for 2 pairs.
-// Each tile's partial sums are folded into a compensated (Kahan) running sum;
-// the NW warp sums are combined in a fixed order with Neumaier's summation.
+// packed f32x2 instructions, in the form of SrcPair: d = r_j - r_i;
+// r2 = |d|^2; q = rsqrt(r2) per half; u = (t_j . d) q^2 with t_j = 3 w_j m_j;
+// b_dip += q^3 (u d + n_j) with n_j = -w_j m_j. That is 18 packed instructions
+// and 2 reciprocal square roots for 2 pairs. Each tile's partial sums are
+// folded into a compensated (Kahan) running sum; the NW warp sums are combined
+// in a fixed order with Neumaier's summation. The FP64-plain kernel sums the
+// two terms apart, A += (mu_j . d) q^5 d and B += q^3 mu_j, and forms 3A - B.
 //
 // When a target group's sources are split over several items, each item writes
 // its compensated partial sums to scratch; the last item of the group to arrive
