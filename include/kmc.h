@@ -184,6 +184,31 @@ kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
  * through tpl_out (may be NULL); tpl = -1 only reads it. */
 kmc_status kmc_targets_per_lane(kmc_ctx *ctx, int32_t tpl, int32_t *tpl_out);
 
+/* Fields of one work item in kmc_plan_items' output. */
+#define KMC_ITEM_FIELDS 8
+
+/* The work decomposition that kmc_run launches for a batch of n_lys lysosomes
+ * of n[l] NPs (host arrays), computed on the host with no GPU, for tests and
+ * tools. Each step of Sec. II.1 runs one block per work item: a group of
+ * 32 * tpl targets of one lysosome (the last group of a lysosome may be
+ * smaller) against one contiguous part of that lysosome's source records
+ * (pairs of NPs for KMC_FP32_MIXED, single NPs for KMC_FP64_PLAIN). Groups
+ * come lysosome by lysosome, largest lysosome first (stable). A group's parts
+ * are consecutive items. chunk > 0 splits a group's sources into parts of
+ * chunk NPs; chunk = 0 splits only to even out one device-wide wave of a
+ * single chain on n_sms SMs at blocks_per_sm blocks each (n_sms = 0: never).
+ * tpl is 1 or 2 (2 with KMC_FP32_MIXED only); chunk a multiple of 64; n[l] >= 1.
+ * items_out (host, capacity cap items): KMC_ITEM_FIELDS int32 per item, in
+ * launch order: lysosome, first target, targets, target group, first source
+ * record, end source record (exclusive), part index, parts in the group.
+ * *n_items receives the item count (also on KMC_ECAPACITY). chain_cut (host,
+ * KMC_MAX_CHAINS + 1 int32): chain q runs items chain_cut[q] .. chain_cut[q +
+ * 1] - 1 (cut at lysosome boundaries into runs of about equal source records);
+ * *n_chains receives the chain count. Bad arguments give KMC_EINVAL. */
+kmc_status kmc_plan_items(const int32_t *n, int32_t n_lys, kmc_precision prec, int32_t tpl,
+                          int32_t chunk, int32_t blocks_per_sm, int32_t n_sms, int32_t *items_out,
+                          int64_t cap, int64_t *n_items, int32_t *chain_cut, int32_t *n_chains);
+
 /* Largest neighbour rank of kmc_local_concentration (the paper uses 20). */
 #define KMC_PHI_MAX_N 64
 

@@ -230,27 +230,27 @@ void drop_graph(kmc_ctx *c) {
 // each and placed last, so that the blocks, which start in order, give every
 // SM q whole groups plus at most one part: the busiest SM then carries
 // q + 1/s group-loads instead of q + 1.
-std::vector<Item> build_items(const kmc_ctx *c, int chunk, int blocks_per_sm, int n_sms,
-                              int *n_groups, int tpl) {
+std::vector<Item> build_items(const std::vector<int> &np, bool fp32, int chunk,
+                              int blocks_per_sm, int n_sms, int *n_groups, int tpl) {
   const int gsize = kmc::kTargets * tpl;  // targets per group
-  std::vector<int> order(c->n_lys);
-  for (int l = 0; l < c->n_lys; ++l) order[l] = l;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return c->n[x] > c->n[y]; });
+  const int n_lys = static_cast<int>(np.size());
+  std::vector<int> order(n_lys);
+  for (int l = 0; l < n_lys; ++l) order[l] = l;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return np[x] > np[y]; });
   struct Group {
     int l, t0, nt, nrec;
   };
   std::vector<Group> groups;
   for (int l : order) {
-    const int n = c->n[l];
-    const int nrec = c->fp32 ? (n + 1) / 2 : n;
+    const int n = np[l];
+    const int nrec = fp32 ? (n + 1) / 2 : n;
     for (int t0 = 0; t0 < n; t0 += gsize) groups.push_back({l, t0, std::min(gsize, n - t0), nrec});
   }
   const int G = static_cast<int>(groups.size());
   std::vector<int> parts(G, 1);
   if (chunk > 0) {
     for (int g = 0; g < G; ++g) {
-      const int rchunk = c->fp32 ? chunk / 2 : chunk;
+      const int rchunk = fp32 ? chunk / 2 : chunk;
       parts[g] = std::max(1, (groups[g].nrec + rchunk - 1) / rchunk);
     }
   } else if (n_sms > 0 && G >= n_sms) {
@@ -290,6 +290,39 @@ std::vector<Item> build_items(const kmc_ctx *c, int chunk, int blocks_per_sm, in
   return items;
 }
 
+// The launch plan of a batch of lysosomes of np[l] NPs: the items in launch
+// order, and the cut of that list into chains. Pure host code (no device
+// call), so that kmc_plan_items can show it without a GPU.
+struct Plan {
+  std::vector<Item> items;
+  int groups = 0;
+  std::vector<int> chain_cut;  // chain q runs items chain_cut[q] .. chain_cut[q + 1] - 1
+};
+
+Plan plan_items(const std::vector<int> &np, bool fp32, int chunk, int blocks_per_sm, int n_sms,
+                int tpl) {
+  Plan p;
+  // with several chains the lysosomes' kernels interleave on the SMs, and the
+  // split that evens out one device-wide wave does not apply
+  const int chains = std::min(static_cast<int>(np.size()), kMaxChains);
+  p.items = build_items(np, fp32, chunk, blocks_per_sm, chains > 1 ? 0 : n_sms, &p.groups, tpl);
+  // chains: cut the item list (lysosome by lysosome, largest first) at
+  // lysosome boundaries into runs of about equal source-record counts
+  long long total = 0, acc = 0;
+  for (const Item &it : p.items) total += it.j1 - it.j0;
+  p.chain_cut.assign(1, 0);
+  for (size_t u = 0; u < p.items.size(); ++u) {
+    acc += p.items[u].j1 - p.items[u].j0;
+    const bool boundary = u + 1 == p.items.size() || p.items[u + 1].l != p.items[u].l;
+    const long long q = static_cast<long long>(p.chain_cut.size());
+    if (boundary && q < chains && acc * chains >= total * q)
+      p.chain_cut.push_back(static_cast<int>(u + 1));
+  }
+  const int n_items = static_cast<int>(p.items.size());
+  if (p.chain_cut.back() != n_items) p.chain_cut.push_back(n_items);
+  return p;
+}
+
 kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   if (c->items_shape == sh && c->d_items) return KMC_OK;
   // until the rebuild completes, no shape's items are valid
@@ -298,12 +331,9 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   KMC_CUDA(cudaGetDevice(&dev));
   KMC_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
   KMC_CUDA(kmc::step_blocks_per_sm(c->fp32, sh.warps, sh.tile, sh.tpl, &per_sm));
-  int groups = 0;
-  // with several chains the lysosomes' kernels interleave on the SMs, and the
-  // split that evens out one device-wide wave does not apply
-  const int chains = std::min(c->n_lys, kMaxChains);
-  const std::vector<Item> items =
-      build_items(c, sh.chunk, per_sm, chains > 1 ? 0 : n_sms, &groups, sh.tpl);
+  const Plan plan = plan_items(c->n, c->fp32, sh.chunk, per_sm, n_sms, sh.tpl);
+  const std::vector<Item> &items = plan.items;
+  const int groups = plan.groups;
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   // a failed allocation leaves the buffer empty (null, capacity 0), so a
   // later call allocates again instead of using a stale capacity
@@ -339,19 +369,7 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   KMC_CUDA(cudaMemset(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap));
   c->n_items = static_cast<int>(items.size());
   c->items_shape = sh;
-  // chains: cut the item list (lysosome by lysosome, largest first) at
-  // lysosome boundaries into runs of about equal source-record counts
-  long long total = 0, acc = 0;
-  for (const Item &it : items) total += it.j1 - it.j0;
-  c->chain_cut.assign(1, 0);
-  for (size_t u = 0; u < items.size(); ++u) {
-    acc += items[u].j1 - items[u].j0;
-    const bool boundary = u + 1 == items.size() || items[u + 1].l != items[u].l;
-    const long long q = static_cast<long long>(c->chain_cut.size());
-    if (boundary && q < chains && acc * chains >= total * q)
-      c->chain_cut.push_back(static_cast<int>(u + 1));
-  }
-  if (c->chain_cut.back() != c->n_items) c->chain_cut.push_back(c->n_items);
+  c->chain_cut = plan.chain_cut;
   return KMC_OK;
 }
 
@@ -849,6 +867,35 @@ kmc_status kmc_set_stream(kmc_ctx *c, void *cuda_stream) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   c->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->own_stream;
+  return KMC_OK;
+}
+
+kmc_status kmc_plan_items(const int32_t *n, int32_t n_lys, kmc_precision prec, int32_t tpl,
+                          int32_t chunk, int32_t blocks_per_sm, int32_t n_sms, int32_t *items_out,
+                          int64_t cap, int64_t *n_items, int32_t *chain_cut, int32_t *n_chains) {
+  if (!n || n_lys < 1 || !n_items || !chain_cut || !n_chains || cap < 0 || (cap > 0 && !items_out))
+    return fail(KMC_EINVAL, "plan: need n[n_lys >= 1], outputs and cap >= 0");
+  if (prec != KMC_FP32_MIXED && prec != KMC_FP64_PLAIN) return fail(KMC_EINVAL, "bad precision");
+  const bool fp32 = prec == KMC_FP32_MIXED;
+  if (tpl != 1 && !(tpl == 2 && fp32))
+    return fail(KMC_EINVAL, "targets per lane: 1, or 2 with KMC_FP32_MIXED");
+  if (chunk < 0 || chunk % 64 != 0 || blocks_per_sm < 1 || n_sms < 0)
+    return fail(KMC_EINVAL, "plan: chunk a multiple of 64, blocks_per_sm >= 1, n_sms >= 0");
+  std::vector<int> np(n, n + n_lys);
+  for (int v : np)
+    if (v < 1) return fail(KMC_EINVAL, "plan: every lysosome needs an NP");
+  const Plan p = plan_items(np, fp32, chunk, blocks_per_sm, n_sms, tpl);
+  *n_items = static_cast<int64_t>(p.items.size());
+  *n_chains = static_cast<int32_t>(p.chain_cut.size()) - 1;
+  for (size_t q = 0; q < p.chain_cut.size(); ++q) chain_cut[q] = p.chain_cut[q];
+  if (static_cast<int64_t>(p.items.size()) > cap)
+    return fail(KMC_ECAPACITY, "plan: %lld items, capacity %lld",
+                static_cast<long long>(p.items.size()), static_cast<long long>(cap));
+  for (size_t u = 0; u < p.items.size(); ++u) {
+    const Item &it = p.items[u];
+    const int32_t f[KMC_ITEM_FIELDS] = {it.l, it.t0, it.nt, it.gid, it.j0, it.j1, it.split, it.nsplit};
+    for (int k = 0; k < KMC_ITEM_FIELDS; ++k) items_out[KMC_ITEM_FIELDS * u + k] = f[k];
+  }
   return KMC_OK;
 }
 

@@ -76,7 +76,7 @@ struct LysDev {
 struct Item {
   int32_t l;       // lysosome
   int32_t t0;      // first target (index within the lysosome)
-  int32_t nt;      // targets, 1..32
+  int32_t nt;      // targets, 1..32 (1..64 with two targets per lane)
   int32_t gid;     // target group (index of its arrival counter)
   int32_t j0, j1;  // source records of this item (relative to the lysosome)
   int32_t split;   // index of this item within its group

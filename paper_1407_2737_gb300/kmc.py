@@ -33,9 +33,10 @@ EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
            "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall",
-           "kmc_regenerate_rsa", "kmc_targets_per_lane")
+           "kmc_regenerate_rsa", "kmc_targets_per_lane", "kmc_plan_items")
 KMC_NOALLOC_MAX_N = 8192
 KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
+KMC_ITEM_FIELDS = 8  # per work item in kmc_plan_items
 KMC_PHI_MAX_N = 64
 
 
@@ -94,6 +95,9 @@ def lib():
                                          C.c_uint32]
             L.kmc_debug_stall.argtypes = [vp]
             L.kmc_targets_per_lane.argtypes = [vp, C.c_int32, _I32]
+            L.kmc_plan_items.argtypes = [_I32, C.c_int32, C.c_int, C.c_int32, C.c_int32,
+                                         C.c_int32, C.c_int32, _I32, C.c_int64, _I64, _I32,
+                                         _I32]
             L.kmc_regenerate_rsa.argtypes = [vp, C.c_int32, C.c_double, C.c_double, C.c_uint64,
                                              C.c_uint32, C.c_int64, _I64]
             L.kmc_destroy.argtypes = [vp]
@@ -199,6 +203,27 @@ def kmc_regenerate_rsa(ctx, lys, radius, diameter, seed, loop, max_candidates=0)
                                     C.c_uint64(int(seed)), C.c_uint32(int(loop)),
                                     int(max_candidates), C.byref(used)))
     return int(used.value)
+
+
+def kmc_plan_items(n, precision, tpl=1, chunk=0, blocks_per_sm=5, n_sms=0):
+    """The work items kmc_run launches for lysosomes of n[l] NPs (host only, no
+    GPU): returns (items, chain_cut), items an int32 array [n_items, 8] of
+    (lysosome, first target, targets, group, first record, end record, part,
+    parts) and chain_cut the list of chain boundaries into items."""
+    nn = np.ascontiguousarray(n, dtype=np.int32)
+    cnt = C.c_int64()
+    nch = C.c_int32()
+    cut = np.zeros(KMC_MAX_CHAINS + 1, dtype=np.int32)
+    args = (nn.ctypes.data_as(_I32), len(nn), int(precision), int(tpl), int(chunk),
+            int(blocks_per_sm), int(n_sms))
+    status = lib().kmc_plan_items(*args, None, 0, C.byref(cnt), cut.ctypes.data_as(_I32),
+                                  C.byref(nch))
+    if status != KMC_ECAPACITY:
+        _check(status)
+    items = np.zeros((max(cnt.value, 1), KMC_ITEM_FIELDS), dtype=np.int32)
+    _check(lib().kmc_plan_items(*args, items.ctypes.data_as(_I32), cnt.value, C.byref(cnt),
+                                cut.ctypes.data_as(_I32), C.byref(nch)))
+    return items[:cnt.value], [int(x) for x in cut[:nch.value + 1]]
 
 
 def kmc_targets_per_lane(ctx, tpl=None):
