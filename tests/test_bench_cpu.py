@@ -37,3 +37,20 @@ def test_bench_options_are_documented():
     assert r.returncode == 0
     for opt in ("--gpus", "--steps", "--warmup", "--impl", "--config", "--row", "--shape"):
         assert opt in r.stdout, opt
+
+
+def test_traffic_figures_come_from_committed_profiles():
+    """Every DRAM-traffic figure the bench reports is one that an ncu summary
+    under profiles/ states, for a workload the bench knows and a launch shape
+    the library accepts."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    prof = os.path.join(ROOT, "profiles")
+    text = "".join(open(os.path.join(prof, f)).read() for f in sorted(os.listdir(prof)))
+    assert bench.STEP_DRAM_BYTES
+    for (cfg, warps, tile, chunk, tpl), nbytes in bench.STEP_DRAM_BYTES.items():
+        assert cfg == "c1" or cfg in bench.CONFIGS, cfg
+        assert warps in (4, 8, 16) and tile & (tile - 1) == 0 and chunk % 64 == 0 and tpl in (1, 2)
+        assert "%.4g MB" % (nbytes / 1e6) in text, (cfg, nbytes)
