@@ -12,6 +12,7 @@
 //             b_dip,i = sum_{j != i} [3 (mu_j . d) d / r^5 - mu_j / r^3],
 //             mu_j = w_j m_j, d = r_j - r_i in units of L.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
 namespace kmc {
@@ -39,6 +40,12 @@ struct __align__(16) SrcPair {
 };
 constexpr int kRecU2 = 5;  // 16-byte words per SrcPair
 static_assert(sizeof(SrcPair) == 16 * kRecU2, "SrcPair is five 16-byte words");
+// the FP32 pair loops read the words as x|y, z|nx, ny|nz, tx|ty, tz
+static_assert(offsetof(SrcPair, z) == 16 && offsetof(SrcPair, nx) == 24 &&
+                  offsetof(SrcPair, ny) == 32 && offsetof(SrcPair, nz) == 40 &&
+                  offsetof(SrcPair, tx) == 48 && offsetof(SrcPair, ty) == 56 &&
+                  offsetof(SrcPair, tz) == 64,
+              "SrcPair word order as the pair loops read it");
 
 // Moment part of a source record from w and the unit moment (every writer
 // uses this, so that records rebuilt from the state match the ones the step
