@@ -75,3 +75,32 @@ def test_header_constants_match_the_binding():
     assert len(defs) >= 2
     for name, value in defs:
         assert getattr(kmc, name) == int(value), name
+
+
+def test_every_context_entry_point_rejects_a_null_context(L):
+    """Each entry point that takes a context answers a NULL one with
+    KMC_EINVAL before any device call; the context-free ones check their
+    sizes and pointers on the host too."""
+    def neutral(t):
+        if t in (C.c_int32, C.c_int, C.c_int64, C.c_uint64, C.c_uint32):
+            return 0
+        if t is C.c_double:
+            return 0.0
+        return None
+    checked = 0
+    for name in kmc.EXPORTS:
+        f = getattr(L, name)
+        at = getattr(f, "argtypes", None)
+        if name == "kmc_destroy" or not at or at[0] is not C.c_void_p:
+            continue
+        assert f(None, *[neutral(t) for t in at[1:]]) == kmc.KMC_EINVAL, name
+        checked += 1
+    assert checked >= 14
+    big = kmc.KMC_NOALLOC_MAX_N + 1
+    cen = np.zeros(3)
+    cp = cen.ctypes.data_as(C.POINTER(C.c_double))
+    assert L.kmc_dipolar_field_noalloc(0, 1, 1, 1, 1e6, cp, 1e-8, 1, None) == kmc.KMC_ECAPACITY
+    assert L.kmc_dipolar_field_noalloc(big, 1, 1, 1, 1e6, cp, 1e-8, 1, None) == kmc.KMC_ECAPACITY
+    assert L.kmc_dipolar_field_noalloc(4, None, 1, 1, 1e6, cp, 1e-8, 1, None) == kmc.KMC_EINVAL
+    assert L.kmc_dipolar_field_noalloc(4, 1, 1, 1, -1.0, cp, 1e-8, 1, None) == kmc.KMC_EINVAL
+    assert L.kmc_mean_run(None, 0, None, 0, 0.0, 0, 0, 0, None, 0, None) == kmc.KMC_EINVAL
