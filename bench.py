@@ -18,6 +18,11 @@ oracle timed on the host cores (cpu_baseline).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--config c0|c1|c2|c3|c4] [--row f1|f2|f4]
 
+The default line also carries, under "configs", the 512-lysosome batch (c3)
+and the 50 000-NP lysosome (c4), each timed over a bounded number of periods
+with its own FP32 roofline fraction, FP64-plain speed-up and end-to-end rate
+(--no-sub skips them).
+
 --config picks another of the paper-shaped workloads for the same measurement
 (c1, the 8 x 2000-NP workload above, is the default and the headline line):
 c0 one 100-NP lysosome; c2 one 8000-NP lysosome at 5 % and 40 mT; c3 512
@@ -414,6 +419,103 @@ def run_reference(args):
     return 0
 
 
+# The batched and the large workloads measured beside the headline (a bounded
+# number of periods per bench step, as stated in each entry): timed bench
+# steps, FP64-plain launch shape pinned (its autotuner would spend tens of
+# seconds on these sizes), FP64 sample length in kMC steps.
+SUB_CONFIGS = {"c3": dict(steps=3, shape64=(4, 64, 0), fp64_steps=20),
+               "c4": dict(steps=2, shape64=(4, 64, 4096), fp64_steps=10)}
+
+
+def measure_sub_config(name, kmc, inputs, torch, stream, flush, warmup, uuid=None):
+    """One workload of SUB_CONFIGS on this GPU: FP32-mixed particle-steps/s
+    and the step kernel's FP32 roofline (CUDA events on the library's stream,
+    L2 flushed between bench steps), the FP64-plain rate on a bounded sample,
+    and the same FP32 run end to end from host buffers (fresh context, run,
+    reads, destroy)."""
+    cfg = SUB_CONFIGS[name]
+    workload, bounded, _ = CONFIGS[name]
+    lyss, run = workload_of(inputs, name)
+    n_steps = run["S"] * run["periods"]
+    n_np = sum(l.n for l in lyss)
+    pairs = sum(l.n * (l.n - 1) for l in lyss)
+    ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+    kmc.kmc_set_stream(ctx, stream.cuda_stream)
+    for _ in range(warmup):  # the first run tunes the launch shape
+        kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
+                    run["seed"])
+    kmc.kmc_sync(ctx)
+    warps, tile, chunk = kmc.kmc_tuning(ctx)
+    tpl = kmc.kmc_targets_per_lane(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(cfg["steps"])]
+    torch.cuda.synchronize()
+    with Clocks(uuid) as clk:
+        for k in range(cfg["steps"]):
+            flush.zero_()
+            ev[k][0].record(stream)
+            kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"],
+                        run["discard"], run["seed"])
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    kmc.kmc_sync(ctx)
+    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    kmc.kmc_destroy(ctx)
+    value = n_np * n_steps * cfg["steps"] / t
+    achieved = FLOPS_PER_PAIR * pairs * n_steps * cfg["steps"] / t / 1e12
+    chains = min(len(lyss), kmc.KMC_MAX_CHAINS)
+    # FP64-plain on a bounded sample (rate only)
+    c64 = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
+    kmc.kmc_set_stream(c64, stream.cuda_stream)
+    kmc.kmc_tuning(c64, *cfg["shape64"])
+    S64 = cfg["fp64_steps"]
+    kmc.kmc_run(c64, run["mu0Hmax"], run["f"], S64, 1, 0, run["seed"])  # graph, warm
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    kmc.kmc_run(c64, run["mu0Hmax"], run["f"], S64, 1, 0, run["seed"])
+    e1.record(stream)
+    kmc.kmc_sync(c64)
+    t64 = e0.elapsed_time(e1) / 1e3
+    kmc.kmc_destroy(c64)
+    v64 = n_np * S64 / t64
+    # end to end from host buffers, one bench step (the tuned shape is cached)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+    kmc.kmc_run(c, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
+                run["seed"])
+    for l in range(len(lyss)):
+        kmc.kmc_read(c, kmc.KMC_READ_SAR, l)
+        kmc.kmc_read(c, kmc.KMC_READ_LOOP_M, l)
+        kmc.kmc_read(c, kmc.KMC_READ_NP_ENERGY, l)
+    kmc.kmc_destroy(c)
+    te = time.perf_counter() - t0
+    n_rec = run["S"] * (run["periods"] - run["discard"])
+    return {
+        "workload": workload, "bench_step": "%d periods (%d discarded) of %d steps" % (
+            bounded[0], bounded[1], run["S"]),
+        "value": value, "unit": UNIT, "ms_per_step": 1e3 * t / cfg["steps"],
+        "steps": cfg["steps"], "warmup": warmup, "particles": n_np,
+        "pair_interactions_per_s": pairs * n_steps * cfg["steps"] / t,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(),
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops(),
+                     "traffic": STEP_DRAM_BYTES.get((name, warps, tile, chunk, tpl)),
+                     "kernel": ("kmc_step_f32_t2<%d>" if tpl == 2 else "kmc_step_f32<%d>")
+                     % warps},
+        "launch": {"warps": warps, "tile": tile, "chunk": chunk, "targets_per_lane": tpl,
+                   "chains": chains},
+        "fp64_plain": {"value": v64, "unit": UNIT, "speedup_fp32_mixed": value / v64,
+                       "sample": "%d steps of the whole workload" % S64,
+                       "launch": dict(zip(("warps", "tile", "chunk"), cfg["shape64"]))},
+        "e2e": {"value": n_np * n_steps / te, "unit": UNIT,
+                "h2d_bytes_per_step": sum(l.n * 7 * 8 for l in lyss) + 8 * len(lyss),
+                "d2h_bytes_per_step": sum(8 + 8 * n_rec + 8 * l.n for l in lyss)},
+        "gpu_launches": 1 + run["periods"] * (run["S"] * chains + 1),
+        "clocks": clk.summary(),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,6 +531,8 @@ def main():
                     help="pin the FP64-plain launch shape as warps,tile,chunk (default: autotuned)")
     ap.add_argument("--config", default="c1", choices=sorted(CONFIGS),
                     help="workload (default c1, the headline line)")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the batched and large workloads measured beside the default line")
     ap.add_argument("--row", default="", choices=["", "f1", "f2", "f2r", "f4"],
                     help="measure an output built on the step instead (see above)")
     args = ap.parse_args()
@@ -583,6 +687,11 @@ def main():
             fp64["sample"] = "%d steps of the whole workload (rate only)" % (units64 // n_np)
         kmc.kmc_destroy(c64)
 
+    subs = None
+    if args.config == "c1" and world == 1 and not args.no_sub:
+        subs = {name: measure_sub_config(name, kmc, inputs, torch, stream, flush, 1, uuid)
+                for name in SUB_CONFIGS}
+
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu and args.gpus == 1:
         # oracle runs of at most ~5e9 pair evaluations each
@@ -625,6 +734,8 @@ def main():
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
+        if subs:
+            line["configs"] = subs
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

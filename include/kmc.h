@@ -88,9 +88,13 @@ enum {
   KMC_READ_AREA = 3,      /* [1] hysteresis area A, J/m^3 per cycle (Sec. III.2.a) */
   KMC_READ_SAR = 4,       /* [1] SAR = A f / rho, W/kg                             */
   KMC_READ_MOMENTS = 5,   /* [n][3] current unit moments                           */
-  KMC_READ_COUNTERS = 6,  /* [4] over the last run: jumps, near-threshold draws
-                             (|u - P| < 1e-9), NP-steps with one minimum, NP-steps
-                             whose working plane needed the fallback               */
+  KMC_READ_COUNTERS = 6,  /* [7] NP-steps of the last run: jumps, near-threshold
+                             draws (|u - P| < 1e-9), profiles with one minimum,
+                             working planes that needed the fallback, FP32 scans
+                             redone in FP64, FP32 barriers recomputed in FP64 near
+                             switching, NPs held because their field, barrier or
+                             probability was not finite. Readable after a device
+                             error (it does not report one)                        */
   KMC_READ_DHDIP = 7,     /* [n] Eq. 6 per NP, T: the dipolar field along z (the
                              applied field's direction) during the step at
                              +mu0 H_max (step 0 of a period) minus that during the
@@ -134,11 +138,17 @@ kmc_status kmc_run(kmc_ctx *ctx, const double *mu0Hmax, int32_t n_amp, double f,
 
 /* Copies output `what` (KMC_READ_*) of lysosome `lys` into buf[cap]. Sets
  * *written to the number of elements (also on KMC_ECAPACITY). Waits for
- * queued work. */
+ * queued work. The results of a run (loop, energies, area, SAR, Eq. 6) report
+ * a device error as kmc_sync does; the state (moments, positions, axes) and
+ * the counters are readable after one. */
 kmc_status kmc_read(kmc_ctx *ctx, int32_t what, int32_t lys, double *buf, int64_t cap,
                     int64_t *written);
 
-/* Waits for queued work and reports device-side errors. */
+/* Waits for queued work and reports device-side errors: KMC_ETIMEOUT (a
+ * staging wait ran out), KMC_ESTATE (an energy profile with more than two
+ * minima, or a non-finite dipolar field or barrier, as two NPs at one point
+ * give: such an NP keeps its moment for the step and is counted). The error
+ * stays set until the next kmc_run or kmc_debug_step. */
 kmc_status kmc_sync(kmc_ctx *ctx);
 
 /* Test hook: one step (steps i-vii) of every NP from the moments m_in
@@ -148,7 +158,12 @@ kmc_status kmc_sync(kmc_ctx *ctx);
  * [N]-major and optional (NULL to skip): m_out [N][3]; B_dip [N][3] dipolar
  * field mu0 H_dip (T); dE [N][2] barriers E3 - E_a (current well a) and
  * E3 - E_b (J, 0 with a single minimum); P [N] jump probability; u [N] draw;
- * flags [N] = n_min | jumped << 2 | near-threshold << 3 | fallback plane << 4. */
+ * flags [N] = n_min | jumped << 2 | near-threshold << 3 | fallback plane << 4 |
+ * FP32 scan redone in FP64 << 5 | FP32 barrier recomputed in FP64 << 6 |
+ * held for a non-finite field or barrier << 7. With the environment variable
+ * KMC_DEBUG_RESCAN=1 an FP32 context scans every target again in FP64 (a test
+ * of that path, which Eq. 2's profiles never need: its derivative has at most
+ * four roots, so FP32 noise at one node cannot raise the count above four). */
 kmc_status kmc_debug_step(kmc_ctx *ctx, const double *mu0Hext, double t_step,
                           uint64_t seed, int64_t step, const double *m_in, double *m_out,
                           double *B_dip, double *dE, double *P, double *u,
@@ -310,33 +325,48 @@ void kmc_destroy(kmc_ctx *ctx);
 #define KMC_NOALLOC_MAX_N 8192
 
 /* The dipolar field of one lysosome, computed like the FP32-mixed pair sum of
- * kmc_run (split source ranges, compensated sums), for callers that cannot call
- * cudaMalloc: code inside another framework's memory pool, processes whose
- * device memory is reserved up front, or libraries handed device pointers by
- * their caller. It allocates nothing. The paper has no counterpart: this entry
- * point exists only for such callers.
+ * kmc_run (split source ranges, compensated sums, the same pair term), for
+ * callers that cannot call cudaMalloc: code inside another framework's memory
+ * pool, processes whose device memory is reserved up front, or libraries
+ * handed device pointers by their caller. It allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call. The paper has no
+ * counterpart: this entry point exists only for such callers.
  *
  *   n       NPs, 1 .. KMC_NOALLOC_MAX_N (otherwise KMC_ECAPACITY)
- *   pos     DEVICE [n][3] centres, m
+ *   pos     DEVICE [n][3] centres, m (8-byte aligned)
  *   m       DEVICE [n][3] unit moments
  *   vol     DEVICE [n] volumes, m^3
  *   Ms      A/m, > 0
  *   center  HOST [3] origin of the float32 frame, m (e.g. the lysosome centre)
  *   length  unit of the float32 frame, m, > 0 (e.g. the NP diameter)
- *   B       DEVICE [n][3] output: mu0 H_dip on every NP (Eq. 1), T
+ *   B       DEVICE [n][3] output: mu0 H_dip on every NP, the all-pairs dipolar
+ *           field of the other NPs, T
+ *   status  DEVICE int32 output, or NULL: KMC_OK, or KMC_ETIMEOUT if a
+ *           shared-memory staging wait of this call ran out (about 2 s); the
+ *           targets it affected then hold NaN in B
  *   cuda_stream  stream to queue on (NULL: the default stream)
- * All pointers are owned by the caller. The call only queues work: B is valid
- * once the stream has reached it. Its working memory is one static device
- * array of about 2 MB that every GPU loading the library holds until the
- * process exits. Every call shares that array and leaves its contents behind;
- * calls that overlap on the GPU (other streams, other host threads) race on it.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Errors: KMC_EINVAL (NULL pointer, Ms or length not
- * positive), KMC_ECAPACITY (n out of range), KMC_ECUDA (launch failed). */
+ * All pointers are owned by the caller. pos, m, vol, B and status must be
+ * device (or managed) memory of the current device, which the call checks
+ * (cudaPointerGetAttributes) before it launches anything. The call only
+ * queues work: B and *status are valid once the stream has reached them.
+ * Its working memory is one static device array of about 2 MB that every GPU
+ * loading the library holds until the process exits. Every call shares that
+ * array and leaves its contents behind (the call clears what must start at
+ * zero); calls that overlap on the GPU (other streams, other host threads)
+ * race on it. The first call on each device, and the first after the
+ * device's context changed, looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Setting the environment variable
+ * KMC_FAULT=noalloc_stall makes every staging wait expect more bytes than
+ * its copy delivers and give up after 1 ms (a test of the timeout path; no
+ * copy is left unfinished). Errors: KMC_EINVAL (NULL or misaligned pointer, a
+ * buffer that is not device memory of the current device, Ms or length not
+ * positive, center not finite), KMC_ECAPACITY (n out of range), KMC_ECUDA
+ * (launch failed). */
 kmc_status kmc_dipolar_field_noalloc(int32_t n, const double *pos, const double *m,
                                      const double *vol, double Ms, const double *center,
-                                     double length, double *B, void *cuda_stream);
+                                     double length, double *B, int32_t *status,
+                                     void *cuda_stream);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char *kmc_last_error(void);

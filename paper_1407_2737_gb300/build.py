@@ -3,6 +3,12 @@
 ``python -m paper_1407_2737_gb300.build`` or :func:`build` compiles every
 ``csrc/*.cu`` file to an object in parallel with nvcc and links
 ``_build/libkmc.so`` (CUDA runtime linked statically). Nothing is installed.
+
+``build(debug=True)`` (``--debug``) builds the same sources with -DKMC_DEBUG
+into ``_build_debug/libkmc.so``: every work item, staged tile and Newton
+bracket is checked against its bounds on the device, and a failed check skips
+the access and is reported by kmc_sync as KMC_ESTATE with the check's site.
+Load it by setting KMC_LIB_PATH to that file before importing the binding.
 """
 from __future__ import annotations
 
@@ -18,6 +24,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkmc.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libkmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -46,12 +54,16 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link libkmc.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile and link libkmc.so (the KMC_DEBUG variant with debug=True);
+    returns its path."""
+    out_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if debug:
+        extra = list(extra) + ["-DKMC_DEBUG"]
+    os.makedirs(out_dir, exist_ok=True)
     srcs = _sources()
     hdrs = _headers()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     jobs = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, [s] + hdrs)]
     cc = nvcc()
 
@@ -68,16 +80,17 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         for msg in ex.map(compile_one, jobs):
             if verbose and msg:
                 print(msg, file=sys.stderr)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".%d.tmp" % os.getpid()
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".%d.tmp" % os.getpid()
         r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True,
                            text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [],
+                debug="--debug" in sys.argv))

@@ -8,12 +8,15 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "kmc.h"
 #include "kmc_launch.h"
@@ -63,6 +66,14 @@ kmc_status fail(kmc_status s, const char *fmt, ...) {
   } while (0)
 
 bool is_finite(double x) { return std::isfinite(x); }
+
+// A named range on the host timeline of a profiler (NVTX; no cost without one).
+struct Phase {
+  explicit Phase(const char *name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+  Phase(const Phase &) = delete;
+  Phase &operator=(const Phase &) = delete;
+};
 
 template <typename V>
 V make4(double x, double y, double z, double w) {
@@ -394,6 +405,8 @@ StepArgs base_args(kmc_ctx *c) {
   a.partial = c->d_partial;
   a.arrivals = c->d_arrivals;
   a.rs = c->d_rs;
+  a.n_items = c->n_items;
+  a.n_lys = c->n_lys;
   return a;
 }
 
@@ -413,13 +426,21 @@ kmc_status refresh_sources(kmc_ctx *c, int par) {
 }
 
 kmc_status check_device_error(kmc_ctx *c) {
-  int32_t e = 0;
-  KMC_CUDA(cudaMemcpyAsync(&e, c->d_err, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+  int32_t ew[2] = {0, 0};
+  KMC_CUDA(cudaMemcpyAsync(ew, c->d_err, sizeof(ew), cudaMemcpyDeviceToHost, c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
+  const int32_t e = ew[0];
+  if (e & kmc::kErrBounds)
+    return fail(KMC_ESTATE, "a bounds check of the debug build failed (site %d); results are "
+                "not valid", ew[1]);
   if (e & kmc::kErrTimeout)
     return fail(KMC_ETIMEOUT, "a device-side wait for a shared-memory copy timed out");
   if (e & kmc::kErrExtrema)
     return fail(KMC_ESTATE, "an energy profile had more than two minima or maxima");
+  if (e & kmc::kErrNonFinite)
+    return fail(KMC_ESTATE,
+                "a dipolar field or barrier was not finite (two NPs at one point?); those NPs "
+                "kept their moments (KMC_READ_COUNTERS counts them)");
   return KMC_OK;
 }
 
@@ -450,6 +471,7 @@ bool shape_ok(const kmc_ctx *c, const Shape &s) {
 // `steps` repeats of one unrecorded step.
 kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int steps, bool period,
                          cudaGraphExec_t *out) {
+  Phase phase("kmc_capture");
   *out = nullptr;
   const int n_chains = static_cast<int>(c->chain_cut.size()) - 1;
   for (int q = 0; q < n_chains; ++q) {
@@ -471,6 +493,7 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
     const int u0 = c->chain_cut[q];
     StepArgs b = a;
     b.items = c->d_items + u0;
+    b.n_items = c->chain_cut[q + 1] - u0;
     // an item's partials: (sum, error) of 3 FP32 or 6 FP64 (two floats each) components
     // per target
     if (split)
@@ -555,6 +578,7 @@ float time_shape(kmc_ctx *c, const Shape &s) {
 }
 
 kmc_status autotune(kmc_ctx *c) {
+  Phase phase("kmc_tune");
   int max_n = 0;
   for (int x : c->n) max_n = std::max(max_n, x);
   const TuneKey key{c->fp32, c->N, c->n_lys, max_n, c->tpl_mode};
@@ -617,7 +641,7 @@ kmc_status autotune(kmc_ctx *c) {
   }
   KMC_CUDA(cudaGetLastError());
   KMC_CUDA(cudaMemcpyAsync(c->d_m, saved.data(), saved.size(), cudaMemcpyHostToDevice, c->stream));
-  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   c->shape = bs;
   {
@@ -673,8 +697,8 @@ kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_p
   KMC_TRY(dalloc(&c->d_eacc, sizeof(double) * N));
   KMC_TRY(dalloc(&c->d_dh, sizeof(double) * N));
   if (c->fp32) KMC_TRY(dalloc(&c->d_pos64, sizeof(dbl4) * N));
-  KMC_TRY(dalloc(&c->d_cnt, sizeof(unsigned long long) * 4 * c->n_lys));
-  KMC_TRY(dalloc(&c->d_err, sizeof(int32_t)));
+  KMC_TRY(dalloc(&c->d_cnt, sizeof(unsigned long long) * kmc::kCounters * c->n_lys));
+  KMC_TRY(dalloc(&c->d_err, 2 * sizeof(int32_t)));  // error bits, failed check site
   KMC_TRY(dalloc(&c->d_rs, sizeof(RunState)));
   KMC_CUDA(cudaMemcpy(c->d_pos, h_pos.data(), vb, cudaMemcpyHostToDevice));
   KMC_CUDA(cudaMemcpy(c->d_axis, h_axis.data(), vb, cudaMemcpyHostToDevice));
@@ -689,8 +713,8 @@ kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_p
   KMC_CUDA(cudaMemset(c->d_dh, 0, sizeof(double) * N));
   if (c->fp32)
     KMC_CUDA(cudaMemcpy(c->d_pos64, h_pos64.data(), sizeof(dbl4) * N, cudaMemcpyHostToDevice));
-  KMC_CUDA(cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * 4 * c->n_lys));
-  KMC_CUDA(cudaMemset(c->d_err, 0, sizeof(int32_t)));
+  KMC_CUDA(cudaMemset(c->d_cnt, 0, sizeof(unsigned long long) * kmc::kCounters * c->n_lys));
+  KMC_CUDA(cudaMemset(c->d_err, 0, 2 * sizeof(int32_t)));
   KMC_CUDA(cudaMemcpy(c->d_lys, c->h_lys.data(), sizeof(LysDev) * c->n_lys,
                       cudaMemcpyHostToDevice));
   return KMC_OK;
@@ -734,6 +758,7 @@ const char *kmc_last_error(void) { return g_last_error.c_str(); }
 
 kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec,
                       kmc_ctx **out) {
+  Phase phase("kmc_create");
   g_last_error.clear();
   if (!out) return fail(KMC_EINVAL, "out is NULL");
   *out = nullptr;
@@ -941,6 +966,7 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
 
 kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, int32_t S,
                    int32_t periods, int32_t discard, uint64_t seed) {
+  Phase phase("kmc_run");
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (!mu0Hmax || (n_amp != 1 && n_amp != c->n_lys))
     return fail(KMC_EINVAL, "need 1 or n_lys = %d amplitudes", c->n_lys);
@@ -974,8 +1000,9 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
   KMC_CUDA(cudaMemsetAsync(c->d_loop, 0, sizeof(long long) * need, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_eacc, 0, sizeof(double) * c->N, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_dh, 0, sizeof(double) * c->N, c->stream));
-  KMC_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long) * 4 * c->n_lys, c->stream));
-  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long) * kmc::kCounters * c->n_lys,
+                           c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
   KMC_TRY(refresh_sources(c, static_cast<int>(c->step_global & 1)));
   RunState rs{c->step_global, 0, 0};
@@ -1009,17 +1036,26 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
 }
 
 kmc_status kmc_sync(kmc_ctx *c) {
+  Phase phase("kmc_sync");
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   return check_device_error(c);
 }
 
 kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t cap,
                     int64_t *written) {
+  Phase phase("kmc_read");
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (written) *written = 0;
   if (lys < 0 || lys >= c->n_lys) return fail(KMC_EINVAL, "lysosome %d out of range", lys);
   if (cap < 0 || (cap > 0 && !buf)) return fail(KMC_EINVAL, "bad output buffer");
-  KMC_TRY(check_device_error(c));
+  if (what == KMC_READ_COUNTERS || what == KMC_READ_MOMENTS || what == KMC_READ_POSITIONS ||
+      what == KMC_READ_AXES) {
+    // state, readable after a device error so that the caller can see what
+    // happened (kmc_sync reports the error)
+    KMC_CUDA(cudaStreamSynchronize(c->stream));
+  } else {
+    KMC_TRY(check_device_error(c));
+  }
   const int n = c->n[lys], o = c->off[lys];
   int64_t need = 0;
   switch (what) {
@@ -1032,7 +1068,7 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
     case KMC_READ_AREA:
     case KMC_READ_SAR: need = 1; break;
     case KMC_READ_MOMENTS: need = 3ll * n; break;
-    case KMC_READ_COUNTERS: need = 4; break;
+    case KMC_READ_COUNTERS: need = kmc::kCounters - 1; break;
     default: return fail(KMC_EINVAL, "unknown output %d", what);
   }
   if (what != KMC_READ_MOMENTS && what != KMC_READ_POSITIONS && what != KMC_READ_AXES &&
@@ -1107,9 +1143,10 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
       break;
     }
     case KMC_READ_COUNTERS: {
-      unsigned long long cn[4];
-      KMC_CUDA(cudaMemcpy(cn, c->d_cnt + 4ll * lys, sizeof(cn), cudaMemcpyDeviceToHost));
-      for (int q = 0; q < 4; ++q) buf[q] = static_cast<double>(cn[q]);
+      unsigned long long cn[kmc::kCounters];
+      KMC_CUDA(cudaMemcpy(cn, c->d_cnt + static_cast<long long>(kmc::kCounters) * lys, sizeof(cn),
+                          cudaMemcpyDeviceToHost));
+      for (int q = 0; q < kmc::kCounters - 1; ++q) buf[q] = static_cast<double>(cn[q]);
       break;
     }
   }
@@ -1119,6 +1156,7 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
 kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint64_t seed,
                           int64_t step, const double *m_in, double *m_out, double *B_dip,
                           double *dE, double *P, double *u, int32_t *flags) {
+  Phase phase("kmc_debug_step");
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (!mu0Hext || !m_in) return fail(KMC_EINVAL, "NULL input");
   if (!(t_step > 0) || !is_finite(t_step)) return fail(KMC_EINVAL, "t_step must be > 0");
@@ -1153,7 +1191,7 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
   KMC_TRY(upload_lys(c));
   RunState rs{step, -1, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
-  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
   StepArgs a = base_args(c);
   a.seed = seed;
@@ -1161,6 +1199,9 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
   a.n_rec = 1;
   a.cos_k = 1.0;
   a.debug = 1;
+  // test of the FP32 path's FP64 rescan, which valid profiles of Eq. 2 never need
+  const char *rescan = std::getenv("KMC_DEBUG_RESCAN");
+  a.force_rescan = c->fp32 && rescan && std::strcmp(rescan, "1") == 0;
   a.dbg.bdip = c->d_dbg;
   a.dbg.dE = c->d_dbg + 3 * N;
   a.dbg.P = c->d_dbg + 5 * N;
@@ -1654,7 +1695,7 @@ kmc_status kmc_debug_stall(kmc_ctx *c) {
   KMC_CUDA(kmc::launch_step(c->fp32, c->shape.warps, c->shape.tile, a, c->n_items, c->stream));
   const kmc_status st = check_device_error(c);  // KMC_ETIMEOUT when the waits ran out
   // the blocks stopped before any write: clear the flag, the context stays usable
-  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   return st == KMC_OK ? fail(KMC_ESTATE, "the stalled waits did not run out") : st;
@@ -1669,6 +1710,7 @@ kmc_status kmc_info(const kmc_ctx *c, int64_t *n_total, int32_t *n_lys, int64_t 
 }
 
 void kmc_destroy(kmc_ctx *c) {
+  Phase phase("kmc_destroy");
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   free_ctx(c);

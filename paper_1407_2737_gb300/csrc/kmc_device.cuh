@@ -1,11 +1,12 @@
-// kmc_device.cuh -- device building blocks of the kMC step (sm_103a):
-// bulk-copy (TMA) staging with bounded mbarrier waits, the Philox4x32-10
-// draw, and the per-NP update of steps iii-vii of Sec. II.1.
+// kmc_device.cuh -- device building blocks of the kMC step (sm_103a): the
+// Philox4x32-10 draw and the per-NP update of steps iii-vii of Sec. II.1
+// (the bulk-copy staging is in kmc_stage.cuh).
 #pragma once
 #include <stdint.h>
 
 #include <type_traits>
 
+#include "kmc_stage.cuh"
 #include "kmc_types.h"
 
 namespace kmc {
@@ -17,92 +18,6 @@ __device__ float g_theta_f[kGrid];
 __device__ float2 g_sc_f[kGrid];
 __device__ double g_theta_d[kGrid];
 __device__ double2 g_sc_d[kGrid];
-
-
-// ---------------------------------------------------------------------------
-// Shared-memory staging by bulk asynchronous copies (TMA engine).
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_init_fence() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void proxy_fence_shared() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// Bulk copy global -> shared; both addresses 16-byte aligned, bytes % 16 == 0.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.b32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Programmatic dependent launch. A step kernel launched with programmatic
-// stream serialisation may start while the previous step is still running;
-// grid_dependency_wait() returns once that grid has completed and its memory
-// is visible (at once when there is no such dependency), so every read of
-// state the previous step writes comes after it. grid_launch_dependents(),
-// once every block has called it or exited, lets the next step's grid launch
-// while this one drains.
-__device__ __forceinline__ void grid_dependency_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-__device__ __forceinline__ void grid_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// Waits for phase `parity` of `bar` for at most limit_ns (2 s); returns false
-// (and sets the error word) if the copy never completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int32_t *err,
-                                                  unsigned long long limit_ns = 2000000000ull) {
-  for (int i = 0; i < 64; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > limit_ns) {
-      atomicOr(err, kErrTimeout);
-      return false;
-    }
-  }
-  return true;
-}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
@@ -143,7 +58,8 @@ struct Prec<float> {
   static constexpr float two_pi = 6.28318530717958647692f;
   static constexpr float plane_tol = 1e-6f;   // |b x a| below this: plane from m
   static constexpr float newton_tol = 2e-9f;  // absolute, on the offset in a cell
-  static constexpr int newton_max = 4;        // from the secant point: quadratic
+  static constexpr int newton_max = 6;        // from the secant point: 2-3 steps for nearly
+                                              // every root, 6 for the slowest seen
   __device__ static float div(float a, float b) { return __fdividef(a, b); }
   __device__ static float theta(int j) { return g_theta_f[j]; }
   __device__ static float2 sc(int j) { return g_sc_f[j]; }
@@ -241,8 +157,16 @@ __device__ __forceinline__ R refine_in_cell(const Profile<R> &pf, R S0, R C0, R 
     }
     const R dd = pf.d2(s, c);
     R xn = (dd != R(0)) ? x - Prec<R>::div(d, dd) : R(0.5) * (lo + hi);
+    // Converged: the step is below the tolerance. Tested before the bracket
+    // safeguard, because a step that rounds to nothing leaves xn on the
+    // bracket end that x itself just became, and the safeguard would then
+    // bisect away from the root it has found.
+    if (fabs(xn - x) < Prec<R>::newton_tol) {
+      x = xn;
+      break;
+    }
     if (!(xn > lo && xn < hi)) xn = R(0.5) * (lo + hi);
-    const bool done = fabs(xn - x) < Prec<R>::newton_tol || hi - lo < Prec<R>::newton_tol;
+    const bool done = hi - lo < Prec<R>::newton_tol;
     x = xn;
     if (done) break;
   }

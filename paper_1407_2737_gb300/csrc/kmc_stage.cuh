@@ -1,0 +1,115 @@
+// kmc_stage.cuh -- shared-memory staging by bulk asynchronous copies (the
+// TMA engine's cp.async.bulk) completing on mbarriers, with waits bounded in
+// time: a copy that never lands makes the wait give up and set a device error
+// word instead of spinning forever. Used by the step kernels (kmc_step.cu)
+// and the no-allocation field (kmc_noalloc.cu).
+#pragma once
+#include <stdint.h>
+
+#include "kmc_types.h"
+
+namespace kmc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void proxy_fence_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy global -> shared; both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Programmatic dependent launch. A step kernel launched with programmatic
+// stream serialisation may start while the previous step is still running;
+// grid_dependency_wait() returns once that grid has completed and its memory
+// is visible (at once when there is no such dependency), so every read of
+// state the previous step writes comes after it. grid_launch_dependents(),
+// once every block has called it or exited, lets the next step's grid launch
+// while this one drains.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Waits for phase `parity` of `bar` for at most limit_ns (2 s); returns false
+// (and sets the error word) if the copy never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int32_t *err,
+                                                  unsigned long long limit_ns = 2000000000ull) {
+  for (int i = 0; i < 64; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > limit_ns) {
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+// The same wait without reporting: true once phase `parity` of `bar` has
+// completed, false after limit_ns.
+__device__ __forceinline__ bool mbar_wait_quiet(uint64_t *bar, uint32_t parity,
+                                                unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
+// After the wait for tile t gave up (double buffering: tile t on barrier
+// t & 1, tile t + 1 possibly issued on the other): one thread waits, again
+// for at most limit_ns each, for the copies that may still be landing in the
+// block's shared memory, so that none lands after the block has ended.
+__device__ __forceinline__ void drain_copies(uint64_t *bar, int t, int ntiles,
+                                             unsigned long long limit_ns) {
+  mbar_wait_quiet(&bar[t & 1], (t >> 1) & 1, limit_ns);
+  if (t + 1 < ntiles) mbar_wait_quiet(&bar[(t + 1) & 1], ((t + 1) >> 1) & 1, limit_ns);
+}
+
+}  // namespace kmc

@@ -38,68 +38,12 @@
 #include <type_traits>
 
 #include "kmc_device.cuh"
+#include "kmc_pair.cuh"
 #include "kmc_launch.h"
 #include "kmc_mean.cuh"
 #include "kmc_regen.cuh"
 
 namespace kmc {
-
-// ---------------------------------------------------------------------------
-// Packed FP32 pairs (f32x2) in 64-bit registers.
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float lo, float hi) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-  f2 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-  f2 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-__device__ __forceinline__ float hsum(f2 v) {
-  float lo, hi;
-  upk(v, lo, hi);
-  return lo + hi;
-}
-
-__device__ __forceinline__ float rsqrt_approx(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Kahan step: adds x to (s, c); the exact sum is s - c.
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
-// Neumaier step: adds x to (s, c); the exact sum is s + c.
-__device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
-  const float t = s + x;
-  if (fabsf(s) >= fabsf(x))
-    c += (s - t) + x;
-  else
-    c += (x - t) + s;
-  s = t;
-}
 
 // ---------------------------------------------------------------------------
 // Pair loops over one staged tile. MASK: the tile holds some of the block's
@@ -108,46 +52,6 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float x) {
 // its register allocation and schedule do not depend on the rest of the
 // kernel (measured: inlined, the loop lost 7 % of its throughput when the
 // update code after it changed).
-
-struct AccF32 {
-  f2 x, y, z;  // packed partial sums of the field (even / odd sources)
-};
-
-// One source record against the lane's target (X, Y, Z): the pair terms of
-// both sources, 18 packed instructions and two rsqrt (see SrcPair).
-template <bool MASK>
-__device__ __forceinline__ void pair_record(const ulonglong2 &a, const ulonglong2 &b,
-                                            const ulonglong2 &c, const ulonglong2 &d, f2 e,
-                                            f2 X, f2 Y, f2 Z, AccF32 &acc) {
-  const f2 dx = sub2(a.x, X), dy = sub2(a.y, Y), dz = sub2(b.x, Z);
-  const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-  float r2l, r2h;
-  upk(r2, r2l, r2h);
-  float il = rsqrt_approx(r2l), ih = rsqrt_approx(r2h);
-  if (MASK) {
-    il = (r2l > 0.0f) ? il : 0.0f;
-    ih = (r2h > 0.0f) ? ih : 0.0f;
-  }
-  const f2 q = pk(il, ih);
-  const f2 q2 = mul2(q, q);
-  const f2 q3 = mul2(q, q2);
-  const f2 u = mul2(fma2(e, dz, fma2(d.y, dy, mul2(d.x, dx))), q2);
-  acc.x = fma2(q3, fma2(u, dx, b.y), acc.x);
-  acc.y = fma2(q3, fma2(u, dy, c.x), acc.y);
-  acc.z = fma2(q3, fma2(u, dz, c.y), acc.z);
-}
-
-// Record r of a staged tile: x | y, z | nx, ny | nz, tx | ty, tz | padding.
-__device__ __forceinline__ void load_record(const ulonglong2 *__restrict__ sp, int r,
-                                            ulonglong2 &a, ulonglong2 &b, ulonglong2 &c,
-                                            ulonglong2 &d, f2 &e) {
-  const ulonglong2 *p = sp + kRecU2 * r;
-  a = p[0];
-  b = p[1];
-  c = p[2];
-  d = p[3];
-  e = reinterpret_cast<const f2 *>(p + 4)[0];
-}
 
 template <bool MASK>
 __device__ __noinline__ AccF32 pair_tile_f32(const ulonglong2 *__restrict__ sp, int cnt,
@@ -294,7 +198,7 @@ __device__ __noinline__ void rescan_fp64(EpiShared<float> &sm, int t) {
 // goes to the bracket's rank in grid order.
 template <typename R>
 __device__ __forceinline__ void refine_bracket(EpiShared<R> &sm, const GridTables<R> &tab, int t,
-                                               int q, int nb) {
+                                               int q, int nb, int32_t *err) {
   Profile<R> pf;
   pf.k2 = sm.k2[t];
   pf.k = sm.k[t];
@@ -303,6 +207,7 @@ __device__ __forceinline__ void refine_bracket(EpiShared<R> &sm, const GridTable
   const int ju = sm.ju[t][q];
   int rank = 0;
   for (int p = 0; p < nb; ++p) rank += sm.ju[t][p] < ju;
+  if (!KMC_DCHECK(ju >= 0 && ju < kGrid && rank >= 0 && rank < 4, err, kSiteBracket)) return;
   const int j = min(max(ju, 0), kGrid - 1);
   const auto sc = tab.sc[j];
   const R h = tab.th[1] - tab.th[0];
@@ -388,7 +293,7 @@ __device__ __forceinline__ TargetState<R> setup_plane(R ax, R ay, R az, R mx, R 
 
 struct Decision {
   double dEa, dEb, P;
-  int nmin, flipped, near, bad;
+  int nmin, flipped, near, bad, polished;
 };
 
 // e^x for an exponent x held in FP64: x log2(e) = n + f exactly split into an
@@ -411,7 +316,7 @@ __device__ __forceinline__ Decision decide(const EpiShared<R> &sm, int t,
                                            R &c_new) {
   Decision o;
   o.dEa = o.dEb = o.P = 0.0;
-  o.flipped = o.near = o.bad = 0;
+  o.flipped = o.near = o.bad = o.polished = 0;
   int cnt = sm.cnt[t];
   if (cnt > 4 || cnt < 0) {
     o.bad = 1;
@@ -474,6 +379,7 @@ __device__ __forceinline__ Decision decide(const EpiShared<R> &sm, int t,
     }
     dEa = e64[2] - e64[0];
     dEb = e64[2] - e64[1];
+    o.polished = 1;
   }
   o.dEa = dEa;
   o.dEb = dEb;
@@ -562,8 +468,9 @@ __device__ __forceinline__ void block_update(
   // iv) scan: lanes over targets, warps over segments of the grid
   segment_scan<R>(sm, tab, warp, nw, lane, nt);
   __syncthreads();
+  bool noisy = false;  // warp 0: this lane's target was scanned again in FP64
   if constexpr (MIXED) {
-    const bool noisy = warp == 0 && lane < nt && sm.cnt[lane] > 4;
+    noisy = warp == 0 && lane < nt && (sm.cnt[lane] > 4 || a.force_rescan);
     if (__syncthreads_or(noisy)) {
       if (noisy) rescan_fp64(sm, lane);
       __syncthreads();
@@ -573,7 +480,7 @@ __device__ __forceinline__ void block_update(
   for (int x = threadIdx.x; x < 4 * nt; x += blockDim.x) {
     const int t = x >> 2, q = x & 3;
     const int nb = min(sm.cnt[t], 4);
-    if (q < nb) refine_bracket<R>(sm, tab, t, q, nb);
+    if (q < nb) refine_bracket<R>(sm, tab, t, q, nb, a.err);
   }
   __syncthreads();
   if (warp != 0) return;
@@ -585,9 +492,15 @@ __device__ __forceinline__ void block_update(
   // only targets < nt have scan results in shared memory
   const Decision r = decide<R, MIXED>(sm, min(lane, nt - 1), st, tin.beta, L.lognu0t,
                                       L.t_zero != 0, u, s_new, c_new);
-  const R mx = fma(c_new, st.ax, s_new * st.ex);
-  const R my = fma(c_new, st.ay, s_new * st.ey);
-  const R mz = fma(c_new, st.az, s_new * st.ez);
+  // Guard: a non-finite field, barrier or probability (two NPs at one point)
+  // leaves the moment as it was; the NP-step is counted and reported.
+  const bool finite = isfinite(sm.h[0][lane]) && isfinite(sm.h[1][lane]) &&
+                      isfinite(sm.h[2][lane]) && isfinite(r.dEa) && isfinite(r.dEb) &&
+                      isfinite(r.P);
+  const R mx = finite ? fma(c_new, st.ax, s_new * st.ex) : m4.x;
+  const R my = finite ? fma(c_new, st.ay, s_new * st.ey) : m4.y;
+  const R mz = finite ? fma(c_new, st.az, s_new * st.ez) : m4.z;
+  const bool jumped = finite && r.flipped;
   const int par = static_cast<int>(step & 1);
   if (active) {
     m4.x = mx;
@@ -625,7 +538,9 @@ __device__ __forceinline__ void block_update(
       a.dbg.dE[2 * i + 1] = r.dEb;
       a.dbg.P[i] = r.P;
       a.dbg.u[i] = u;
-      a.dbg.flags[i] = r.nmin | (r.flipped << 2) | (r.near << 3) | (st.degenerate << 4);
+      a.dbg.flags[i] = r.nmin | (jumped ? kFlagJumped : 0) | (r.near ? kFlagNear : 0) |
+                       (st.degenerate ? kFlagFallback : 0) | (noisy ? kFlagRescan : 0) |
+                       (r.polished ? kFlagPolish : 0) | (finite ? 0 : kFlagNonFinite);
     }
   }
   // loop record and counters: one atomic each per block
@@ -638,17 +553,26 @@ __device__ __forceinline__ void block_update(
                     &a.loop_m[static_cast<long long>(it.l) * a.n_rec + rec]),
                 static_cast<unsigned long long>(__double2ll_rn(c * kLoopScale)));
   }
-  const unsigned fl = __ballot_sync(0xffffffffu, active && r.flipped);
+  const unsigned fl = __ballot_sync(0xffffffffu, active && jumped);
   const unsigned ne = __ballot_sync(0xffffffffu, active && r.near);
   const unsigned mo = __ballot_sync(0xffffffffu, active && r.nmin == 1);
   const unsigned dg = __ballot_sync(0xffffffffu, active && st.degenerate);
+  const unsigned rs = __ballot_sync(0xffffffffu, active && noisy);
+  const unsigned po = __ballot_sync(0xffffffffu, active && r.polished);
+  const unsigned nf = __ballot_sync(0xffffffffu, active && !finite);
   const unsigned bd = __ballot_sync(0xffffffffu, active && r.bad);
   if (lane == 0) {
-    unsigned long long *c = a.counters + 4ll * it.l;
-    if (fl) atomicAdd(c + 0, static_cast<unsigned long long>(__popc(fl)));
-    if (ne) atomicAdd(c + 1, static_cast<unsigned long long>(__popc(ne)));
-    if (mo) atomicAdd(c + 2, static_cast<unsigned long long>(__popc(mo)));
-    if (dg) atomicAdd(c + 3, static_cast<unsigned long long>(__popc(dg)));
+    unsigned long long *c = a.counters + static_cast<long long>(kCounters) * it.l;
+    if (fl) atomicAdd(c + kCntJumps, static_cast<unsigned long long>(__popc(fl)));
+    if (ne) atomicAdd(c + kCntNear, static_cast<unsigned long long>(__popc(ne)));
+    if (mo) atomicAdd(c + kCntOneMin, static_cast<unsigned long long>(__popc(mo)));
+    if (dg) atomicAdd(c + kCntFallback, static_cast<unsigned long long>(__popc(dg)));
+    if (rs) atomicAdd(c + kCntRescan, static_cast<unsigned long long>(__popc(rs)));
+    if (po) atomicAdd(c + kCntPolish, static_cast<unsigned long long>(__popc(po)));
+    if (nf) {
+      atomicAdd(c + kCntNonFinite, static_cast<unsigned long long>(__popc(nf)));
+      atomicOr(a.err, kErrNonFinite);
+    }
     if (bd) atomicOr(a.err, kErrExtrema);
   }
 }
@@ -676,7 +600,11 @@ __device__ __forceinline__ bool staged_loop(int ntiles, uint64_t *bar, int32_t *
     const bool ok = mbar_wait_bounded(&bar[b], (t >> 1) & 1, err, limit_ns);
     if (ok) body(b, t);
     // every warp is done with buffer b; a failed wait anywhere stops all
-    if (!__syncthreads_and(ok)) return false;
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) drain_copies(bar, t, ntiles, limit_ns);
+      __syncthreads();
+      return false;
+    }
     if (threadIdx.x == 0 && t + 2 < ntiles) {
       proxy_fence_shared();
       issue(t + 2);
@@ -697,6 +625,38 @@ constexpr size_t epi_bytes(int warps) {
 // The buffer is sized for the FP64 kernel's 6 doubles per target.
 constexpr int kPartF32 = 6 * kTargets;
 
+// KMC_DEBUG builds: the block's work item lies inside the launch, its
+// lysosome and that lysosome's target and source ranges (records of NPs:
+// pairs in FP32, single NPs in FP64), and its part index is consistent; a
+// failed check skips the block. Release builds compile this to `true`.
+__device__ __forceinline__ bool item_in_bounds(const StepArgs &a, int tpl, bool fp32) {
+#ifdef KMC_DEBUG
+  if (!KMC_DCHECK(static_cast<int>(blockIdx.x) < a.n_items, a.err, kSiteItem)) return false;
+  const Item it = a.items[blockIdx.x];
+  if (!KMC_DCHECK(it.l >= 0 && it.l < a.n_lys, a.err, kSiteLys)) return false;
+  const LysDev L = a.lys[it.l];
+  if (!KMC_DCHECK(it.t0 >= 0 && it.nt >= 1 && it.nt <= kTargets * tpl && it.t0 + it.nt <= L.n,
+                  a.err, kSiteTargets))
+    return false;
+  const int nrec = fp32 ? (L.n + 1) / 2 : L.n;
+  if (!KMC_DCHECK(it.j0 >= 0 && it.j0 < it.j1 && it.j1 <= nrec, a.err, kSiteSources))
+    return false;
+  if (!KMC_DCHECK(it.nsplit >= 1 && it.split >= 0 && it.split < it.nsplit && it.gid >= 0 &&
+                      static_cast<int>(blockIdx.x) >= it.split,
+                  a.err, kSiteSplit))
+    return false;
+#endif
+  return true;
+}
+
+// KMC_DEBUG builds: tile t of an item covers records r0 .. r0 + cnt - 1 inside
+// the item's range and fits the staging buffer.
+__device__ __forceinline__ bool tile_in_bounds(const StepArgs &a, const Item &it, int r0, int cnt,
+                                               int tile) {
+  return KMC_DCHECK(r0 >= it.j0 && cnt >= 1 && cnt <= tile && r0 + cnt <= it.j1, a.err,
+                    kSiteTile);
+}
+
 // ---------------------------------------------------------------------------
 // FP32-mixed step kernel.
 template <int NW>
@@ -707,6 +667,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
   __shared__ int s_last;
   __shared__ GridTables<float> tab;
   tab.load();
+  if (!item_in_bounds(a, 1, true)) return;
   const Item it = a.items[blockIdx.x];
   const LysDev L = a.lys[it.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -731,6 +692,10 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
     const int b = t & 1;
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
+    if (!tile_in_bounds(a, it, r0, cnt, tile)) {
+      mbar_expect_tx(&bar[b], 0);  // no copy: the phase completes, the error is set
+      return;
+    }
     const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
     mbar_expect_tx(&bar[b], bytes);
     bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
@@ -858,6 +823,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
   __shared__ GridTables<float> tab;
   __shared__ float s_h1[3][kTargets];  // second half's field while the first updates
   tab.load();
+  if (!item_in_bounds(a, 2, true)) return;
   const Item it = a.items[blockIdx.x];
   const LysDev L = a.lys[it.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -889,6 +855,10 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
     const int b = t & 1;
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
+    if (!tile_in_bounds(a, it, r0, cnt, tile)) {
+      mbar_expect_tx(&bar[b], 0);  // no copy: the phase completes, the error is set
+      return;
+    }
     const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
     mbar_expect_tx(&bar[b], bytes);
     bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
@@ -1003,6 +973,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
   __shared__ int s_last;
   __shared__ GridTables<double> tab;
   tab.load();
+  if (!item_in_bounds(a, 1, false)) return;
   const Item it = a.items[blockIdx.x];
   const LysDev L = a.lys[it.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1027,6 +998,10 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
     const int b = t & 1;
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
+    if (!tile_in_bounds(a, it, r0, cnt, tile)) {
+      mbar_expect_tx(&bar[b], 0);  // no copy: the phase completes, the error is set
+      return;
+    }
     const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(dbl4);
     mbar_expect_tx(&bar[b], 2 * bytes + a.stall_tx);
     bulk_g2s(spos + b * tile, gpos + r0, bytes, &bar[b]);

@@ -120,7 +120,7 @@ struct StepArgs {
   long long *loop_m;        // [n_lys][n_rec] volume-weighted mean m_z in fixed point
                             // (units of 2^-62): integer sums do not depend on the
                             // order in which blocks add, so runs are reproducible
-  unsigned long long *counters;  // [n_lys][4]
+  unsigned long long *counters;  // [n_lys][kCounters] (enum below)
   int32_t *err;             // device error word
   float *partial;           // scratch: [items][12][32] floats of partial sums
   int32_t *arrivals;        // scratch: [groups] arrival counters, zero between launches
@@ -133,13 +133,16 @@ struct StepArgs {
   int32_t n_rec;            // recorded steps per lysosome (loop_m stride)
   DebugOut dbg;
   int32_t debug;
-  int32_t pad;
+  int32_t force_rescan;     // test hook (kmc_debug_step only): every FP32 target is
+                            // scanned again in FP64, as a noisy scan would be
   // failure-detection test hook (FP64 kernel): every tile's expected byte
   // count exceeds its copies by stall_tx, so its wait can only run out, after
   // stall_wait_ns; 0 in every production launch
   uint32_t stall_tx;
-  uint32_t pad2;
+  int32_t n_items;          // work items of this launch (bounds checks of KMC_DEBUG builds)
   unsigned long long stall_wait_ns;
+  int32_t n_lys;            // lysosomes of the context (bounds checks of KMC_DEBUG builds)
+  int32_t pad3;
 };
 
 // Ref. [8] mode (kmc_mean.cuh): per lysosome, per work item, arguments.
@@ -216,6 +219,55 @@ struct RegenArgs {
 enum : int32_t {
   kErrTimeout = 1,     // an mbarrier wait gave up
   kErrExtrema = 2,     // more than two minima or maxima (cannot happen for Eq. 2)
+  kErrNonFinite = 4,   // a non-finite dipolar field, barrier or probability: the
+                       // NP kept its moment (two NPs at one point, e.g. closer
+                       // than the float32 frame resolves)
+  kErrBounds = 8,      // KMC_DEBUG builds: an index failed its bounds check; the
+                       // access was skipped and err[1] holds the check's site
+};
+
+// Sites of the KMC_DEBUG bounds checks (err[1] holds the first that failed).
+enum : int32_t {
+  kSiteItem = 1,       // block index beyond the launch's work items
+  kSiteLys = 2,        // item's lysosome beyond the context's
+  kSiteTargets = 3,    // item's targets outside its lysosome, or more than a block holds
+  kSiteSources = 4,    // item's source records outside its lysosome's
+  kSiteSplit = 5,      // item's part index or part count inconsistent
+  kSiteTile = 6,       // a staged tile beyond the item's source records or the buffer
+  kSiteBracket = 7,    // a bracket's grid node or rank outside the scan's tables
+};
+
+#ifdef KMC_DEBUG
+// Records a failed check (error bit and, first come, its site).
+__device__ __forceinline__ void debug_fail(int32_t *err, int32_t site) {
+  atomicOr(err, kErrBounds);
+  atomicCAS(err + 1, 0, site);
+}
+#define KMC_DCHECK(cond, err, site) ((cond) ? true : (kmc::debug_fail((err), (site)), false))
+#else
+#define KMC_DCHECK(cond, err, site) true
+#endif
+
+// Per-lysosome counters of a run, in NP-steps (KMC_READ_COUNTERS).
+enum : int32_t {
+  kCntJumps = 0,       // moments that jumped (u < P)
+  kCntNear = 1,        // draws within 1e-9 of P
+  kCntOneMin = 2,      // profiles with a single minimum
+  kCntFallback = 3,    // working planes spanned by axis and moment (field along axis)
+  kCntRescan = 4,      // FP32 scans redone in FP64 (more than four sign changes)
+  kCntPolish = 5,      // FP32 barriers recomputed in FP64 near switching
+  kCntNonFinite = 6,   // NPs held because the field or barrier was not finite
+  kCounters = 8,       // slots per lysosome (the last is reserved, always 0)
+};
+
+// Bits of the test hook's per-NP flags (kmc_debug_step).
+enum : int32_t {
+  kFlagJumped = 1 << 2,
+  kFlagNear = 1 << 3,
+  kFlagFallback = 1 << 4,
+  kFlagRescan = 1 << 5,
+  kFlagPolish = 1 << 6,
+  kFlagNonFinite = 1 << 7,
 };
 
 }  // namespace kmc

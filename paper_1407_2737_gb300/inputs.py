@@ -15,7 +15,7 @@ without overlap, with random easy axes. This module builds such inputs:
 * centres snapped to the float32 grid in units of d about the lysosome centre
   (the origin), so that the float32 copy held by the GPU path is the same
   geometry as the float64 copy held by the oracle (a shift of at most 3e-8 d
-  for R = 50 d).
+  for R = 50 d); snap=False keeps them as drawn.
 
 It holds no step of the kinetic Monte-Carlo method; both the oracle and the
 CUDA path take its output as input. Random numbers come from numpy's PCG64
@@ -118,11 +118,15 @@ def snap_to_float32(pos, d):
 
 
 def make_lysosome(n, d, c, Ms=1e6, Keff=1.3e4, T=300.0, tau0=1e-10, seed=0,
-                  rho=5200.0):
-    """One synthetic lysosome: n NPs of diameter d (m) at concentration c."""
+                  rho=5200.0, snap=True):
+    """One synthetic lysosome: n NPs of diameter d (m) at concentration c.
+    snap=False keeps the centres as drawn (float64), so that the float32 frame
+    of the GPU path rounds them as it would a caller's positions."""
     rng = np.random.Generator(np.random.PCG64(seed))
     R = lysosome_radius(n, d, c)
-    pos = snap_to_float32(rsa_positions(n, d, R, rng), d) if n > 0 else np.zeros((0, 3))
+    pos = rsa_positions(n, d, R, rng) if n > 0 else np.zeros((0, 3))
+    if snap:
+        pos = snap_to_float32(pos, d)
     axis = random_axes(n, rng)
     vol = np.full(n, sphere_volume(d))
     return Lysosome(pos=pos, axis=axis, vol=vol, Ms=float(Ms), Keff=float(Keff),
@@ -199,12 +203,12 @@ def config_small(seed=0):
     return [lys], run
 
 
-def config_single2000(replicas=8, seed=0):
+def config_single2000(replicas=8, seed=0, snap=True):
     """A lysosome of 2000 NPs, d = 14 nm, K_eff = 2e4 J/m^3, 10 % volume
     concentration, otherwise as the 100-NP case; `replicas` copies run as
     independent random streams (the seeds of the kMC draws)."""
     lys = make_lysosome(2000, 14e-9, 0.10, Ms=1e6, Keff=2e4, T=300.0, tau0=1e-10,
-                        seed=seed)
+                        seed=seed, snap=snap)
     run = dict(mu0Hmax=0.020, f=1e5, S=200, periods=20, discard=5, seed=seed)
     return replicate(lys, replicas), run
 
@@ -238,11 +242,11 @@ def config_batched(n_lys=512, seed=0, sigma_ln=0.5):
     return lys, run
 
 
-def config_large50000(seed=0):
+def config_large50000(seed=0, snap=True):
     """A lysosome of 50000 NPs, d = 16 nm, K_eff = 3e4 J/m^3, 10 % volume
     concentration, mu0 H_max = 40 mT, f = 100 kHz, 500 steps per period,
     50 periods (5 discarded)."""
     lys = make_lysosome(50000, 16e-9, 0.10, Ms=1e6, Keff=3e4, T=300.0, tau0=1e-10,
-                        seed=seed)
+                        seed=seed, snap=snap)
     run = dict(mu0Hmax=0.040, f=1e5, S=500, periods=50, discard=5, seed=seed)
     return [lys], run

@@ -15,7 +15,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libkmc.so")
+# KMC_LIB_PATH selects another build of the same library (the KMC_DEBUG one)
+LIB_PATH = os.environ.get("KMC_LIB_PATH") or os.path.join(_HERE, "_build", "libkmc.so")
 
 KMC_OK, KMC_EINVAL, KMC_ENOMEM, KMC_ECUDA, KMC_ETIMEOUT, KMC_ESTATE, KMC_ECAPACITY, \
     KMC_EIO = range(8)
@@ -38,6 +39,9 @@ KMC_NOALLOC_MAX_N = 8192
 KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
 KMC_ITEM_FIELDS = 8  # per work item in kmc_plan_items
 KMC_PHI_MAX_N = 64
+# KMC_READ_COUNTERS slots
+(CNT_JUMPS, CNT_NEAR, CNT_ONE_MIN, CNT_FALLBACK, CNT_RESCAN, CNT_POLISH,
+ CNT_NONFINITE) = range(7)
 
 
 class KmcError(RuntimeError):
@@ -83,7 +87,7 @@ def lib():
             L.kmc_info.argtypes = [vp, _I64, _I32, _I64]
             L.kmc_tuning.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, _I32, _I32, _I32]
             L.kmc_dipolar_field_noalloc.argtypes = [C.c_int32, vp, vp, vp, C.c_double, _D,
-                                                    C.c_double, vp, vp]
+                                                    C.c_double, vp, vp, vp]
             L.kmc_local_concentration.argtypes = [vp, C.c_int32, C.c_int32, _D, C.c_int64,
                                                   _I64]
             L.kmc_shell_profile.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, _D,
@@ -279,7 +283,8 @@ def kmc_debug_step(ctx, mu0Hext, t_step, seed, step, m_in):
                                 _dp(out["dE"]), _dp(out["P"]), _dp(out["u"]),
                                 out["flags"].ctypes.data_as(_I32)))
     f = out["flags"]
-    out.update(n_min=f & 3, flipped=(f >> 2) & 1, near=(f >> 3) & 1, degenerate=(f >> 4) & 1)
+    out.update(n_min=f & 3, flipped=(f >> 2) & 1, near=(f >> 3) & 1, degenerate=(f >> 4) & 1,
+               rescan=(f >> 5) & 1, polish=(f >> 6) & 1, nonfinite=(f >> 7) & 1)
     return out
 
 
@@ -312,14 +317,17 @@ def kmc_tuning(ctx, warps=None, tile=None, chunk=0):
 
 
 def kmc_dipolar_field_noalloc(n, pos_dev, m_dev, vol_dev, Ms, center, length, B_dev,
-                              stream_handle=0):
+                              stream_handle=0, status_dev=0):
     """Calls the no-allocation field entry point. pos_dev, m_dev, vol_dev and
     B_dev are device addresses (integers, e.g. a tensor's data_ptr()) of
-    caller-owned float64 buffers; center is a host (3,) origin in m."""
+    caller-owned float64 buffers; status_dev the address of a caller-owned
+    int32 that receives the call's device-side status (0: none); center is a
+    host (3,) origin in m."""
     cen = _f64(center, (3,))
     _check(lib().kmc_dipolar_field_noalloc(int(n), C.c_void_p(pos_dev), C.c_void_p(m_dev),
                                            C.c_void_p(vol_dev), float(Ms), _dp(cen),
                                            float(length), C.c_void_p(B_dev),
+                                           C.c_void_p(status_dev or 0),
                                            C.c_void_p(stream_handle or 0)))
 
 

@@ -99,8 +99,18 @@ def test_every_context_entry_point_rejects_a_null_context(L):
     big = kmc.KMC_NOALLOC_MAX_N + 1
     cen = np.zeros(3)
     cp = cen.ctypes.data_as(C.POINTER(C.c_double))
-    assert L.kmc_dipolar_field_noalloc(0, 1, 1, 1, 1e6, cp, 1e-8, 1, None) == kmc.KMC_ECAPACITY
-    assert L.kmc_dipolar_field_noalloc(big, 1, 1, 1, 1e6, cp, 1e-8, 1, None) == kmc.KMC_ECAPACITY
-    assert L.kmc_dipolar_field_noalloc(4, None, 1, 1, 1e6, cp, 1e-8, 1, None) == kmc.KMC_EINVAL
-    assert L.kmc_dipolar_field_noalloc(4, 1, 1, 1, -1.0, cp, 1e-8, 1, None) == kmc.KMC_EINVAL
+    assert L.kmc_dipolar_field_noalloc(0, 1, 1, 1, 1e6, cp, 1e-8, 1, None, None) == kmc.KMC_ECAPACITY
+    assert L.kmc_dipolar_field_noalloc(big, 1, 1, 1, 1e6, cp, 1e-8, 1, None, None) == kmc.KMC_ECAPACITY
+    assert L.kmc_dipolar_field_noalloc(4, None, 1, 1, 1e6, cp, 1e-8, 1, None, None) == kmc.KMC_EINVAL
+    assert L.kmc_dipolar_field_noalloc(4, 1, 1, 1, -1.0, cp, 1e-8, 1, None, None) == kmc.KMC_EINVAL
     assert L.kmc_mean_run(None, 0, None, 0, 0.0, 0, 0, 0, None, 0, None) == kmc.KMC_EINVAL
+
+
+def test_debug_build_compiles_and_exports_the_same_entry_points():
+    """The KMC_DEBUG build (bounds checks on the device) is a separate library
+    with the same ABI; here it is only built and inspected (no GPU)."""
+    lib = kbuild.build(debug=True)
+    assert lib != kbuild.LIB and os.path.exists(lib)
+    D = C.CDLL(lib)
+    for n in declared_entry_points():
+        assert hasattr(D, n), n

@@ -2,7 +2,9 @@
 
 Tolerances (derived from the arithmetic, FP64 path):
 * dipolar field: |dB_i| <= 1e-12 * sum_j |term_ij| (the two sides sum the same
-  terms in different orders; each rounding is <= 2^-53 of a partial sum);
+  terms in different orders; each rounding is <= 2^-53 of a partial sum), the
+  reading of the north star's "1e-12 relative" for a sum whose terms cancel;
+  where they cancel by at most a factor 4, also |dB_i| <= 1e-12 |B_i|;
 * barriers: |d(E3 - E_a)| <= 1e-12 |E3 - E_a| + 1e-14 E_scale, E_scale =
   K_eff V + M_S V |B| (each energy carries a few ulp of E_scale);
 * jump probabilities: |dP| <= 1e-12 P + 1e-13;
@@ -93,11 +95,23 @@ def test_fp64_step_parity(tile, warps, chunk):
     g = kmc.kmc_debug_step(ctx, Hs, t_step, 11, 1000, m)
     o = oracle_steps(lyss, m, Hs, t_step, 11, 1000)
     off = 0
+    worst = 0.0
     for ly in lyss:
         sl = slice(off, off + ly.n)
         off += ly.n
-        tol = 1e-12 * abs_term_sum(ly, m[sl])
-        assert np.all(np.abs(g["B_dip"][sl] - o["B_dip"][sl]) <= tol[:, None] + 1e-300)
+        scale = abs_term_sum(ly, m[sl])
+        tol = 1e-12 * scale
+        dB = np.abs(g["B_dip"][sl] - o["B_dip"][sl])
+        assert np.all(dB <= tol[:, None] + 1e-300)
+        # relative to |B_i| where the terms cancel by at most a factor 4: the
+        # summation error is then below n u sum_j |term_ij| <= 4 n u |B_i|, n <= 257
+        Bn = np.linalg.norm(o["B_dip"][sl], axis=1)
+        ok = (Bn > 0.0) & (Bn >= 0.25 * scale)  # a lone NP has no field at all
+        rel = np.linalg.norm(dB, axis=1)[ok] / Bn[ok]
+        if rel.size:
+            worst = max(worst, float(rel.max()))
+            assert rel.max() <= 1e-12
+    print("FP64 field: max |dB_i| / |B_i| = %.2e (NPs without heavy cancellation)" % worst)
     assert np.array_equal(g["n_min"], o["n_min"])
     two = o["n_min"] == 2
     vols = np.concatenate([l.vol for l in lyss])
