@@ -33,8 +33,9 @@ stated in the line's config; their FP64 and oracle legs run bounded samples.
 --row measures one of the outputs built on top of the step instead, with its
 own metric: f1 the local concentration phi_N of Eq. 8 (N = 10) on the 50 000-NP
 lysosome, f2 the regeneration of axes and positions between loops on the same
-lysosome (lattice and disorder), f2r its random sequential addition, f4 the Ref.
-[8] mean-magnetisation mode on the 8 x 2000-NP workload.
+lysosome (lattice and disorder), f2r its random sequential addition, f3 the
+symmetric evaluation of pairs (T_ij = T_ji) against the ordered pair loop, f4
+the Ref. [8] mean-magnetisation mode on the 8 x 2000-NP workload.
 """
 from __future__ import annotations
 
@@ -235,6 +236,8 @@ def run_row(args):
                 times.append(e0.elapsed_time(e1) / 1e3)
         return sum(times) / len(times)
 
+    if args.row == "f3":
+        return run_pair_forms(args, oracle, inputs, threads)
     if args.row in ("f1", "f2", "f2r"):
         (lys,), _ = inputs.config_large50000(seed=0)
         n = lys.n
@@ -376,6 +379,69 @@ def run_row(args):
                 "cpu_baseline": {"value": l0.n * run["S"] * 2 / tc, "unit": "particle-steps/s",
                                  "cores": 1, "kind": "oracle",
                                  "sample": "2 periods of one 2000-NP lysosome (%.1f s)" % tc}}
+    line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                 "data": "synthetic"})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_pair_forms(args, oracle, inputs, threads):
+    """Row f3: symmetric pair evaluation (each pair's geometry serving both of
+    its ordered pairs, by lane rotation) against the step kernels' ordered
+    pair loop at one, two and three targets per lane, over resident source
+    tiles (csrc/bench/pair_forms.cu, checked there against Eq. 1 in FP64)."""
+    from paper_1407_2737_gb300 import build as kbuild
+    src = os.path.join(ROOT, "paper_1407_2737_gb300", "csrc", "bench", "pair_forms.cu")
+    exe = os.path.join(kbuild.BUILD, "pair_forms")
+    os.makedirs(kbuild.BUILD, exist_ok=True)
+    if not os.path.exists(exe) or os.path.getmtime(exe) < os.path.getmtime(src):
+        subprocess.run([kbuild.nvcc()] + kbuild.ARCH + ["-O3", "-std=c++17",
+                        "--expt-relaxed-constexpr", "-I" + kbuild.CSRC, src, "-o", exe],
+                       check=True)
+    forms = {}
+    for k in range(args.warmup + args.steps):
+        r = subprocess.run([exe], capture_output=True, text=True, check=True)
+        if k < args.warmup:
+            continue
+        for line in r.stdout.split("\n"):
+            p = line.split()
+            if len(p) == 4:
+                forms.setdefault(p[0], []).append((float(p[1]), float(p[2]), float(p[3])))
+    summary = {name: {"pairs_per_s": statistics.median(v[0] for v in vals),
+                      "frac": statistics.median(v[1] for v in vals),
+                      "max_rel_err_vs_fp64": max(v[2] for v in vals)}
+               for name, vals in forms.items()}
+    sym = summary["symmetric_lane_rotation"]
+    best = max((v for k, v in summary.items() if k.startswith("ordered")),
+               key=lambda v: v["pairs_per_s"])
+    (lys,), _ = inputs.config_large50000(seed=0)
+    idx = np.arange(0, lys.n, lys.n // 32)
+    m = oracle.initial_moments(lys.axis)
+    t0 = time.perf_counter()
+    oracle.dipolar_field_at(lys.pos, lys.vol, lys.Ms, m, idx)
+    tc = time.perf_counter() - t0
+    line = {"metric": "ordered pair interactions/s of the Eq. 1 pair loop, symmetric (lane "
+                      "rotation) form",
+            "value": sym["pairs_per_s"], "unit": "pairs/s",
+            "ms_per_step": None, "dtype": "f32",
+            "config": {"workload": "resident source tiles, sources and targets uniform in a "
+                                   "ball of radius 40 NP diameters (the 50 000-NP lysosome's)",
+                       "row": "f3", "forms": summary,
+                       "symmetric_over_best_ordered": sym["pairs_per_s"] / best["pairs_per_s"]},
+            "roofline": {"bound": "alu", "achieved": 30 * sym["pairs_per_s"] / 1e12,
+                         "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
+                         "frac": 30 * sym["pairs_per_s"] / 1e12 / fp32_peak_tflops(),
+                         "traffic": None, "kernel": "symmetric_pairs",
+                         "note": "30 flops per ordered pair; the symmetric form executes 28 "
+                                 "FP32 operations, one rsqrt and three shuffles per pair "
+                                 "(two ordered pairs), the ordered form 18 packed operations "
+                                 "and two rsqrt per two ordered pairs"},
+            "e2e": None,
+            "gpu_launches": 4 * 21 * args.steps,
+            "cpu_baseline": {"value": len(idx) * (lys.n - 1) / tc, "unit": "pairs/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": "Eq. 1 at %d NPs of the 50 000-NP lysosome" % len(idx)}}
     line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                  "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                  "data": "synthetic"})
@@ -533,7 +599,7 @@ def main():
                     help="workload (default c1, the headline line)")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the batched and large workloads measured beside the default line")
-    ap.add_argument("--row", default="", choices=["", "f1", "f2", "f2r", "f4"],
+    ap.add_argument("--row", default="", choices=["", "f1", "f2", "f2r", "f3", "f4"],
                     help="measure an output built on the step instead (see above)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -191,12 +191,12 @@ kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
                       int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out);
 
 /* Targets per lane of the FP32 step kernel: 1 (a block takes 32 targets, one
- * per lane) or 2 (64 targets, two per lane, so that each staged source record
- * feeds two independent chains; FP32 contexts only, KMC_EINVAL on FP64). The
- * two give the same bits at the same warps, tile and chunk. 0 (the default)
- * lets the autotuner choose; a pinned value also applies to a shape set by
- * kmc_tuning. The value in use (0 before the first tuning) is returned
- * through tpl_out (may be NULL); tpl = -1 only reads it. */
+ * per lane), 2 or 3 (64 or 96 targets, two or three per lane, so that each
+ * staged source record feeds that many independent chains; FP32 contexts only,
+ * KMC_EINVAL on FP64). All give the same bits at the same warps, tile and
+ * chunk. 0 (the default) lets the autotuner choose; a pinned value also
+ * applies to a shape set by kmc_tuning. The value in use (0 before the first
+ * tuning) is returned through tpl_out (may be NULL); tpl = -1 only reads it. */
 kmc_status kmc_targets_per_lane(kmc_ctx *ctx, int32_t tpl, int32_t *tpl_out);
 
 /* Fields of one work item in kmc_plan_items' output. */
@@ -210,9 +210,12 @@ kmc_status kmc_targets_per_lane(kmc_ctx *ctx, int32_t tpl, int32_t *tpl_out);
  * (pairs of NPs for KMC_FP32_MIXED, single NPs for KMC_FP64_PLAIN). Groups
  * come lysosome by lysosome, largest lysosome first (stable). A group's parts
  * are consecutive items. chunk > 0 splits a group's sources into parts of
- * chunk NPs; chunk = 0 splits only to even out one device-wide wave of a
- * single chain on n_sms SMs at blocks_per_sm blocks each (n_sms = 0: never).
- * tpl is 1 or 2 (2 with KMC_FP32_MIXED only); chunk a multiple of 64; n[l] >= 1.
+ * chunk NPs and, for a single chain spanning several waves of n_sms SMs x
+ * blocks_per_sm blocks (n_sms > 0), gives the last groups one part more each
+ * until the items fill whole waves; chunk = 0 splits only to even out one
+ * device-wide wave of a single chain (n_sms = 0: never).
+ * tpl is 1, 2 or 3 (2 and 3 with KMC_FP32_MIXED only); chunk a multiple of 64;
+ * n[l] >= 1.
  * items_out (host, capacity cap items): KMC_ITEM_FIELDS int32 per item, in
  * launch order: lysosome, first target, targets, target group, first source
  * record, end source record (exclusive), part index, parts in the group.

@@ -115,7 +115,7 @@ __global__ void sources_f64(const dbl4 *__restrict__ pos, const dbl4 *__restrict
 
 struct Shape {
   int warps = 0, tile = 0, chunk = 0;
-  int tpl = 1;  // targets per lane: 2 runs 64-target groups (FP32 two-target kernel)
+  int tpl = 1;  // targets per lane: 2 or 3 run 64- or 96-target groups (FP32 only)
   bool operator==(const Shape &o) const {
     return warps == o.warps && tile == o.tile && chunk == o.chunk && tpl == o.tpl;
   }
@@ -194,7 +194,7 @@ struct kmc_ctx {
   size_t arrivals_cap = 0;
   Shape items_shape;  // shape the items were built for
   std::vector<int> chain_cut;  // chain q runs items chain_cut[q] .. chain_cut[q + 1] - 1
-  int tpl_mode = 0;            // targets per lane: 0 = the autotuner's choice, else 1 or 2
+  int tpl_mode = 0;            // targets per lane: 0 = the autotuner's choice, else 1, 2 or 3
   cudaStream_t chain_st[kMaxChains] = {};  // branches 1.. of the period graph
   cudaEvent_t chain_ev[kMaxChains] = {};   // [0] fork, [q] join of branch q
   // debug outputs, allocated on first use
@@ -263,6 +263,27 @@ std::vector<Item> build_items(const std::vector<int> &np, bool fp32, int chunk,
     for (int g = 0; g < G; ++g) {
       const int rchunk = fp32 ? chunk / 2 : chunk;
       parts[g] = std::max(1, (groups[g].nrec + rchunk - 1) / rchunk);
+    }
+    // A single chain over several waves of items: the last wave would hold
+    // N mod slots full-size items and leave the other slots idle until they
+    // end, since the next step waits for the whole launch. The last groups
+    // (placed last, as they come) take one part more each until the items
+    // fill whole waves; their smaller items then end the launch.
+    const long long slots = static_cast<long long>(n_sms) * blocks_per_sm;
+    long long N = 0;
+    for (int g = 0; g < G; ++g) N += parts[g];
+    if (n_sms > 0 && N > slots && N % slots != 0) {
+      long long extra = slots - N % slots;
+      for (int round = 0; extra > 0 && round < 64; ++round) {
+        bool grew = false;
+        for (int g = G - 1; g >= 0 && extra > 0; --g) {
+          if (parts[g] >= groups[g].nrec) continue;  // a part holds one record at least
+          ++parts[g];
+          --extra;
+          grew = true;
+        }
+        if (!grew) break;
+      }
     }
   } else if (n_sms > 0 && G >= n_sms) {
     const int q = G / n_sms, r = G % n_sms;
@@ -609,7 +630,7 @@ kmc_status autotune(kmc_ctx *c) {
   bs.warps = 4;
   bs.tile = 64;
   bs.chunk = 0;
-  bs.tpl = c->tpl_mode == 2 ? 2 : 1;
+  bs.tpl = c->tpl_mode != 0 ? c->tpl_mode : 1;
   const int warps_c[] = {4, 8};
   const int tiles_f32[] = {64, 128, 256, 512};
   const int tiles_f64[] = {32, 64, 128, 128};  // (the FP64 list has three distinct tiles)
@@ -622,9 +643,9 @@ kmc_status autotune(kmc_ctx *c) {
       for (int ch : chunks) {
         if (ch > 0 && ch >= max_n) continue;
         if (ch > 0 && ch < (c->fp32 ? 2 : 1) * t) continue;
-        for (int tpl = 1; tpl <= 2; ++tpl) {
+        for (int tpl = 1; tpl <= 3; ++tpl) {
           if (c->tpl_mode != 0 && tpl != c->tpl_mode) continue;
-          if (tpl == 2 && !c->fp32) continue;
+          if (tpl > 1 && !c->fp32) continue;
           Shape s;
           s.warps = w;
           s.tile = t;
@@ -902,8 +923,8 @@ kmc_status kmc_plan_items(const int32_t *n, int32_t n_lys, kmc_precision prec, i
     return fail(KMC_EINVAL, "plan: need n[n_lys >= 1], outputs and cap >= 0");
   if (prec != KMC_FP32_MIXED && prec != KMC_FP64_PLAIN) return fail(KMC_EINVAL, "bad precision");
   const bool fp32 = prec == KMC_FP32_MIXED;
-  if (tpl != 1 && !(tpl == 2 && fp32))
-    return fail(KMC_EINVAL, "targets per lane: 1, or 2 with KMC_FP32_MIXED");
+  if (tpl != 1 && !((tpl == 2 || tpl == 3) && fp32))
+    return fail(KMC_EINVAL, "targets per lane: 1, or 2 or 3 with KMC_FP32_MIXED");
   if (chunk < 0 || chunk % 64 != 0 || blocks_per_sm < 1 || n_sms < 0)
     return fail(KMC_EINVAL, "plan: chunk a multiple of 64, blocks_per_sm >= 1, n_sms >= 0");
   std::vector<int> np(n, n + n_lys);
@@ -927,9 +948,10 @@ kmc_status kmc_plan_items(const int32_t *n, int32_t n_lys, kmc_precision prec, i
 kmc_status kmc_targets_per_lane(kmc_ctx *c, int32_t tpl, int32_t *tpl_out) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (tpl != -1) {
-    if (tpl < 0 || tpl > 2) return fail(KMC_EINVAL, "targets per lane: 0 (autotuned), 1 or 2");
-    if (tpl == 2 && !c->fp32)
-      return fail(KMC_EINVAL, "two targets per lane run on FP32 contexts");
+    if (tpl < 0 || tpl > 3)
+      return fail(KMC_EINVAL, "targets per lane: 0 (autotuned), 1, 2 or 3");
+    if (tpl > 1 && !c->fp32)
+      return fail(KMC_EINVAL, "two or three targets per lane run on FP32 contexts");
     c->tpl_mode = tpl;
     // a pinned choice applies to the shape in use; 0 leaves it to the autotuner
     if (tpl != 0 && c->shape.warps != 0) c->shape.tpl = tpl;
@@ -950,7 +972,7 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
     s.warps = warps;
     s.tile = tile;
     s.chunk = chunk;
-    s.tpl = c->tpl_mode == 2 ? 2 : 1;
+    s.tpl = c->tpl_mode != 0 ? c->tpl_mode : 1;
     if (!shape_ok(c, s))
       return fail(KMC_EINVAL,
                   "bad shape: warps in {4, 8, 16}, tile a power of two in [32, %d], chunk a "

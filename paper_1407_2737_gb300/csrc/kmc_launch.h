@@ -16,7 +16,8 @@ size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl = 1);
 // warps in {4, 8, 16}; tile = sources per staged tile. With pdl the launch
 // may overlap the tail of the previous kernel on st (programmatic dependent
 // launch); the kernel waits for that kernel before it reads any state.
-// tpl = 2 (FP32 only): items are 64-target groups, two targets per lane.
+// tpl = 2 or 3 (FP32 only): items are 64- or 96-target groups, two or three
+// targets per lane.
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
                         cudaStream_t st, bool pdl = false, int tpl = 1);
 

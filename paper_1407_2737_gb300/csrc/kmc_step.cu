@@ -778,59 +778,101 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
 }
 
 // ---------------------------------------------------------------------------
-// FP32-mixed step with two targets per lane: the block takes a group of 64
-// targets, lane t holding targets t0 + t and t0 + 32 + t, so that every staged
-// source record feeds two independent chains. Each target's sums are formed by
-// the same packed operations over the same records as in kmc_step_f32, and the
-// warps and source parts are combined in the same order, so the fields, and
-// hence the whole step, are the same bits. The two halves then run steps
-// iii-vii one after the other with the same update code.
-struct AccF32x2 {
-  AccF32 a, b;  // first and second target of the lane
+// FP32-mixed step with TPL targets per lane (2 or 3): the block takes a group
+// of 32 TPL targets, lane t holding targets t0 + t, t0 + 32 + t, ..., so that
+// every staged source record feeds TPL independent chains. Each target's sums
+// are formed by the same packed operations over the same records as in
+// kmc_step_f32, and the warps and source parts are combined in the same order,
+// so the fields, and hence the whole step, are the same bits. The 32-target
+// parts of the group then run steps iii-vii one after the other with the same
+// update code.
+template <int TPL>
+struct AccF32N {
+  AccF32 t[TPL];  // the lane's targets, in order
 };
 
+// The loops for two and three targets take their targets' positions as
+// separate arguments (registers), each record feeding every target in turn;
+// the targets already give independent chains, so the loop is not unrolled.
 template <bool MASK>
-__device__ __noinline__ AccF32x2 pair_tile_f32_2t(const ulonglong2 *__restrict__ sp, int cnt,
-                                                   int first, int stride, f2 X0, f2 Y0, f2 Z0,
-                                                   f2 X1, f2 Y1, f2 Z1) {
-  AccF32x2 acc;
-  acc.a.x = acc.a.y = acc.a.z = 0ull;
-  acc.b = acc.a;
-  // the two targets already give two independent chains
+__device__ __noinline__ AccF32N<2> pair_tile_f32_2t(const ulonglong2 *__restrict__ sp, int cnt,
+                                                    int first, int stride, f2 X0, f2 Y0, f2 Z0,
+                                                    f2 X1, f2 Y1, f2 Z1) {
+  AccF32N<2> acc;
+  acc.t[0].x = acc.t[0].y = acc.t[0].z = 0ull;
+  acc.t[1] = acc.t[0];
 #pragma unroll 1
   for (int r = first; r < cnt; r += stride) {
     ulonglong2 a, b, c, d;
     f2 e;
     load_record(sp, r, a, b, c, d, e);
-    pair_record<MASK>(a, b, c, d, e, X0, Y0, Z0, acc.a);
-    pair_record<MASK>(a, b, c, d, e, X1, Y1, Z1, acc.b);
+    pair_record<MASK>(a, b, c, d, e, X0, Y0, Z0, acc.t[0]);
+    pair_record<MASK>(a, b, c, d, e, X1, Y1, Z1, acc.t[1]);
   }
   return acc;
 }
 
-// Dynamic shared memory of the two-target kernel after its pair loop: the
-// warps' (sum, -error) pairs of both halves, then the update state.
-constexpr size_t epi_bytes_t2(int warps) {
-  return static_cast<size_t>(warps) * 12 * kTargets * sizeof(float) + sizeof(EpiShared<float>) + 64;
+template <bool MASK>
+__device__ __noinline__ AccF32N<3> pair_tile_f32_3t(const ulonglong2 *__restrict__ sp, int cnt,
+                                                    int first, int stride, f2 X0, f2 Y0, f2 Z0,
+                                                    f2 X1, f2 Y1, f2 Z1, f2 X2, f2 Y2, f2 Z2) {
+  AccF32N<3> acc;
+  acc.t[0].x = acc.t[0].y = acc.t[0].z = 0ull;
+  acc.t[1] = acc.t[0];
+  acc.t[2] = acc.t[0];
+#pragma unroll 1
+  for (int r = first; r < cnt; r += stride) {
+    ulonglong2 a, b, c, d;
+    f2 e;
+    load_record(sp, r, a, b, c, d, e);
+    pair_record<MASK>(a, b, c, d, e, X0, Y0, Z0, acc.t[0]);
+    pair_record<MASK>(a, b, c, d, e, X1, Y1, Z1, acc.t[1]);
+    pair_record<MASK>(a, b, c, d, e, X2, Y2, Z2, acc.t[2]);
+  }
+  return acc;
 }
 
-template <int NW>
-__global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int tile) {
+// Dynamic shared memory of the multi-target kernel after its pair loop: the
+// warps' (sum, -error) pairs of every target, then the update state.
+constexpr size_t epi_bytes_tn(int warps, int tpl) {
+  return static_cast<size_t>(warps) * 6 * tpl * kTargets * sizeof(float) +
+         sizeof(EpiShared<float>) + 64;
+}
+
+// Three targets per lane want 164 registers (3 blocks of 4 warps per SM); capped
+// at 128, the 4-warp kernel keeps 4 blocks per SM for a 12-byte spill in the
+// update, which times the same as two targets per lane instead of 5 % slower.
+template <int NW, int TPL>
+__global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
+    kmc_step_f32_tn(const StepArgs a, int tile) {
+  static_assert(TPL == 2 || TPL == 3, "two or three targets per lane");
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *dyn = smem + 16;
   __shared__ int s_last;
   __shared__ GridTables<float> tab;
-  __shared__ float s_h1[3][kTargets];  // second half's field while the first updates
+  __shared__ float s_hr[TPL - 1][3][kTargets];  // later parts' fields while the first updates
   tab.load();
-  if (!item_in_bounds(a, 2, true)) return;
+  if (!item_in_bounds(a, TPL, true)) return;
   const Item it = a.items[blockIdx.x];
   const LysDev L = a.lys[it.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nt0 = min(it.nt, kTargets), nt1 = it.nt - nt0;
+  int ntk[TPL];  // targets of each 32-target part
+#pragma unroll
+  for (int k = 0; k < TPL; ++k) ntk[k] = min(max(it.nt - k * kTargets, 0), kTargets);
   const float4 *pos = static_cast<const float4 *>(a.pos);
-  const float4 pi0 = pos[L.off + it.t0 + min(lane, nt0 - 1)];
-  const float4 pi1 = nt1 > 0 ? pos[L.off + it.t0 + kTargets + min(lane, nt1 - 1)] : pi0;
+  f2 X[TPL], Y[TPL], Z[TPL];
+  {
+    const float4 p0 = pos[L.off + it.t0 + min(lane, ntk[0] - 1)];
+#pragma unroll
+    for (int k = 0; k < TPL; ++k) {
+      const float4 p =
+          ntk[k] > 0 ? pos[L.off + it.t0 + k * kTargets + min(lane, ntk[k] - 1)] : p0;
+      X[k] = pk(p.x, p.x);
+      Y[k] = pk(p.y, p.y);
+      Z[k] = pk(p.z, p.z);
+    }
+  }
   grid_dependency_wait();
   const long long step = a.rs->step_base + a.k_local;
   const int per = a.rs->period;
@@ -839,14 +881,12 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
   const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
 
   Item h0 = it;
-  h0.nt = nt0;
+  h0.nt = ntk[0];
   TargetIn<float4> tin;
   if (warp == 0) tin = load_target<float4>(a, L, h0, step, lane);
-  const f2 X0 = pk(pi0.x, pi0.x), Y0 = pk(pi0.y, pi0.y), Z0 = pk(pi0.z, pi0.z);
-  const f2 X1 = pk(pi1.x, pi1.x), Y1 = pk(pi1.y, pi1.y), Z1 = pk(pi1.z, pi1.z);
-  float s6[6], c6[6];
+  float sk[3 * TPL], ck[3 * TPL];  // Kahan sums: target k, component c at 3 k + c
 #pragma unroll
-  for (int c = 0; c < 6; ++c) s6[c] = c6[c] = 0.f;
+  for (int c = 0; c < 3 * TPL; ++c) sk[c] = ck[c] = 0.f;
   const int nrec = it.j1 - it.j0;
   const int ntiles = (nrec + tile - 1) / tile;
   const int own0 = it.t0 >> 1, own1 = (it.t0 + it.nt - 1) >> 1;  // records holding targets
@@ -868,50 +908,58 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
     const int cnt = min(tile, it.j1 - r0);
     const bool mask = (r0 <= own1) && (own0 < r0 + cnt);
     const ulonglong2 *sp = buf + static_cast<size_t>(b) * tile * kRecU2;
-    const AccF32x2 acc = mask ? pair_tile_f32_2t<true>(sp, cnt, warp, NW, X0, Y0, Z0, X1, Y1, Z1)
-                              : pair_tile_f32_2t<false>(sp, cnt, warp, NW, X0, Y0, Z0, X1, Y1, Z1);
-    kahan_add(s6[0], c6[0], hsum(acc.a.x));
-    kahan_add(s6[1], c6[1], hsum(acc.a.y));
-    kahan_add(s6[2], c6[2], hsum(acc.a.z));
-    kahan_add(s6[3], c6[3], hsum(acc.b.x));
-    kahan_add(s6[4], c6[4], hsum(acc.b.y));
-    kahan_add(s6[5], c6[5], hsum(acc.b.z));
+    AccF32N<TPL> acc;
+    if constexpr (TPL == 2) {
+      acc = mask ? pair_tile_f32_2t<true>(sp, cnt, warp, NW, X[0], Y[0], Z[0], X[1], Y[1], Z[1])
+                 : pair_tile_f32_2t<false>(sp, cnt, warp, NW, X[0], Y[0], Z[0], X[1], Y[1], Z[1]);
+    } else {
+      acc = mask ? pair_tile_f32_3t<true>(sp, cnt, warp, NW, X[0], Y[0], Z[0], X[1], Y[1], Z[1],
+                                          X[2], Y[2], Z[2])
+                 : pair_tile_f32_3t<false>(sp, cnt, warp, NW, X[0], Y[0], Z[0], X[1], Y[1], Z[1],
+                                           X[2], Y[2], Z[2]);
+    }
+#pragma unroll
+    for (int k = 0; k < TPL; ++k) {
+      kahan_add(sk[3 * k + 0], ck[3 * k + 0], hsum(acc.t[k].x));
+      kahan_add(sk[3 * k + 1], ck[3 * k + 1], hsum(acc.t[k].y));
+      kahan_add(sk[3 * k + 2], ck[3 * k + 2], hsum(acc.t[k].z));
+    }
   };
   if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
 
-  // cross-warp combine in a fixed order, per half as in kmc_step_f32
-  float *wp = reinterpret_cast<float *>(dyn);  // [NW][12][32]: 6 sums, then 6 errors
+  // cross-warp combine in a fixed order, per target as in kmc_step_f32
+  constexpr int kW = 6 * TPL;                  // floats per lane and warp
+  float *wp = reinterpret_cast<float *>(dyn);  // [NW][6 TPL][32]: 3 TPL sums, then 3 TPL errors
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    wp[(warp * 12 + c) * 32 + lane] = s6[c];
-    wp[(warp * 12 + 6 + c) * 32 + lane] = -c6[c];
+  for (int c = 0; c < 3 * TPL; ++c) {
+    wp[(warp * kW + c) * 32 + lane] = sk[c];
+    wp[(warp * kW + 3 * TPL + c) * 32 + lane] = -ck[c];
   }
   __syncthreads();
   EpiShared<float> &sm =
-      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 12 * 32 * 4);
-  // hi[0..2], lo[0..2]: first half; hi[3..5], lo[3..5]: second half
-  float hi[6], lo[6];
+      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * kW * 32 * 4);
+  float hi[3 * TPL], lo[3 * TPL];
   if (warp == 0) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < 3 * TPL; ++c) {
       float s = 0.f, e = 0.f;
       for (int w = 0; w < NW; ++w) {
-        neumaier_add(s, e, wp[(w * 12 + c) * 32 + lane]);
-        e += wp[(w * 12 + 6 + c) * 32 + lane];
+        neumaier_add(s, e, wp[(w * kW + c) * 32 + lane]);
+        e += wp[(w * kW + 3 * TPL + c) * 32 + lane];
       }
       hi[c] = s;
       lo[c] = e;
     }
     if (it.nsplit > 1) {
-      // the two halves' partials, each laid out as kmc_step_f32's
-      float *part = a.partial + static_cast<size_t>(blockIdx.x) * 2 * kPartF32;
+      // every part's partials, each laid out as kmc_step_f32's
+      float *part = a.partial + static_cast<size_t>(blockIdx.x) * TPL * kPartF32;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        __stcg(part + c * 32 + lane, hi[c]);
-        __stcg(part + (3 + c) * 32 + lane, lo[c]);
-        __stcg(part + kPartF32 + c * 32 + lane, hi[3 + c]);
-        __stcg(part + kPartF32 + (3 + c) * 32 + lane, lo[3 + c]);
-      }
+      for (int k = 0; k < TPL; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          __stcg(part + k * kPartF32 + c * 32 + lane, hi[3 * k + c]);
+          __stcg(part + k * kPartF32 + (3 + c) * 32 + lane, lo[3 * k + c]);
+        }
       __threadfence();
     }
   }
@@ -922,14 +970,14 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
     if (!s_last) return;  // another item of the group finishes the step
     __threadfence();
     if (warp == 0) {
-      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * 2 * kPartF32;
+      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * TPL * kPartF32;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const int o = (c < 3 ? 0 : kPartF32) + (c % 3) * 32 + lane;
+      for (int c = 0; c < 3 * TPL; ++c) {
+        const int o = (c / 3) * kPartF32 + (c % 3) * 32 + lane;
         float s = 0.f, e = 0.f;
         for (int q = 0; q < it.nsplit; ++q) {
-          neumaier_add(s, e, __ldcg(base + q * 2 * kPartF32 + o));
-          e += __ldcg(base + q * 2 * kPartF32 + o + 3 * 32);
+          neumaier_add(s, e, __ldcg(base + q * TPL * kPartF32 + o));
+          e += __ldcg(base + q * TPL * kPartF32 + o + 3 * 32);
         }
         hi[c] = s;
         lo[c] = e;
@@ -938,27 +986,30 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32_t2(const StepArgs a, int
     }
   }
   if (warp == 0) {
-    // the first half's field; the second half's waits in shared memory
+    // the first part's field; the others' wait in shared memory
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       sm.h[c][lane] = hi[c] + lo[c];
-      s_h1[c][lane] = hi[3 + c] + lo[3 + c];
+#pragma unroll
+      for (int k = 1; k < TPL; ++k) s_hr[k - 1][c][lane] = hi[3 * k + c] + lo[3 * k + c];
     }
   }
   __syncthreads();
   block_update<float4, true>(a, L, h0, step, rec, tin, sm, tab);
-  if (nt1 > 0) {
+#pragma unroll 1
+  for (int k = 1; k < TPL; ++k) {
+    if (ntk[k] == 0) break;
     __syncthreads();
-    Item h1 = it;
-    h1.t0 = it.t0 + kTargets;
-    h1.nt = nt1;
+    Item hk = it;
+    hk.t0 = it.t0 + k * kTargets;
+    hk.nt = ntk[k];
     if (warp == 0) {
-      tin = load_target<float4>(a, L, h1, step, lane);
+      tin = load_target<float4>(a, L, hk, step, lane);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) sm.h[c][lane] = s_h1[c][lane];
+      for (int c = 0; c < 3; ++c) sm.h[c][lane] = s_hr[k - 1][c][lane];
     }
     __syncthreads();
-    block_update<float4, true>(a, L, h1, step, rec, tin, sm, tab);
+    block_update<float4, true>(a, L, hk, step, rec, tin, sm, tab);
   }
   grid_launch_dependents();
 }
@@ -1080,7 +1131,7 @@ size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl) {
   const size_t stage = prec_fp32 ? 2 * static_cast<size_t>(tile) * sizeof(SrcPair)
                                  : 4 * static_cast<size_t>(tile) * sizeof(dbl4);
   const size_t epi = !prec_fp32 ? epi_bytes<double>(warps)
-                                : (tpl == 2 ? epi_bytes_t2(warps) : epi_bytes<float>(warps));
+                                : (tpl >= 2 ? epi_bytes_tn(warps, tpl) : epi_bytes<float>(warps));
   return 16 + (stage > epi ? stage : epi);
 }
 
@@ -1106,8 +1157,12 @@ template <int NW>
 static cudaError_t launch_f32(const StepArgs &a, int n_items, int tile, cudaStream_t st,
                               bool pdl, int tpl) {
   if (tpl == 2)
-    return launch_items(kmc_step_f32_t2<NW>, a, n_items, NW * 32, step_smem_bytes(1, NW, tile, 2),
-                        tile, st, pdl);
+    return launch_items(kmc_step_f32_tn<NW, 2>, a, n_items, NW * 32,
+                        step_smem_bytes(1, NW, tile, 2), tile, st, pdl);
+  if (tpl == 3)
+    return launch_items(kmc_step_f32_tn<NW, 3>, a, n_items, NW * 32,
+                        step_smem_bytes(1, NW, tile, 3), tile, st, pdl);
+  if (tpl != 1) return cudaErrorInvalidValue;
   return launch_items(kmc_step_f32<NW>, a, n_items, NW * 32, step_smem_bytes(1, NW, tile, 1), tile,
                       st, pdl);
 }
@@ -1149,9 +1204,17 @@ cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int 
   const int th = warps * 32;
   if (prec_fp32 && tpl == 2) {
     switch (warps) {
-      case 4: return occupancy(kmc_step_f32_t2<4>, th, smem, blocks);
-      case 8: return occupancy(kmc_step_f32_t2<8>, th, smem, blocks);
-      case 16: return occupancy(kmc_step_f32_t2<16>, th, smem, blocks);
+      case 4: return occupancy(kmc_step_f32_tn<4, 2>, th, smem, blocks);
+      case 8: return occupancy(kmc_step_f32_tn<8, 2>, th, smem, blocks);
+      case 16: return occupancy(kmc_step_f32_tn<16, 2>, th, smem, blocks);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (prec_fp32 && tpl == 3) {
+    switch (warps) {
+      case 4: return occupancy(kmc_step_f32_tn<4, 3>, th, smem, blocks);
+      case 8: return occupancy(kmc_step_f32_tn<8, 3>, th, smem, blocks);
+      case 16: return occupancy(kmc_step_f32_tn<16, 3>, th, smem, blocks);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -1224,9 +1287,12 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<16>);
-  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_t2<4>);
-  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_t2<8>);
-  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_t2<16>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<4, 2>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<8, 2>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<16, 2>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<4, 3>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<8, 3>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<16, 3>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<16>);

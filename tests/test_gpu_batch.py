@@ -136,14 +136,15 @@ def test_chained_batch_checkpoint_resume_is_bit_identical(tmp_path):
             assert np.array_equal(x, y)
 
 
-def test_two_targets_per_lane_give_the_same_bits():
-    """The two-target kernel (64-target groups, two per lane) forms every
-    target's sums with the same operations in the same order as the one-target
-    kernel and runs the same update: identical outputs at the same shape."""
+def test_two_and_three_targets_per_lane_give_the_same_bits():
+    """The multi-target kernels (64- or 96-target groups, two or three per lane)
+    form every target's sums with the same operations in the same order as the
+    one-target kernel and run the same update: identical outputs at the same
+    shape, including ragged last groups and split source ranges."""
     lyss = [inputs.make_lysosome(n, 12e-9, 0.05, seed=70 + q) for q, n in enumerate([700, 97, 33, 1])]
     for shape in [(4, 64, 0), (4, 128, 256), (8, 64, 128)]:
         out = []
-        for tpl in (1, 2):
+        for tpl in (1, 2, 3):
             ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
             kmc.kmc_targets_per_lane(ctx, tpl)
             kmc.kmc_tuning(ctx, *shape)
@@ -154,11 +155,13 @@ def test_two_targets_per_lane_give_the_same_bits():
                                   kmc.KMC_READ_NP_ENERGY, kmc.KMC_READ_DHDIP,
                                   kmc.KMC_READ_COUNTERS)])
             kmc.kmc_destroy(ctx)
-        for x, y in zip(*out):
-            assert np.array_equal(x, y), shape
+        for other in out[1:]:
+            for x, y in zip(out[0], other):
+                assert np.array_equal(x, y), shape
     lys64 = inputs.make_lysosome(40, 12e-9, 0.05, seed=1)
     ctx = kmc.kmc_create([lys64], kmc.KMC_FP64_PLAIN, center=np.zeros(3))
-    with pytest.raises(kmc.KmcError) as e:
-        kmc.kmc_targets_per_lane(ctx, 2)
-    assert e.value.status == kmc.KMC_EINVAL
+    for tpl in (2, 3):
+        with pytest.raises(kmc.KmcError) as e:
+            kmc.kmc_targets_per_lane(ctx, tpl)
+        assert e.value.status == kmc.KMC_EINVAL
     kmc.kmc_destroy(ctx)

@@ -47,7 +47,11 @@ def _check_plan(n, prec, tpl, chunk, bps, n_sms):
         assert end == nrec[l]
         if chunk > 0:
             rchunk = chunk // 2 if prec == FP32 else chunk
-            assert parts == max(1, math.ceil(nrec[l] / rchunk))
+            nominal = max(1, math.ceil(nrec[l] / rchunk))
+            if len(n) == 1 and n_sms > 0:
+                assert nominal <= parts <= nrec[l]  # a single chain may fill its last wave
+            else:
+                assert parts == nominal
         u += parts
         gid += 1
     for c in covered:
@@ -61,7 +65,7 @@ def _check_plan(n, prec, tpl, chunk, bps, n_sms):
     return items, cut
 
 
-@pytest.mark.parametrize("prec,tpl", [(FP32, 1), (FP32, 2), (FP64, 1)])
+@pytest.mark.parametrize("prec,tpl", [(FP32, 1), (FP32, 2), (FP32, 3), (FP64, 1)])
 @pytest.mark.parametrize("chunk", [0, 64, 256, 1024])
 def test_random_batches_cover_every_pair_once(prec, tpl, chunk):
     rng = np.random.default_rng(100 + tpl + chunk)
@@ -132,9 +136,32 @@ def test_no_wave_split_without_sms_or_with_chains():
 
 
 def test_plan_rejects_bad_arguments():
-    for args in [([100], FP64, 2, 0, 5, 0), ([100], FP32, 3, 0, 5, 0), ([100], FP32, 1, 100, 5, 0),
+    for args in [([100], FP64, 2, 0, 5, 0), ([100], FP64, 3, 0, 5, 0), ([100], FP32, 4, 0, 5, 0),
+                 ([100], FP32, 1, 100, 5, 0),
                  ([100, 0], FP32, 1, 0, 5, 0), ([100], FP32, 1, 0, 0, 0), ([], FP32, 1, 0, 5, 0),
                  ([100], 7, 1, 0, 5, 0)]:
         with pytest.raises(kmc.KmcError) as e:
             kmc.kmc_plan_items(*args)
         assert e.value.status == kmc.KMC_EINVAL, args
+
+
+@pytest.mark.parametrize("n,tpl,chunk,bps", [(50000, 2, 8192, 2), (50000, 2, 4096, 4),
+                                             (50000, 1, 1024, 5), (8000, 1, 2048, 5),
+                                             (3000, 3, 256, 4)])
+def test_single_chain_split_fills_whole_waves(n, tpl, chunk, bps):
+    """One lysosome split by chunk over several waves: the last groups take one
+    part more each until the items fill whole waves of n_sms x blocks_per_sm
+    (the last wave would otherwise hold a few full-size items while the rest
+    of the GPU waits), so the smaller items come last."""
+    n_sms = 152
+    items, cut = _check_plan([n], FP32, tpl, chunk, bps, n_sms)
+    slots = n_sms * bps
+    groups = [items[u] for u in range(len(items)) if items[u, 6] == 0]
+    parts = np.array([g[7] for g in groups])
+    nominal = math.ceil(((n + 1) // 2) / (chunk // 2))
+    if len(groups) * nominal > slots:
+        assert len(items) % slots == 0
+        assert np.all(np.diff(parts) >= 0)  # the groups with more parts come last
+        assert parts.max() - parts.min() <= 1 + (slots // len(groups))
+    else:
+        assert np.all(parts == nominal)
