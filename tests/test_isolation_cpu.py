@@ -49,8 +49,8 @@ def test_bench_and_entry_use_the_oracle_only_in_their_cpu_legs():
 
 
 def test_cuda_path_and_oracle_share_no_code():
-    native = (glob.glob(os.path.join(PKG, "csrc", "*")) +
-              glob.glob(os.path.join(ROOT, "include", "*.h")))
+    native = [f for f in glob.glob(os.path.join(PKG, "csrc", "**", "*"), recursive=True)
+              if os.path.isfile(f)] + glob.glob(os.path.join(ROOT, "include", "*.h"))
     assert native
     for f in native:
         text = open(f).read()
