@@ -48,10 +48,11 @@ namespace kmc {
 // ---------------------------------------------------------------------------
 // Pair loops over one staged tile. MASK: the tile holds some of the block's
 // own targets, so the self term (r2 = 0; distinct NPs are never coincident)
-// is dropped. The FP32 loop is a function of its own (not inlined) so that
-// its register allocation and schedule do not depend on the rest of the
-// kernel (measured: inlined, the loop lost 7 % of its throughput when the
-// update code after it changed).
+// is dropped. The one-target FP32 loop is a function of its own (not
+// inlined) so that its register allocation and schedule do not depend on the
+// rest of the kernel (measured: inlined, the loop lost 7 % of its throughput
+// when the update code after it changed, and the 8 x 2000-NP workload still
+// runs 2.6 % slower with it inlined).
 
 template <bool MASK>
 __device__ __noinline__ AccF32 pair_tile_f32(const ulonglong2 *__restrict__ sp, int cnt,
@@ -792,16 +793,20 @@ struct AccF32N {
 };
 
 // The loops for two and three targets take their targets' positions as
-// separate arguments (registers), each record feeding every target in turn;
-// the targets already give independent chains, so the loop is not unrolled.
+// separate arguments, each record feeding every target in turn. Unlike the
+// one-target loop they are inlined: out of line, the call's argument passing
+// held 122 (two targets) and 164 (three) registers where inlined they take 107
+// and 128, and the 50 000-NP and 512-lysosome workloads ran 5-6 % faster. The
+// two-target loop is unrolled twice (four independent chains per lane; +1 %
+// on the batch), the three-target loop not at all (its three chains suffice).
 template <bool MASK>
-__device__ __noinline__ AccF32N<2> pair_tile_f32_2t(const ulonglong2 *__restrict__ sp, int cnt,
-                                                    int first, int stride, f2 X0, f2 Y0, f2 Z0,
-                                                    f2 X1, f2 Y1, f2 Z1) {
+__device__ __forceinline__ AccF32N<2> pair_tile_f32_2t(const ulonglong2 *__restrict__ sp, int cnt,
+                                                       int first, int stride, f2 X0, f2 Y0, f2 Z0,
+                                                       f2 X1, f2 Y1, f2 Z1) {
   AccF32N<2> acc;
   acc.t[0].x = acc.t[0].y = acc.t[0].z = 0ull;
   acc.t[1] = acc.t[0];
-#pragma unroll 1
+#pragma unroll 2
   for (int r = first; r < cnt; r += stride) {
     ulonglong2 a, b, c, d;
     f2 e;
@@ -813,7 +818,7 @@ __device__ __noinline__ AccF32N<2> pair_tile_f32_2t(const ulonglong2 *__restrict
 }
 
 template <bool MASK>
-__device__ __noinline__ AccF32N<3> pair_tile_f32_3t(const ulonglong2 *__restrict__ sp, int cnt,
+__device__ __forceinline__ AccF32N<3> pair_tile_f32_3t(const ulonglong2 *__restrict__ sp, int cnt,
                                                     int first, int stride, f2 X0, f2 Y0, f2 Z0,
                                                     f2 X1, f2 Y1, f2 Z1, f2 X2, f2 Y2, f2 Z2) {
   AccF32N<3> acc;
@@ -839,9 +844,7 @@ constexpr size_t epi_bytes_tn(int warps, int tpl) {
          sizeof(EpiShared<float>) + 64;
 }
 
-// Three targets per lane want 164 registers (3 blocks of 4 warps per SM); capped
-// at 128, the 4-warp kernel keeps 4 blocks per SM for a 12-byte spill in the
-// update, which times the same as two targets per lane instead of 5 % slower.
+// Three targets per lane, 4 warps: held at 4 blocks per SM (128 registers).
 template <int NW, int TPL>
 __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
     kmc_step_f32_tn(const StepArgs a, int tile) {
