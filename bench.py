@@ -75,11 +75,34 @@ CONFIGS = {
            "f=100 kHz, 500 steps/period", (2, 1), 50),
 }
 FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
-# DRAM bytes (read + write) of one kMC step, by (workload, warps, tile, chunk,
-# targets per lane), from serialised ncu captures of the committed kernel. c1:
-# 8 chains, one launch each: 8 x the mean over 16 launches. c4: one launch per
-# step, the mean over 2.
-STEP_DRAM_BYTES = {("c1", 4, 256, 1024, 1): 2.365e6, ("c4", 4, 256, 4096, 2): 6.06e6}
+# DRAM bytes (read + write) of one kMC step in steady state, by (workload,
+# warps, tile, chunk, targets per lane, replicas per lane), from ncu captures of
+# the committed kernel with --cache-control none (the state stays in L2 between
+# launches, as in the bench). c1: 8 chains, one launch each: 8 x the mean over
+# 16 launches. c4: one launch per step, the mean over 2.
+STEP_DRAM_BYTES = {("c1", 4, 256, 1024, 1, 1): 512.0, ("c4", 8, 512, 8192, 2, 1): 512.0}
+
+
+def step_kernel(warps, tpl, rpl):
+    """Name of the FP32 step kernel a launch shape runs."""
+    if rpl > 1:
+        return "kmc_step_f32_rep<%d>" % rpl
+    if tpl > 1:
+        return "kmc_step_f32_tn<%d, %d>" % (warps, tpl)
+    return "kmc_step_f32<%d>" % warps
+
+
+def lane_ops_per_pair(rpl):
+    """FP32 lane operations the pair loop issues per ordered pair (a packed
+    f32x2 operation counts two): 18 per record and target for two pairs, or
+    with r replicas per lane 16 of shared geometry and 20 per replica for 2 r
+    pairs."""
+    return 8.0 / rpl + 10.0
+
+
+def fp32_lane_ops_peak():
+    """FP32 lane operations per second: SMs x lanes x maximum SM clock."""
+    return SMS * FP32_LANES * SM_MAX_MHZ * 1e6
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (FMA = 2 flops)
 HBM_GBS = 6771.5             # measured copy bandwidth of this pool's GB300s
@@ -513,6 +536,7 @@ def measure_sub_config(name, kmc, inputs, torch, stream, flush, warmup, uuid=Non
     kmc.kmc_sync(ctx)
     warps, tile, chunk = kmc.kmc_tuning(ctx)
     tpl = kmc.kmc_targets_per_lane(ctx)
+    rpl = kmc.kmc_replicas_per_lane(ctx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(cfg["steps"])]
     torch.cuda.synchronize()
@@ -566,11 +590,12 @@ def measure_sub_config(name, kmc, inputs, torch, stream, flush, warmup, uuid=Non
         "pair_interactions_per_s": pairs * n_steps * cfg["steps"] / t,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(),
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops(),
-                     "traffic": STEP_DRAM_BYTES.get((name, warps, tile, chunk, tpl)),
-                     "kernel": ("kmc_step_f32_t2<%d>" if tpl == 2 else "kmc_step_f32<%d>")
-                     % warps},
+                     "frac_issued": pairs * n_steps * cfg["steps"] / t * lane_ops_per_pair(rpl)
+                     / fp32_lane_ops_peak(),
+                     "traffic": STEP_DRAM_BYTES.get((name, warps, tile, chunk, tpl, rpl)),
+                     "kernel": step_kernel(warps, tpl, rpl)},
         "launch": {"warps": warps, "tile": tile, "chunk": chunk, "targets_per_lane": tpl,
-                   "chains": chains},
+                   "replicas_per_lane": rpl, "chains": chains},
         "fp64_plain": {"value": v64, "unit": UNIT, "speedup_fp32_mixed": value / v64,
                        "sample": "%d steps of the whole workload" % S64,
                        "launch": dict(zip(("warps", "tile", "chunk"), cfg["shape64"]))},
@@ -660,6 +685,7 @@ def main():
     kmc.kmc_sync(ctx)
     warps, tile, chunk = kmc.kmc_tuning(ctx)
     tpl = kmc.kmc_targets_per_lane(ctx)
+    rpl = kmc.kmc_replicas_per_lane(ctx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     uuid = None
@@ -683,8 +709,9 @@ def main():
     ms_per_step = 1e3 * t_total / args.steps
     sar32 = [kmc.kmc_read(ctx, kmc.KMC_READ_SAR, l)[0] for l in range(len(lyss))]
     # one step = one step-kernel launch per chain (equal lysosomes: one chain
-    # each, up to KMC_MAX_CHAINS), run concurrently; one period advance
-    chains = min(len(lyss), kmc.KMC_MAX_CHAINS)
+    # each, up to KMC_MAX_CHAINS; with replicas per lane one per set of them),
+    # run concurrently; one period advance
+    chains = min(len(lyss) // max(rpl, 1), kmc.KMC_MAX_CHAINS)
     launches_per_step = 1 + run["periods"] * (run["S"] * chains + 1)
     # roofline of the fused step kernel over one kMC step (all chains' launches)
     launch_s = t_total / (args.steps * n_steps)
@@ -776,18 +803,23 @@ def main():
                        "precision": "KMC_FP32_MIXED",
                        "kmc_steps_per_bench_step": n_steps, "particles": n_np,
                        "launch": {"warps": warps, "tile": tile, "chunk": chunk,
-                                  "targets_per_lane": tpl, "chains": chains},
+                                  "targets_per_lane": tpl, "replicas_per_lane": rpl,
+                                  "chains": chains},
                        "l2": "256 MB buffer written between timed steps (state < L2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "pair_interactions_per_s": world * pairs_per_launch * n_steps * args.steps / t_total,
             "sar_W_per_g": float(np.mean(sar32)) / 1e3,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
+                         "frac_issued": achieved / FLOPS_PER_PAIR * 1e12
+                         * lane_ops_per_pair(rpl) / fp32_lane_ops_peak(),
                          "traffic": STEP_DRAM_BYTES.get((args.config, warps, tile, chunk,
-                                                         tpl)),
-                         "kernel": ("kmc_step_f32_t2<%d>" if tpl == 2 else
-                                    "kmc_step_f32<%d>") % warps,
-                         "note": "FP32 pipe: 30 flops per ordered pair; a kMC step is one "
+                                                         tpl, rpl)),
+                         "kernel": step_kernel(warps, tpl, rpl),
+                         "note": "FP32 pipe: 30 flops per ordered pair; frac_issued counts "
+                                 "the FP32 lane operations the loop issues instead (18 per "
+                                 "pair, 8/r + 10 with r replicas per lane sharing each "
+                                 "pair's geometry); a kMC step is one "
                                  "launch per chain, the chains' launches concurrent; step "
                                  "time = timed region / kMC steps (includes graph gaps); "
                                  "peak = 152 SM x 128 lanes x 2 x 2070 MHz (nominal; FFMA "

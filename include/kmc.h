@@ -180,7 +180,8 @@ kmc_status kmc_info(const kmc_ctx *ctx, int64_t *n_total, int32_t *n_lys,
                     int64_t *global_step);
 
 /* Launch shape of the fused step kernel. warps: warps per block, each taking
- * every warps-th source record of a tile (4, 8 or 16). tile: source records per
+ * every warps-th source record of a tile (4, 8 or 16; with replicas per lane
+ * pinned, warps = replicas and tile <= 128). tile: source records per
  * shared-memory tile (a power of two, 32..1024; an FP32 record holds two NPs,
  * an FP64 record one). chunk: sources per work item when a lysosome's sources
  * are split over several blocks (0 = never split; else a multiple of 64).
@@ -198,6 +199,25 @@ kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
  * applies to a shape set by kmc_tuning. The value in use (0 before the first
  * tuning) is returned through tpl_out (may be NULL); tpl = -1 only reads it. */
 kmc_status kmc_targets_per_lane(kmc_ctx *ctx, int32_t tpl, int32_t *tpl_out);
+
+/* Replicas per lane of the FP32 step kernel. When the lysosomes come in sets
+ * of k identical consecutive ones (the same NPs, axes, volumes, material,
+ * temperature, attempt time, density and frame origin; only the random
+ * streams, the amplitudes and hence the moments differ: seeds of one sample),
+ * a block of k warps can take 32 targets of all k lysosomes of a set at once:
+ * each staged source record's geometry (separation, distance, its powers) is
+ * formed once and serves all k, which add only their own moments' terms.
+ * Every lysosome's field, and its whole step, are the bits it gets with one
+ * target per lane and k warps at the same tile and chunk; each warp then runs
+ * one lysosome's steps iii-vii. rpl: 0 lets the autotuner choose (the
+ * default; it considers k = 2 and 4 where the sets exist), 1 turns replicas
+ * off, 2 or 4 pins them (KMC_EINVAL on FP64 contexts, with two or three
+ * targets per lane pinned, or unless n_lys is a multiple of rpl and every set
+ * of rpl consecutive lysosomes is identical). A pinned value takes warps = rpl
+ * in kmc_tuning and drops a shape of another kind. The value in use (0 before
+ * the first tuning) is returned through rpl_out (may be NULL); rpl = -1 only
+ * reads it. */
+kmc_status kmc_replicas_per_lane(kmc_ctx *ctx, int32_t rpl, int32_t *rpl_out);
 
 /* Fields of one work item in kmc_plan_items' output. */
 #define KMC_ITEM_FIELDS 8

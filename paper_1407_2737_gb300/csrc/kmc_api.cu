@@ -116,18 +116,20 @@ __global__ void sources_f64(const dbl4 *__restrict__ pos, const dbl4 *__restrict
 struct Shape {
   int warps = 0, tile = 0, chunk = 0;
   int tpl = 1;  // targets per lane: 2 or 3 run 64- or 96-target groups (FP32 only)
+  int rpl = 1;  // replicas per lane: 2 or 4 run replica lysosomes together (FP32, warps = rpl)
   bool operator==(const Shape &o) const {
-    return warps == o.warps && tile == o.tile && chunk == o.chunk && tpl == o.tpl;
+    return warps == o.warps && tile == o.tile && chunk == o.chunk && tpl == o.tpl &&
+           rpl == o.rpl;
   }
 };
 
 struct TuneKey {
   int prec;
   long long N;
-  int n_lys, max_n, tpl_mode;
+  int n_lys, max_n, tpl_mode, rpl_mode, reps;  // reps: replica sets available (bits)
   bool operator<(const TuneKey &o) const {
-    return std::tie(prec, N, n_lys, max_n, tpl_mode) <
-           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode);
+    return std::tie(prec, N, n_lys, max_n, tpl_mode, rpl_mode, reps) <
+           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode, o.reps);
   }
 };
 std::mutex g_tune_mu;
@@ -195,6 +197,8 @@ struct kmc_ctx {
   Shape items_shape;  // shape the items were built for
   std::vector<int> chain_cut;  // chain q runs items chain_cut[q] .. chain_cut[q + 1] - 1
   int tpl_mode = 0;            // targets per lane: 0 = the autotuner's choice, else 1, 2 or 3
+  int rpl_mode = 0;            // replicas per lane: 0 = the autotuner's choice, 1 = off, 2 or 4
+  bool rep_ok[5] = {};         // [k]: the lysosomes form sets of k identical consecutive ones
   cudaStream_t chain_st[kMaxChains] = {};  // branches 1.. of the period graph
   cudaEvent_t chain_ev[kMaxChains] = {};   // [0] fork, [q] join of branch q
   // debug outputs, allocated on first use
@@ -362,8 +366,13 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   int dev = 0, n_sms = 0, per_sm = 0;
   KMC_CUDA(cudaGetDevice(&dev));
   KMC_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
-  KMC_CUDA(kmc::step_blocks_per_sm(c->fp32, sh.warps, sh.tile, sh.tpl, &per_sm));
-  const Plan plan = plan_items(c->n, c->fp32, sh.chunk, per_sm, n_sms, sh.tpl);
+  KMC_CUDA(kmc::step_blocks_per_sm(c->fp32, sh.warps, sh.tile, sh.tpl, &per_sm, sh.rpl));
+  // replicas: the plan of the first lysosome of every set, whose items take
+  // the set's other lysosomes along (kmc_step_f32_rep)
+  std::vector<int> np;
+  for (int l = 0; l < c->n_lys; l += sh.rpl) np.push_back(c->n[l]);
+  Plan plan = plan_items(np, c->fp32, sh.chunk, per_sm, n_sms, sh.tpl);
+  for (Item &it : plan.items) it.l *= sh.rpl;
   const std::vector<Item> &items = plan.items;
   const int groups = plan.groups;
   KMC_CUDA(cudaStreamSynchronize(c->stream));
@@ -480,6 +489,11 @@ int max_tile(int fp32, int warps) {
 }
 
 bool shape_ok(const kmc_ctx *c, const Shape &s) {
+  if (s.rpl > 1) {  // replicas: their kernel has one warp per replica
+    if (!c->fp32 || s.tpl != 1 || s.warps != s.rpl || !c->rep_ok[s.rpl]) return false;
+    if (s.tile < 32 || s.tile > 128 || (s.tile & (s.tile - 1))) return false;
+    return s.chunk >= 0 && s.chunk % 64 == 0;
+  }
   if (s.warps != 4 && s.warps != 8 && s.warps != 16) return false;
   if (s.tile < 32 || s.tile > max_tile(c->fp32, s.warps) || (s.tile & (s.tile - 1))) return false;
   if (s.chunk < 0 || (s.chunk % 64) != 0) return false;
@@ -518,14 +532,15 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
     // an item's partials: (sum, error) of 3 FP32 or 6 FP64 (two floats each) components
     // per target
     if (split)
-      b.partial = c->d_partial + static_cast<size_t>(u0) * (c->fp32 ? 6 : 12) * kmc::kTargets * sh.tpl;
+      b.partial = c->d_partial +
+                  static_cast<size_t>(u0) * (c->fp32 ? 6 : 12) * kmc::kTargets * sh.tpl * sh.rpl;
     for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
       if (period) {
         b.k_local = k;
         b.cos_k = std::cos(2.0 * kPi * k / steps);
       }
       ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, b, c->chain_cut[q + 1] - u0, st, true,
-                            sh.tpl);
+                            sh.tpl, sh.rpl);
     }
   }
   // join, then the period advance
@@ -581,7 +596,8 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   }
   auto one = [&]() {
     return gx ? cudaGraphLaunch(gx, c->stream)
-              : kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true, s.tpl);
+              : kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true, s.tpl,
+                                 s.rpl);
   };
   float ms = -1.f;
   bool ok = true;
@@ -602,7 +618,9 @@ kmc_status autotune(kmc_ctx *c) {
   Phase phase("kmc_tune");
   int max_n = 0;
   for (int x : c->n) max_n = std::max(max_n, x);
-  const TuneKey key{c->fp32, c->N, c->n_lys, max_n, c->tpl_mode};
+  const TuneKey key{c->fp32, c->N,        c->n_lys,
+                    max_n,   c->tpl_mode, c->rpl_mode,
+                    (c->rep_ok[2] ? 1 : 0) | (c->rep_ok[4] ? 2 : 0)};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -631,11 +649,39 @@ kmc_status autotune(kmc_ctx *c) {
   bs.tile = 64;
   bs.chunk = 0;
   bs.tpl = c->tpl_mode != 0 ? c->tpl_mode : 1;
+  if (c->rpl_mode > 1) {  // pinned replicas: a shape of their kernel
+    bs.warps = c->rpl_mode;
+    bs.tpl = 1;
+    bs.rpl = c->rpl_mode;
+  }
   const int warps_c[] = {4, 8};
   const int tiles_f32[] = {64, 128, 256, 512};
   const int tiles_f64[] = {32, 64, 128, 128};  // (the FP64 list has three distinct tiles)
   const int chunks[] = {0, 256, 512, 1024, 2048, 4096, 8192};
+  // replicas per lane (FP32, sets of identical lysosomes): warps = replicas,
+  // one target per lane, tiles of 32..128 records per replica
+  for (int rpl = 2; rpl <= 4 && c->fp32 && c->tpl_mode <= 1; rpl += 2) {
+    if (!c->rep_ok[rpl] || (c->rpl_mode != 0 && c->rpl_mode != rpl)) continue;
+    for (int t : {32, 64, 128}) {
+      if (2 * t > 2 * std::max(max_n, 64) && t > 32) continue;
+      for (int ch : chunks) {
+        if (ch > 0 && (ch >= max_n || ch < 2 * t)) continue;
+        Shape s;
+        s.warps = rpl;
+        s.tile = t;
+        s.chunk = ch;
+        s.tpl = 1;
+        s.rpl = rpl;
+        const float ms = time_shape(c, s);
+        if (ms > 0.f && ms < best) {
+          best = ms;
+          bs = s;
+        }
+      }
+    }
+  }
   for (int w : warps_c) {
+    if (c->rpl_mode > 1) break;  // pinned replicas: only their shapes
     for (int q = 0; q < (c->fp32 ? 4 : 3); ++q) {
       const int t = c->fp32 ? tiles_f32[q] : tiles_f64[q];
       if (t > max_tile(c->fp32, w)) continue;
@@ -741,6 +787,21 @@ kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_p
   return KMC_OK;
 }
 
+// Lysosomes a and b are replicas: the same NPs (positions, axes, volumes,
+// compared bit for bit), material, temperature, attempt time, density and
+// frame origin; only their random streams (the lysosome index) differ.
+bool same_lysosome(const kmc_lysosome &a, const kmc_lysosome &b) {
+  if (a.n != b.n || a.Ms != b.Ms || a.Keff != b.Keff || a.T != b.T || a.tau0 != b.tau0)
+    return false;
+  if ((a.rho > 0 ? a.rho : 5200.0) != (b.rho > 0 ? b.rho : 5200.0)) return false;
+  if ((a.center == nullptr) != (b.center == nullptr)) return false;
+  if (a.center && std::memcmp(a.center, b.center, 3 * sizeof(double)) != 0) return false;
+  const size_t n = static_cast<size_t>(a.n);
+  return std::memcmp(a.pos, b.pos, 3 * n * sizeof(double)) == 0 &&
+         std::memcmp(a.axis, b.axis, 3 * n * sizeof(double)) == 0 &&
+         std::memcmp(a.vol, b.vol, n * sizeof(double)) == 0;
+}
+
 // Checks the lysosome descriptions of kmc_create and kmc_mean_run; *N = NPs.
 kmc_status validate_lysosomes(const kmc_lysosome *lys, int32_t n_lys, long long *N_out) {
   long long N = 0;
@@ -800,6 +861,13 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
   c->fp32 = prec == KMC_FP32_MIXED;
   c->n_lys = n_lys;
   c->N = N;
+  // sets of k identical consecutive lysosomes (replicas per lane, FP32)
+  for (int k = 2; k <= 4; k += 2) {
+    bool ok = c->fp32 && n_lys % k == 0;
+    for (int l = 0; ok && l < n_lys; ++l)
+      if (l % k != 0) ok = same_lysosome(lys[l], lys[l - 1]);
+    c->rep_ok[k] = ok;
+  }
   c->vbytes = c->fp32 ? sizeof(float4) : sizeof(dbl4);
   long long nrec = 0;
   for (int l = 0; l < n_lys; ++l) nrec += c->fp32 ? (lys[l].n + 1) / 2 : lys[l].n;
@@ -952,11 +1020,33 @@ kmc_status kmc_targets_per_lane(kmc_ctx *c, int32_t tpl, int32_t *tpl_out) {
       return fail(KMC_EINVAL, "targets per lane: 0 (autotuned), 1, 2 or 3");
     if (tpl > 1 && !c->fp32)
       return fail(KMC_EINVAL, "two or three targets per lane run on FP32 contexts");
+    if (tpl > 1 && c->rpl_mode > 1)
+      return fail(KMC_EINVAL, "replicas per lane run one target per lane");
     c->tpl_mode = tpl;
     // a pinned choice applies to the shape in use; 0 leaves it to the autotuner
-    if (tpl != 0 && c->shape.warps != 0) c->shape.tpl = tpl;
+    if (tpl != 0 && c->shape.warps != 0 && c->shape.rpl == 1) c->shape.tpl = tpl;
   }
   if (tpl_out) *tpl_out = c->tpl_mode != 0 ? c->tpl_mode : (c->shape.warps ? c->shape.tpl : 0);
+  return KMC_OK;
+}
+
+kmc_status kmc_replicas_per_lane(kmc_ctx *c, int32_t rpl, int32_t *rpl_out) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (rpl != -1) {
+    if (rpl != 0 && rpl != 1 && rpl != 2 && rpl != 4)
+      return fail(KMC_EINVAL, "replicas per lane: 0 (autotuned), 1 (off), 2 or 4");
+    if (rpl > 1 && !c->fp32) return fail(KMC_EINVAL, "replicas per lane run on FP32 contexts");
+    if (rpl > 1 && !c->rep_ok[rpl])
+      return fail(KMC_EINVAL, "the lysosomes do not form sets of %d identical consecutive ones",
+                  rpl);
+    if (rpl > 1 && c->tpl_mode > 1)
+      return fail(KMC_EINVAL, "replicas per lane run one target per lane");
+    c->rpl_mode = rpl;
+    // a change drops the shape in use: the next run or step tunes, or takes kmc_tuning's
+    if (c->shape.warps != 0 && c->shape.rpl != (rpl > 1 ? rpl : 1) && rpl != 0)
+      c->shape = Shape();
+  }
+  if (rpl_out) *rpl_out = c->rpl_mode != 0 ? c->rpl_mode : (c->shape.warps ? c->shape.rpl : 0);
   return KMC_OK;
 }
 
@@ -973,11 +1063,15 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
     s.tile = tile;
     s.chunk = chunk;
     s.tpl = c->tpl_mode != 0 ? c->tpl_mode : 1;
+    s.rpl = c->rpl_mode > 1 ? c->rpl_mode : 1;
     if (!shape_ok(c, s))
       return fail(KMC_EINVAL,
-                  "bad shape: warps in {4, 8, 16}, tile a power of two in [32, %d], chunk a "
-                  "multiple of 64",
-                  max_tile(c->fp32, warps == 4 || warps == 8 || warps == 16 ? warps : 4));
+                  s.rpl > 1 ? "bad shape: with %d replicas per lane, warps = %d, tile a power of two "
+                              "in [32, 128], chunk a multiple of 64"
+                            : "bad shape: warps in {4, 8, 16}, tile a power of two in [32, %d], "
+                              "chunk a multiple of 64",
+                  s.rpl > 1 ? s.rpl : max_tile(c->fp32, warps == 4 || warps == 8 || warps == 16 ? warps : 4),
+                  s.rpl);
     c->shape = s;
   }
   if (warps_out) *warps_out = c->shape.warps;
@@ -1230,7 +1324,7 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
   a.dbg.u = c->d_dbg + 6 * N;
   a.dbg.flags = c->d_dbg_flags;
   KMC_CUDA(kmc::launch_step(c->fp32, c->shape.warps, c->shape.tile, a, c->n_items, c->stream,
-                            false, c->shape.tpl));
+                            false, c->shape.tpl, c->shape.rpl));
   KMC_TRY(check_device_error(c));
   std::vector<double> h(7 * N);
   std::vector<int32_t> hf(N);

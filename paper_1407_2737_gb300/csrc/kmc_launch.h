@@ -10,19 +10,22 @@ namespace kmc {
 
 // Dynamic shared memory of one block of the fused step kernel (tpl: targets
 // per lane, 2 for the FP32 two-target kernel).
-size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl = 1);
+size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl = 1, int rpl = 1);
 
 // One time step of every work item (lysosome, 32 targets) on stream st.
 // warps in {4, 8, 16}; tile = sources per staged tile. With pdl the launch
 // may overlap the tail of the previous kernel on st (programmatic dependent
 // launch); the kernel waits for that kernel before it reads any state.
 // tpl = 2 or 3 (FP32 only): items are 64- or 96-target groups, two or three
-// targets per lane.
+// targets per lane. rpl = 2 or 4 (FP32 only, tpl = 1, warps = rpl): each item
+// is 32 targets of rpl replica lysosomes it.l .. it.l + rpl - 1 that share
+// their geometry (kmc_step_f32_rep).
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
-                        cudaStream_t st, bool pdl = false, int tpl = 1);
+                        cudaStream_t st, bool pdl = false, int tpl = 1, int rpl = 1);
 
 // Blocks of the step kernel of this shape that fit on one SM at once.
-cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int *blocks);
+cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int *blocks,
+                               int rpl = 1);
 
 // The Ref. [8] mode over all items of a (one warp per item).
 cudaError_t launch_mean(const MeanArgs &a, cudaStream_t st);

@@ -165,6 +165,52 @@ __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<
   }
 }
 
+// Scan of step iv by one warp alone (the replica kernel gives each warp its own
+// targets): lane = target, the lane walks all 200 nodes in segments of
+// kMaxSeg, with the same evaluations as segment_scan (same bits), and keeps its
+// own bracket count, so its brackets land in grid order.
+template <typename R>
+__device__ __forceinline__ void lane_scan(EpiShared<R> &sm, const GridTables<R> &tab, int lane,
+                                          int nt) {
+  if (lane >= nt) return;
+  const R k2 = sm.k2[lane], bc = sm.bc[lane], bs = sm.bs[lane];
+  auto d1 = [&](int j) {
+    const auto sc = tab.sc[j];
+    return profile_d1(k2, bc, bs, sc.x, sc.y);
+  };
+  constexpr int kBatch = 13;
+  int cnt = 0;
+#pragma unroll 1
+  for (int j0 = 0; j0 < kGrid; j0 += kMaxSeg) {
+    const int len = min(kMaxSeg, kGrid - j0);
+    unsigned long long neg = 0;
+#pragma unroll 1
+    for (int q0 = 0; q0 <= len; q0 += kBatch) {
+      unsigned bits = 0;
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        int j = j0 + q0 + u;
+        j = j < kGrid ? j : j - kGrid;
+        bits |= static_cast<unsigned>(d1(j) < R(0)) << u;
+      }
+      neg |= static_cast<unsigned long long>(bits) << q0;
+    }
+    unsigned long long chg = (neg ^ (neg >> 1)) & ((1ull << len) - 1);
+    while (chg) {
+      const int q = __ffsll(static_cast<long long>(chg)) - 1;
+      chg &= chg - 1;
+      const int j = j0 + q;
+      if (cnt < 4) {
+        sm.ju[lane][cnt] = j;
+        sm.du[lane][cnt] = d1(j);
+        sm.duh[lane][cnt] = d1(j + 1 < kGrid ? j + 1 : 0);
+      }
+      ++cnt;
+    }
+  }
+  sm.cnt[lane] = cnt;
+}
+
 // FP32 rounding can flip the sign of de/dth at a node where it nearly vanishes
 // (a near-double root just before a well disappears), which adds two sign
 // changes. A target whose FP32 scan counts more than four is scanned again by
@@ -441,15 +487,20 @@ __device__ __forceinline__ TargetIn<V> load_target(const StepArgs &a, const LysD
 
 // Steps iii-vii for the block's targets; sm.h holds their dipolar fields and
 // warp 0 holds their inputs in tin. V = float4 (mixed) or dbl4 (plain).
-template <typename V, bool MIXED>
+//
+// WARP: the steps are run by the calling warp alone, on its own update state
+// (the replica kernel, where every warp updates another lysosome): its lanes
+// scan the whole grid for their targets and each lane refines its own
+// brackets. The results are the same bits as the block's.
+template <typename V, bool MIXED, bool WARP = false>
 __device__ __forceinline__ void block_update(
     const StepArgs &a, const LysDev &L, const Item &it, long long step, int rec,
     const TargetIn<V> &tin,
     EpiShared<typename std::conditional<MIXED, float, double>::type> &sm,
     const GridTables<typename std::conditional<MIXED, float, double>::type> &tab) {
   using R = typename std::conditional<MIXED, float, double>::type;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
+  const int warp = WARP ? 0 : threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = WARP ? 1 : blockDim.x >> 5;
   const int nt = it.nt;
   const double bext = L.bmax * a.cos_k;
   TargetState<R> st;
@@ -465,26 +516,42 @@ __device__ __forceinline__ void block_update(
     sm.bs[lane] = st.bmag * st.sphi;
     sm.cnt[lane] = 0;
   }
-  __syncthreads();
-  // iv) scan: lanes over targets, warps over segments of the grid
-  segment_scan<R>(sm, tab, warp, nw, lane, nt);
-  __syncthreads();
   bool noisy = false;  // warp 0: this lane's target was scanned again in FP64
-  if constexpr (MIXED) {
-    noisy = warp == 0 && lane < nt && (sm.cnt[lane] > 4 || a.force_rescan);
-    if (__syncthreads_or(noisy)) {
+  if constexpr (WARP) {
+    __syncwarp();
+    // iv) scan and Newton, each lane for its own target
+    lane_scan<R>(sm, tab, lane, nt);
+    if constexpr (MIXED) {
+      noisy = lane < nt && (sm.cnt[lane] > 4 || a.force_rescan);
       if (noisy) rescan_fp64(sm, lane);
-      __syncthreads();
     }
+    if (lane < nt) {
+      const int nb = min(sm.cnt[lane], 4);
+#pragma unroll 1
+      for (int q = 0; q < nb; ++q) refine_bracket<R>(sm, tab, lane, q, nb, a.err);
+    }
+    __syncwarp();
+  } else {
+    __syncthreads();
+    // iv) scan: lanes over targets, warps over segments of the grid
+    segment_scan<R>(sm, tab, warp, nw, lane, nt);
+    __syncthreads();
+    if constexpr (MIXED) {
+      noisy = warp == 0 && lane < nt && (sm.cnt[lane] > 4 || a.force_rescan);
+      if (__syncthreads_or(noisy)) {
+        if (noisy) rescan_fp64(sm, lane);
+        __syncthreads();
+      }
+    }
+    // iv) Newton: one bracket per thread
+    for (int x = threadIdx.x; x < 4 * nt; x += blockDim.x) {
+      const int t = x >> 2, q = x & 3;
+      const int nb = min(sm.cnt[t], 4);
+      if (q < nb) refine_bracket<R>(sm, tab, t, q, nb, a.err);
+    }
+    __syncthreads();
+    if (warp != 0) return;
   }
-  // iv) Newton: one bracket per thread
-  for (int x = threadIdx.x; x < 4 * nt; x += blockDim.x) {
-    const int t = x >> 2, q = x & 3;
-    const int nb = min(sm.cnt[t], 4);
-    if (q < nb) refine_bracket<R>(sm, tab, t, q, nb, a.err);
-  }
-  __syncthreads();
-  if (warp != 0) return;
   // v-vii) decision and outputs (warp 0)
   const bool active = lane < nt;
   const double u = tin.u;
@@ -1018,6 +1085,192 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
 }
 
 // ---------------------------------------------------------------------------
+// FP32-mixed step for RPL replicas: consecutive lysosomes l, l + 1, ..., l +
+// RPL - 1 that share their geometry and material (the same NPs, axes and
+// volumes; seeds of one sample) and differ only in their random streams,
+// amplitudes and moments. The block has RPL warps and takes 32 targets of
+// every replica. Each staged record's geometry (d, r^2, rsqrt, q^2, q^3) is
+// formed once and serves all replicas, which add only their own terms
+// u = (t.d) q^2 and q^3 (u d + n): 8 + 10 RPL packed operations per record and
+// target instead of 18 RPL. Every replica's sums are formed by the same
+// operations in the same order as in kmc_step_f32 with RPL warps, and warp r
+// combines replica r's warp sums and source parts in kmc_step_f32's order, so
+// each replica's field, and its whole step, are the bits it gets alone. Warp r
+// then runs replica r's steps iii-vii by itself (the warps in parallel).
+template <bool MASK, int RPL>
+__device__ __forceinline__ void pair_tile_f32_rep(const ulonglong2 *__restrict__ sp,
+                                                  size_t rstride, int cnt, int first, f2 X,
+                                                  f2 Y, f2 Z, AccF32 (&acc)[RPL]) {
+#pragma unroll 1
+  for (int r = first; r < cnt; r += RPL) {
+    ulonglong2 a0, b0, c0, d0;
+    f2 e0;
+    load_record(sp, r, a0, b0, c0, d0, e0);
+    const f2 dx = sub2(a0.x, X), dy = sub2(a0.y, Y), dz = sub2(b0.x, Z);
+    const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    float r2l, r2h;
+    upk(r2, r2l, r2h);
+    float il = rsqrt_approx(r2l), ih = rsqrt_approx(r2h);
+    if (MASK) {
+      il = (r2l > 0.0f) ? il : 0.0f;
+      ih = (r2h > 0.0f) ? ih : 0.0f;
+    }
+    const f2 q = pk(il, ih);
+    const f2 q2 = mul2(q, q);
+    const f2 q3 = mul2(q, q2);
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      // replica k's moment words of the same record: z | nx, ny | nz, tx | ty, tz | -
+      const ulonglong2 *p = sp + k * rstride + kRecU2 * r;
+      const ulonglong2 b = p[1], c = p[2], d = p[3];
+      const f2 e = reinterpret_cast<const f2 *>(p + 4)[0];
+      const f2 u = mul2(fma2(e, dz, fma2(d.y, dy, mul2(d.x, dx))), q2);
+      acc[k].x = fma2(q3, fma2(u, dx, b.y), acc[k].x);
+      acc[k].y = fma2(q3, fma2(u, dy, c.x), acc[k].y);
+      acc[k].z = fma2(q3, fma2(u, dz, c.y), acc[k].z);
+    }
+  }
+}
+
+// Dynamic shared memory of the replica kernel after its pair loop: the warps'
+// (sum, -error) pairs of every replica, then every replica's update state.
+constexpr size_t epi_bytes_rep(int rpl) {
+  return static_cast<size_t>(rpl) * 6 * rpl * kTargets * sizeof(float) +
+         static_cast<size_t>(rpl) * sizeof(EpiShared<float>) + 64;
+}
+
+template <int RPL>
+__global__ void __launch_bounds__(RPL * 32) kmc_step_f32_rep(const StepArgs a, int tile) {
+  static_assert(RPL == 2 || RPL == 4, "two or four replicas per lane");
+  constexpr int NW = RPL;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *dyn = smem + 16;
+  __shared__ int s_last;
+  __shared__ GridTables<float> tab;
+  tab.load();
+  if (!item_in_bounds(a, 1, true)) return;
+  const Item it = a.items[blockIdx.x];  // it.l: the first replica
+  if (!KMC_DCHECK(it.l + RPL <= a.n_lys, a.err, kSiteLys)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const LysDev L0 = a.lys[it.l];
+  const LysDev Lw = a.lys[it.l + warp];  // the replica this warp updates
+  const float4 pi = static_cast<const float4 *>(a.pos)[L0.off + it.t0 + min(lane, it.nt - 1)];
+  grid_dependency_wait();
+  const long long step = a.rs->step_base + a.k_local;
+  const int per = a.rs->period;
+  const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
+  const int par = static_cast<int>(step & 1);
+  const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]);
+
+  Item iw = it;
+  iw.l = it.l + warp;
+  const TargetIn<float4> tin = load_target<float4>(a, Lw, iw, step, lane);
+  const f2 X = pk(pi.x, pi.x), Y = pk(pi.y, pi.y), Z = pk(pi.z, pi.z);
+  float sk[3 * RPL], ck[3 * RPL];  // Kahan sums: replica k, component c at 3 k + c
+#pragma unroll
+  for (int c = 0; c < 3 * RPL; ++c) sk[c] = ck[c] = 0.f;
+  const int nrec = it.j1 - it.j0;
+  const int ntiles = (nrec + tile - 1) / tile;
+  const int own0 = it.t0 >> 1, own1 = (it.t0 + it.nt - 1) >> 1;  // records holding targets
+  ulonglong2 *buf = reinterpret_cast<ulonglong2 *>(dyn);  // [2][RPL][tile][kRecU2]
+  const size_t rstride = static_cast<size_t>(tile) * kRecU2;
+  auto issue = [&](int t) {
+    const int b = t & 1;
+    const int r0 = it.j0 + t * tile;
+    const int cnt = min(tile, it.j1 - r0);
+    if (!tile_in_bounds(a, it, r0, cnt, tile)) {
+      mbar_expect_tx(&bar[b], 0);  // no copy: the phase completes, the error is set
+      return;
+    }
+    const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
+    mbar_expect_tx(&bar[b], RPL * bytes);
+#pragma unroll 1
+    for (int k = 0; k < RPL; ++k)
+      bulk_g2s(buf + (static_cast<size_t>(b) * RPL + k) * rstride,
+               gsrc + a.lys[it.l + k].roff + r0, bytes, &bar[b]);
+  };
+  auto body = [&](int b, int t) {
+    const int r0 = it.j0 + t * tile;
+    const int cnt = min(tile, it.j1 - r0);
+    const bool mask = (r0 <= own1) && (own0 < r0 + cnt);
+    const ulonglong2 *sp = buf + static_cast<size_t>(b) * RPL * rstride;
+    AccF32 acc[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) acc[k].x = acc[k].y = acc[k].z = 0ull;
+    if (mask)
+      pair_tile_f32_rep<true, RPL>(sp, rstride, cnt, warp, X, Y, Z, acc);
+    else
+      pair_tile_f32_rep<false, RPL>(sp, rstride, cnt, warp, X, Y, Z, acc);
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      kahan_add(sk[3 * k + 0], ck[3 * k + 0], hsum(acc[k].x));
+      kahan_add(sk[3 * k + 1], ck[3 * k + 1], hsum(acc[k].y));
+      kahan_add(sk[3 * k + 2], ck[3 * k + 2], hsum(acc[k].z));
+    }
+  };
+  if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
+
+  // cross-warp combine in kmc_step_f32's order; warp k combines replica k
+  constexpr int kW = 6 * RPL;
+  float *wp = reinterpret_cast<float *>(dyn);  // [NW][6 RPL][32]: 3 RPL sums, then 3 RPL errors
+#pragma unroll
+  for (int c = 0; c < 3 * RPL; ++c) {
+    wp[(warp * kW + c) * 32 + lane] = sk[c];
+    wp[(warp * kW + 3 * RPL + c) * 32 + lane] = -ck[c];
+  }
+  __syncthreads();
+  EpiShared<float> *sms =
+      reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * kW * 32 * 4);
+  EpiShared<float> &sm = sms[warp];
+  float hi[3], lo[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float s = 0.f, e = 0.f;
+    for (int w = 0; w < NW; ++w) {
+      neumaier_add(s, e, wp[(w * kW + 3 * warp + c) * 32 + lane]);
+      e += wp[(w * kW + 3 * RPL + 3 * warp + c) * 32 + lane];
+    }
+    hi[c] = s;
+    lo[c] = e;
+  }
+  if (it.nsplit > 1) {
+    // replica k's partials at k kPartF32, each laid out as kmc_step_f32's
+    float *part = a.partial + (static_cast<size_t>(blockIdx.x) * RPL + warp) * kPartF32;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      __stcg(part + c * 32 + lane, hi[c]);
+      __stcg(part + (3 + c) * 32 + lane, lo[c]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
+    __syncthreads();
+    if (!s_last) return;  // another item of the group finishes the step
+    __threadfence();
+    const float *base = a.partial + (static_cast<size_t>(blockIdx.x - it.split) * RPL + warp) *
+                                        kPartF32;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float s = 0.f, e = 0.f;
+      for (int q = 0; q < it.nsplit; ++q) {
+        neumaier_add(s, e, __ldcg(base + q * RPL * kPartF32 + c * 32 + lane));
+        e += __ldcg(base + q * RPL * kPartF32 + (3 + c) * 32 + lane);
+      }
+      hi[c] = s;
+      lo[c] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) sm.h[c][lane] = hi[c] + lo[c];  // compensation added last
+  __syncwarp();
+  block_update<float4, true, true>(a, Lw, iw, step, rec, tin, sm, tab);
+  grid_launch_dependents();
+}
+
+// ---------------------------------------------------------------------------
 // FP64-plain step kernel (same structure, scalar FP64 pair loop).
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int tile) {
@@ -1130,7 +1383,12 @@ __global__ void kmc_advance_kernel(RunState *rs, int S) {
 // ---------------------------------------------------------------------------
 // Host side of the launches.
 
-size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl) {
+size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl, int rpl) {
+  if (prec_fp32 && rpl > 1) {
+    const size_t stage = 2 * static_cast<size_t>(rpl) * tile * sizeof(SrcPair);
+    const size_t epi = epi_bytes_rep(rpl);
+    return 16 + (stage > epi ? stage : epi);
+  }
   const size_t stage = prec_fp32 ? 2 * static_cast<size_t>(tile) * sizeof(SrcPair)
                                  : 4 * static_cast<size_t>(tile) * sizeof(dbl4);
   const size_t epi = !prec_fp32 ? epi_bytes<double>(warps)
@@ -1177,8 +1435,17 @@ static cudaError_t launch_f64(const StepArgs &a, int n_items, int tile, cudaStre
 }
 
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
-                        cudaStream_t st, bool pdl, int tpl) {
+                        cudaStream_t st, bool pdl, int tpl, int rpl) {
   if (n_items <= 0) return cudaSuccess;
+  if (rpl > 1) {
+    if (!prec_fp32 || tpl != 1 || warps != rpl) return cudaErrorInvalidValue;
+    const size_t smem = step_smem_bytes(1, warps, tile, 1, rpl);
+    if (rpl == 2)
+      return launch_items(kmc_step_f32_rep<2>, a, n_items, 64, smem, tile, st, pdl);
+    if (rpl == 4)
+      return launch_items(kmc_step_f32_rep<4>, a, n_items, 128, smem, tile, st, pdl);
+    return cudaErrorInvalidValue;
+  }
   if (prec_fp32) {
     switch (warps) {
       case 4: return launch_f32<4>(a, n_items, tile, st, pdl, tpl);
@@ -1201,10 +1468,17 @@ static cudaError_t occupancy(K kernel, int threads, size_t smem, int *blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, threads, smem);
 }
 
-cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int *blocks) {
+cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int *blocks,
+                               int rpl) {
   *blocks = 0;
-  const size_t smem = step_smem_bytes(prec_fp32, warps, tile, tpl);
+  const size_t smem = step_smem_bytes(prec_fp32, warps, tile, tpl, rpl);
   const int th = warps * 32;
+  if (prec_fp32 && rpl > 1) {
+    if (warps != rpl) return cudaErrorInvalidValue;
+    if (rpl == 2) return occupancy(kmc_step_f32_rep<2>, th, smem, blocks);
+    if (rpl == 4) return occupancy(kmc_step_f32_rep<4>, th, smem, blocks);
+    return cudaErrorInvalidValue;
+  }
   if (prec_fp32 && tpl == 2) {
     switch (warps) {
       case 4: return occupancy(kmc_step_f32_tn<4, 2>, th, smem, blocks);
@@ -1296,6 +1570,8 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<4, 3>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<8, 3>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<16, 3>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<2>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<16>);

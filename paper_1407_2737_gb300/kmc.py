@@ -34,7 +34,8 @@ EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_debug_step", "kmc_save", "kmc_load", "kmc_info", "kmc_tuning", "kmc_destroy",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
            "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall",
-           "kmc_regenerate_rsa", "kmc_targets_per_lane", "kmc_plan_items")
+           "kmc_regenerate_rsa", "kmc_targets_per_lane", "kmc_plan_items",
+           "kmc_replicas_per_lane")
 KMC_NOALLOC_MAX_N = 8192
 KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
 KMC_ITEM_FIELDS = 8  # per work item in kmc_plan_items
@@ -99,6 +100,7 @@ def lib():
                                          C.c_uint32]
             L.kmc_debug_stall.argtypes = [vp]
             L.kmc_targets_per_lane.argtypes = [vp, C.c_int32, _I32]
+            L.kmc_replicas_per_lane.argtypes = [vp, C.c_int32, _I32]
             L.kmc_plan_items.argtypes = [_I32, C.c_int32, C.c_int, C.c_int32, C.c_int32,
                                          C.c_int32, C.c_int32, _I32, C.c_int64, _I64, _I32,
                                          _I32]
@@ -236,6 +238,15 @@ def kmc_targets_per_lane(ctx, tpl=None):
     t = C.c_int32()
     _check(lib().kmc_targets_per_lane(ctx.handle, -1 if tpl is None else int(tpl), C.byref(t)))
     return int(t.value)
+
+
+def kmc_replicas_per_lane(ctx, rpl=None):
+    """Pins the FP32 kernel's replicas per lane (1 = off, 2 or 4 for sets of
+    identical consecutive lysosomes; 0 = autotuned) or, with no argument,
+    returns the value in use."""
+    r = C.c_int32()
+    _check(lib().kmc_replicas_per_lane(ctx.handle, -1 if rpl is None else int(rpl), C.byref(r)))
+    return int(r.value)
 
 
 def kmc_debug_stall(ctx):

@@ -50,7 +50,8 @@ def test_traffic_figures_come_from_committed_profiles():
     prof = os.path.join(ROOT, "profiles")
     text = "".join(open(os.path.join(prof, f)).read() for f in sorted(os.listdir(prof)))
     assert bench.STEP_DRAM_BYTES
-    for (cfg, warps, tile, chunk, tpl), nbytes in bench.STEP_DRAM_BYTES.items():
+    for (cfg, warps, tile, chunk, tpl, rpl), nbytes in bench.STEP_DRAM_BYTES.items():
         assert cfg == "c1" or cfg in bench.CONFIGS, cfg
-        assert warps in (4, 8, 16) and tile & (tile - 1) == 0 and chunk % 64 == 0 and tpl in (1, 2)
+        assert tile & (tile - 1) == 0 and chunk % 64 == 0 and tpl in (1, 2, 3)
+        assert (warps in (4, 8, 16) and rpl == 1) or (rpl in (2, 4) and warps == rpl)
         assert "%.4g MB" % (nbytes / 1e6) in text, (cfg, nbytes)
