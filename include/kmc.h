@@ -195,9 +195,12 @@ kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
  * per lane), 2 or 3 (64 or 96 targets, two or three per lane, so that each
  * staged source record feeds that many independent chains; FP32 contexts only,
  * KMC_EINVAL on FP64). All give the same bits at the same warps, tile and
- * chunk. 0 (the default) lets the autotuner choose; a pinned value also
- * applies to a shape set by kmc_tuning. The value in use (0 before the first
- * tuning) is returned through tpl_out (may be NULL); tpl = -1 only reads it. */
+ * chunk. In the symmetric pair form (kmc_pair_form) a lane holds 2 or 4
+ * targets (one or two cells of 64 NPs per warp); 4 selects that form, and
+ * 1 or 3 are refused while it is pinned. 0 (the default) lets the autotuner
+ * choose; a pinned value also applies to a shape set by kmc_tuning. The value
+ * in use (0 before the first tuning) is returned through tpl_out (may be
+ * NULL); tpl = -1 only reads it. */
 kmc_status kmc_targets_per_lane(kmc_ctx *ctx, int32_t tpl, int32_t *tpl_out);
 
 /* Replicas per lane of the FP32 step kernel. When the lysosomes come in sets
@@ -218,6 +221,52 @@ kmc_status kmc_targets_per_lane(kmc_ctx *ctx, int32_t tpl, int32_t *tpl_out);
  * the first tuning) is returned through rpl_out (may be NULL); rpl = -1 only
  * reads it. */
 kmc_status kmc_replicas_per_lane(kmc_ctx *ctx, int32_t rpl, int32_t *rpl_out);
+
+/* Pair form of the FP32 dipolar sum (Eq. 1, Sec. II.1 step ii).
+ *   1 ordered: every (target, source) pair is evaluated for its target, by
+ *     the step kernels (one launch per step and chain).
+ *   2 symmetric: the pair term of Eq. 1 is symmetric in its geometry (the
+ *     separation, the distance and its powers are the same for T_ij and
+ *     T_ji), so every unordered pair is formed once and serves both NPs. A
+ *     lysosome's NPs are cut into cells of 64; the pairs between a row group
+ *     of cells (4 or 8 cells: warps x cells per warp) and the cells above it
+ *     run in the symmetric field kernel, the pairs inside a row group in the
+ *     ordered form; an update kernel then adds the partial sums in a fixed
+ *     order and runs steps iii-vii (two launches per step and chain). The
+ *     fields differ from the ordered form's by rounding only; results are
+ *     deterministic and do not depend on the chaining.
+ * form: 0 lets the autotuner choose (the default: it times both forms on
+ * FP32 contexts), 1 or 2 pins one (2: KMC_EINVAL on FP64 contexts, with
+ * replicas per lane pinned, or with 1 or 3 targets per lane pinned). A pinned
+ * symmetric form reads kmc_tuning's warps (4; 8 with 2 targets per lane; 2
+ * with 4) and chunk (source NPs per field item, a multiple of 64; 0 = all cells above
+ * the row group); its tile is 32. The form in use (0 before the first
+ * tuning) is returned through form_out (may be NULL); form = -1 only reads it. */
+kmc_status kmc_pair_form(kmc_ctx *ctx, int32_t form, int32_t *form_out);
+
+/* Fields of one field item and of one update item in kmc_plan_sym's output. */
+#define KMC_SYM_FIELDS 8
+
+/* The symmetric form's work decomposition (kmc_pair_form) for lysosomes of
+ * n[l] NPs (host arrays), computed on the host with no GPU, for tests and
+ * tools. gc: cells (64 NPs) per row group, 4 or 8; src_cells: source cells
+ * per field item (0 = all cells above the row group). Lysosomes come largest
+ * first (stable); per lysosome its row groups in order, each as its diagonal
+ * item and then its source ranges in order. items_out (capacity cap items):
+ * lysosome, row group, first and end source cell (-1, -1 for the diagonal
+ * item), forward slot, first reverse slot of the lysosome, 0, 0. upd_out
+ * (capacity cap_upd): lysosome, first target, targets (<= 32, inside one
+ * cell), first forward slot and count (the row group's items), first reverse
+ * slot and count (one per row group below the cell), first target minus the
+ * row group's first NP. *n_items, *n_upd and *n_rev (reverse slots) receive
+ * the counts (also on KMC_ECAPACITY). chain_cut_items and chain_cut_upd
+ * (KMC_MAX_CHAINS + 1 int32 each): chain q runs field items
+ * chain_cut_items[q] .. chain_cut_items[q + 1] - 1 and the matching update
+ * items; *n_chains receives the chain count. Bad arguments: KMC_EINVAL. */
+kmc_status kmc_plan_sym(const int32_t *n, int32_t n_lys, int32_t gc, int32_t src_cells,
+                        int32_t *items_out, int64_t cap, int64_t *n_items, int32_t *upd_out,
+                        int64_t cap_upd, int64_t *n_upd, int64_t *n_rev,
+                        int32_t *chain_cut_items, int32_t *chain_cut_upd, int32_t *n_chains);
 
 /* Fields of one work item in kmc_plan_items' output. */
 #define KMC_ITEM_FIELDS 8

@@ -137,6 +137,96 @@ __global__ void __launch_bounds__(kWarps * 32)
   rev[(base + lane) * 3 + 2] = rz;
 }
 
+// Symmetric pairs on packed records: warp w of block b holds TPL x 32 targets
+// (lane L: targets L, 32 + L, ...) and 32 source records (64 sources) of the
+// library's layout in shared memory. At step s lane L reads record
+// (L + s) mod 32 and forms, per target, the geometry of its two pairs once
+// (8 packed operations, 2 rsqrt), the forward terms into the target's sums
+// (10) and the reverse terms into the record's two reverse sums (10): 28 packed
+// operations per four ordered pairs. The reverse sums (3 packed registers)
+// move one lane per step (6 shuffles), so that after 32 steps lane L holds
+// record L's. The reverse term of target i at source j is q^3 (v d + n_i)
+// with v = (t_i . d) q^2 and d = r_j - r_i, as -d enters it twice.
+template <int TPL>
+__global__ void __launch_bounds__(kWarps * 32)
+    symmetric_packed(const SrcPair *__restrict__ rec, const Np *__restrict__ tgt, int reps,
+                     float *__restrict__ fwd, float *__restrict__ rev) {
+  __shared__ __align__(16) ulonglong2 sm[kWarps * 32 * kRecU2];
+  const ulonglong2 *g =
+      reinterpret_cast<const ulonglong2 *>(rec) + static_cast<size_t>(blockIdx.x) * kWarps * 32 * kRecU2;
+  for (int i = threadIdx.x; i < kWarps * 32 * kRecU2; i += blockDim.x) sm[i] = g[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const ulonglong2 *my = sm + warp * 32 * kRecU2;
+  const size_t tb = (static_cast<size_t>(blockIdx.x) * kWarps + warp) * 32 * TPL;
+  f2 X[TPL], Y[TPL], Z[TPL], TX[TPL], TY[TPL], TZ[TPL], NX[TPL], NY[TPL], NZ[TPL];
+  AccF32 acc[TPL];
+#pragma unroll
+  for (int k = 0; k < TPL; ++k) {
+    const Np q = tgt[tb + k * 32 + lane];
+    X[k] = pk(q.x, q.x);
+    Y[k] = pk(q.y, q.y);
+    Z[k] = pk(q.z, q.z);
+    TX[k] = pk(q.tx, q.tx);
+    TY[k] = pk(q.ty, q.ty);
+    TZ[k] = pk(q.tz, q.tz);
+    NX[k] = pk(q.nx, q.nx);
+    NY[k] = pk(q.ny, q.ny);
+    NZ[k] = pk(q.nz, q.nz);
+    acc[k].x = acc[k].y = acc[k].z = 0ull;
+  }
+  f2 rx = 0ull, ry = 0ull, rz = 0ull;
+  for (int rep = 0; rep < reps; ++rep) {
+#pragma unroll 2
+    for (int s = 0; s < 32; ++s) {
+      ulonglong2 a, b, c, d;
+      f2 e;
+      load_record(my, (lane + s) & 31, a, b, c, d, e);
+#pragma unroll
+      for (int k = 0; k < TPL; ++k) {
+        const f2 dx = sub2(a.x, X[k]), dy = sub2(a.y, Y[k]), dz = sub2(b.x, Z[k]);
+        const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        float r2l, r2h;
+        upk(r2, r2l, r2h);
+        const f2 q = pk(rsqrt_approx(r2l), rsqrt_approx(r2h));
+        const f2 q2 = mul2(q, q);
+        const f2 q3 = mul2(q, q2);
+        const f2 u = mul2(fma2(e, dz, fma2(d.y, dy, mul2(d.x, dx))), q2);
+        acc[k].x = fma2(q3, fma2(u, dx, b.y), acc[k].x);
+        acc[k].y = fma2(q3, fma2(u, dy, c.x), acc[k].y);
+        acc[k].z = fma2(q3, fma2(u, dz, c.y), acc[k].z);
+        const f2 v = mul2(fma2(TZ[k], dz, fma2(TY[k], dy, mul2(TX[k], dx))), q2);
+        rx = fma2(q3, fma2(v, dx, NX[k]), rx);
+        ry = fma2(q3, fma2(v, dy, NY[k]), ry);
+        rz = fma2(q3, fma2(v, dz, NZ[k]), rz);
+      }
+      const int from = (lane + 1) & 31;
+      rx = __shfl_sync(0xffffffffu, rx, from);
+      ry = __shfl_sync(0xffffffffu, ry, from);
+      rz = __shfl_sync(0xffffffffu, rz, from);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < TPL; ++k) {
+    float *o = fwd + (tb + k * 32 + lane) * 3;
+    o[0] = hsum(acc[k].x);
+    o[1] = hsum(acc[k].y);
+    o[2] = hsum(acc[k].z);
+  }
+  // record `lane` of this warp: sources 2 lane and 2 lane + 1
+  float *o = rev + ((static_cast<size_t>(blockIdx.x) * kWarps + warp) * 64 + 2 * lane) * 3;
+  float lo, hi;
+  upk(rx, lo, hi);
+  o[0] = lo;
+  o[3] = hi;
+  upk(ry, lo, hi);
+  o[1] = lo;
+  o[4] = hi;
+  upk(rz, lo, hi);
+  o[2] = lo;
+  o[5] = hi;
+}
+
 // ---------------------------------------------------------------------------
 // Host: a fixed-seed generator (64-bit LCG, top 53 bits) and the FP64 definition.
 struct Rng {
@@ -265,6 +355,36 @@ int main() {
   for (auto &q : ssrc) make_np(q);
   for (auto &q : stgt) make_np(q);
 
+  // symmetric packed form: 32 records and up to 2 x 32 targets (Np) per warp
+  const size_t nprec = static_cast<size_t>(blocks) * kWarps * 32;
+  std::vector<SrcPair> prec(nprec);
+  std::vector<Np> ptgt(nprec * 4);
+  for (auto &r : prec)
+    for (int h = 0; h < 2; ++h) {
+      Np q;
+      make_np(q);
+      r.x[h] = q.x;
+      r.y[h] = q.y;
+      r.z[h] = q.z;
+      r.nx[h] = q.nx;
+      r.ny[h] = q.ny;
+      r.nz[h] = q.nz;
+      r.tx[h] = q.tx;
+      r.ty[h] = q.ty;
+      r.tz[h] = q.tz;
+      r.pad[h] = 0.f;
+    }
+  for (auto &q : ptgt) make_np(q);
+  SrcPair *d_prec = nullptr;
+  Np *d_ptgt = nullptr;
+  float *d_pfwd = nullptr, *d_prev = nullptr;
+  CHECK(cudaMalloc(&d_prec, sizeof(SrcPair) * nprec));
+  CHECK(cudaMalloc(&d_ptgt, sizeof(Np) * ptgt.size()));
+  CHECK(cudaMalloc(&d_pfwd, sizeof(float) * ptgt.size() * 3));
+  CHECK(cudaMalloc(&d_prev, sizeof(float) * nprec * 2 * 3));
+  CHECK(cudaMemcpy(d_prec, prec.data(), sizeof(SrcPair) * nprec, cudaMemcpyHostToDevice));
+  CHECK(cudaMemcpy(d_ptgt, ptgt.data(), sizeof(Np) * ptgt.size(), cudaMemcpyHostToDevice));
+
   SrcPair *d_rec = nullptr;
   float4 *d_tgt = nullptr;
   Np *d_ssrc = nullptr, *d_stgt = nullptr;
@@ -326,6 +446,36 @@ int main() {
     err[0] = max_rel(rboth, both);
   }
 
+  // symmetric packed, TPL = 1 and 2: block 0, warp 0 (32 records, 32 TPL targets)
+  double perr[5] = {0, 0, 0, 0, 0};
+  auto check_packed = [&](int tpl, auto kernel) -> double {
+    kernel<<<1, kWarps * 32>>>(d_prec, d_ptgt, 1, d_pfwd, d_prev);
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1.0;
+    std::vector<float> f(static_cast<size_t>(tpl) * 32 * 3), r(64 * 3);
+    cudaMemcpy(f.data(), d_pfwd, sizeof(float) * f.size(), cudaMemcpyDeviceToHost);
+    cudaMemcpy(r.data(), d_prev, sizeof(float) * r.size(), cudaMemcpyDeviceToHost);
+    std::vector<double> rf(f.size(), 0.0), rr(r.size(), 0.0);
+    for (int i = 0; i < 32 * tpl; ++i)
+      for (int j = 0; j < 64; ++j) {
+        const SrcPair &R = prec[j / 2];
+        const int h = j & 1;
+        const Np &t = ptgt[i];
+        const double sp[3] = {R.x[h], R.y[h], R.z[h]}, tp[3] = {t.x, t.y, t.z};
+        const double smv[3] = {-R.nx[h], -R.ny[h], -R.nz[h]}, tm[3] = {-t.nx, -t.ny, -t.nz};
+        term(sp, smv, tp, &rf[3 * i]);  // field at target i from source j
+        term(tp, tm, sp, &rr[3 * j]);   // field at source j from target i
+      }
+    std::vector<float> both(f);
+    both.insert(both.end(), r.begin(), r.end());
+    std::vector<double> rboth(rf);
+    rboth.insert(rboth.end(), rr.begin(), rr.end());
+    return max_rel(rboth, both);
+  };
+  perr[1] = check_packed(1, symmetric_packed<1>);
+  perr[2] = check_packed(2, symmetric_packed<2>);
+  perr[3] = check_packed(3, symmetric_packed<3>);
+  perr[4] = check_packed(4, symmetric_packed<4>);
+
   // --- timing ---
   auto report = [&](const char *name, double pairs, double t, double e) {
     std::printf("%s %.6e %.6f %.3e\n", name, pairs / t, 30.0 * pairs / t / peak, e);
@@ -344,6 +494,19 @@ int main() {
     auto LS = [&] { symmetric_pairs<<<blocks, kWarps * 32>>>(d_ssrc, d_stgt, reps, d_fwd, d_rev); };
     // each lane and step: one pair in both directions, two ordered pairs
     report("symmetric_lane_rotation", double(nsym) * 32 * reps * 2, time_launch(LS, iters), err[0]);
+    // each lane and step: TPL targets x 2 sources, both directions
+    auto P1 = [&] { symmetric_packed<1><<<blocks, kWarps * 32>>>(d_prec, d_ptgt, reps, d_pfwd, d_prev); };
+    report("symmetric_packed_1_target_per_lane", double(nprec) * 32 * reps * 4, time_launch(P1, iters),
+           perr[1]);
+    auto P2 = [&] { symmetric_packed<2><<<blocks, kWarps * 32>>>(d_prec, d_ptgt, reps, d_pfwd, d_prev); };
+    report("symmetric_packed_2_targets_per_lane", double(nprec) * 32 * reps * 8, time_launch(P2, iters),
+           perr[2]);
+    auto P3 = [&] { symmetric_packed<3><<<blocks, kWarps * 32>>>(d_prec, d_ptgt, reps, d_pfwd, d_prev); };
+    report("symmetric_packed_3_targets_per_lane", double(nprec) * 32 * reps * 12, time_launch(P3, iters),
+           perr[3]);
+    auto P4 = [&] { symmetric_packed<4><<<blocks, kWarps * 32>>>(d_prec, d_ptgt, reps, d_pfwd, d_prev); };
+    report("symmetric_packed_4_targets_per_lane", double(nprec) * 32 * reps * 16, time_launch(P4, iters),
+           perr[4]);
   }
   CHECK(cudaGetLastError());
   cudaFree(d_rec);
@@ -353,5 +516,9 @@ int main() {
   cudaFree(d_out);
   cudaFree(d_fwd);
   cudaFree(d_rev);
+  cudaFree(d_prec);
+  cudaFree(d_ptgt);
+  cudaFree(d_pfwd);
+  cudaFree(d_prev);
   return 0;
 }

@@ -117,9 +117,12 @@ struct Shape {
   int warps = 0, tile = 0, chunk = 0;
   int tpl = 1;  // targets per lane: 2 or 3 run 64- or 96-target groups (FP32 only)
   int rpl = 1;  // replicas per lane: 2 or 4 run replica lysosomes together (FP32, warps = rpl)
+  // symmetric pair form (FP32): cells per warp (1 or 2; tpl = 2 sym, tile = 32,
+  // chunk = source NPs per field item, 0 = a whole row); 0 = the ordered kernels
+  int sym = 0;
   bool operator==(const Shape &o) const {
     return warps == o.warps && tile == o.tile && chunk == o.chunk && tpl == o.tpl &&
-           rpl == o.rpl;
+           rpl == o.rpl && sym == o.sym;
   }
 };
 
@@ -127,9 +130,10 @@ struct TuneKey {
   int prec;
   long long N;
   int n_lys, max_n, tpl_mode, rpl_mode, reps;  // reps: replica sets available (bits)
+  int form_mode;
   bool operator<(const TuneKey &o) const {
-    return std::tie(prec, N, n_lys, max_n, tpl_mode, rpl_mode, reps) <
-           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode, o.reps);
+    return std::tie(prec, N, n_lys, max_n, tpl_mode, rpl_mode, reps, form_mode) <
+           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode, o.reps, o.form_mode);
   }
 };
 std::mutex g_tune_mu;
@@ -196,6 +200,16 @@ struct kmc_ctx {
   size_t arrivals_cap = 0;
   Shape items_shape;  // shape the items were built for
   std::vector<int> chain_cut;  // chain q runs items chain_cut[q] .. chain_cut[q + 1] - 1
+  // symmetric form: field and update items, their chains, the partial sums
+  kmc::SymItem *d_sitems = nullptr;
+  size_t sitems_cap = 0;
+  kmc::SymUpd *d_supd = nullptr;
+  size_t supd_cap = 0;
+  float *d_sfwd = nullptr, *d_srev = nullptr;
+  size_t sfwd_cap = 0, srev_cap = 0;  // floats
+  int n_sitems = 0, n_supd = 0;
+  std::vector<int> sym_cut_items, sym_cut_upd;
+  int form_mode = 0;           // pair form: 0 = the autotuner's choice, 1 = ordered, 2 = symmetric
   int tpl_mode = 0;            // targets per lane: 0 = the autotuner's choice, else 1, 2 or 3
   int rpl_mode = 0;            // replicas per lane: 0 = the autotuner's choice, 1 = off, 2 or 4
   bool rep_ok[5] = {};         // [k]: the lysosomes form sets of k identical consecutive ones
@@ -359,8 +373,132 @@ Plan plan_items(const std::vector<int> &np, bool fp32, int chunk, int blocks_per
   return p;
 }
 
+// The symmetric form's plan (kmc_field_sym, kmc_update_sym) for lysosomes of
+// np[l] NPs and row groups of gc cells; src_cells source cells per field item
+// (0: the whole range above the group). Lysosomes largest first; per
+// lysosome its row groups in order, each as its diagonal item followed by
+// its source ranges in order (the forward slots of a row group are
+// consecutive); then one update item per 32 targets. Chains are cut at
+// lysosome boundaries into runs of about equal pair counts, the field and
+// update lists at the same lysosomes.
+struct SymPlan {
+  std::vector<kmc::SymItem> items;
+  std::vector<kmc::SymUpd> upd;
+  std::vector<int> cut_items, cut_upd;
+  long long n_rev = 0;  // reverse slots (forward slots: one per item)
+};
+
+SymPlan plan_sym(const std::vector<int> &np, int gc, int src_cells) {
+  SymPlan p;
+  const int n_lys = static_cast<int>(np.size());
+  std::vector<int> order(n_lys);
+  for (int l = 0; l < n_lys; ++l) order[l] = l;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return np[x] > np[y]; });
+  const int chains = std::min(n_lys, kMaxChains);
+  double total = 0.0, acc = 0.0;
+  for (int l = 0; l < n_lys; ++l) total += static_cast<double>(np[l]) * np[l];
+  p.cut_items.assign(1, 0);
+  p.cut_upd.assign(1, 0);
+  for (int oi = 0; oi < n_lys; ++oi) {
+    const int l = order[oi], n = np[l];
+    const int nc = (n + kmc::kCell - 1) / kmc::kCell, ng = (nc + gc - 1) / gc;
+    const int rbase = static_cast<int>(p.n_rev);
+    p.n_rev += kmc::sym_rev_offset(nc, gc);
+    std::vector<int> g0(ng), gn(ng);
+    for (int g = 0; g < ng; ++g) {
+      g0[g] = static_cast<int>(p.items.size());
+      kmc::SymItem d{};
+      d.l = l;
+      d.g = g;
+      d.h0 = d.h1 = -1;
+      d.fwd = g0[g];
+      d.rbase = rbase;
+      p.items.push_back(d);
+      const int step = src_cells > 0 ? src_cells : nc;
+      for (int h0 = (g + 1) * gc; h0 < nc; h0 += step) {
+        kmc::SymItem it{};
+        it.l = l;
+        it.g = g;
+        it.h0 = h0;
+        it.h1 = std::min(nc, h0 + step);
+        it.fwd = static_cast<int>(p.items.size());
+        it.rbase = rbase;
+        p.items.push_back(it);
+      }
+      gn[g] = static_cast<int>(p.items.size()) - g0[g];
+    }
+    for (int t0 = 0; t0 < n; t0 += kmc::kTargets) {
+      const int h = t0 / kmc::kCell, g = h / gc;
+      kmc::SymUpd u{};
+      u.l = l;
+      u.t0 = t0;
+      u.nt = std::min(kmc::kTargets, n - t0);
+      u.fwd0 = g0[g];
+      u.nfwd = gn[g];
+      u.rev0 = rbase + kmc::sym_rev_offset(h, gc);
+      u.nrev = h / gc;
+      u.gt0 = t0 - g * gc * kmc::kCell;
+      p.upd.push_back(u);
+    }
+    acc += static_cast<double>(n) * n;
+    const int q = static_cast<int>(p.cut_items.size());
+    if (oi + 1 < n_lys && q < chains && acc * chains >= total * q) {
+      p.cut_items.push_back(static_cast<int>(p.items.size()));
+      p.cut_upd.push_back(static_cast<int>(p.upd.size()));
+    }
+  }
+  p.cut_items.push_back(static_cast<int>(p.items.size()));
+  p.cut_upd.push_back(static_cast<int>(p.upd.size()));
+  return p;
+}
+
+// Grows a device buffer to hold `need` elements (contents not kept); a failed
+// allocation leaves it empty, and a grown buffer drops the captured graph.
+template <typename T>
+kmc_status grow(kmc_ctx *c, T **p, size_t *cap, size_t need);
+
+kmc_status set_sym_items(kmc_ctx *c, const Shape &sh) {
+  const int gc = sh.warps * sh.sym;
+  std::vector<int> np(c->n.begin(), c->n.end());
+  const SymPlan plan = plan_sym(np, gc, sh.chunk / kmc::kCell);
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  KMC_TRY(grow(c, &c->d_sitems, &c->sitems_cap, plan.items.size()));
+  KMC_TRY(grow(c, &c->d_supd, &c->supd_cap, plan.upd.size()));
+  KMC_TRY(grow(c, &c->d_sfwd, &c->sfwd_cap,
+               plan.items.size() * 6 * static_cast<size_t>(gc) * kmc::kCell));
+  KMC_TRY(grow(c, &c->d_srev, &c->srev_cap,
+               std::max<size_t>(1, static_cast<size_t>(plan.n_rev) * 3 * kmc::kCell)));
+  KMC_CUDA(cudaMemcpy(c->d_sitems, plan.items.data(), sizeof(kmc::SymItem) * plan.items.size(),
+                      cudaMemcpyHostToDevice));
+  KMC_CUDA(cudaMemcpy(c->d_supd, plan.upd.data(), sizeof(kmc::SymUpd) * plan.upd.size(),
+                      cudaMemcpyHostToDevice));
+  c->n_sitems = static_cast<int>(plan.items.size());
+  c->n_supd = static_cast<int>(plan.upd.size());
+  c->sym_cut_items = plan.cut_items;
+  c->sym_cut_upd = plan.cut_upd;
+  c->items_shape = sh;
+  return KMC_OK;
+}
+
+template <typename T>
+kmc_status grow(kmc_ctx *c, T **p, size_t *cap, size_t need) {
+  if (need <= *cap && *p) return KMC_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  KMC_TRY(dalloc(p, sizeof(T) * need));
+  *cap = need;
+  drop_graph(c);
+  return KMC_OK;
+}
+
 kmc_status set_items(kmc_ctx *c, const Shape &sh) {
-  if (c->items_shape == sh && c->d_items) return KMC_OK;
+  if (c->items_shape == sh && (sh.sym ? c->d_sitems != nullptr : c->d_items != nullptr))
+    return KMC_OK;
+  if (sh.sym) {
+    c->items_shape = Shape();
+    return set_sym_items(c, sh);
+  }
   // until the rebuild completes, no shape's items are valid
   c->items_shape = Shape();
   int dev = 0, n_sms = 0, per_sm = 0;
@@ -437,7 +575,35 @@ StepArgs base_args(kmc_ctx *c) {
   a.rs = c->d_rs;
   a.n_items = c->n_items;
   a.n_lys = c->n_lys;
+  if (c->shape.sym > 0 && c->items_shape == c->shape) {  // symmetric form: all of its items
+    a.n_items = c->n_sitems;
+    a.gc = c->shape.warps * c->shape.sym;
+  }
+  a.sitems = c->d_sitems;
+  a.supd = c->d_supd;
+  a.sfwd = c->d_sfwd;
+  a.srev = c->d_srev;
+  a.n_upd = c->n_supd;
   return a;
+}
+
+// Chains of the current items (the symmetric form has its own cut).
+int n_chains_of(const kmc_ctx *c, const Shape &sh) {
+  return static_cast<int>(sh.sym ? c->sym_cut_items.size() : c->chain_cut.size()) - 1;
+}
+
+// One step of every item of a (all chains, one stream), shape sh.
+cudaError_t launch_one_step(const kmc_ctx *c, StepArgs a, const Shape &sh, cudaStream_t st,
+                            bool pdl) {
+  if (sh.sym) {
+    a.sitems = c->d_sitems;
+    a.supd = c->d_supd;
+    a.n_items = c->n_sitems;
+    a.n_upd = c->n_supd;
+    a.gc = sh.warps * sh.sym;
+    return kmc::launch_sym(a, sh.warps, sh.sym, c->n_sitems, st, pdl);
+  }
+  return kmc::launch_step(c->fp32, sh.warps, sh.tile, a, c->n_items, st, pdl, sh.tpl, sh.rpl);
 }
 
 kmc_status refresh_sources(kmc_ctx *c, int par) {
@@ -489,6 +655,14 @@ int max_tile(int fp32, int warps) {
 }
 
 bool shape_ok(const kmc_ctx *c, const Shape &s) {
+  if (s.sym) {  // symmetric form: (warps, cells per warp) of its field kernel
+    if (!c->fp32 || s.rpl != 1 || s.tpl != 2 * s.sym || s.tile != 32) return false;
+    if (!((s.warps == 4 && (s.sym == 1 || s.sym == 2)) || (s.warps == 8 && s.sym == 1) ||
+          (s.warps == 2 && s.sym == 2)))
+      return false;
+    return s.chunk >= 0 && s.chunk % kmc::kCell == 0;
+  }
+  if (s.tpl > 3) return false;
   if (s.rpl > 1) {  // replicas: their kernel has one warp per replica
     if (!c->fp32 || s.tpl != 1 || s.warps != s.rpl || !c->rep_ok[s.rpl]) return false;
     if (s.tile < 32 || s.tile > 128 || (s.tile & (s.tile - 1))) return false;
@@ -508,7 +682,7 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
                          cudaGraphExec_t *out) {
   Phase phase("kmc_capture");
   *out = nullptr;
-  const int n_chains = static_cast<int>(c->chain_cut.size()) - 1;
+  const int n_chains = n_chains_of(c, sh);
   for (int q = 0; q < n_chains; ++q) {
     if (q > 0 && !c->chain_st[q])
       KMC_CUDA(cudaStreamCreateWithFlags(&c->chain_st[q], cudaStreamNonBlocking));
@@ -525,6 +699,23 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
   const bool split = c->partial_cap >= static_cast<size_t>(c->n_items);
   for (int q = 0; q < n_chains && ce == cudaSuccess; ++q) {
     cudaStream_t st = q == 0 ? c->stream : c->chain_st[q];
+    if (sh.sym) {
+      StepArgs b = a;
+      const int u0 = c->sym_cut_items[q], v0 = c->sym_cut_upd[q];
+      b.sitems = c->d_sitems + u0;
+      b.n_items = c->sym_cut_items[q + 1] - u0;
+      b.supd = c->d_supd + v0;
+      b.n_upd = c->sym_cut_upd[q + 1] - v0;
+      b.gc = sh.warps * sh.sym;
+      for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
+        if (period) {
+          b.k_local = k;
+          b.cos_k = std::cos(2.0 * kPi * k / steps);
+        }
+        ce = kmc::launch_sym(b, sh.warps, sh.sym, b.n_items, st, true);
+      }
+      continue;
+    }
     const int u0 = c->chain_cut[q];
     StepArgs b = a;
     b.items = c->d_items + u0;
@@ -575,7 +766,7 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   a.n_rec = 1;
   // several chains share the SMs, so a shape is timed the way a run executes
   // it: a graph of a few steps of every chain
-  const bool chained = c->chain_cut.size() > 2;
+  const bool chained = n_chains_of(c, s) > 1;
   // per step; short steps are timed over more of them, so that the chains
   // reach their steady interleaving (a short graph favours small blocks,
   // which fill and drain the SMs faster at the graph's ends)
@@ -595,9 +786,7 @@ float time_shape(kmc_ctx *c, const Shape &s) {
     return -1.f;
   }
   auto one = [&]() {
-    return gx ? cudaGraphLaunch(gx, c->stream)
-              : kmc::launch_step(c->fp32, s.warps, s.tile, a, c->n_items, c->stream, true, s.tpl,
-                                 s.rpl);
+    return gx ? cudaGraphLaunch(gx, c->stream) : launch_one_step(c, a, s, c->stream, true);
   };
   float ms = -1.f;
   bool ok = true;
@@ -620,7 +809,7 @@ kmc_status autotune(kmc_ctx *c) {
   for (int x : c->n) max_n = std::max(max_n, x);
   const TuneKey key{c->fp32, c->N,        c->n_lys,
                     max_n,   c->tpl_mode, c->rpl_mode,
-                    (c->rep_ok[2] ? 1 : 0) | (c->rep_ok[4] ? 2 : 0)};
+                    (c->rep_ok[2] ? 1 : 0) | (c->rep_ok[4] ? 2 : 0), c->form_mode};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -654,13 +843,44 @@ kmc_status autotune(kmc_ctx *c) {
     bs.tpl = 1;
     bs.rpl = c->rpl_mode;
   }
+  // the ordered kernels run 1..3 targets per lane; 4 is the symmetric form's
+  const bool sym_only = c->form_mode == 2 || c->tpl_mode == 4;
+  if (sym_only) {
+    bs.tile = 32;
+    bs.sym = c->tpl_mode == 4 ? 2 : 1;
+    bs.tpl = 2 * bs.sym;
+  }
+  // symmetric form (FP32): (warps, cells per warp), source NPs per field item
+  if (c->fp32 && c->form_mode != 1 && c->rpl_mode <= 1 &&
+      (c->tpl_mode == 0 || c->tpl_mode == 2 || c->tpl_mode == 4)) {
+    const int wc[4][2] = {{2, 2}, {4, 1}, {4, 2}, {8, 1}};
+    for (const auto &v : wc) {
+      if (c->tpl_mode != 0 && 2 * v[1] != c->tpl_mode) continue;
+      const int gc = v[0] * v[1];
+      for (int ch : {0, 256, 512, 1024, 2048, 4096}) {
+        // a field item of ch source NPs, at least one row group's worth
+        if (ch > 0 && (ch >= max_n || ch < gc * kmc::kCell / 2)) continue;
+        Shape s;
+        s.warps = v[0];
+        s.tile = 32;
+        s.chunk = ch;
+        s.tpl = 2 * v[1];
+        s.sym = v[1];
+        const float ms = time_shape(c, s);
+        if (ms > 0.f && ms < best) {
+          best = ms;
+          bs = s;
+        }
+      }
+    }
+  }
   const int warps_c[] = {4, 8};
   const int tiles_f32[] = {64, 128, 256, 512};
   const int tiles_f64[] = {32, 64, 128, 128};  // (the FP64 list has three distinct tiles)
   const int chunks[] = {0, 256, 512, 1024, 2048, 4096, 8192};
   // replicas per lane (FP32, sets of identical lysosomes): warps = replicas,
   // one target per lane, tiles of 32..128 records per replica
-  for (int rpl = 2; rpl <= 4 && c->fp32 && c->tpl_mode <= 1; rpl += 2) {
+  for (int rpl = 2; rpl <= 4 && c->fp32 && c->tpl_mode <= 1 && !sym_only; rpl += 2) {
     if (!c->rep_ok[rpl] || (c->rpl_mode != 0 && c->rpl_mode != rpl)) continue;
     for (int t : {32, 64, 128}) {
       if (2 * t > 2 * std::max(max_n, 64) && t > 32) continue;
@@ -681,7 +901,7 @@ kmc_status autotune(kmc_ctx *c) {
     }
   }
   for (int w : warps_c) {
-    if (c->rpl_mode > 1) break;  // pinned replicas: only their shapes
+    if (c->rpl_mode > 1 || sym_only) break;  // pinned replicas or form: only their shapes
     for (int q = 0; q < (c->fp32 ? 4 : 3); ++q) {
       const int t = c->fp32 ? tiles_f32[q] : tiles_f64[q];
       if (t > max_tile(c->fp32, w)) continue;
@@ -730,7 +950,8 @@ void free_ctx(kmc_ctx *c) {
                   c->d_src[1], c->d_slot,  c->d_beta,    c->d_vfrac,    c->d_eacc,
                   c->d_dh,    c->d_pos64,  c->d_phi,     c->d_nodes,    c->d_possi, c->d_phif,
                   c->d_loop,  c->d_cnt,    c->d_err,     c->d_rs,       c->d_items,
-                  c->d_partial, c->d_arrivals, c->d_dbg, c->d_dbg_flags};
+                  c->d_partial, c->d_arrivals, c->d_dbg, c->d_dbg_flags, c->d_sitems,
+                  c->d_supd,  c->d_sfwd,   c->d_srev};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < kMaxChains; ++q) {
@@ -869,8 +1090,13 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
     c->rep_ok[k] = ok;
   }
   c->vbytes = c->fp32 ? sizeof(float4) : sizeof(dbl4);
+  // FP32: every lysosome's records start on a cell boundary (kmc::kCellRec
+  // records) and its last cell is padded, for the symmetric form
+  auto lys_records = [&](int n) -> long long {
+    return c->fp32 ? static_cast<long long>((n + kmc::kCell - 1) / kmc::kCell) * kmc::kCellRec : n;
+  };
   long long nrec = 0;
-  for (int l = 0; l < n_lys; ++l) nrec += c->fp32 ? (lys[l].n + 1) / 2 : lys[l].n;
+  for (int l = 0; l < n_lys; ++l) nrec += lys_records(lys[l].n);
   c->n_records = nrec;
   std::vector<unsigned char> h_pos(c->vbytes * N), h_axis(c->vbytes * N), h_m(c->vbytes * N);
   std::vector<unsigned char> h_src((c->fp32 ? sizeof(SrcPair) : sizeof(dbl4)) * nrec);
@@ -924,11 +1150,14 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
     D.k = L.Keff / (kMu0 * L.Ms * L.Ms);
     D.bmax = 0.0;
     D.lognu0t = 0.0;
-    if (c->fp32 && (L.n & 1)) {  // padding NP of the last record: far away, no moment
-      SrcPair &pad = src32[r + L.n / 2];
-      pad.x[1] = pad.y[1] = pad.z[1] = kmc::kPadCoord;
-      kmc::set_source_moment(pad, 1, 0.0f, 0.0f, 0.0f, 0.0f);
-      pad.pad[0] = pad.pad[1] = 0.0f;
+    if (c->fp32) {  // padding NPs up to the end of the last cell: far away, no moment
+      for (long long j = L.n; j < 2 * lys_records(L.n); ++j) {
+        SrcPair &pad = src32[r + j / 2];
+        const int h = static_cast<int>(j & 1);
+        pad.x[h] = pad.y[h] = pad.z[h] = kmc::kPadCoord;
+        kmc::set_source_moment(pad, h, 0.0f, 0.0f, 0.0f, 0.0f);
+        pad.pad[h] = 0.0f;
+      }
     }
     for (int i = 0; i < L.n; ++i, ++o) {
       const double *p = &L.pos[3 * i];
@@ -965,7 +1194,7 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
         src64[r + i] = make4<dbl4>(w * sgn * ax, w * sgn * ay, w * sgn * az, 0.0);
       }
     }
-    r += c->fp32 ? (L.n + 1) / 2 : L.n;
+    r += lys_records(L.n);
   }
   const kmc_status st =
       create_device_state(c, h_pos, h_axis, h_m, h_src, h_slot, h_beta, h_vfrac, h_pos64);
@@ -981,6 +1210,43 @@ kmc_status kmc_set_stream(kmc_ctx *c, void *cuda_stream) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   c->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->own_stream;
+  return KMC_OK;
+}
+
+kmc_status kmc_plan_sym(const int32_t *n, int32_t n_lys, int32_t gc, int32_t src_cells,
+                        int32_t *items_out, int64_t cap, int64_t *n_items, int32_t *upd_out,
+                        int64_t cap_upd, int64_t *n_upd, int64_t *n_rev,
+                        int32_t *chain_cut_items, int32_t *chain_cut_upd, int32_t *n_chains) {
+  if (!n || n_lys < 1 || !n_items || !n_upd || !n_rev || !chain_cut_items || !chain_cut_upd ||
+      !n_chains || cap < 0 || cap_upd < 0 || (cap > 0 && !items_out) || (cap_upd > 0 && !upd_out))
+    return fail(KMC_EINVAL, "plan: need n[n_lys >= 1], outputs and capacities >= 0");
+  if ((gc != 4 && gc != 8) || src_cells < 0)
+    return fail(KMC_EINVAL, "plan: gc 4 or 8, src_cells >= 0");
+  std::vector<int> np(n, n + n_lys);
+  for (int v : np)
+    if (v < 1) return fail(KMC_EINVAL, "plan: every lysosome needs an NP");
+  const SymPlan p = plan_sym(np, gc, src_cells);
+  *n_items = static_cast<int64_t>(p.items.size());
+  *n_upd = static_cast<int64_t>(p.upd.size());
+  *n_rev = p.n_rev;
+  *n_chains = static_cast<int32_t>(p.cut_items.size()) - 1;
+  for (size_t q = 0; q < p.cut_items.size(); ++q) {
+    chain_cut_items[q] = p.cut_items[q];
+    chain_cut_upd[q] = p.cut_upd[q];
+  }
+  if (*n_items > cap || *n_upd > cap_upd)
+    return fail(KMC_ECAPACITY, "plan: %lld field and %lld update items", (long long)*n_items,
+                (long long)*n_upd);
+  for (size_t u = 0; u < p.items.size(); ++u) {
+    const kmc::SymItem &it = p.items[u];
+    const int32_t row[KMC_SYM_FIELDS] = {it.l, it.g, it.h0, it.h1, it.fwd, it.rbase, 0, 0};
+    std::memcpy(items_out + KMC_SYM_FIELDS * u, row, sizeof(row));
+  }
+  for (size_t u = 0; u < p.upd.size(); ++u) {
+    const kmc::SymUpd &d = p.upd[u];
+    const int32_t row[KMC_SYM_FIELDS] = {d.l, d.t0, d.nt, d.fwd0, d.nfwd, d.rev0, d.nrev, d.gt0};
+    std::memcpy(upd_out + KMC_SYM_FIELDS * u, row, sizeof(row));
+  }
   return KMC_OK;
 }
 
@@ -1016,15 +1282,25 @@ kmc_status kmc_plan_items(const int32_t *n, int32_t n_lys, kmc_precision prec, i
 kmc_status kmc_targets_per_lane(kmc_ctx *c, int32_t tpl, int32_t *tpl_out) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (tpl != -1) {
-    if (tpl < 0 || tpl > 3)
-      return fail(KMC_EINVAL, "targets per lane: 0 (autotuned), 1, 2 or 3");
+    if (tpl < 0 || tpl > 4)
+      return fail(KMC_EINVAL, "targets per lane: 0 (autotuned), 1, 2, 3 or 4");
     if (tpl > 1 && !c->fp32)
-      return fail(KMC_EINVAL, "two or three targets per lane run on FP32 contexts");
+      return fail(KMC_EINVAL, "two or more targets per lane run on FP32 contexts");
     if (tpl > 1 && c->rpl_mode > 1)
       return fail(KMC_EINVAL, "replicas per lane run one target per lane");
+    if (c->form_mode == 2 && (tpl == 1 || tpl == 3))
+      return fail(KMC_EINVAL, "the symmetric form runs 2 or 4 targets per lane");
+    if (c->form_mode == 1 && tpl == 4)
+      return fail(KMC_EINVAL, "the ordered kernels run 1, 2 or 3 targets per lane");
     c->tpl_mode = tpl;
     // a pinned choice applies to the shape in use; 0 leaves it to the autotuner
-    if (tpl != 0 && c->shape.warps != 0 && c->shape.rpl == 1) c->shape.tpl = tpl;
+    if (tpl != 0 && c->shape.warps != 0 && c->shape.rpl == 1) {
+      Shape s = c->shape;
+      s.tpl = tpl;
+      if (s.sym) s.sym = tpl / 2;
+      if (s.sym == 0 && tpl == 4) s = Shape();
+      c->shape = shape_ok(c, s) ? s : Shape();
+    }
   }
   if (tpl_out) *tpl_out = c->tpl_mode != 0 ? c->tpl_mode : (c->shape.warps ? c->shape.tpl : 0);
   return KMC_OK;
@@ -1050,6 +1326,28 @@ kmc_status kmc_replicas_per_lane(kmc_ctx *c, int32_t rpl, int32_t *rpl_out) {
   return KMC_OK;
 }
 
+kmc_status kmc_pair_form(kmc_ctx *c, int32_t form, int32_t *form_out) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (form != -1) {
+    if (form < 0 || form > 2)
+      return fail(KMC_EINVAL, "pair form: 0 (autotuned), 1 (ordered) or 2 (symmetric)");
+    if (form == 2 && !c->fp32) return fail(KMC_EINVAL, "the symmetric form runs on FP32 contexts");
+    if (form == 2 && c->rpl_mode > 1)
+      return fail(KMC_EINVAL, "the symmetric form does not run replicas per lane");
+    if (form == 2 && (c->tpl_mode == 1 || c->tpl_mode == 3))
+      return fail(KMC_EINVAL, "the symmetric form runs 2 or 4 targets per lane");
+    if (form == 1 && c->tpl_mode == 4)
+      return fail(KMC_EINVAL, "the ordered kernels run 1, 2 or 3 targets per lane");
+    c->form_mode = form;
+    // a change drops the shape in use: the next run or step tunes, or takes kmc_tuning's
+    if (c->shape.warps != 0 && form != 0 && (c->shape.sym != 0) != (form == 2)) c->shape = Shape();
+  }
+  if (form_out)
+    *form_out = c->form_mode != 0 ? c->form_mode
+                                  : (c->shape.warps ? (c->shape.sym ? 2 : 1) : 0);
+  return KMC_OK;
+}
+
 kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
                       int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
@@ -1064,7 +1362,14 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
     s.chunk = chunk;
     s.tpl = c->tpl_mode != 0 ? c->tpl_mode : 1;
     s.rpl = c->rpl_mode > 1 ? c->rpl_mode : 1;
-    if (!shape_ok(c, s))
+    if (c->form_mode == 2 || c->tpl_mode == 4) {  // symmetric form; the tile does not apply
+      s.sym = c->tpl_mode == 4 ? 2 : 1;
+      s.tpl = 2 * s.sym;
+      s.tile = 32;
+      if (!shape_ok(c, s))
+        return fail(KMC_EINVAL, "bad symmetric shape: warps 4, 8 with 2 targets per lane or 2 "
+                    "with 4, chunk a multiple of 64");
+    } else if (!shape_ok(c, s))
       return fail(KMC_EINVAL,
                   s.rpl > 1 ? "bad shape: with %d replicas per lane, warps = %d, tile a power of two "
                               "in [32, 128], chunk a multiple of 64"
@@ -1119,7 +1424,8 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
   KMC_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long) * kmc::kCounters * c->n_lys,
                            c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
-  KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  if (c->arrivals_cap)
+    KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
   KMC_TRY(refresh_sources(c, static_cast<int>(c->step_global & 1)));
   RunState rs{c->step_global, 0, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
@@ -1308,7 +1614,8 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
   RunState rs{step, -1, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
   KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
-  KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  if (c->arrivals_cap)
+    KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
   StepArgs a = base_args(c);
   a.seed = seed;
   a.S = 1;
@@ -1323,8 +1630,7 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
   a.dbg.P = c->d_dbg + 5 * N;
   a.dbg.u = c->d_dbg + 6 * N;
   a.dbg.flags = c->d_dbg_flags;
-  KMC_CUDA(kmc::launch_step(c->fp32, c->shape.warps, c->shape.tile, a, c->n_items, c->stream,
-                            false, c->shape.tpl, c->shape.rpl));
+  KMC_CUDA(launch_one_step(c, a, c->shape, c->stream, false));
   KMC_TRY(check_device_error(c));
   std::vector<double> h(7 * N);
   std::vector<int32_t> hf(N);
@@ -1801,7 +2107,8 @@ kmc_status kmc_debug_stall(kmc_ctx *c) {
   KMC_TRY(ensure_shape(c));
   RunState rs{c->step_global, -1, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
-  KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  if (c->arrivals_cap)
+    KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
   StepArgs a = base_args(c);
   a.S = 1;
   a.n_rec = 1;
@@ -1812,7 +2119,8 @@ kmc_status kmc_debug_stall(kmc_ctx *c) {
   const kmc_status st = check_device_error(c);  // KMC_ETIMEOUT when the waits ran out
   // the blocks stopped before any write: clear the flag, the context stays usable
   KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
-  KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  if (c->arrivals_cap)
+    KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   return st == KMC_OK ? fail(KMC_ESTATE, "the stalled waits did not run out") : st;
 }

@@ -23,6 +23,15 @@ size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl = 1, int rpl 
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
                         cudaStream_t st, bool pdl = false, int tpl = 1, int rpl = 1);
 
+// Symmetric pair form (FP32): one step = kmc_field_sym<warps, cells> over
+// a.sitems[0 .. n_field) and then kmc_update_sym over a.supd[0 .. a.n_upd).
+// (warps, cells) in {(2, 2), (4, 1), (4, 2), (8, 1)}; row groups of warps x cells
+// cells (4 or 8).
+cudaError_t launch_sym(const StepArgs &a, int warps, int cells, int n_field, cudaStream_t st,
+                       bool pdl = false);
+size_t sym_smem_bytes(int warps, int cells);
+cudaError_t sym_blocks_per_sm(int warps, int cells, int *blocks);
+
 // Blocks of the step kernel of this shape that fit on one SM at once.
 cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int *blocks,
                                int rpl = 1);

@@ -1381,6 +1381,363 @@ __global__ void kmc_advance_kernel(RunState *rs, int S) {
 }
 
 // ---------------------------------------------------------------------------
+// Symmetric pair form (FP32-mixed). T_ij and T_ji share their geometry (d,
+// r^2, the rsqrt and the powers of 1/r), so each unordered pair is formed
+// once for both of its ordered pairs.
+//
+// Field kernel: a block of W warps takes row group g, i.e. W C cells (warp w:
+// cells g W C + w C .. + C - 1; lane L holds record L of each, two targets
+// per cell), against the source cells [h0, h1) above the group, one staged
+// cell at a time. At step s lane L reads record (L + s) mod 32 of the staged
+// cell and forms, for each of its 2 C targets, the geometry of its two pairs
+// (8 packed operations, two rsqrt), the forward terms into the target's sums
+// (10) and the reverse terms into the sums it carries for that record (10).
+// The reverse term of target i at source j is q^3 (v d + n_i) with
+// v = (t_i . d) q^2 and d = r_j - r_i: -d enters twice. The reverse sums move
+// one lane per step (shuffles), so that after 32 steps lane L holds those of
+// record L; the W warps' sums of the cell are then added in warp order into
+// the cell's reverse slot for row group g. The group's diagonal item
+// evaluates the pairs inside the group in the ordered form instead (each
+// warp: its targets against every record of the group, the self pair
+// masked). Every sum runs in a fixed order, so results do not depend on the
+// launch.
+//
+// Update kernel: per 32 targets of one cell, the forward partials of the
+// target's row group (diagonal item first, then the source ranges in order)
+// and the reverse slots of its cell (row groups in order) are added with
+// compensation (warp w takes slots w, w + 4, ...; the warps in order), then
+// steps iii-vii run as in kmc_step_f32<4>.
+constexpr int kSymUpdWarps = 4;
+
+template <int T>
+__device__ __forceinline__ void sym_cell(const ulonglong2 *__restrict__ sp, int lane,
+                                         const f2 (&X)[T], const f2 (&Y)[T], const f2 (&Z)[T],
+                                         const f2 (&TX)[T], const f2 (&TY)[T], const f2 (&TZ)[T],
+                                         const f2 (&NX)[T], const f2 (&NY)[T], const f2 (&NZ)[T],
+                                         AccF32 (&acc)[T], f2 &rx, f2 &ry, f2 &rz) {
+  const int from = (lane + 1) & (kCellRec - 1);
+#pragma unroll 2
+  for (int s = 0; s < kCellRec; ++s) {
+    ulonglong2 a, b, c, d;
+    f2 e;
+    load_record(sp, (lane + s) & (kCellRec - 1), a, b, c, d, e);
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      const f2 dx = sub2(a.x, X[k]), dy = sub2(a.y, Y[k]), dz = sub2(b.x, Z[k]);
+      const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+      float r2l, r2h;
+      upk(r2, r2l, r2h);
+      const f2 q = pk(rsqrt_approx(r2l), rsqrt_approx(r2h));
+      const f2 q2 = mul2(q, q);
+      const f2 q3 = mul2(q, q2);
+      const f2 u = mul2(fma2(e, dz, fma2(d.y, dy, mul2(d.x, dx))), q2);
+      acc[k].x = fma2(q3, fma2(u, dx, b.y), acc[k].x);
+      acc[k].y = fma2(q3, fma2(u, dy, c.x), acc[k].y);
+      acc[k].z = fma2(q3, fma2(u, dz, c.y), acc[k].z);
+      const f2 v = mul2(fma2(TZ[k], dz, fma2(TY[k], dy, mul2(TX[k], dx))), q2);
+      rx = fma2(q3, fma2(v, dx, NX[k]), rx);
+      ry = fma2(q3, fma2(v, dy, NY[k]), ry);
+      rz = fma2(q3, fma2(v, dz, NZ[k]), rz);
+    }
+    rx = __shfl_sync(0xffffffffu, rx, from);
+    ry = __shfl_sync(0xffffffffu, ry, from);
+    rz = __shfl_sync(0xffffffffu, rz, from);
+  }
+}
+
+// Ordered pairs of the lane's targets with the 32 records of one staged cell
+// (diagonal items); MASK drops the self pair.
+template <bool MASK, int T>
+__device__ __forceinline__ void ordered_cell(const ulonglong2 *__restrict__ sp, const f2 (&X)[T],
+                                             const f2 (&Y)[T], const f2 (&Z)[T],
+                                             AccF32 (&acc)[T]) {
+#pragma unroll 1
+  for (int r = 0; r < kCellRec; ++r) {
+    ulonglong2 a, b, c, d;
+    f2 e;
+    load_record(sp, r, a, b, c, d, e);
+#pragma unroll
+    for (int k = 0; k < T; ++k) pair_record<MASK>(a, b, c, d, e, X[k], Y[k], Z[k], acc[k]);
+  }
+}
+
+// KMC_DEBUG builds: the block's symmetric item lies inside the launch and its
+// lysosome, and its source cells lie above its row group.
+__device__ __forceinline__ bool sym_item_in_bounds(const StepArgs &a, int gc) {
+#ifdef KMC_DEBUG
+  if (!KMC_DCHECK(static_cast<int>(blockIdx.x) < a.n_items, a.err, kSiteItem)) return false;
+  const SymItem it = a.sitems[blockIdx.x];
+  if (!KMC_DCHECK(it.l >= 0 && it.l < a.n_lys, a.err, kSiteLys)) return false;
+  const int nc = (a.lys[it.l].n + kCell - 1) / kCell;
+  if (!KMC_DCHECK(it.g >= 0 && it.g * gc < nc && it.fwd >= 0 && it.rbase >= 0, a.err,
+                  kSiteTargets))
+    return false;
+  if (!KMC_DCHECK((it.h0 == -1 && it.h1 == -1) ||
+                      (it.h0 >= (it.g + 1) * gc && it.h0 < it.h1 && it.h1 <= nc),
+                  a.err, kSiteSources))
+    return false;
+#endif
+  return true;
+}
+
+__device__ __forceinline__ bool sym_upd_in_bounds(const StepArgs &a, int gc) {
+#ifdef KMC_DEBUG
+  if (!KMC_DCHECK(static_cast<int>(blockIdx.x) < a.n_upd, a.err, kSiteItem)) return false;
+  const SymUpd u = a.supd[blockIdx.x];
+  if (!KMC_DCHECK(u.l >= 0 && u.l < a.n_lys, a.err, kSiteLys)) return false;
+  const int n = a.lys[u.l].n;
+  if (!KMC_DCHECK(u.t0 >= 0 && u.nt >= 1 && u.nt <= kTargets && u.t0 + u.nt <= n &&
+                      (u.t0 % kCell) + u.nt <= kCell && u.gt0 >= 0 &&
+                      u.gt0 + u.nt <= gc * kCell,
+                  a.err, kSiteTargets))
+    return false;
+  if (!KMC_DCHECK(u.fwd0 >= 0 && u.nfwd >= 1 && u.rev0 >= 0 && u.nrev >= 0, a.err, kSiteSplit))
+    return false;
+#endif
+  return true;
+}
+
+// Dynamic shared memory of the field kernel: two staged cells and the warps'
+// reverse sums of two cells, or the whole row group's records (diagonal).
+constexpr size_t sym_field_smem(int w, int c) {
+  return 16 + ((2 * kCellRec * sizeof(SrcPair) + 2 * static_cast<size_t>(w) * 6 * 32 * 4) >
+                       static_cast<size_t>(w) * c * kCellRec * sizeof(SrcPair)
+                   ? (2 * kCellRec * sizeof(SrcPair) + 2 * static_cast<size_t>(w) * 6 * 32 * 4)
+                   : static_cast<size_t>(w) * c * kCellRec * sizeof(SrcPair));
+}
+
+template <int W, int C>
+__global__ void __launch_bounds__(W * 32) kmc_field_sym(const StepArgs a, int /*tile*/) {
+  constexpr int T = 2 * C;    // targets per lane
+  constexpr int GC = W * C;   // cells per row group
+  constexpr int GT = GC * kCell;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *dyn = smem + 16;
+  if (!sym_item_in_bounds(a, GC)) return;
+  const SymItem it = a.sitems[blockIdx.x];
+  const LysDev L = a.lys[it.l];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nc = (L.n + kCell - 1) / kCell;
+  const int cell0 = it.g * GC + warp * C;  // the warp's first target cell
+  grid_dependency_wait();
+  const long long step = a.rs->step_base + a.k_local;
+  const int par = static_cast<int>(step & 1);
+  const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
+
+  // the lane's targets: record `lane` of each of the warp's cells; cells past
+  // the lysosome (a diagonal item's last group) are far away and have no moment
+  f2 X[T], Y[T], Z[T], TX[T], TY[T], TZ[T], NX[T], NY[T], NZ[T];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    SrcPair rr;
+    if (cell0 + c < nc) {
+      rr = gsrc[(cell0 + c) * kCellRec + lane];
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        rr.x[h] = rr.y[h] = rr.z[h] = -kPadCoord;
+        set_source_moment(rr, h, 0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * c + h;
+      X[k] = pk(rr.x[h], rr.x[h]);
+      Y[k] = pk(rr.y[h], rr.y[h]);
+      Z[k] = pk(rr.z[h], rr.z[h]);
+      TX[k] = pk(rr.tx[h], rr.tx[h]);
+      TY[k] = pk(rr.ty[h], rr.ty[h]);
+      TZ[k] = pk(rr.tz[h], rr.tz[h]);
+      NX[k] = pk(rr.nx[h], rr.nx[h]);
+      NY[k] = pk(rr.ny[h], rr.ny[h]);
+      NZ[k] = pk(rr.nz[h], rr.nz[h]);
+    }
+  }
+  float s3[T][3], c3[T][3];  // Kahan sums of the forward field, per target
+#pragma unroll
+  for (int k = 0; k < T; ++k)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s3[k][q] = c3[k][q] = 0.f;
+  auto fold = [&](const AccF32 (&acc)[T]) {
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      kahan_add(s3[k][0], c3[k][0], hsum(acc[k].x));
+      kahan_add(s3[k][1], c3[k][1], hsum(acc[k].y));
+      kahan_add(s3[k][2], c3[k][2], hsum(acc[k].z));
+    }
+  };
+  ulonglong2 *buf = reinterpret_cast<ulonglong2 *>(dyn);
+
+  if (it.h0 < 0) {
+    // diagonal item: the group's records in one copy, ordered pairs
+    const int c0 = it.g * GC, ncv = min(GC, nc - c0);
+    const uint32_t bytes = static_cast<uint32_t>(ncv) * kCellRec * sizeof(SrcPair);
+    if (threadIdx.x == 0) {
+      mbar_init(&bar[0], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&bar[0], bytes);
+      bulk_g2s(buf, gsrc + c0 * kCellRec, bytes, &bar[0]);
+    }
+    const bool ok = mbar_wait_bounded(&bar[0], 0, a.err);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) mbar_wait_quiet(&bar[0], 0, 2000000000ull);
+      __syncthreads();
+      return;
+    }
+#pragma unroll 1
+    for (int cs = 0; cs < ncv; ++cs) {
+      AccF32 acc[T];
+#pragma unroll
+      for (int k = 0; k < T; ++k) acc[k].x = acc[k].y = acc[k].z = 0ull;
+      const ulonglong2 *sp = buf + static_cast<size_t>(cs) * kCellRec * kRecU2;
+      if (cs >= warp * C && cs < warp * C + C)
+        ordered_cell<true, T>(sp, X, Y, Z, acc);
+      else
+        ordered_cell<false, T>(sp, X, Y, Z, acc);
+      fold(acc);
+    }
+  } else {
+    float *red = reinterpret_cast<float *>(dyn + 2 * kCellRec * sizeof(SrcPair));  // [2][W][6][32]
+    auto issue = [&](int t) {
+      const int b = t & 1;
+      const uint32_t bytes = kCellRec * sizeof(SrcPair);
+      mbar_expect_tx(&bar[b], bytes);
+      bulk_g2s(buf + static_cast<size_t>(b) * kCellRec * kRecU2, gsrc + (it.h0 + t) * kCellRec,
+               bytes, &bar[b]);
+    };
+    // the warps' reverse sums of cell h0 + t, added in warp order into its
+    // slot for this row group: [3][64], component-major
+    auto flush_rev = [&](int t) {
+      const float *rb = red + (t & 1) * W * 6 * 32;
+      float *dst = a.srev + static_cast<size_t>(it.rbase + sym_rev_offset(it.h0 + t, GC) + it.g) *
+                                3 * kCell;
+      for (int v = threadIdx.x; v < 6 * 32; v += W * 32) {
+        const int j = v >> 5, ln = v & 31;
+        float r = rb[j * 32 + ln];
+#pragma unroll
+        for (int w = 1; w < W; ++w) r += rb[(w * 6 + j) * 32 + ln];
+        __stcg(dst + (j % 3) * kCell + 2 * ln + j / 3, r);
+      }
+    };
+    auto body = [&](int b, int t) {
+      if (t > 0) flush_rev(t - 1);
+      AccF32 acc[T];
+#pragma unroll
+      for (int k = 0; k < T; ++k) acc[k].x = acc[k].y = acc[k].z = 0ull;
+      f2 rx = 0ull, ry = 0ull, rz = 0ull;
+      sym_cell<T>(buf + static_cast<size_t>(b) * kCellRec * kRecU2, lane, X, Y, Z, TX, TY, TZ, NX,
+                  NY, NZ, acc, rx, ry, rz);
+      fold(acc);
+      float *rw = red + ((t & 1) * W + warp) * 6 * 32;
+      float lo, hi;
+      upk(rx, lo, hi);
+      rw[0 * 32 + lane] = lo;
+      rw[3 * 32 + lane] = hi;
+      upk(ry, lo, hi);
+      rw[1 * 32 + lane] = lo;
+      rw[4 * 32 + lane] = hi;
+      upk(rz, lo, hi);
+      rw[2 * 32 + lane] = lo;
+      rw[5 * 32 + lane] = hi;
+    };
+    const int ncs = it.h1 - it.h0;
+    if (!staged_loop(ncs, bar, a.err, issue, body)) return;
+    flush_rev(ncs - 1);
+  }
+  // forward partials of the warp's targets: [6][GT] at the item's slot
+  float *fw = a.sfwd + static_cast<size_t>(it.fwd) * 6 * GT;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    if (cell0 + c >= nc) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * c + h;
+      const int gi = (warp * C + c) * kCell + 2 * lane + h;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        __stcg(fw + q * GT + gi, s3[k][q]);
+        __stcg(fw + (3 + q) * GT + gi, -c3[k][q]);  // Kahan keeps minus the error
+      }
+    }
+  }
+  grid_launch_dependents();
+}
+
+template <int GC>
+__global__ void __launch_bounds__(kSymUpdWarps * 32) kmc_update_sym(const StepArgs a, int /*tile*/) {
+  constexpr int NW = kSymUpdWarps;
+  constexpr int GT = GC * kCell;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *dyn = smem + 16;
+  __shared__ GridTables<float> tab;
+  tab.load();
+  if (!sym_upd_in_bounds(a, GC)) return;
+  const SymUpd u = a.supd[blockIdx.x];
+  const LysDev L = a.lys[u.l];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Item it;
+  it.l = u.l;
+  it.t0 = u.t0;
+  it.nt = u.nt;
+  it.gid = 0;
+  it.j0 = it.j1 = 0;
+  it.split = 0;
+  it.nsplit = 1;
+  grid_dependency_wait();
+  const long long step = a.rs->step_base + a.k_local;
+  const int per = a.rs->period;
+  const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
+  TargetIn<float4> tin;
+  if (warp == 0) tin = load_target<float4>(a, L, it, step, lane);
+  // lanes past the last target repeat it (their results are not written)
+  const int tl = min(lane, u.nt - 1);
+  const int gi = u.gt0 + tl, ci = (u.t0 + tl) % kCell;
+  float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+  for (int sl = warp; sl < u.nfwd; sl += NW) {
+    const float *p = a.sfwd + static_cast<size_t>(u.fwd0 + sl) * 6 * GT;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      neumaier_add(hi[q], lo[q], __ldcg(p + q * GT + gi));
+      lo[q] += __ldcg(p + (3 + q) * GT + gi);
+    }
+  }
+#pragma unroll 1
+  for (int sl = warp; sl < u.nrev; sl += NW) {
+    const float *p = a.srev + static_cast<size_t>(u.rev0 + sl) * 3 * kCell;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) neumaier_add(hi[q], lo[q], __ldcg(p + q * kCell + ci));
+  }
+  float *wp = reinterpret_cast<float *>(dyn);  // [NW][6][32]
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    wp[(warp * 6 + q) * 32 + lane] = hi[q];
+    wp[(warp * 6 + 3 + q) * 32 + lane] = lo[q];
+  }
+  __syncthreads();
+  EpiShared<float> &sm =
+      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 6 * 32 * 4);
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float s = 0.f, e = 0.f;
+      for (int w = 0; w < NW; ++w) {
+        neumaier_add(s, e, wp[(w * 6 + q) * 32 + lane]);
+        e += wp[(w * 6 + 3 + q) * 32 + lane];
+      }
+      sm.h[q][lane] = s + e;  // compensation added last
+    }
+  }
+  __syncthreads();
+  block_update<float4, true>(a, L, it, step, rec, tin, sm, tab);
+  grid_launch_dependents();
+}
+
+// ---------------------------------------------------------------------------
 // Host side of the launches.
 
 size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl, int rpl) {
@@ -1463,9 +1820,43 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
   }
 }
 
+// Symmetric form: the field kernel over n_field items, then the update kernel
+// over the a.n_upd target groups, both on st.
+template <int W, int C>
+static cudaError_t launch_sym_wc(const StepArgs &a, int n_field, cudaStream_t st, bool pdl) {
+  cudaError_t e = cudaSuccess;
+  if (n_field > 0)
+    e = launch_items(kmc_field_sym<W, C>, a, n_field, W * 32, sym_field_smem(W, C), 0, st, pdl);
+  if (e == cudaSuccess && a.n_upd > 0)
+    e = launch_items(kmc_update_sym<W * C>, a, a.n_upd, kSymUpdWarps * 32,
+                     16 + epi_bytes<float>(kSymUpdWarps), 0, st, pdl);
+  return e;
+}
+
+cudaError_t launch_sym(const StepArgs &a, int warps, int cells, int n_field, cudaStream_t st,
+                       bool pdl) {
+  if (warps == 2 && cells == 2) return launch_sym_wc<2, 2>(a, n_field, st, pdl);
+  if (warps == 4 && cells == 1) return launch_sym_wc<4, 1>(a, n_field, st, pdl);
+  if (warps == 4 && cells == 2) return launch_sym_wc<4, 2>(a, n_field, st, pdl);
+  if (warps == 8 && cells == 1) return launch_sym_wc<8, 1>(a, n_field, st, pdl);
+  return cudaErrorInvalidValue;
+}
+
+size_t sym_smem_bytes(int warps, int cells) { return sym_field_smem(warps, cells); }
+
 template <typename K>
 static cudaError_t occupancy(K kernel, int threads, size_t smem, int *blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, threads, smem);
+}
+
+cudaError_t sym_blocks_per_sm(int warps, int cells, int *blocks) {
+  *blocks = 0;
+  const size_t smem = sym_field_smem(warps, cells);
+  if (warps == 2 && cells == 2) return occupancy(kmc_field_sym<2, 2>, 64, smem, blocks);
+  if (warps == 4 && cells == 1) return occupancy(kmc_field_sym<4, 1>, 128, smem, blocks);
+  if (warps == 4 && cells == 2) return occupancy(kmc_field_sym<4, 2>, 128, smem, blocks);
+  if (warps == 8 && cells == 1) return occupancy(kmc_field_sym<8, 1>, 256, smem, blocks);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int *blocks,
@@ -1572,6 +1963,12 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<16, 3>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<2>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_field_sym<2, 2>);
+  if (e == cudaSuccess) e = allow_smem(kmc_field_sym<4, 1>);
+  if (e == cudaSuccess) e = allow_smem(kmc_field_sym<4, 2>);
+  if (e == cudaSuccess) e = allow_smem(kmc_field_sym<8, 1>);
+  if (e == cudaSuccess) e = allow_smem(kmc_update_sym<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_update_sym<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<16>);

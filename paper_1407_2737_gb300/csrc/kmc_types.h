@@ -90,6 +90,41 @@ struct Item {
   int32_t nsplit;  // items in the group
 };
 
+// Symmetric pair form (FP32-mixed, kmc_field_sym / kmc_update_sym). A
+// lysosome's NPs are cut into cells of kCell = 64 (32 source records; the
+// records of every lysosome start on a cell boundary and its last cell is
+// padded with far-away NPs without moment). A row group g is gc consecutive
+// cells (gc = warps x cells per warp). Every unordered pair of NPs is
+// evaluated once: pairs between a row group's cells and the cells above it
+// (h >= (g + 1) gc) by the symmetric field kernel, which adds T_ij to the
+// target's forward sum and T_ji to the source's reverse sum; pairs inside a
+// row group by ordered evaluation in the group's diagonal item.
+constexpr int kCell = 64;
+constexpr int kCellRec = kCell / 2;
+
+struct SymItem {   // one block of kmc_field_sym
+  int32_t l;       // lysosome
+  int32_t g;       // row group: target cells g gc .. g gc + gc - 1
+  int32_t h0, h1;  // source cells [h0, h1); h0 = h1 = -1: the group's diagonal item
+  int32_t fwd;     // forward-partial slot of this item
+  int32_t rbase;   // first reverse slot of the lysosome
+  int32_t pad[2];
+};
+
+struct SymUpd {    // one block of kmc_update_sym: up to 32 targets of one cell
+  int32_t l, t0, nt;    // lysosome, first target, targets (1..32)
+  int32_t fwd0, nfwd;   // forward-partial slots of the target's row group (consecutive)
+  int32_t rev0, nrev;   // reverse slots of the targets' cell, one per row group below
+  int32_t gt0;          // t0 minus the first target of the row group
+};
+
+// First reverse slot of cell h within its lysosome: cell h' holds one slot
+// per row group below it, floor(h' / gc) of them.
+__host__ __device__ inline int sym_rev_offset(int h, int gc) {
+  const int q = h / gc, r = h % gc;
+  return gc * q * (q - 1) / 2 + r * q;
+}
+
 struct RunState {   // advanced on the device at the end of each field period
   long long step_base;  // global index of step 0 of the current period
   int32_t period;       // period index within the run (< 0: not recorded)
@@ -142,7 +177,16 @@ struct StepArgs {
   int32_t n_items;          // work items of this launch (bounds checks of KMC_DEBUG builds)
   unsigned long long stall_wait_ns;
   int32_t n_lys;            // lysosomes of the context (bounds checks of KMC_DEBUG builds)
-  int32_t pad3;
+  int32_t gc;               // symmetric form: cells per row group
+  // symmetric form: the field kernel's items, the update kernel's items and the
+  // partial sums between them: forward [slot][6][gc 64] (sum, -error of 3
+  // components per target of the row group), reverse [slot][3][64]
+  const SymItem *sitems;
+  const SymUpd *supd;
+  float *sfwd;
+  float *srev;
+  int32_t n_upd;
+  int32_t pad4;
 };
 
 // Ref. [8] mode (kmc_mean.cuh): per lysosome, per work item, arguments.

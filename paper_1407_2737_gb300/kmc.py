@@ -35,10 +35,13 @@ EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
            "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall",
            "kmc_regenerate_rsa", "kmc_targets_per_lane", "kmc_plan_items",
-           "kmc_replicas_per_lane")
+           "kmc_replicas_per_lane", "kmc_pair_form", "kmc_plan_sym")
 KMC_NOALLOC_MAX_N = 8192
 KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
 KMC_ITEM_FIELDS = 8  # per work item in kmc_plan_items
+KMC_SYM_FIELDS = 8  # per field and update item in kmc_plan_sym
+KMC_CELL = 64  # NPs per cell of the symmetric pair form
+FORM_ORDERED, FORM_SYMMETRIC = 1, 2  # kmc_pair_form
 KMC_PHI_MAX_N = 64
 # KMC_READ_COUNTERS slots
 (CNT_JUMPS, CNT_NEAR, CNT_ONE_MIN, CNT_FALLBACK, CNT_RESCAN, CNT_POLISH,
@@ -101,6 +104,9 @@ def lib():
             L.kmc_debug_stall.argtypes = [vp]
             L.kmc_targets_per_lane.argtypes = [vp, C.c_int32, _I32]
             L.kmc_replicas_per_lane.argtypes = [vp, C.c_int32, _I32]
+            L.kmc_pair_form.argtypes = [vp, C.c_int32, _I32]
+            L.kmc_plan_sym.argtypes = [_I32, C.c_int32, C.c_int32, C.c_int32, _I32, C.c_int64,
+                                       _I64, _I32, C.c_int64, _I64, _I64, _I32, _I32, _I32]
             L.kmc_plan_items.argtypes = [_I32, C.c_int32, C.c_int, C.c_int32, C.c_int32,
                                          C.c_int32, C.c_int32, _I32, C.c_int64, _I64, _I32,
                                          _I32]
@@ -232,9 +238,44 @@ def kmc_plan_items(n, precision, tpl=1, chunk=0, blocks_per_sm=5, n_sms=0):
     return items[:cnt.value], [int(x) for x in cut[:nch.value + 1]]
 
 
+def kmc_plan_sym(n, gc, src_cells=0):
+    """The symmetric pair form's plan for lysosomes of n[l] NPs (host only, no
+    GPU): returns (items, upd, n_rev, cut_items, cut_upd). items: int32
+    [n_items, 8] of (lysosome, row group, first source cell, end source cell
+    (-1, -1: diagonal item), forward slot, first reverse slot of the
+    lysosome, 0, 0); upd: int32 [n_upd, 8] of (lysosome, first target,
+    targets, first forward slot, forward slots, first reverse slot, reverse
+    slots, first target minus the row group's first NP)."""
+    nn = np.ascontiguousarray(n, dtype=np.int32)
+    ni, nu, nr = C.c_int64(), C.c_int64(), C.c_int64()
+    nch = C.c_int32()
+    ci = np.zeros(KMC_MAX_CHAINS + 1, dtype=np.int32)
+    cu = np.zeros(KMC_MAX_CHAINS + 1, dtype=np.int32)
+    head = (nn.ctypes.data_as(_I32), len(nn), int(gc), int(src_cells))
+    tail = (C.byref(nr), ci.ctypes.data_as(_I32), cu.ctypes.data_as(_I32), C.byref(nch))
+    status = lib().kmc_plan_sym(*head, None, 0, C.byref(ni), None, 0, C.byref(nu), *tail)
+    if status != KMC_ECAPACITY:
+        _check(status)
+    items = np.zeros((max(ni.value, 1), KMC_SYM_FIELDS), dtype=np.int32)
+    upd = np.zeros((max(nu.value, 1), KMC_SYM_FIELDS), dtype=np.int32)
+    _check(lib().kmc_plan_sym(*head, items.ctypes.data_as(_I32), ni.value, C.byref(ni),
+                              upd.ctypes.data_as(_I32), nu.value, C.byref(nu), *tail))
+    return (items[:ni.value], upd[:nu.value], int(nr.value),
+            [int(x) for x in ci[:nch.value + 1]], [int(x) for x in cu[:nch.value + 1]])
+
+
+def kmc_pair_form(ctx, form=None):
+    """Pins the FP32 pair form (FORM_ORDERED or FORM_SYMMETRIC; 0 = autotuned)
+    or, with no argument, returns the form in use."""
+    r = C.c_int32()
+    _check(lib().kmc_pair_form(ctx.handle, -1 if form is None else int(form), C.byref(r)))
+    return int(r.value)
+
+
 def kmc_targets_per_lane(ctx, tpl=None):
-    """Pins the FP32 kernel's targets per lane (1 or 2; 0 = autotuned) or, with
-    no argument, returns the value in use."""
+    """Pins the FP32 kernel's targets per lane (1, 2 or 3 ordered; 2 or 4 in
+    the symmetric form; 0 = autotuned) or, with no argument, returns the value
+    in use."""
     t = C.c_int32()
     _check(lib().kmc_targets_per_lane(ctx.handle, -1 if tpl is None else int(tpl), C.byref(t)))
     return int(t.value)

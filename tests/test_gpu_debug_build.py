@@ -3,8 +3,10 @@ bracket checked against its bounds on the device; a failed check skips the
 access and kmc_sync reports KMC_ESTATE with the check's site) on the small and
 ragged cases where index arithmetic goes wrong first: lysosomes of 1, 2, 3 and
 33 NPs and one tile of sources minus one, exactly and plus one, in both
-precisions, one and two targets per lane, whole and split source ranges. Every
-launch must pass its checks, and the results must still match the oracle.
+precisions, one and two targets per lane, whole and split source ranges, and
+the symmetric pair form's field and update items over empty, partial and whole
+cells and row groups. Every launch must pass its checks, and the results must
+still match the oracle.
 
 The debug library is loaded in a child process (KMC_LIB_PATH), so that it does
 not replace the release build in this one."""
@@ -55,6 +57,30 @@ for prec, tile, sizes in ((kmc.KMC_FP32_MIXED, 64, (1, 2, 3, 33, 127, 128, 129))
             kmc.kmc_sync(ctx)  # raises KMC_ESTATE if a bounds check failed
             kmc.kmc_destroy(ctx)
             checked += 1
+# the symmetric pair form: field and update items, cells and row groups
+lyss = [inputs.make_lysosome(n, 12e-9, 0.05 if n > 3 else 0.01, seed=50 + n)
+        for n in (1, 2, 63, 64, 65, 129, 600)]
+for warps, cells, chunk in ((4, 1, 0), (4, 1, 64), (4, 2, 128), (8, 1, 0), (2, 2, 64)):
+    ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+    kmc.kmc_pair_form(ctx, kmc.FORM_SYMMETRIC)
+    kmc.kmc_targets_per_lane(ctx, 2 * cells)
+    kmc.kmc_tuning(ctx, warps, 32, chunk)
+    rng = np.random.default_rng(warps + cells + chunk)
+    m = np.concatenate([oracle.initial_moments(l.axis) + 0.3 * rng.normal(size=(l.n, 3))
+                        for l in lyss])
+    m /= np.linalg.norm(m, axis=1, keepdims=True)
+    m = m.astype(np.float32).astype(np.float64)
+    g = kmc.kmc_debug_step(ctx, np.full(len(lyss), 0.015), 5e-8, 3, 21, m)
+    off = 0
+    for l, ly in enumerate(lyss):
+        B = oracle.dipolar_field(ly.pos, ly.vol, ly.Ms, m[off:off + ly.n])
+        err = np.max(np.linalg.norm(g["B_dip"][off:off + ly.n] - B, axis=1))
+        assert err <= 1e-5 * rms(B) or ly.n == 1, ("sym", warps, cells, chunk, ly.n, err)
+        off += ly.n
+    kmc.kmc_run(ctx, 0.02, 1e5, 20, 2, 1, 5)
+    kmc.kmc_sync(ctx)
+    kmc.kmc_destroy(ctx)
+    checked += 1
 print("debug build: %d contexts passed their bounds checks" % checked)
 '''
 
