@@ -100,6 +100,45 @@ def lane_ops_per_pair(rpl):
     return 8.0 / rpl + 10.0
 
 
+def launch_info(kmc, ctx, lyss):
+    """The FP32 launch shape a context runs, its kernels and chains, and the
+    FP32 lane operations its pair loops issue per ordered pair. In the
+    symmetric form these come from its plan: a diagonal item issues 18 per
+    ordered pair of its row group (whole cells, padding included), an
+    off-diagonal item 28 packed operations per record and target, i.e. 14 lane
+    operations per ordered pair, over its cells."""
+    warps, tile, chunk = kmc.kmc_tuning(ctx)
+    tpl = kmc.kmc_targets_per_lane(ctx)
+    rpl = kmc.kmc_replicas_per_lane(ctx)
+    form = kmc.kmc_pair_form(ctx)
+    n = [l.n for l in lyss]
+    pairs = sum(v * (v - 1) for v in n)
+    launch = {"warps": warps, "tile": tile, "chunk": chunk, "targets_per_lane": tpl,
+              "replicas_per_lane": rpl}
+    if form == kmc.FORM_SYMMETRIC:
+        cells, cell = tpl // 2, kmc.KMC_CELL
+        gc = warps * cells
+        items, upd, _, cut, _ = kmc.kmc_plan_sym(n, gc, chunk // cell)
+        ops = 0
+        for l, g, h0, h1 in items[:, :4].tolist():
+            if h0 < 0:
+                ncv = min(gc, -(-n[l] // cell) - g * gc)
+                ops += 18 * (gc * cell) * (ncv * cell)
+            else:
+                ops += 14 * 2 * (gc * cell) * ((h1 - h0) * cell)
+        chains = len(cut) - 1
+        launch.update({"pair_form": "symmetric", "chains": chains, "field_items": len(items),
+                       "update_items": len(upd)})
+        return {"launch": launch, "kernel": "kmc_field_sym<%d, %d> + kmc_update_sym<%d>" % (
+                    warps, cells, gc), "lane_ops_per_pair": ops / pairs, "chains": chains,
+                "launches_per_step": 2 * chains, "key": (warps, tile, chunk, tpl, rpl, "sym")}
+    chains = min(len(lyss) // max(rpl, 1), kmc.KMC_MAX_CHAINS)
+    launch.update({"pair_form": "ordered", "chains": chains})
+    return {"launch": launch, "kernel": step_kernel(warps, tpl, rpl),
+            "lane_ops_per_pair": lane_ops_per_pair(rpl), "chains": chains,
+            "launches_per_step": chains, "key": (warps, tile, chunk, tpl, rpl)}
+
+
 def fp32_lane_ops_peak():
     """FP32 lane operations per second: SMs x lanes x maximum SM clock."""
     return SMS * FP32_LANES * SM_MAX_MHZ * 1e6
@@ -534,9 +573,7 @@ def measure_sub_config(name, kmc, inputs, torch, stream, flush, warmup, uuid=Non
         kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
                     run["seed"])
     kmc.kmc_sync(ctx)
-    warps, tile, chunk = kmc.kmc_tuning(ctx)
-    tpl = kmc.kmc_targets_per_lane(ctx)
-    rpl = kmc.kmc_replicas_per_lane(ctx)
+    info = launch_info(kmc, ctx, lyss)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(cfg["steps"])]
     torch.cuda.synchronize()
@@ -553,7 +590,6 @@ def measure_sub_config(name, kmc, inputs, torch, stream, flush, warmup, uuid=Non
     kmc.kmc_destroy(ctx)
     value = n_np * n_steps * cfg["steps"] / t
     achieved = FLOPS_PER_PAIR * pairs * n_steps * cfg["steps"] / t / 1e12
-    chains = min(len(lyss), kmc.KMC_MAX_CHAINS)
     # FP64-plain on a bounded sample (rate only)
     c64 = kmc.kmc_create(lyss, kmc.KMC_FP64_PLAIN, center=np.zeros(3))
     kmc.kmc_set_stream(c64, stream.cuda_stream)
@@ -590,19 +626,19 @@ def measure_sub_config(name, kmc, inputs, torch, stream, flush, warmup, uuid=Non
         "pair_interactions_per_s": pairs * n_steps * cfg["steps"] / t,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops(),
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops(),
-                     "frac_issued": pairs * n_steps * cfg["steps"] / t * lane_ops_per_pair(rpl)
-                     / fp32_lane_ops_peak(),
-                     "traffic": STEP_DRAM_BYTES.get((name, warps, tile, chunk, tpl, rpl)),
-                     "kernel": step_kernel(warps, tpl, rpl)},
-        "launch": {"warps": warps, "tile": tile, "chunk": chunk, "targets_per_lane": tpl,
-                   "replicas_per_lane": rpl, "chains": chains},
+                     "frac_issued": pairs * n_steps * cfg["steps"] / t
+                     * info["lane_ops_per_pair"] / fp32_lane_ops_peak(),
+                     "lane_ops_per_pair": info["lane_ops_per_pair"],
+                     "traffic": STEP_DRAM_BYTES.get((name,) + info["key"]),
+                     "kernel": info["kernel"]},
+        "launch": info["launch"],
         "fp64_plain": {"value": v64, "unit": UNIT, "speedup_fp32_mixed": value / v64,
                        "sample": "%d steps of the whole workload" % S64,
                        "launch": dict(zip(("warps", "tile", "chunk"), cfg["shape64"]))},
         "e2e": {"value": n_np * n_steps / te, "unit": UNIT,
                 "h2d_bytes_per_step": sum(l.n * 7 * 8 for l in lyss) + 8 * len(lyss),
                 "d2h_bytes_per_step": sum(8 + 8 * n_rec + 8 * l.n for l in lyss)},
-        "gpu_launches": 1 + run["periods"] * (run["S"] * chains + 1),
+        "gpu_launches": 1 + run["periods"] * (run["S"] * info["launches_per_step"] + 1),
         "clocks": clk.summary(),
     }
 
@@ -683,9 +719,7 @@ def main():
         kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],
                     run["seed"])
     kmc.kmc_sync(ctx)
-    warps, tile, chunk = kmc.kmc_tuning(ctx)
-    tpl = kmc.kmc_targets_per_lane(ctx)
-    rpl = kmc.kmc_replicas_per_lane(ctx)
+    info = launch_info(kmc, ctx, lyss)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     uuid = None
@@ -711,8 +745,7 @@ def main():
     # one step = one step-kernel launch per chain (equal lysosomes: one chain
     # each, up to KMC_MAX_CHAINS; with replicas per lane one per set of them),
     # run concurrently; one period advance
-    chains = min(len(lyss) // max(rpl, 1), kmc.KMC_MAX_CHAINS)
-    launches_per_step = 1 + run["periods"] * (run["S"] * chains + 1)
+    launches_per_step = 1 + run["periods"] * (run["S"] * info["launches_per_step"] + 1)
     # roofline of the fused step kernel over one kMC step (all chains' launches)
     launch_s = t_total / (args.steps * n_steps)
     achieved = FLOPS_PER_PAIR * pairs_per_launch / launch_s / 1e12
@@ -802,9 +835,7 @@ def main():
                                       "%d periods (%d discarded) of the workload" % bounded),
                        "precision": "KMC_FP32_MIXED",
                        "kmc_steps_per_bench_step": n_steps, "particles": n_np,
-                       "launch": {"warps": warps, "tile": tile, "chunk": chunk,
-                                  "targets_per_lane": tpl, "replicas_per_lane": rpl,
-                                  "chains": chains},
+                       "launch": info["launch"],
                        "l2": "256 MB buffer written between timed steps (state < L2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "pair_interactions_per_s": world * pairs_per_launch * n_steps * args.steps / t_total,
@@ -812,15 +843,16 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "frac_issued": achieved / FLOPS_PER_PAIR * 1e12
-                         * lane_ops_per_pair(rpl) / fp32_lane_ops_peak(),
-                         "traffic": STEP_DRAM_BYTES.get((args.config, warps, tile, chunk,
-                                                         tpl, rpl)),
-                         "kernel": step_kernel(warps, tpl, rpl),
+                         * info["lane_ops_per_pair"] / fp32_lane_ops_peak(),
+                         "lane_ops_per_pair": info["lane_ops_per_pair"],
+                         "traffic": STEP_DRAM_BYTES.get((args.config,) + info["key"]),
+                         "kernel": info["kernel"],
                          "note": "FP32 pipe: 30 flops per ordered pair; frac_issued counts "
                                  "the FP32 lane operations the loop issues instead (18 per "
                                  "pair, 8/r + 10 with r replicas per lane sharing each "
-                                 "pair's geometry); a kMC step is one "
-                                 "launch per chain, the chains' launches concurrent; step "
+                                 "pair's geometry, 14 in the symmetric form's off-diagonal "
+                                 "items); a kMC step is one launch per chain (two in the "
+                                 "symmetric form), the chains' launches concurrent; step "
                                  "time = timed region / kMC steps (includes graph gaps); "
                                  "peak = 152 SM x 128 lanes x 2 x 2070 MHz (nominal; FFMA "
                                  "chains measured 74.6 TFLOP/s); traffic = ncu DRAM bytes of "

@@ -1402,11 +1402,14 @@ __global__ void kmc_advance_kernel(RunState *rs, int S) {
 // masked). Every sum runs in a fixed order, so results do not depend on the
 // launch.
 //
-// Update kernel: per 32 targets of one cell, the forward partials of the
-// target's row group (diagonal item first, then the source ranges in order)
-// and the reverse slots of its cell (row groups in order) are added with
-// compensation (warp w takes slots w, w + 4, ...; the warps in order), then
-// steps iii-vii run as in kmc_step_f32<4>.
+// Update kernel: each warp takes one update item, 32 targets of one cell: it
+// adds, with compensation, the forward partials of the targets' row group
+// (diagonal item first, then the source ranges in order) and the reverse
+// slots of their cell (row groups in order), then runs steps iii-vii for its
+// targets alone (the warp-level path of block_update, whose results are those
+// of the block-cooperative one). The update is a separate kernel here, so its
+// throughput, not its latency, counts: no warp waits while another sets up
+// planes or decides.
 constexpr int kSymUpdWarps = 4;
 
 template <int T>
@@ -1480,10 +1483,10 @@ __device__ __forceinline__ bool sym_item_in_bounds(const StepArgs &a, int gc) {
   return true;
 }
 
-__device__ __forceinline__ bool sym_upd_in_bounds(const StepArgs &a, int gc) {
+__device__ __forceinline__ bool sym_upd_in_bounds(const StepArgs &a, int gc, int ui) {
 #ifdef KMC_DEBUG
-  if (!KMC_DCHECK(static_cast<int>(blockIdx.x) < a.n_upd, a.err, kSiteItem)) return false;
-  const SymUpd u = a.supd[blockIdx.x];
+  if (!KMC_DCHECK(ui < a.n_upd, a.err, kSiteItem)) return false;
+  const SymUpd u = a.supd[ui];
   if (!KMC_DCHECK(u.l >= 0 && u.l < a.n_lys, a.err, kSiteLys)) return false;
   const int n = a.lys[u.l].n;
   if (!KMC_DCHECK(u.t0 >= 0 && u.nt >= 1 && u.nt <= kTargets && u.t0 + u.nt <= n &&
@@ -1675,10 +1678,12 @@ __global__ void __launch_bounds__(kSymUpdWarps * 32) kmc_update_sym(const StepAr
   unsigned char *dyn = smem + 16;
   __shared__ GridTables<float> tab;
   tab.load();
-  if (!sym_upd_in_bounds(a, GC)) return;
-  const SymUpd u = a.supd[blockIdx.x];
-  const LysDev L = a.lys[u.l];
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ui = blockIdx.x * NW + warp;  // this warp's update item
+  if (ui >= a.n_upd || !sym_upd_in_bounds(a, GC, ui)) return;
+  const SymUpd u = a.supd[ui];
+  const LysDev L = a.lys[u.l];
   Item it;
   it.l = u.l;
   it.t0 = u.t0;
@@ -1691,49 +1696,53 @@ __global__ void __launch_bounds__(kSymUpdWarps * 32) kmc_update_sym(const StepAr
   const long long step = a.rs->step_base + a.k_local;
   const int per = a.rs->period;
   const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
-  TargetIn<float4> tin;
-  if (warp == 0) tin = load_target<float4>(a, L, it, step, lane);
+  const TargetIn<float4> tin = load_target<float4>(a, L, it, step, lane);
   // lanes past the last target repeat it (their results are not written)
   const int tl = min(lane, u.nt - 1);
   const int gi = u.gt0 + tl, ci = (u.t0 + tl) % kCell;
+  // the slots in order; each batch's loads are issued before its additions
   float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+  constexpr int kFwdBatch = 4, kRevBatch = 8;
 #pragma unroll 1
-  for (int sl = warp; sl < u.nfwd; sl += NW) {
-    const float *p = a.sfwd + static_cast<size_t>(u.fwd0 + sl) * 6 * GT;
+  for (int s0 = 0; s0 < u.nfwd; s0 += kFwdBatch) {
+    float v[kFwdBatch][6];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      neumaier_add(hi[q], lo[q], __ldcg(p + q * GT + gi));
-      lo[q] += __ldcg(p + (3 + q) * GT + gi);
+    for (int b = 0; b < kFwdBatch; ++b) {
+      const float *p = a.sfwd + static_cast<size_t>(u.fwd0 + min(s0 + b, u.nfwd - 1)) * 6 * GT;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v[b][q] = __ldcg(p + q * GT + gi);
     }
-  }
-#pragma unroll 1
-  for (int sl = warp; sl < u.nrev; sl += NW) {
-    const float *p = a.srev + static_cast<size_t>(u.rev0 + sl) * 3 * kCell;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) neumaier_add(hi[q], lo[q], __ldcg(p + q * kCell + ci));
-  }
-  float *wp = reinterpret_cast<float *>(dyn);  // [NW][6][32]
+    for (int b = 0; b < kFwdBatch; ++b) {
+      if (s0 + b >= u.nfwd) break;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    wp[(warp * 6 + q) * 32 + lane] = hi[q];
-    wp[(warp * 6 + 3 + q) * 32 + lane] = lo[q];
-  }
-  __syncthreads();
-  EpiShared<float> &sm =
-      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 6 * 32 * 4);
-  if (warp == 0) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      float s = 0.f, e = 0.f;
-      for (int w = 0; w < NW; ++w) {
-        neumaier_add(s, e, wp[(w * 6 + q) * 32 + lane]);
-        e += wp[(w * 6 + 3 + q) * 32 + lane];
+      for (int q = 0; q < 3; ++q) {
+        neumaier_add(hi[q], lo[q], v[b][q]);
+        lo[q] += v[b][3 + q];
       }
-      sm.h[q][lane] = s + e;  // compensation added last
     }
   }
-  __syncthreads();
-  block_update<float4, true>(a, L, it, step, rec, tin, sm, tab);
+#pragma unroll 1
+  for (int s0 = 0; s0 < u.nrev; s0 += kRevBatch) {
+    float v[kRevBatch][3];
+#pragma unroll
+    for (int b = 0; b < kRevBatch; ++b) {
+      const float *p = a.srev + static_cast<size_t>(u.rev0 + min(s0 + b, u.nrev - 1)) * 3 * kCell;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[b][q] = __ldcg(p + q * kCell + ci);
+    }
+#pragma unroll
+    for (int b = 0; b < kRevBatch; ++b) {
+      if (s0 + b >= u.nrev) break;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) neumaier_add(hi[q], lo[q], v[b][q]);
+    }
+  }
+  EpiShared<float> &sm = reinterpret_cast<EpiShared<float> *>(dyn)[warp];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) sm.h[q][lane] = hi[q] + lo[q];  // compensation added last
+  __syncwarp();
+  block_update<float4, true, true>(a, L, it, step, rec, tin, sm, tab);
   grid_launch_dependents();
 }
 
@@ -1828,8 +1837,8 @@ static cudaError_t launch_sym_wc(const StepArgs &a, int n_field, cudaStream_t st
   if (n_field > 0)
     e = launch_items(kmc_field_sym<W, C>, a, n_field, W * 32, sym_field_smem(W, C), 0, st, pdl);
   if (e == cudaSuccess && a.n_upd > 0)
-    e = launch_items(kmc_update_sym<W * C>, a, a.n_upd, kSymUpdWarps * 32,
-                     16 + epi_bytes<float>(kSymUpdWarps), 0, st, pdl);
+    e = launch_items(kmc_update_sym<W * C>, a, (a.n_upd + kSymUpdWarps - 1) / kSymUpdWarps,
+                     kSymUpdWarps * 32, 16 + kSymUpdWarps * sizeof(EpiShared<float>), 0, st, pdl);
   return e;
 }
 

@@ -104,7 +104,7 @@ def test_batched_workload_against_oracle():
     lyss, run = inputs.config_batched(n_lys=512, seed=0)
     ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
     kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"])  # tunes
-    shape = kmc.kmc_tuning(ctx) + (kmc.kmc_targets_per_lane(ctx),)
+    shape = kmc.kmc_tuning(ctx) + (kmc.kmc_targets_per_lane(ctx), kmc.kmc_pair_form(ctx))
     m_all = np.concatenate([kmc.kmc_read(ctx, kmc.KMC_READ_MOMENTS, l) for l in range(512)])
     axes = [kmc.kmc_read(ctx, kmc.KMC_READ_AXES, l) for l in range(512)]
     offs = np.concatenate([[0], np.cumsum([l.n for l in lyss])])
@@ -131,7 +131,8 @@ def test_batched_workload_against_oracle():
         tot_c += c
         tot_a += a
     assert tot_c >= 0.95 * (tot_c + tot_a), (tot_c, tot_a)
-    assert shape[3] in (1, 2)
+    # ordered kernels at 1-3 targets per lane, or the symmetric form at 2 or 4
+    assert shape[3] in ((1, 2, 3) if shape[4] == kmc.FORM_ORDERED else (2, 4)), shape
 
 
 def test_batched_subset_fp64_flip_for_flip():
