@@ -76,11 +76,14 @@ CONFIGS = {
 }
 FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
 # DRAM bytes (read + write) of one kMC step in steady state, by (workload,
-# warps, tile, chunk, targets per lane, replicas per lane), from ncu captures of
-# the committed kernel with --cache-control none (the state stays in L2 between
-# launches, as in the bench). c1: 8 chains, one launch each: 8 x the mean over
-# 16 launches. c4: one launch per step, the mean over 2.
-STEP_DRAM_BYTES = {("c1", 4, 256, 1024, 1, 1): 512.0, ("c4", 8, 512, 8192, 2, 1): 512.0}
+# warps, tile, chunk, targets per lane, replicas per lane[, "sym"]), from ncu
+# captures of the committed kernels with --cache-control none (the state stays
+# in L2 between launches, as in the bench). c1: 8 chains, one launch each: 8 x
+# the mean over 16 launches. c4: one launch per step, the mean over 2; in the
+# symmetric form one field and one update launch, which write and read back
+# the partial sums (88.7 MB per step at 512-NP items, partly held in L2).
+STEP_DRAM_BYTES = {("c1", 4, 256, 1024, 1, 1): 512.0, ("c4", 8, 512, 8192, 2, 1): 512.0,
+                   ("c4", 4, 32, 512, 4, 1, "sym"): 97.05e6}
 
 
 def step_kernel(warps, tpl, rpl):

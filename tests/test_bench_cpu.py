@@ -50,8 +50,14 @@ def test_traffic_figures_come_from_committed_profiles():
     prof = os.path.join(ROOT, "profiles")
     text = "".join(open(os.path.join(prof, f)).read() for f in sorted(os.listdir(prof)))
     assert bench.STEP_DRAM_BYTES
-    for (cfg, warps, tile, chunk, tpl, rpl), nbytes in bench.STEP_DRAM_BYTES.items():
+    for key, nbytes in bench.STEP_DRAM_BYTES.items():
+        (cfg, warps, tile, chunk, tpl, rpl), sym = key[:6], key[6:] == ("sym",)
+        assert len(key) == 6 or sym, key
         assert cfg == "c1" or cfg in bench.CONFIGS, cfg
-        assert tile & (tile - 1) == 0 and chunk % 64 == 0 and tpl in (1, 2, 3)
-        assert (warps in (4, 8, 16) and rpl == 1) or (rpl in (2, 4) and warps == rpl)
+        assert tile & (tile - 1) == 0 and chunk % 64 == 0
+        if sym:
+            assert tile == 32 and rpl == 1 and (warps, tpl) in ((4, 2), (4, 4), (8, 2), (2, 4))
+        else:
+            assert tpl in (1, 2, 3)
+            assert (warps in (4, 8, 16) and rpl == 1) or (rpl in (2, 4) and warps == rpl)
         assert "%.4g MB" % (nbytes / 1e6) in text, (cfg, nbytes)
