@@ -244,6 +244,20 @@ kmc_status kmc_replicas_per_lane(kmc_ctx *ctx, int32_t rpl, int32_t *rpl_out);
  * tuning) is returned through form_out (may be NULL); form = -1 only reads it. */
 kmc_status kmc_pair_form(kmc_ctx *ctx, int32_t form, int32_t *form_out);
 
+/* Cluster split of the FP32 one-target-per-lane step kernel. When every
+ * target group's sources are split into exactly two parts (kmc_tuning's chunk
+ * with one target per lane), the two parts can run as the two CTAs of a
+ * thread-block cluster: the second hands its sums to the first through
+ * distributed shared memory, and the first adds them in split order and runs
+ * steps iii-vii. That replaces the exchange through global memory (stores,
+ * fences, an arrival counter) with two cluster barriers; the results are the
+ * same bits. mode: 0 lets the autotuner choose (the default: it times both
+ * where the plan allows), 1 off, 2 on (KMC_EINVAL on FP64 contexts; a run or
+ * debug step whose plan does not split every group in two fails with
+ * KMC_EINVAL). The value in use (0 before the first tuning) is returned
+ * through mode_out (may be NULL); mode = -1 only reads it. */
+kmc_status kmc_cluster_split(kmc_ctx *ctx, int32_t mode, int32_t *mode_out);
+
 /* Fields of one field item and of one update item in kmc_plan_sym's output. */
 #define KMC_SYM_FIELDS 8
 

@@ -120,9 +120,13 @@ struct Shape {
   // symmetric pair form (FP32): cells per warp (1 or 2; tpl = 2 sym, tile = 32,
   // chunk = source NPs per field item, 0 = a whole row); 0 = the ordered kernels
   int sym = 0;
+  // cluster split (FP32, one target per lane): 2 = every target group's two
+  // source parts run as a two-CTA cluster and exchange their sums through
+  // distributed shared memory; 0 = through global memory
+  int cl = 0;
   bool operator==(const Shape &o) const {
     return warps == o.warps && tile == o.tile && chunk == o.chunk && tpl == o.tpl &&
-           rpl == o.rpl && sym == o.sym;
+           rpl == o.rpl && sym == o.sym && cl == o.cl;
   }
 };
 
@@ -130,10 +134,11 @@ struct TuneKey {
   int prec;
   long long N;
   int n_lys, max_n, tpl_mode, rpl_mode, reps;  // reps: replica sets available (bits)
-  int form_mode;
+  int form_mode, cl_mode;
   bool operator<(const TuneKey &o) const {
-    return std::tie(prec, N, n_lys, max_n, tpl_mode, rpl_mode, reps, form_mode) <
-           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode, o.reps, o.form_mode);
+    return std::tie(prec, N, n_lys, max_n, tpl_mode, rpl_mode, reps, form_mode, cl_mode) <
+           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode, o.reps, o.form_mode,
+                    o.cl_mode);
   }
 };
 std::mutex g_tune_mu;
@@ -210,6 +215,7 @@ struct kmc_ctx {
   int n_sitems = 0, n_supd = 0;
   std::vector<int> sym_cut_items, sym_cut_upd;
   int form_mode = 0;           // pair form: 0 = the autotuner's choice, 1 = ordered, 2 = symmetric
+  int cl_mode = 0;             // cluster split: 0 = the autotuner's choice, 1 = off, 2 = on
   int tpl_mode = 0;            // targets per lane: 0 = the autotuner's choice, else 1, 2 or 3
   int rpl_mode = 0;            // replicas per lane: 0 = the autotuner's choice, 1 = off, 2 or 4
   bool rep_ok[5] = {};         // [k]: the lysosomes form sets of k identical consecutive ones
@@ -511,6 +517,11 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   for (int l = 0; l < c->n_lys; l += sh.rpl) np.push_back(c->n[l]);
   Plan plan = plan_items(np, c->fp32, sh.chunk, per_sm, n_sms, sh.tpl);
   for (Item &it : plan.items) it.l *= sh.rpl;
+  if (sh.cl == 2) {  // two-CTA clusters: exactly two parts per group, item 2 g + part
+    for (size_t u = 0; u < plan.items.size(); ++u)
+      if (plan.items[u].nsplit != 2 || plan.items[u].split != static_cast<int>(u & 1))
+        return fail(KMC_EINVAL, "the cluster split needs exactly two source parts per group");
+  }
   const std::vector<Item> &items = plan.items;
   const int groups = plan.groups;
   KMC_CUDA(cudaStreamSynchronize(c->stream));
@@ -603,7 +614,8 @@ cudaError_t launch_one_step(const kmc_ctx *c, StepArgs a, const Shape &sh, cudaS
     a.gc = sh.warps * sh.sym;
     return kmc::launch_sym(a, sh.warps, sh.sym, c->n_sitems, st, pdl);
   }
-  return kmc::launch_step(c->fp32, sh.warps, sh.tile, a, c->n_items, st, pdl, sh.tpl, sh.rpl);
+  return kmc::launch_step(c->fp32, sh.warps, sh.tile, a, c->n_items, st, pdl, sh.tpl, sh.rpl,
+                          sh.cl);
 }
 
 kmc_status refresh_sources(kmc_ctx *c, int par) {
@@ -663,6 +675,8 @@ bool shape_ok(const kmc_ctx *c, const Shape &s) {
     return s.chunk >= 0 && s.chunk % kmc::kCell == 0;
   }
   if (s.tpl > 3) return false;
+  if (s.cl != 0 && (s.cl != 2 || !c->fp32 || s.tpl != 1 || s.rpl != 1 || s.chunk <= 0))
+    return false;
   if (s.rpl > 1) {  // replicas: their kernel has one warp per replica
     if (!c->fp32 || s.tpl != 1 || s.warps != s.rpl || !c->rep_ok[s.rpl]) return false;
     if (s.tile < 32 || s.tile > 128 || (s.tile & (s.tile - 1))) return false;
@@ -731,7 +745,7 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
         b.cos_k = std::cos(2.0 * kPi * k / steps);
       }
       ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, b, c->chain_cut[q + 1] - u0, st, true,
-                            sh.tpl, sh.rpl);
+                            sh.tpl, sh.rpl, sh.cl);
     }
   }
   // join, then the period advance
@@ -809,7 +823,8 @@ kmc_status autotune(kmc_ctx *c) {
   for (int x : c->n) max_n = std::max(max_n, x);
   const TuneKey key{c->fp32, c->N,        c->n_lys,
                     max_n,   c->tpl_mode, c->rpl_mode,
-                    (c->rep_ok[2] ? 1 : 0) | (c->rep_ok[4] ? 2 : 0), c->form_mode};
+                    (c->rep_ok[2] ? 1 : 0) | (c->rep_ok[4] ? 2 : 0), c->form_mode,
+                    c->cl_mode};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -917,10 +932,22 @@ kmc_status autotune(kmc_ctx *c) {
           s.tile = t;
           s.chunk = ch;
           s.tpl = tpl;
-          const float ms = time_shape(c, s);
-          if (ms > 0.f && ms < best) {
-            best = ms;
-            bs = s;
+          if (c->cl_mode != 2) {
+            const float ms = time_shape(c, s);
+            if (ms > 0.f && ms < best) {
+              best = ms;
+              bs = s;
+            }
+          }
+          // the same shape with each group's two parts as a two-CTA cluster
+          // (time_shape fails unless every group has exactly two parts)
+          if (c->fp32 && tpl == 1 && ch > 0 && c->cl_mode != 1) {
+            s.cl = 2;
+            const float mc = time_shape(c, s);
+            if (mc > 0.f && mc < best) {
+              best = mc;
+              bs = s;
+            }
           }
         }
       }
@@ -1348,6 +1375,25 @@ kmc_status kmc_pair_form(kmc_ctx *c, int32_t form, int32_t *form_out) {
   return KMC_OK;
 }
 
+kmc_status kmc_cluster_split(kmc_ctx *c, int32_t mode, int32_t *mode_out) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (mode != -1) {
+    if (mode < 0 || mode > 2) return fail(KMC_EINVAL, "cluster split: 0 (autotuned), 1 (off), 2 (on)");
+    if (mode == 2 && !c->fp32) return fail(KMC_EINVAL, "the cluster split runs on FP32 contexts");
+    c->cl_mode = mode;
+    // the shape in use follows a pinned choice
+    if (mode != 0 && c->shape.warps != 0 && c->shape.sym == 0 && c->shape.rpl == 1 &&
+        c->shape.tpl == 1) {
+      Shape s = c->shape;
+      s.cl = mode == 2 ? 2 : 0;
+      c->shape = shape_ok(c, s) ? s : Shape();
+    }
+  }
+  if (mode_out)
+    *mode_out = c->cl_mode != 0 ? c->cl_mode : (c->shape.warps ? (c->shape.cl ? 2 : 1) : 0);
+  return KMC_OK;
+}
+
 kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
                       int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
@@ -1362,7 +1408,9 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
     s.chunk = chunk;
     s.tpl = c->tpl_mode != 0 ? c->tpl_mode : 1;
     s.rpl = c->rpl_mode > 1 ? c->rpl_mode : 1;
+    s.cl = (c->cl_mode == 2 && s.tpl == 1 && s.rpl == 1) ? 2 : 0;
     if (c->form_mode == 2 || c->tpl_mode == 4) {  // symmetric form; the tile does not apply
+      s.cl = 0;
       s.sym = c->tpl_mode == 4 ? 2 : 1;
       s.tpl = 2 * s.sym;
       s.tile = 32;

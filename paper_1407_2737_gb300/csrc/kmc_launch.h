@@ -20,8 +20,12 @@ size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl = 1, int rpl 
 // targets per lane. rpl = 2 or 4 (FP32 only, tpl = 1, warps = rpl): each item
 // is 32 targets of rpl replica lysosomes it.l .. it.l + rpl - 1 that share
 // their geometry (kmc_step_f32_rep).
+// cl = 2 (FP32, one target per lane): every target group has exactly two
+// source parts, items 2 g and 2 g + 1, which run as a two-CTA cluster and
+// exchange their sums through distributed shared memory; n_items even.
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
-                        cudaStream_t st, bool pdl = false, int tpl = 1, int rpl = 1);
+                        cudaStream_t st, bool pdl = false, int tpl = 1, int rpl = 1,
+                        int cl = 0);
 
 // Symmetric pair form (FP32): one step = kmc_field_sym<warps, cells> over
 // a.sitems[0 .. n_field) and then kmc_update_sym over a.supd[0 .. a.n_upd).

@@ -727,7 +727,13 @@ __device__ __forceinline__ bool tile_in_bounds(const StepArgs &a, const Item &it
 
 // ---------------------------------------------------------------------------
 // FP32-mixed step kernel.
-template <int NW>
+// CL: the two source parts of every target group run as the two CTAs of a
+// thread-block cluster (rank = part); part 1 hands its combined sums to part
+// 0 through distributed shared memory instead of global memory, fences and an
+// arrival counter, and part 0 adds them in split order (the same operations,
+// so the same bits) and runs the update. Every thread of both CTAs passes the
+// same two cluster barriers, on the failure paths too.
+template <int NW, bool CL = false>
 __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int tile) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -735,7 +741,16 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
   __shared__ int s_last;
   __shared__ GridTables<float> tab;
   tab.load();
-  if (!item_in_bounds(a, 1, true)) return;
+  if (!item_in_bounds(a, 1, true) ||
+      (CL && !KMC_DCHECK(a.items[blockIdx.x].nsplit == 2 &&
+                             static_cast<int>(blockIdx.x & 1) == a.items[blockIdx.x].split,
+                         a.err, kSiteSplit))) {
+    if constexpr (CL) {
+      cluster_sync();
+      cluster_sync();
+    }
+    return;
+  }
   const Item it = a.items[blockIdx.x];
   const LysDev L = a.lys[it.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -779,7 +794,13 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
     kahan_add(s3[1], c3[1], hsum(acc.y));
     kahan_add(s3[2], c3[2], hsum(acc.z));
   };
-  if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
+  if (!staged_loop(ntiles, bar, a.err, issue, body)) {
+    if constexpr (CL) {
+      cluster_sync();
+      cluster_sync();
+    }
+    return;
+  }
 
   // cross-warp combine in a fixed order: value = hi + lo per component
   float *wp = reinterpret_cast<float *>(dyn);  // [NW][6][32]
@@ -803,7 +824,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
       hi[c] = s;
       lo[c] = e;
     }
-    if (it.nsplit > 1) {
+    if (!CL && it.nsplit > 1) {
       float *part = a.partial + static_cast<size_t>(blockIdx.x) * kPartF32;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -813,7 +834,31 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
       __threadfence();
     }
   }
-  if (it.nsplit > 1) {
+  if constexpr (CL) {
+    __shared__ float s_xch[6][kTargets];  // part 1's (sum, error) per component
+    if (warp == 0 && it.split == 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        s_xch[c][lane] = hi[c];
+        s_xch[3 + c][lane] = lo[c];
+      }
+    }
+    cluster_sync();
+    if (warp == 0 && it.split == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float s = 0.f, e = 0.f;
+        neumaier_add(s, e, hi[c]);
+        e += lo[c];
+        neumaier_add(s, e, ld_cluster(&s_xch[c][lane], 1));
+        e += ld_cluster(&s_xch[3 + c][lane], 1);
+        hi[c] = s;
+        lo[c] = e;
+      }
+    }
+    cluster_sync();  // part 0 has read part 1's shared memory
+    if (it.split != 0) return;
+  } else if (it.nsplit > 1) {
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
     __syncthreads();
@@ -1766,23 +1811,42 @@ size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl, int rpl) {
 // programmatic stream serialisation attribute.
 template <typename K>
 static cudaError_t launch_items(K kernel, const StepArgs &a, int n_items, int threads,
-                                size_t smem, int tile, cudaStream_t st, bool pdl) {
+                                size_t smem, int tile, cudaStream_t st, bool pdl,
+                                int cluster = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(n_items));
   cfg.blockDim = dim3(static_cast<unsigned>(threads));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (cluster > 1) {
+    if (n_items % cluster != 0) return cudaErrorInvalidValue;
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = static_cast<unsigned>(cluster);
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kernel, a, tile);
 }
 
 template <int NW>
 static cudaError_t launch_f32(const StepArgs &a, int n_items, int tile, cudaStream_t st,
-                              bool pdl, int tpl) {
+                              bool pdl, int tpl, int cl) {
+  if (cl == 2) {
+    if (tpl != 1) return cudaErrorInvalidValue;
+    return launch_items(kmc_step_f32<NW, true>, a, n_items, NW * 32,
+                        step_smem_bytes(1, NW, tile, 1), tile, st, pdl, 2);
+  }
+  if (cl != 0) return cudaErrorInvalidValue;
   if (tpl == 2)
     return launch_items(kmc_step_f32_tn<NW, 2>, a, n_items, NW * 32,
                         step_smem_bytes(1, NW, tile, 2), tile, st, pdl);
@@ -1801,8 +1865,9 @@ static cudaError_t launch_f64(const StepArgs &a, int n_items, int tile, cudaStre
 }
 
 cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, int n_items,
-                        cudaStream_t st, bool pdl, int tpl, int rpl) {
+                        cudaStream_t st, bool pdl, int tpl, int rpl, int cl) {
   if (n_items <= 0) return cudaSuccess;
+  if (cl != 0 && (!prec_fp32 || rpl > 1)) return cudaErrorInvalidValue;
   if (rpl > 1) {
     if (!prec_fp32 || tpl != 1 || warps != rpl) return cudaErrorInvalidValue;
     const size_t smem = step_smem_bytes(1, warps, tile, 1, rpl);
@@ -1814,9 +1879,9 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
   }
   if (prec_fp32) {
     switch (warps) {
-      case 4: return launch_f32<4>(a, n_items, tile, st, pdl, tpl);
-      case 8: return launch_f32<8>(a, n_items, tile, st, pdl, tpl);
-      case 16: return launch_f32<16>(a, n_items, tile, st, pdl, tpl);
+      case 4: return launch_f32<4>(a, n_items, tile, st, pdl, tpl, cl);
+      case 8: return launch_f32<8>(a, n_items, tile, st, pdl, tpl, cl);
+      case 16: return launch_f32<16>(a, n_items, tile, st, pdl, tpl, cl);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -1964,6 +2029,9 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<16>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32<4, true>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32<8, true>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32<16, true>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<4, 2>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<8, 2>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<16, 2>);

@@ -5,7 +5,7 @@ ragged cases where index arithmetic goes wrong first: lysosomes of 1, 2, 3 and
 33 NPs and one tile of sources minus one, exactly and plus one, in both
 precisions, one and two targets per lane, whole and split source ranges, and
 the symmetric pair form's field and update items over empty, partial and whole
-cells and row groups. Every launch must pass its checks, and the results must
+cells and row groups, and the cluster split. Every launch must pass its checks, and the results must
 still match the oracle.
 
 The debug library is loaded in a child process (KMC_LIB_PATH), so that it does
@@ -81,6 +81,16 @@ for warps, cells, chunk in ((4, 1, 0), (4, 1, 64), (4, 2, 128), (8, 1, 0), (2, 2
     kmc.kmc_sync(ctx)
     kmc.kmc_destroy(ctx)
     checked += 1
+# the cluster split: two-CTA clusters over groups of exactly two source parts
+lyss = [inputs.make_lysosome(n, 12e-9, 0.05, seed=30 + n) for n in (2000, 1030)]
+ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
+kmc.kmc_targets_per_lane(ctx, 1)
+kmc.kmc_cluster_split(ctx, 2)
+kmc.kmc_tuning(ctx, 4, 128, 1024)
+kmc.kmc_run(ctx, 0.02, 1e5, 20, 2, 1, 5)
+kmc.kmc_sync(ctx)
+kmc.kmc_destroy(ctx)
+checked += 1
 print("debug build: %d contexts passed their bounds checks" % checked)
 '''
 
