@@ -116,7 +116,8 @@ __global__ void sources_f64(const dbl4 *__restrict__ pos, const dbl4 *__restrict
 struct Shape {
   int warps = 0, tile = 0, chunk = 0;
   int tpl = 1;  // targets per lane: 2 or 3 run 64- or 96-target groups (FP32 only)
-  int rpl = 1;  // replicas per lane: 2 or 4 run replica lysosomes together (FP32, warps = rpl)
+  int rpl = 1;  // replicas per lane: 2 or 4 run replica lysosomes together (FP32, warps =
+                // rpl or 4 rpl: one or four warps per replica)
   // symmetric pair form (FP32): cells per warp (1 or 2; tpl = 2 sym, tile = 32,
   // chunk = source NPs per field item, 0 = a whole row); 0 = the ordered kernels
   int sym = 0;
@@ -678,7 +679,9 @@ bool shape_ok(const kmc_ctx *c, const Shape &s) {
   if (s.cl != 0 && (s.cl != 2 || !c->fp32 || s.tpl != 1 || s.rpl != 1 || s.chunk <= 0))
     return false;
   if (s.rpl > 1) {  // replicas: their kernel has one warp per replica
-    if (!c->fp32 || s.tpl != 1 || s.warps != s.rpl || !c->rep_ok[s.rpl]) return false;
+    if (!c->fp32 || s.tpl != 1 || (s.warps != s.rpl && s.warps != 4 * s.rpl) ||
+        !c->rep_ok[s.rpl])
+      return false;
     if (s.tile < 32 || s.tile > 128 || (s.tile & (s.tile - 1))) return false;
     return s.chunk >= 0 && s.chunk % 64 == 0;
   }
@@ -893,24 +896,26 @@ kmc_status autotune(kmc_ctx *c) {
   const int tiles_f32[] = {64, 128, 256, 512};
   const int tiles_f64[] = {32, 64, 128, 128};  // (the FP64 list has three distinct tiles)
   const int chunks[] = {0, 256, 512, 1024, 2048, 4096, 8192};
-  // replicas per lane (FP32, sets of identical lysosomes): warps = replicas,
-  // one target per lane, tiles of 32..128 records per replica
+  // replicas per lane (FP32, sets of identical lysosomes): one or four warps
+  // per replica, one target per lane, tiles of 32..128 records per replica
   for (int rpl = 2; rpl <= 4 && c->fp32 && c->tpl_mode <= 1 && !sym_only; rpl += 2) {
     if (!c->rep_ok[rpl] || (c->rpl_mode != 0 && c->rpl_mode != rpl)) continue;
-    for (int t : {32, 64, 128}) {
-      if (2 * t > 2 * std::max(max_n, 64) && t > 32) continue;
-      for (int ch : chunks) {
-        if (ch > 0 && (ch >= max_n || ch < 2 * t)) continue;
-        Shape s;
-        s.warps = rpl;
-        s.tile = t;
-        s.chunk = ch;
-        s.tpl = 1;
-        s.rpl = rpl;
-        const float ms = time_shape(c, s);
-        if (ms > 0.f && ms < best) {
-          best = ms;
-          bs = s;
+    for (int wpr : {1, 4}) {
+      for (int t : {32, 64, 128}) {
+        if (2 * t > 2 * std::max(max_n, 64) && t > 32) continue;
+        for (int ch : chunks) {
+          if (ch > 0 && (ch >= max_n || ch < 2 * t)) continue;
+          Shape s;
+          s.warps = rpl * wpr;
+          s.tile = t;
+          s.chunk = ch;
+          s.tpl = 1;
+          s.rpl = rpl;
+          const float ms = time_shape(c, s);
+          if (ms > 0.f && ms < best) {
+            best = ms;
+            bs = s;
+          }
         }
       }
     }
@@ -1419,8 +1424,8 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
                     "with 4, chunk a multiple of 64");
     } else if (!shape_ok(c, s))
       return fail(KMC_EINVAL,
-                  s.rpl > 1 ? "bad shape: with %d replicas per lane, warps = %d, tile a power of two "
-                              "in [32, 128], chunk a multiple of 64"
+                  s.rpl > 1 ? "bad shape: with %d replicas per lane, warps = %d or four times that, "
+                              "tile a power of two in [32, 128], chunk a multiple of 64"
                             : "bad shape: warps in {4, 8, 16}, tile a power of two in [32, %d], "
                               "chunk a multiple of 64",
                   s.rpl > 1 ? s.rpl : max_tile(c->fp32, warps == 4 || warps == 8 || warps == 16 ? warps : 4),

@@ -17,9 +17,9 @@ size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl = 1, int rpl 
 // may overlap the tail of the previous kernel on st (programmatic dependent
 // launch); the kernel waits for that kernel before it reads any state.
 // tpl = 2 or 3 (FP32 only): items are 64- or 96-target groups, two or three
-// targets per lane. rpl = 2 or 4 (FP32 only, tpl = 1, warps = rpl): each item
-// is 32 targets of rpl replica lysosomes it.l .. it.l + rpl - 1 that share
-// their geometry (kmc_step_f32_rep).
+// targets per lane. rpl = 2 or 4 (FP32 only, tpl = 1, warps = rpl or 4 rpl):
+// each item is 32 targets of rpl replica lysosomes it.l .. it.l + rpl - 1 that
+// share their geometry (kmc_step_f32_rep, one or four warps per replica).
 // cl = 2 (FP32, one target per lane): every target group has exactly two
 // source parts, items 2 g and 2 g + 1, which run as a two-CTA cluster and
 // exchange their sums through distributed shared memory; n_items even.

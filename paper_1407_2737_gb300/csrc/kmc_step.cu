@@ -491,16 +491,54 @@ __device__ __forceinline__ TargetIn<V> load_target(const StepArgs &a, const LysD
 // WARP: the steps are run by the calling warp alone, on its own update state
 // (the replica kernel, where every warp updates another lysosome): its lanes
 // scan the whole grid for their targets and each lane refines its own
-// brackets. The results are the same bits as the block's.
-template <typename V, bool MIXED, bool WARP = false>
+// brackets. GROUP > 0: they are run by the gid-th group of GROUP warps of the
+// block on that group's update state, with named barriers, several groups
+// side by side (the replica kernel with several warps per replica). The
+// results are the same bits as the block's.
+// Barriers of a block_update that the whole block runs (GROUP = 0:
+// __syncthreads), or that a group of GROUP warps runs (warps gid GROUP ..
+// gid GROUP + GROUP - 1, named barrier 1 + gid), several groups side by side.
+template <int GROUP>
+struct UpdateSync {
+  static __device__ __forceinline__ void sync(int gid) {
+    if constexpr (GROUP == 0) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + gid), "n"(GROUP * 32) : "memory");
+    }
+  }
+  static __device__ __forceinline__ bool sync_or(int gid, bool p) {
+    if constexpr (GROUP == 0) {
+      return __syncthreads_or(p) != 0;
+    } else {
+      uint32_t r;
+      asm volatile(
+          "{\n\t.reg .pred q, o;\n\t"
+          "setp.ne.u32 q, %1, 0;\n\t"
+          "bar.red.or.pred o, %2, %3, q;\n\t"
+          "selp.u32 %0, 1, 0, o;\n\t}"
+          : "=r"(r)
+          : "r"(static_cast<uint32_t>(p)), "r"(1 + gid), "n"(GROUP * 32)
+          : "memory");
+      return r != 0;
+    }
+  }
+};
+
+template <typename V, bool MIXED, bool WARP = false, int GROUP = 0>
 __device__ __forceinline__ void block_update(
     const StepArgs &a, const LysDev &L, const Item &it, long long step, int rec,
     const TargetIn<V> &tin,
     EpiShared<typename std::conditional<MIXED, float, double>::type> &sm,
-    const GridTables<typename std::conditional<MIXED, float, double>::type> &tab) {
+    const GridTables<typename std::conditional<MIXED, float, double>::type> &tab, int gid = 0) {
   using R = typename std::conditional<MIXED, float, double>::type;
-  const int warp = WARP ? 0 : threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = WARP ? 1 : blockDim.x >> 5;
+  using Sync = UpdateSync<GROUP>;
+  // this update's threads: the block, or a group of GROUP warps
+  const int gtid = GROUP ? static_cast<int>(threadIdx.x) - gid * GROUP * 32
+                         : static_cast<int>(threadIdx.x);
+  const int gthreads = GROUP ? GROUP * 32 : static_cast<int>(blockDim.x);
+  const int warp = WARP ? 0 : gtid >> 5, lane = threadIdx.x & 31;
+  const int nw = WARP ? 1 : gthreads >> 5;
   const int nt = it.nt;
   const double bext = L.bmax * a.cos_k;
   TargetState<R> st;
@@ -532,19 +570,19 @@ __device__ __forceinline__ void block_update(
     }
     __syncwarp();
   } else {
-    __syncthreads();
+    Sync::sync(gid);
     // iv) scan: lanes over targets, warps over segments of the grid
     segment_scan<R>(sm, tab, warp, nw, lane, nt);
-    __syncthreads();
+    Sync::sync(gid);
     if constexpr (MIXED) {
       noisy = warp == 0 && lane < nt && (sm.cnt[lane] > 4 || a.force_rescan);
-      if (__syncthreads_or(noisy)) {
+      if (Sync::sync_or(gid, noisy)) {
         if (noisy) rescan_fp64(sm, lane);
-        __syncthreads();
+        Sync::sync(gid);
       }
     }
     // iv) Newton: one bracket per thread
-    for (int x = threadIdx.x; x < 4 * nt; x += blockDim.x) {
+    for (int x = gtid; x < 4 * nt; x += gthreads) {
       const int t = x >> 2, q = x & 3;
       const int nb = min(sm.cnt[t], 4);
       if (q < nb) refine_bracket<R>(sm, tab, t, q, nb, a.err);
@@ -1138,16 +1176,19 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
 // formed once and serves all replicas, which add only their own terms
 // u = (t.d) q^2 and q^3 (u d + n): 8 + 10 RPL packed operations per record and
 // target instead of 18 RPL. Every replica's sums are formed by the same
-// operations in the same order as in kmc_step_f32 with RPL warps, and warp r
-// combines replica r's warp sums and source parts in kmc_step_f32's order, so
-// each replica's field, and its whole step, are the bits it gets alone. Warp r
-// then runs replica r's steps iii-vii by itself (the warps in parallel).
-template <bool MASK, int RPL>
+// operations in the same order as in kmc_step_f32 with NW = RPL WPR warps,
+// and the first warp of group r (warps r WPR .. r WPR + WPR - 1) combines
+// replica r's warp sums and source parts in kmc_step_f32's order, so each
+// replica's field, and its whole step, are the bits it gets alone. Group r
+// then runs replica r's steps iii-vii (the groups in parallel): one warp by
+// itself (WPR = 1), or four warps block-cooperatively on named barriers
+// (WPR = 4), which keeps the update's latency that of one block.
+template <bool MASK, int RPL, int NW>
 __device__ __forceinline__ void pair_tile_f32_rep(const ulonglong2 *__restrict__ sp,
                                                   size_t rstride, int cnt, int first, f2 X,
                                                   f2 Y, f2 Z, AccF32 (&acc)[RPL]) {
 #pragma unroll 1
-  for (int r = first; r < cnt; r += RPL) {
+  for (int r = first; r < cnt; r += NW) {
     ulonglong2 a0, b0, c0, d0;
     f2 e0;
     load_record(sp, r, a0, b0, c0, d0, e0);
@@ -1179,15 +1220,17 @@ __device__ __forceinline__ void pair_tile_f32_rep(const ulonglong2 *__restrict__
 
 // Dynamic shared memory of the replica kernel after its pair loop: the warps'
 // (sum, -error) pairs of every replica, then every replica's update state.
-constexpr size_t epi_bytes_rep(int rpl) {
-  return static_cast<size_t>(rpl) * 6 * rpl * kTargets * sizeof(float) +
+constexpr size_t epi_bytes_rep(int rpl, int nw) {
+  return static_cast<size_t>(nw) * 6 * rpl * kTargets * sizeof(float) +
          static_cast<size_t>(rpl) * sizeof(EpiShared<float>) + 64;
 }
 
-template <int RPL>
-__global__ void __launch_bounds__(RPL * 32) kmc_step_f32_rep(const StepArgs a, int tile) {
+template <int RPL, int WPR = 1>
+__global__ void __launch_bounds__(RPL * WPR * 32, (RPL == 2 && WPR == 4) ? 2 : 0)
+    kmc_step_f32_rep(const StepArgs a, int tile) {
   static_assert(RPL == 2 || RPL == 4, "two or four replicas per lane");
-  constexpr int NW = RPL;
+  static_assert(WPR == 1 || WPR == 4, "one or four warps per replica");
+  constexpr int NW = RPL * WPR;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *dyn = smem + 16;
@@ -1198,8 +1241,10 @@ __global__ void __launch_bounds__(RPL * 32) kmc_step_f32_rep(const StepArgs a, i
   const Item it = a.items[blockIdx.x];  // it.l: the first replica
   if (!KMC_DCHECK(it.l + RPL <= a.n_lys, a.err, kSiteLys)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rk = WPR == 1 ? warp : warp / WPR;        // the replica this warp's group updates
+  const bool lead = WPR == 1 || warp % WPR == 0;      // the group's first warp
   const LysDev L0 = a.lys[it.l];
-  const LysDev Lw = a.lys[it.l + warp];  // the replica this warp updates
+  const LysDev Lw = a.lys[it.l + rk];
   const float4 pi = static_cast<const float4 *>(a.pos)[L0.off + it.t0 + min(lane, it.nt - 1)];
   grid_dependency_wait();
   const long long step = a.rs->step_base + a.k_local;
@@ -1209,7 +1254,7 @@ __global__ void __launch_bounds__(RPL * 32) kmc_step_f32_rep(const StepArgs a, i
   const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]);
 
   Item iw = it;
-  iw.l = it.l + warp;
+  iw.l = it.l + rk;
   const TargetIn<float4> tin = load_target<float4>(a, Lw, iw, step, lane);
   const f2 X = pk(pi.x, pi.x), Y = pk(pi.y, pi.y), Z = pk(pi.z, pi.z);
   float sk[3 * RPL], ck[3 * RPL];  // Kahan sums: replica k, component c at 3 k + c
@@ -1244,9 +1289,9 @@ __global__ void __launch_bounds__(RPL * 32) kmc_step_f32_rep(const StepArgs a, i
 #pragma unroll
     for (int k = 0; k < RPL; ++k) acc[k].x = acc[k].y = acc[k].z = 0ull;
     if (mask)
-      pair_tile_f32_rep<true, RPL>(sp, rstride, cnt, warp, X, Y, Z, acc);
+      pair_tile_f32_rep<true, RPL, NW>(sp, rstride, cnt, warp, X, Y, Z, acc);
     else
-      pair_tile_f32_rep<false, RPL>(sp, rstride, cnt, warp, X, Y, Z, acc);
+      pair_tile_f32_rep<false, RPL, NW>(sp, rstride, cnt, warp, X, Y, Z, acc);
 #pragma unroll
     for (int k = 0; k < RPL; ++k) {
       kahan_add(sk[3 * k + 0], ck[3 * k + 0], hsum(acc[k].x));
@@ -1256,7 +1301,8 @@ __global__ void __launch_bounds__(RPL * 32) kmc_step_f32_rep(const StepArgs a, i
   };
   if (!staged_loop(ntiles, bar, a.err, issue, body)) return;
 
-  // cross-warp combine in kmc_step_f32's order; warp k combines replica k
+  // cross-warp combine in kmc_step_f32's order; group k's first warp combines
+  // replica k
   constexpr int kW = 6 * RPL;
   float *wp = reinterpret_cast<float *>(dyn);  // [NW][6 RPL][32]: 3 RPL sums, then 3 RPL errors
 #pragma unroll
@@ -1267,51 +1313,63 @@ __global__ void __launch_bounds__(RPL * 32) kmc_step_f32_rep(const StepArgs a, i
   __syncthreads();
   EpiShared<float> *sms =
       reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * kW * 32 * 4);
-  EpiShared<float> &sm = sms[warp];
-  float hi[3], lo[3];
+  EpiShared<float> &sm = sms[rk];
+  float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+  if (lead) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    float s = 0.f, e = 0.f;
-    for (int w = 0; w < NW; ++w) {
-      neumaier_add(s, e, wp[(w * kW + 3 * warp + c) * 32 + lane]);
-      e += wp[(w * kW + 3 * RPL + 3 * warp + c) * 32 + lane];
+    for (int c = 0; c < 3; ++c) {
+      float s = 0.f, e = 0.f;
+      for (int w = 0; w < NW; ++w) {
+        neumaier_add(s, e, wp[(w * kW + 3 * rk + c) * 32 + lane]);
+        e += wp[(w * kW + 3 * RPL + 3 * rk + c) * 32 + lane];
+      }
+      hi[c] = s;
+      lo[c] = e;
     }
-    hi[c] = s;
-    lo[c] = e;
   }
   if (it.nsplit > 1) {
     // replica k's partials at k kPartF32, each laid out as kmc_step_f32's
-    float *part = a.partial + (static_cast<size_t>(blockIdx.x) * RPL + warp) * kPartF32;
+    if (lead) {
+      float *part = a.partial + (static_cast<size_t>(blockIdx.x) * RPL + rk) * kPartF32;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      __stcg(part + c * 32 + lane, hi[c]);
-      __stcg(part + (3 + c) * 32 + lane, lo[c]);
+      for (int c = 0; c < 3; ++c) {
+        __stcg(part + c * 32 + lane, hi[c]);
+        __stcg(part + (3 + c) * 32 + lane, lo[c]);
+      }
+      __threadfence();
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
     __syncthreads();
     if (!s_last) return;  // another item of the group finishes the step
     __threadfence();
-    const float *base = a.partial + (static_cast<size_t>(blockIdx.x - it.split) * RPL + warp) *
-                                        kPartF32;
+    if (lead) {
+      const float *base =
+          a.partial + (static_cast<size_t>(blockIdx.x - it.split) * RPL + rk) * kPartF32;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float s = 0.f, e = 0.f;
-      for (int q = 0; q < it.nsplit; ++q) {
-        neumaier_add(s, e, __ldcg(base + q * RPL * kPartF32 + c * 32 + lane));
-        e += __ldcg(base + q * RPL * kPartF32 + (3 + c) * 32 + lane);
+      for (int c = 0; c < 3; ++c) {
+        float s = 0.f, e = 0.f;
+        for (int q = 0; q < it.nsplit; ++q) {
+          neumaier_add(s, e, __ldcg(base + q * RPL * kPartF32 + c * 32 + lane));
+          e += __ldcg(base + q * RPL * kPartF32 + (3 + c) * 32 + lane);
+        }
+        hi[c] = s;
+        lo[c] = e;
       }
-      hi[c] = s;
-      lo[c] = e;
     }
     __syncthreads();
     if (threadIdx.x == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
   }
+  if (lead) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) sm.h[c][lane] = hi[c] + lo[c];  // compensation added last
-  __syncwarp();
-  block_update<float4, true, true>(a, Lw, iw, step, rec, tin, sm, tab);
+    for (int c = 0; c < 3; ++c) sm.h[c][lane] = hi[c] + lo[c];  // compensation added last
+  }
+  if constexpr (WPR == 1) {
+    __syncwarp();
+    block_update<float4, true, true>(a, Lw, iw, step, rec, tin, sm, tab);
+  } else {
+    block_update<float4, true, false, WPR>(a, Lw, iw, step, rec, tin, sm, tab, rk);
+  }
   grid_launch_dependents();
 }
 
@@ -1797,7 +1855,7 @@ __global__ void __launch_bounds__(kSymUpdWarps * 32) kmc_update_sym(const StepAr
 size_t step_smem_bytes(int prec_fp32, int warps, int tile, int tpl, int rpl) {
   if (prec_fp32 && rpl > 1) {
     const size_t stage = 2 * static_cast<size_t>(rpl) * tile * sizeof(SrcPair);
-    const size_t epi = epi_bytes_rep(rpl);
+    const size_t epi = epi_bytes_rep(rpl, warps);
     return 16 + (stage > epi ? stage : epi);
   }
   const size_t stage = prec_fp32 ? 2 * static_cast<size_t>(tile) * sizeof(SrcPair)
@@ -1869,12 +1927,17 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
   if (n_items <= 0) return cudaSuccess;
   if (cl != 0 && (!prec_fp32 || rpl > 1)) return cudaErrorInvalidValue;
   if (rpl > 1) {
-    if (!prec_fp32 || tpl != 1 || warps != rpl) return cudaErrorInvalidValue;
+    if (!prec_fp32 || tpl != 1 || (warps != rpl && warps != 4 * rpl)) return cudaErrorInvalidValue;
     const size_t smem = step_smem_bytes(1, warps, tile, 1, rpl);
-    if (rpl == 2)
-      return launch_items(kmc_step_f32_rep<2>, a, n_items, 64, smem, tile, st, pdl);
-    if (rpl == 4)
-      return launch_items(kmc_step_f32_rep<4>, a, n_items, 128, smem, tile, st, pdl);
+    const int th = warps * 32;
+    if (rpl == 2 && warps == 2)
+      return launch_items(kmc_step_f32_rep<2>, a, n_items, th, smem, tile, st, pdl);
+    if (rpl == 4 && warps == 4)
+      return launch_items(kmc_step_f32_rep<4>, a, n_items, th, smem, tile, st, pdl);
+    if (rpl == 2 && warps == 8)
+      return launch_items(kmc_step_f32_rep<2, 4>, a, n_items, th, smem, tile, st, pdl);
+    if (rpl == 4 && warps == 16)
+      return launch_items(kmc_step_f32_rep<4, 4>, a, n_items, th, smem, tile, st, pdl);
     return cudaErrorInvalidValue;
   }
   if (prec_fp32) {
@@ -1939,9 +2002,10 @@ cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int 
   const size_t smem = step_smem_bytes(prec_fp32, warps, tile, tpl, rpl);
   const int th = warps * 32;
   if (prec_fp32 && rpl > 1) {
-    if (warps != rpl) return cudaErrorInvalidValue;
-    if (rpl == 2) return occupancy(kmc_step_f32_rep<2>, th, smem, blocks);
-    if (rpl == 4) return occupancy(kmc_step_f32_rep<4>, th, smem, blocks);
+    if (rpl == 2 && warps == 2) return occupancy(kmc_step_f32_rep<2>, th, smem, blocks);
+    if (rpl == 4 && warps == 4) return occupancy(kmc_step_f32_rep<4>, th, smem, blocks);
+    if (rpl == 2 && warps == 8) return occupancy(kmc_step_f32_rep<2, 4>, th, smem, blocks);
+    if (rpl == 4 && warps == 16) return occupancy(kmc_step_f32_rep<4, 4>, th, smem, blocks);
     return cudaErrorInvalidValue;
   }
   if (prec_fp32 && tpl == 2) {
@@ -2040,6 +2104,8 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<16, 3>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<2>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<2, 4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<4, 4>);
   if (e == cudaSuccess) e = allow_smem(kmc_field_sym<2, 2>);
   if (e == cudaSuccess) e = allow_smem(kmc_field_sym<4, 1>);
   if (e == cudaSuccess) e = allow_smem(kmc_field_sym<4, 2>);

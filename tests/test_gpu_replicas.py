@@ -2,10 +2,11 @@
 different random streams, as seed averages are) stepped together, each staged
 source record's geometry serving every lysosome of the set.
 
-With four replicas per lane (four warps, one per lysosome) every lysosome's
-sums are formed by the same operations in the same order as with one target
-per lane and four warps, and its update is the same code run by one warp, so
-whole runs must give the same bits. With two (two warps, records interleaved
+With four replicas per lane (four warps, one per lysosome; or sixteen, four
+per lysosome) every lysosome's sums are formed by the same operations in the
+same order as with one target per lane and as many warps, and its update is
+the same code run by one warp or a group of four, so whole runs must give the
+same bits. With two (two warps, records interleaved
 over two warps) the summation order differs: the fields are checked against
 the oracle within the FP32 field tolerance of the other tests (1e-5 of rms)."""
 import numpy as np
@@ -52,6 +53,21 @@ def test_four_replicas_per_lane_give_the_bits_of_one_target_per_lane(tile, chunk
     ref, used1 = _run(lyss, 1, (4, tile, chunk), H)
     got, used4 = _run(lyss, 4, (4, tile, chunk), H)
     assert (used1, used4) == (1, 4)
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("rpl,tile,chunk", [(4, 64, 0), (4, 32, 128), (2, 128, 256), (2, 64, 0)])
+def test_four_warps_per_replica_give_the_bits_of_one_target_per_lane(rpl, tile, chunk):
+    """Four warps per replica (4 rpl warps; each replica's steps iii-vii run by
+    its own group of four warps on named barriers) against one target per lane
+    with as many warps, at the same tile and source split."""
+    ly = inputs.make_lysosome(300, 12e-9, 0.06, seed=83)
+    lyss = inputs.replicate(ly, 8)
+    H = [0.012 + 0.003 * q for q in range(8)]
+    ref, used1 = _run(lyss, 1, (4 * rpl, tile, chunk), H)
+    got, usedr = _run(lyss, rpl, (4 * rpl, tile, chunk), H)
+    assert (used1, usedr) == (1, rpl)
     for x, y in zip(ref, got):
         assert np.array_equal(x, y)
 
