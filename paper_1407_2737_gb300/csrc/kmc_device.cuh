@@ -57,9 +57,14 @@ template <>
 struct Prec<float> {
   static constexpr float two_pi = 6.28318530717958647692f;
   static constexpr float plane_tol = 1e-6f;   // |b x a| below this: plane from m
-  static constexpr float newton_tol = 2e-9f;  // absolute, on the offset in a cell
-  static constexpr int newton_max = 6;        // from the secant point: 2-3 steps for nearly
-                                              // every root, 6 for the slowest seen
+  // Newton stops once a step is below newton_tol (absolute, on the offset in
+  // a cell of 0.0314 rad). With de/dth and its derivative in FP32 the step
+  // itself carries rounding noise of order 1e-8..1e-7 rad, so the tolerance
+  // sits above it: a tighter one is never met and every root runs to
+  // newton_max. From the secant start the convergence is quadratic, so the
+  // root is then within rounding (~1e-7 rad) after 2-3 steps.
+  static constexpr float newton_tol = 3e-7f;
+  static constexpr int newton_max = 6;
   __device__ static float div(float a, float b) { return __fdividef(a, b); }
   __device__ static float theta(int j) { return g_theta_f[j]; }
   __device__ static float2 sc(int j) { return g_sc_f[j]; }
