@@ -74,6 +74,27 @@ __device__ __forceinline__ float ld_cluster(const float *p, uint32_t rank) {
   return v;
 }
 
+// Arrival of a block at the counter of its target group once its partial sums
+// are stored (by any of its threads, plain or .cg stores): a block barrier, then
+// one release-acquire add by thread 0, which publishes with it the stores the
+// barrier ordered before it. Every thread learns whether the block arrived
+// last (nsplit - 1 arrivals before it); the last block reads the others'
+// partials after the second barrier, which orders those reads after the
+// acquire. *flag is a shared int.
+__device__ __forceinline__ bool arrive_last(int32_t *counter, int nsplit, int *flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
+                 : "=r"(old)
+                 : "l"(counter)
+                 : "memory");
+    *flag = old == nsplit - 1;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

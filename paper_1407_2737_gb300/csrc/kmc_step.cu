@@ -869,7 +869,6 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
         __stcg(part + c * 32 + lane, hi[c]);
         __stcg(part + (3 + c) * 32 + lane, lo[c]);
       }
-      __threadfence();
     }
   }
   if constexpr (CL) {
@@ -897,11 +896,8 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
     cluster_sync();  // part 0 has read part 1's shared memory
     if (it.split != 0) return;
   } else if (it.nsplit > 1) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
-    __syncthreads();
-    if (!s_last) return;  // another item of the group finishes the step
-    __threadfence();
+    // another item of the group finishes the step
+    if (!arrive_last(&a.arrivals[it.gid], it.nsplit, &s_last)) return;
     if (warp == 0) {
       const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * kPartF32;
 #pragma unroll
@@ -1113,15 +1109,11 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
           __stcg(part + k * kPartF32 + c * 32 + lane, hi[3 * k + c]);
           __stcg(part + k * kPartF32 + (3 + c) * 32 + lane, lo[3 * k + c]);
         }
-      __threadfence();
     }
   }
   if (it.nsplit > 1) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
-    __syncthreads();
-    if (!s_last) return;  // another item of the group finishes the step
-    __threadfence();
+    // another item of the group finishes the step
+    if (!arrive_last(&a.arrivals[it.gid], it.nsplit, &s_last)) return;
     if (warp == 0) {
       const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * TPL * kPartF32;
 #pragma unroll
@@ -1336,13 +1328,9 @@ __global__ void __launch_bounds__(RPL * WPR * 32, (RPL == 2 && WPR == 4) ? 2 : 0
         __stcg(part + c * 32 + lane, hi[c]);
         __stcg(part + (3 + c) * 32 + lane, lo[c]);
       }
-      __threadfence();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
-    __syncthreads();
-    if (!s_last) return;  // another item of the group finishes the step
-    __threadfence();
+    // another item of the group finishes the step
+    if (!arrive_last(&a.arrivals[it.gid], it.nsplit, &s_last)) return;
     if (lead) {
       const float *base =
           a.partial + (static_cast<size_t>(blockIdx.x - it.split) * RPL + rk) * kPartF32;
@@ -1445,15 +1433,10 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f64(const StepArgs a, int ti
           reinterpret_cast<double *>(a.partial + static_cast<size_t>(blockIdx.x) * 12 * 32);
 #pragma unroll
       for (int c = 0; c < 6; ++c) __stcg(part + c * 32 + lane, tot[c]);
-      __threadfence();
     }
   }
   if (it.nsplit > 1) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.arrivals[it.gid], 1) == it.nsplit - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    if (!arrive_last(&a.arrivals[it.gid], it.nsplit, &s_last)) return;
     if (warp == 0) {
       const double *base = reinterpret_cast<const double *>(
           a.partial + static_cast<size_t>(blockIdx.x - it.split) * 12 * 32);
