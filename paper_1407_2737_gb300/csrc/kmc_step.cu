@@ -587,7 +587,7 @@ __device__ __forceinline__ void block_update(
       const int nb = min(sm.cnt[t], 4);
       if (q < nb) refine_bracket<R>(sm, tab, t, q, nb, a.err);
     }
-    __syncthreads();
+    Sync::sync(gid);
     if (warp != 0) return;
   }
   // v-vii) decision and outputs (warp 0)
