@@ -132,11 +132,14 @@ def launch_info(kmc, ctx, lyss):
             else:
                 ops += 14 * 2 * (gc * cell) * ((h1 - h0) * cell)
         chains = len(cut) - 1
+        block = kmc.kmc_sym_update(ctx) == 2
         launch.update({"pair_form": "symmetric", "chains": chains, "field_items": len(items),
-                       "update_items": len(upd)})
-        return {"launch": launch, "kernel": "kmc_field_sym<%d, %d> + kmc_update_sym<%d>" % (
-                    warps, cells, gc), "lane_ops_per_pair": ops / pairs, "chains": chains,
-                "launches_per_step": 2 * chains, "key": (warps, tile, chunk, tpl, rpl, "sym")}
+                       "update_items": len(upd), "update": "block" if block else "warp"})
+        return {"launch": launch, "kernel": "kmc_field_sym<%d, %d> + kmc_update_sym%s<%d>" % (
+                    warps, cells, "_block" if block else "", gc),
+                "lane_ops_per_pair": ops / pairs, "chains": chains,
+                "launches_per_step": 2 * chains,
+                "key": (warps, tile, chunk, tpl, rpl, "sym") + (("block",) if block else ())}
     chains = min(len(lyss) // max(rpl, 1), kmc.KMC_MAX_CHAINS)
     launch.update({"pair_form": "ordered", "chains": chains})
     return {"launch": launch, "kernel": step_kernel(warps, tpl, rpl),

@@ -244,6 +244,19 @@ kmc_status kmc_replicas_per_lane(kmc_ctx *ctx, int32_t rpl, int32_t *rpl_out);
  * tuning) is returned through form_out (may be NULL); form = -1 only reads it. */
 kmc_status kmc_pair_form(kmc_ctx *ctx, int32_t form, int32_t *form_out);
 
+/* Update kernel of the symmetric pair form (kmc_pair_form = 2): 1 gives each
+ * update item (32 targets of one cell) one warp, which adds the item's forward
+ * and reverse partial sums in slot order and runs steps iii-vii alone; 2 gives
+ * it a block of four warps, which share the gather (warp w taking slots w,
+ * w + 4, ...; the warps then added in order) and run steps iii-vii together.
+ * The first is faster where items are many and their slots few (batches of
+ * small lysosomes), the second where a target gathers many slots (large
+ * lysosomes). The two round the field sums differently, each in a fixed
+ * order. mode: 0 lets the autotuner choose (the default), 1 or 2 pins one.
+ * The value in use (0 before the first tuning or outside the symmetric
+ * form) is returned through mode_out (may be NULL); mode = -1 only reads it. */
+kmc_status kmc_sym_update(kmc_ctx *ctx, int32_t mode, int32_t *mode_out);
+
 /* Cluster split of the FP32 one-target-per-lane step kernel. When every
  * target group's sources are split into exactly two parts (kmc_tuning's chunk
  * with one target per lane), the two parts can run as the two CTAs of a

@@ -125,9 +125,11 @@ struct Shape {
   // source parts run as a two-CTA cluster and exchange their sums through
   // distributed shared memory; 0 = through global memory
   int cl = 0;
+  // symmetric form's update kernel: 0 = one warp per update item, 1 = one block
+  int supd = 0;
   bool operator==(const Shape &o) const {
     return warps == o.warps && tile == o.tile && chunk == o.chunk && tpl == o.tpl &&
-           rpl == o.rpl && sym == o.sym && cl == o.cl;
+           rpl == o.rpl && sym == o.sym && cl == o.cl && supd == o.supd;
   }
 };
 
@@ -135,11 +137,11 @@ struct TuneKey {
   int prec;
   long long N;
   int n_lys, max_n, tpl_mode, rpl_mode, reps;  // reps: replica sets available (bits)
-  int form_mode, cl_mode;
+  int form_mode, cl_mode, supd_mode;
   bool operator<(const TuneKey &o) const {
-    return std::tie(prec, N, n_lys, max_n, tpl_mode, rpl_mode, reps, form_mode, cl_mode) <
-           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode, o.reps, o.form_mode,
-                    o.cl_mode);
+    return std::tie(prec, N, n_lys, max_n, tpl_mode, rpl_mode, reps, form_mode, cl_mode,
+                    supd_mode) < std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode,
+                                          o.reps, o.form_mode, o.cl_mode, o.supd_mode);
   }
 };
 std::mutex g_tune_mu;
@@ -217,6 +219,7 @@ struct kmc_ctx {
   std::vector<int> sym_cut_items, sym_cut_upd;
   int form_mode = 0;           // pair form: 0 = the autotuner's choice, 1 = ordered, 2 = symmetric
   int cl_mode = 0;             // cluster split: 0 = the autotuner's choice, 1 = off, 2 = on
+  int supd_mode = 0;           // symmetric update: 0 = the autotuner's, 1 = warp, 2 = block per item
   int tpl_mode = 0;            // targets per lane: 0 = the autotuner's choice, else 1, 2 or 3
   int rpl_mode = 0;            // replicas per lane: 0 = the autotuner's choice, 1 = off, 2 or 4
   bool rep_ok[5] = {};         // [k]: the lysosomes form sets of k identical consecutive ones
@@ -613,7 +616,7 @@ cudaError_t launch_one_step(const kmc_ctx *c, StepArgs a, const Shape &sh, cudaS
     a.n_items = c->n_sitems;
     a.n_upd = c->n_supd;
     a.gc = sh.warps * sh.sym;
-    return kmc::launch_sym(a, sh.warps, sh.sym, c->n_sitems, st, pdl);
+    return kmc::launch_sym(a, sh.warps, sh.sym, c->n_sitems, st, pdl, sh.supd);
   }
   return kmc::launch_step(c->fp32, sh.warps, sh.tile, a, c->n_items, st, pdl, sh.tpl, sh.rpl,
                           sh.cl);
@@ -668,6 +671,7 @@ int max_tile(int fp32, int warps) {
 }
 
 bool shape_ok(const kmc_ctx *c, const Shape &s) {
+  if (s.supd != 0 && (s.sym == 0 || s.supd != 1)) return false;
   if (s.sym) {  // symmetric form: (warps, cells per warp) of its field kernel
     if (!c->fp32 || s.rpl != 1 || s.tpl != 2 * s.sym || s.tile != 32) return false;
     if (!((s.warps == 4 && (s.sym == 1 || s.sym == 2)) || (s.warps == 8 && s.sym == 1) ||
@@ -729,7 +733,7 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
           b.k_local = k;
           b.cos_k = std::cos(2.0 * kPi * k / steps);
         }
-        ce = kmc::launch_sym(b, sh.warps, sh.sym, b.n_items, st, true);
+        ce = kmc::launch_sym(b, sh.warps, sh.sym, b.n_items, st, true, sh.supd);
       }
       continue;
     }
@@ -827,7 +831,7 @@ kmc_status autotune(kmc_ctx *c) {
   const TuneKey key{c->fp32, c->N,        c->n_lys,
                     max_n,   c->tpl_mode, c->rpl_mode,
                     (c->rep_ok[2] ? 1 : 0) | (c->rep_ok[4] ? 2 : 0), c->form_mode,
-                    c->cl_mode};
+                    c->cl_mode, c->supd_mode};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -884,11 +888,22 @@ kmc_status autotune(kmc_ctx *c) {
         s.chunk = ch;
         s.tpl = 2 * v[1];
         s.sym = v[1];
+        s.supd = c->supd_mode == 2 ? 1 : 0;
         const float ms = time_shape(c, s);
         if (ms > 0.f && ms < best) {
           best = ms;
           bs = s;
         }
+      }
+    }
+    // the best symmetric shape with the other update kernel
+    if (bs.sym && c->supd_mode == 0) {
+      Shape s = bs;
+      s.supd = 1;
+      const float ms = time_shape(c, s);
+      if (ms > 0.f && ms < best) {
+        best = ms;
+        bs = s;
       }
     }
   }
@@ -1380,6 +1395,20 @@ kmc_status kmc_pair_form(kmc_ctx *c, int32_t form, int32_t *form_out) {
   return KMC_OK;
 }
 
+kmc_status kmc_sym_update(kmc_ctx *c, int32_t mode, int32_t *mode_out) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (mode != -1) {
+    if (mode < 0 || mode > 2)
+      return fail(KMC_EINVAL, "symmetric update: 0 (autotuned), 1 (warp per item), 2 (block)");
+    c->supd_mode = mode;
+    if (mode != 0 && c->shape.warps != 0 && c->shape.sym != 0) c->shape.supd = mode == 2 ? 1 : 0;
+  }
+  if (mode_out)
+    *mode_out = c->supd_mode != 0 ? c->supd_mode
+                                  : (c->shape.warps && c->shape.sym ? 1 + c->shape.supd : 0);
+  return KMC_OK;
+}
+
 kmc_status kmc_cluster_split(kmc_ctx *c, int32_t mode, int32_t *mode_out) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (mode != -1) {
@@ -1416,6 +1445,7 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
     s.cl = (c->cl_mode == 2 && s.tpl == 1 && s.rpl == 1) ? 2 : 0;
     if (c->form_mode == 2 || c->tpl_mode == 4) {  // symmetric form; the tile does not apply
       s.cl = 0;
+      s.supd = c->supd_mode == 2 ? 1 : 0;
       s.sym = c->tpl_mode == 4 ? 2 : 1;
       s.tpl = 2 * s.sym;
       s.tile = 32;

@@ -31,8 +31,10 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
 // a.sitems[0 .. n_field) and then kmc_update_sym over a.supd[0 .. a.n_upd).
 // (warps, cells) in {(2, 2), (4, 1), (4, 2), (8, 1)}; row groups of warps x cells
 // cells (4 or 8).
+// upd: 0 = kmc_update_sym (one warp per update item), 1 = kmc_update_sym_block
+// (one block per item).
 cudaError_t launch_sym(const StepArgs &a, int warps, int cells, int n_field, cudaStream_t st,
-                       bool pdl = false);
+                       bool pdl = false, int upd = 0);
 size_t sym_smem_bytes(int warps, int cells);
 cudaError_t sym_blocks_per_sm(int warps, int cells, int *blocks);
 

@@ -1832,6 +1832,85 @@ __global__ void __launch_bounds__(kSymUpdWarps * 32) kmc_update_sym(const StepAr
   grid_launch_dependents();
 }
 
+// The update kernel with one block per update item (kmc_pair_form's update
+// mode 1): the block's four warps share the gather of the item's partial
+// slots (warp w takes slots w, w + 4, ..., then the warps are added in order)
+// and run steps iii-vii block-cooperatively. Where a target gathers many
+// slots (large lysosomes) the shorter gather outweighs the idle warps of the
+// block-cooperative update; kmc_update_sym is faster where items are many
+// and slots few. The two give different roundings of the field sums, each in
+// a fixed order.
+template <int GC>
+__global__ void __launch_bounds__(kSymUpdWarps * 32)
+    kmc_update_sym_block(const StepArgs a, int /*tile*/) {
+  constexpr int NW = kSymUpdWarps;
+  constexpr int GT = GC * kCell;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char *dyn = smem + 16;
+  __shared__ GridTables<float> tab;
+  tab.load();
+  if (!sym_upd_in_bounds(a, GC, static_cast<int>(blockIdx.x))) return;
+  const SymUpd u = a.supd[blockIdx.x];
+  const LysDev L = a.lys[u.l];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Item it;
+  it.l = u.l;
+  it.t0 = u.t0;
+  it.nt = u.nt;
+  it.gid = 0;
+  it.j0 = it.j1 = 0;
+  it.split = 0;
+  it.nsplit = 1;
+  grid_dependency_wait();
+  const long long step = a.rs->step_base + a.k_local;
+  const int per = a.rs->period;
+  const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
+  TargetIn<float4> tin;
+  if (warp == 0) tin = load_target<float4>(a, L, it, step, lane);
+  // lanes past the last target repeat it (their results are not written)
+  const int tl = min(lane, u.nt - 1);
+  const int gi = u.gt0 + tl, ci = (u.t0 + tl) % kCell;
+  float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+  for (int sl = warp; sl < u.nfwd; sl += NW) {
+    const float *p = a.sfwd + static_cast<size_t>(u.fwd0 + sl) * 6 * GT;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      neumaier_add(hi[q], lo[q], __ldcg(p + q * GT + gi));
+      lo[q] += __ldcg(p + (3 + q) * GT + gi);
+    }
+  }
+#pragma unroll 1
+  for (int sl = warp; sl < u.nrev; sl += NW) {
+    const float *p = a.srev + static_cast<size_t>(u.rev0 + sl) * 3 * kCell;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) neumaier_add(hi[q], lo[q], __ldcg(p + q * kCell + ci));
+  }
+  float *wp = reinterpret_cast<float *>(dyn);  // [NW][6][32]
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    wp[(warp * 6 + q) * 32 + lane] = hi[q];
+    wp[(warp * 6 + 3 + q) * 32 + lane] = lo[q];
+  }
+  __syncthreads();
+  EpiShared<float> &sm =
+      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * 6 * 32 * 4);
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float s = 0.f, e = 0.f;
+      for (int w = 0; w < NW; ++w) {
+        neumaier_add(s, e, wp[(w * 6 + q) * 32 + lane]);
+        e += wp[(w * 6 + 3 + q) * 32 + lane];
+      }
+      sm.h[q][lane] = s + e;  // compensation added last
+    }
+  }
+  __syncthreads();
+  block_update<float4, true>(a, L, it, step, rec, tin, sm, tab);
+  grid_launch_dependents();
+}
+
 // ---------------------------------------------------------------------------
 // Host side of the launches.
 
@@ -1943,22 +2022,30 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
 // Symmetric form: the field kernel over n_field items, then the update kernel
 // over the a.n_upd target groups, both on st.
 template <int W, int C>
-static cudaError_t launch_sym_wc(const StepArgs &a, int n_field, cudaStream_t st, bool pdl) {
+static cudaError_t launch_sym_wc(const StepArgs &a, int n_field, cudaStream_t st, bool pdl,
+                                 int upd) {
   cudaError_t e = cudaSuccess;
   if (n_field > 0)
     e = launch_items(kmc_field_sym<W, C>, a, n_field, W * 32, sym_field_smem(W, C), 0, st, pdl);
-  if (e == cudaSuccess && a.n_upd > 0)
-    e = launch_items(kmc_update_sym<W * C>, a, (a.n_upd + kSymUpdWarps - 1) / kSymUpdWarps,
-                     kSymUpdWarps * 32, 16 + kSymUpdWarps * sizeof(EpiShared<float>), 0, st, pdl);
+  if (e == cudaSuccess && a.n_upd > 0) {
+    if (upd == 1)
+      e = launch_items(kmc_update_sym_block<W * C>, a, a.n_upd, kSymUpdWarps * 32,
+                       16 + epi_bytes<float>(kSymUpdWarps), 0, st, pdl);
+    else
+      e = launch_items(kmc_update_sym<W * C>, a, (a.n_upd + kSymUpdWarps - 1) / kSymUpdWarps,
+                       kSymUpdWarps * 32, 16 + kSymUpdWarps * sizeof(EpiShared<float>), 0, st,
+                       pdl);
+  }
   return e;
 }
 
 cudaError_t launch_sym(const StepArgs &a, int warps, int cells, int n_field, cudaStream_t st,
-                       bool pdl) {
-  if (warps == 2 && cells == 2) return launch_sym_wc<2, 2>(a, n_field, st, pdl);
-  if (warps == 4 && cells == 1) return launch_sym_wc<4, 1>(a, n_field, st, pdl);
-  if (warps == 4 && cells == 2) return launch_sym_wc<4, 2>(a, n_field, st, pdl);
-  if (warps == 8 && cells == 1) return launch_sym_wc<8, 1>(a, n_field, st, pdl);
+                       bool pdl, int upd) {
+  if (upd != 0 && upd != 1) return cudaErrorInvalidValue;
+  if (warps == 2 && cells == 2) return launch_sym_wc<2, 2>(a, n_field, st, pdl, upd);
+  if (warps == 4 && cells == 1) return launch_sym_wc<4, 1>(a, n_field, st, pdl, upd);
+  if (warps == 4 && cells == 2) return launch_sym_wc<4, 2>(a, n_field, st, pdl, upd);
+  if (warps == 8 && cells == 1) return launch_sym_wc<8, 1>(a, n_field, st, pdl, upd);
   return cudaErrorInvalidValue;
 }
 
@@ -2095,6 +2182,8 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_field_sym<8, 1>);
   if (e == cudaSuccess) e = allow_smem(kmc_update_sym<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_update_sym<8>);
+  if (e == cudaSuccess) e = allow_smem(kmc_update_sym_block<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_update_sym_block<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f64<16>);

@@ -35,7 +35,8 @@ EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_last_error", "kmc_dipolar_field_noalloc", "kmc_local_concentration",
            "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall",
            "kmc_regenerate_rsa", "kmc_targets_per_lane", "kmc_plan_items",
-           "kmc_replicas_per_lane", "kmc_pair_form", "kmc_plan_sym", "kmc_cluster_split")
+           "kmc_replicas_per_lane", "kmc_pair_form", "kmc_plan_sym", "kmc_cluster_split",
+           "kmc_sym_update")
 KMC_NOALLOC_MAX_N = 8192
 KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
 KMC_ITEM_FIELDS = 8  # per work item in kmc_plan_items
@@ -106,6 +107,7 @@ def lib():
             L.kmc_replicas_per_lane.argtypes = [vp, C.c_int32, _I32]
             L.kmc_pair_form.argtypes = [vp, C.c_int32, _I32]
             L.kmc_cluster_split.argtypes = [vp, C.c_int32, _I32]
+            L.kmc_sym_update.argtypes = [vp, C.c_int32, _I32]
             L.kmc_plan_sym.argtypes = [_I32, C.c_int32, C.c_int32, C.c_int32, _I32, C.c_int64,
                                        _I64, _I32, C.c_int64, _I64, _I64, _I32, _I32, _I32]
             L.kmc_plan_items.argtypes = [_I32, C.c_int32, C.c_int, C.c_int32, C.c_int32,
@@ -270,6 +272,15 @@ def kmc_pair_form(ctx, form=None):
     or, with no argument, returns the form in use."""
     r = C.c_int32()
     _check(lib().kmc_pair_form(ctx.handle, -1 if form is None else int(form), C.byref(r)))
+    return int(r.value)
+
+
+def kmc_sym_update(ctx, mode=None):
+    """Pins the symmetric form's update kernel (1 = one warp per update item,
+    2 = one block; 0 = autotuned) or, with no argument, returns the one in
+    use."""
+    r = C.c_int32()
+    _check(lib().kmc_sym_update(ctx.handle, -1 if mode is None else int(mode), C.byref(r)))
     return int(r.value)
 
 

@@ -51,8 +51,8 @@ def test_traffic_figures_come_from_committed_profiles():
     text = "".join(open(os.path.join(prof, f)).read() for f in sorted(os.listdir(prof)))
     assert bench.STEP_DRAM_BYTES
     for key, nbytes in bench.STEP_DRAM_BYTES.items():
-        (cfg, warps, tile, chunk, tpl, rpl), sym = key[:6], key[6:] == ("sym",)
-        assert len(key) == 6 or sym, key
+        (cfg, warps, tile, chunk, tpl, rpl), sym = key[:6], key[6:7] == ("sym",)
+        assert len(key) == 6 or (sym and key[7:] in ((), ("block",))), key
         assert cfg == "c1" or cfg in bench.CONFIGS, cfg
         assert tile & (tile - 1) == 0 and chunk % 64 == 0
         if sym:

@@ -60,10 +60,12 @@ for prec, tile, sizes in ((kmc.KMC_FP32_MIXED, 64, (1, 2, 3, 33, 127, 128, 129))
 # the symmetric pair form: field and update items, cells and row groups
 lyss = [inputs.make_lysosome(n, 12e-9, 0.05 if n > 3 else 0.01, seed=50 + n)
         for n in (1, 2, 63, 64, 65, 129, 600)]
-for warps, cells, chunk in ((4, 1, 0), (4, 1, 64), (4, 2, 128), (8, 1, 0), (2, 2, 64)):
+for warps, cells, chunk, upd in ((4, 1, 0, 1), (4, 1, 64, 1), (4, 2, 128, 1), (8, 1, 0, 1),
+                                 (2, 2, 64, 1), (4, 2, 128, 2), (8, 1, 64, 2)):
     ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
     kmc.kmc_pair_form(ctx, kmc.FORM_SYMMETRIC)
     kmc.kmc_targets_per_lane(ctx, 2 * cells)
+    kmc.kmc_sym_update(ctx, upd)
     kmc.kmc_tuning(ctx, warps, 32, chunk)
     rng = np.random.default_rng(warps + cells + chunk)
     m = np.concatenate([oracle.initial_moments(l.axis) + 0.3 * rng.normal(size=(l.n, 3))

@@ -30,28 +30,32 @@ def _built():
     kbuild.build()
 
 
-def _pin(ctx, warps, cells, chunk):
+def _pin(ctx, warps, cells, chunk, upd=1):
     kmc.kmc_pair_form(ctx, SYM)
     kmc.kmc_targets_per_lane(ctx, 2 * cells)
+    kmc.kmc_sym_update(ctx, upd)
     kmc.kmc_tuning(ctx, warps, 32, chunk)
 
 
-SHAPES = [(4, 1, 0), (4, 1, 64), (4, 1, 256), (4, 2, 0), (4, 2, 128), (8, 1, 0), (8, 1, 192),
-          (2, 2, 0), (2, 2, 320)]
+# (warps, cells per warp, source NPs per field item, update kernel: 1 = a warp
+# per update item, 2 = a block)
+SHAPES = [(4, 1, 0, 1), (4, 1, 64, 1), (4, 1, 256, 1), (4, 2, 0, 1), (4, 2, 128, 1),
+          (8, 1, 0, 1), (8, 1, 192, 1), (2, 2, 0, 1), (2, 2, 320, 1),
+          (4, 2, 0, 2), (4, 2, 128, 2), (8, 1, 192, 2), (2, 2, 64, 2)]
 
 
-@pytest.mark.parametrize("warps,cells,chunk", SHAPES)
-def test_fields_of_ragged_lysosomes(warps, cells, chunk):
+@pytest.mark.parametrize("warps,cells,chunk,upd", SHAPES)
+def test_fields_of_ragged_lysosomes(warps, cells, chunk, upd):
     sizes = (1, 2, 63, 64, 65, 300, 1100)
     lyss = [inputs.make_lysosome(n, 12e-9, 0.05 if n > 2 else 0.01, seed=60 + n) for n in sizes]
     ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
-    _pin(ctx, warps, cells, chunk)
+    _pin(ctx, warps, cells, chunk, upd)
     rng = np.random.default_rng(warps * 10 + cells + chunk)
     m = np.concatenate([perturbed(l.axis, rng, 0.3) for l in lyss])
     m = m.astype(np.float32).astype(np.float64)
     H = [0.01 * (q % 3) - 0.01 for q in range(len(lyss))]
     g = kmc.kmc_debug_step(ctx, H, 5e-8, 3, 71, m)
-    assert kmc.kmc_pair_form(ctx) == SYM
+    assert kmc.kmc_pair_form(ctx) == SYM and kmc.kmc_sym_update(ctx) == upd
     assert kmc.kmc_tuning(ctx) == (warps, 32, chunk)
     kmc.kmc_destroy(ctx)
     off = 0
@@ -82,11 +86,13 @@ def test_update_against_oracle_at_2000_nps():
     assert c >= 0.95 * (c + a), (c, a)
 
 
-def test_large_lysosome_sampled():
-    """50 000 NPs, 4 warps of two cells, 2048-NP source ranges."""
+@pytest.mark.parametrize("upd", [1, 2])
+def test_large_lysosome_sampled(upd):
+    """50 000 NPs, 4 warps of two cells, 2048-NP source ranges, both update
+    kernels."""
     (ly,), run = inputs.config_large50000(seed=0)
     ctx = kmc.kmc_create([ly], kmc.KMC_FP32_MIXED, center=np.zeros(3))
-    _pin(ctx, 4, 2, 2048)
+    _pin(ctx, 4, 2, 2048, upd)
     rng = np.random.default_rng(13)
     m32 = perturbed(ly.axis, rng, 0.3).astype(np.float32).astype(np.float64)
     t_step = 1.0 / (run["f"] * run["S"])
@@ -143,7 +149,7 @@ def _run(lyss, H, shape):
     return out
 
 
-@pytest.mark.parametrize("shape", [(4, 1, 128), (4, 2, 0)])
+@pytest.mark.parametrize("shape", [(4, 1, 128, 1), (4, 2, 0, 1), (4, 2, 256, 2)])
 def test_runs_are_deterministic_and_independent_of_the_batch(shape):
     lyss = [inputs.make_lysosome(n, 12e-9, 0.06, seed=90 + n) for n in (700, 300, 1300)]
     H = [0.015, 0.02, 0.012]
