@@ -244,6 +244,30 @@ kmc_status kmc_replicas_per_lane(kmc_ctx *ctx, int32_t rpl, int32_t *rpl_out);
  * tuning) is returned through form_out (may be NULL); form = -1 only reads it. */
 kmc_status kmc_pair_form(kmc_ctx *ctx, int32_t form, int32_t *form_out);
 
+/* Persistent period of the FP32 one-target-per-lane step (Sec. II.1 steps
+ * i-vii, S steps per field period). 2 runs every field period as one
+ * cooperative launch: each block keeps its work item for the whole period and
+ * a grid-wide barrier separates the steps (the update of Sec. II.2 is
+ * synchronous: a step reads only the moments of the step before), in place of
+ * one launch per step and chain. The barrier is bounded in time (2 s): a block
+ * that never arrives makes the others give up, kmc_sync then returns
+ * KMC_ETIMEOUT, and every block leaves the period at a step boundary. It needs
+ * every work item's block resident at once; a plan with more items fails with
+ * KMC_EINVAL. The results are the bits of the per-step launches at the same
+ * warps (4 or 8), tile and chunk. mode: 0 lets the autotuner choose (the
+ * default: it times both where the plan fits), 1 off, 2 on (KMC_EINVAL on FP64
+ * contexts). The value in use (0 before the first tuning) is returned through
+ * mode_out (may be NULL); mode = -1 only reads it. */
+kmc_status kmc_persistent(kmc_ctx *ctx, int32_t mode, int32_t *mode_out);
+
+/* Failure-detection test hook of the persistent period: runs 4 steps in which
+ * block 0 does not arrive at the grid barrier after step 1, with the barrier's
+ * limit cut to 1 ms. The other blocks give up, nothing faults, and the call
+ * returns KMC_ETIMEOUT as designed (KMC_ESTATE if the barrier did not run out)
+ * and clears the error word. The moments advance by up to two steps.
+ * KMC_EINVAL unless the context's shape is the persistent period. */
+kmc_status kmc_debug_grid_stall(kmc_ctx *ctx);
+
 /* Update kernel of the symmetric pair form (kmc_pair_form = 2): 1 gives each
  * update item (32 targets of one cell) one warp, which adds the item's forward
  * and reverse partial sums in slot order and runs steps iii-vii alone; 2 gives

@@ -127,9 +127,12 @@ struct Shape {
   int cl = 0;
   // symmetric form's update kernel: 0 = one warp per update item, 1 = one block
   int supd = 0;
+  // 1: the whole field period as one persistent cooperative launch (FP32, one
+  // target per lane) with a grid barrier after each step
+  int persist = 0;
   bool operator==(const Shape &o) const {
     return warps == o.warps && tile == o.tile && chunk == o.chunk && tpl == o.tpl &&
-           rpl == o.rpl && sym == o.sym && cl == o.cl && supd == o.supd;
+           rpl == o.rpl && sym == o.sym && cl == o.cl && supd == o.supd && persist == o.persist;
   }
 };
 
@@ -137,11 +140,12 @@ struct TuneKey {
   int prec;
   long long N;
   int n_lys, max_n, tpl_mode, rpl_mode, reps;  // reps: replica sets available (bits)
-  int form_mode, cl_mode, supd_mode;
+  int form_mode, cl_mode, supd_mode, persist_mode;
   bool operator<(const TuneKey &o) const {
     return std::tie(prec, N, n_lys, max_n, tpl_mode, rpl_mode, reps, form_mode, cl_mode,
-                    supd_mode) < std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode,
-                                          o.reps, o.form_mode, o.cl_mode, o.supd_mode);
+                    supd_mode, persist_mode) <
+           std::tie(o.prec, o.N, o.n_lys, o.max_n, o.tpl_mode, o.rpl_mode, o.reps, o.form_mode,
+                    o.cl_mode, o.supd_mode, o.persist_mode);
   }
 };
 std::mutex g_tune_mu;
@@ -220,6 +224,11 @@ struct kmc_ctx {
   int form_mode = 0;           // pair form: 0 = the autotuner's choice, 1 = ordered, 2 = symmetric
   int cl_mode = 0;             // cluster split: 0 = the autotuner's choice, 1 = off, 2 = on
   int supd_mode = 0;           // symmetric update: 0 = the autotuner's, 1 = warp, 2 = block per item
+  int persist_mode = 0;        // persistent period: 0 = the autotuner's choice, 1 = off, 2 = on
+  // persistent period: the steps' cosines and the grid barrier's counters
+  double *d_cosk = nullptr;
+  size_t cosk_cap = 0;
+  uint32_t *d_gbar = nullptr;
   int tpl_mode = 0;            // targets per lane: 0 = the autotuner's choice, else 1, 2 or 3
   int rpl_mode = 0;            // replicas per lane: 0 = the autotuner's choice, 1 = off, 2 or 4
   bool rep_ok[5] = {};         // [k]: the lysosomes form sets of k identical consecutive ones
@@ -521,6 +530,13 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
   for (int l = 0; l < c->n_lys; l += sh.rpl) np.push_back(c->n[l]);
   Plan plan = plan_items(np, c->fp32, sh.chunk, per_sm, n_sms, sh.tpl);
   for (Item &it : plan.items) it.l *= sh.rpl;
+  if (sh.persist) {  // one cooperative launch: every item's block resident at once
+    int per = 0;
+    KMC_CUDA(kmc::persist_blocks_per_sm(sh.warps, sh.tile, &per));
+    if (static_cast<long long>(plan.items.size()) > static_cast<long long>(per) * n_sms)
+      return fail(KMC_EINVAL, "the persistent period needs every work item resident (%zu items, "
+                  "%d x %d blocks)", plan.items.size(), per, n_sms);
+  }
   if (sh.cl == 2) {  // two-CTA clusters: exactly two parts per group, item 2 g + part
     for (size_t u = 0; u < plan.items.size(); ++u)
       if (plan.items[u].nsplit != 2 || plan.items[u].split != static_cast<int>(u & 1))
@@ -599,7 +615,41 @@ StepArgs base_args(kmc_ctx *c) {
   a.sfwd = c->d_sfwd;
   a.srev = c->d_srev;
   a.n_upd = c->n_supd;
+  a.cosk = c->d_cosk;
+  a.gbar = c->d_gbar;
+  a.barrier_ns = 2000000000ull;  // 2 s
+  a.stall_block = -1;
+  a.stall_step = -1;
   return a;
+}
+
+// The persistent period's cosine table for `steps` steps (the values the
+// per-step launches of a period graph receive) and its barrier counters.
+kmc_status prepare_persist(kmc_ctx *c, int steps) {
+  if (!c->d_gbar) KMC_TRY(dalloc(&c->d_gbar, 2 * sizeof(uint32_t)));
+  if (static_cast<size_t>(steps) > c->cosk_cap) {
+    if (c->d_cosk) cudaFree(c->d_cosk);
+    c->d_cosk = nullptr;
+    c->cosk_cap = 0;
+    KMC_TRY(dalloc(&c->d_cosk, sizeof(double) * steps));
+    c->cosk_cap = static_cast<size_t>(steps);
+  }
+  std::vector<double> cs(static_cast<size_t>(steps));
+  for (int k = 0; k < steps; ++k) cs[k] = std::cos(2.0 * kPi * k / steps);
+  KMC_CUDA(cudaMemcpyAsync(c->d_cosk, cs.data(), sizeof(double) * cs.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  return KMC_OK;
+}
+
+// One persistent launch of `steps` steps (the barrier counters zeroed first).
+cudaError_t launch_period(kmc_ctx *c, StepArgs a, const Shape &sh, int steps) {
+  a.S = steps;
+  a.cosk = c->d_cosk;
+  a.gbar = c->d_gbar;
+  cudaError_t e = cudaMemsetAsync(c->d_gbar, 0, 2 * sizeof(uint32_t), c->stream);
+  if (e == cudaSuccess) e = kmc::launch_persist(a, sh.warps, sh.tile, c->n_items, c->stream);
+  return e;
 }
 
 // Chains of the current items (the symmetric form has its own cut).
@@ -672,6 +722,9 @@ int max_tile(int fp32, int warps) {
 
 bool shape_ok(const kmc_ctx *c, const Shape &s) {
   if (s.supd != 0 && (s.sym == 0 || s.supd != 1)) return false;
+  if (s.persist != 0 && (s.persist != 1 || !c->fp32 || s.tpl != 1 || s.rpl != 1 || s.sym != 0 ||
+                         s.cl != 0 || (s.warps != 4 && s.warps != 8)))
+    return false;
   if (s.sym) {  // symmetric form: (warps, cells per warp) of its field kernel
     if (!c->fp32 || s.rpl != 1 || s.tpl != 2 * s.sym || s.tile != 32) return false;
     if (!((s.warps == 4 && (s.sym == 1 || s.sym == 2)) || (s.warps == 8 && s.sym == 1) ||
@@ -785,6 +838,27 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   a.cos_k = 1.0;
   a.S = 1;
   a.n_rec = 1;
+  if (s.persist) {  // a persistent launch of 32 steps, timed twice after one
+    constexpr int kSteps = 32;
+    if (prepare_persist(c, kSteps) != KMC_OK) return -1.f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return -1.f;
+    }
+    bool ok = launch_period(c, a, s, kSteps) == cudaSuccess;
+    if (ok) ok = cudaEventRecord(e0, c->stream) == cudaSuccess;
+    for (int r = 0; r < 2 && ok; ++r) ok = launch_period(c, a, s, kSteps) == cudaSuccess;
+    if (ok) ok = cudaEventRecord(e1, c->stream) == cudaSuccess;
+    if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = -1.f;
+    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms /= 2 * kSteps;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return ok ? ms : -1.f;
+  }
   // several chains share the SMs, so a shape is timed the way a run executes
   // it: a graph of a few steps of every chain
   const bool chained = n_chains_of(c, s) > 1;
@@ -831,7 +905,7 @@ kmc_status autotune(kmc_ctx *c) {
   const TuneKey key{c->fp32, c->N,        c->n_lys,
                     max_n,   c->tpl_mode, c->rpl_mode,
                     (c->rep_ok[2] ? 1 : 0) | (c->rep_ok[4] ? 2 : 0), c->form_mode,
-                    c->cl_mode, c->supd_mode};
+                    c->cl_mode, c->supd_mode, c->persist_mode};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -952,7 +1026,7 @@ kmc_status autotune(kmc_ctx *c) {
           s.tile = t;
           s.chunk = ch;
           s.tpl = tpl;
-          if (c->cl_mode != 2) {
+          if (c->cl_mode != 2 && c->persist_mode != 2) {
             const float ms = time_shape(c, s);
             if (ms > 0.f && ms < best) {
               best = ms;
@@ -961,12 +1035,24 @@ kmc_status autotune(kmc_ctx *c) {
           }
           // the same shape with each group's two parts as a two-CTA cluster
           // (time_shape fails unless every group has exactly two parts)
-          if (c->fp32 && tpl == 1 && ch > 0 && c->cl_mode != 1) {
-            s.cl = 2;
-            const float mc = time_shape(c, s);
+          if (c->fp32 && tpl == 1 && ch > 0 && c->cl_mode != 1 && c->persist_mode != 2) {
+            Shape sc = s;
+            sc.cl = 2;
+            const float mc = time_shape(c, sc);
             if (mc > 0.f && mc < best) {
               best = mc;
-              bs = s;
+              bs = sc;
+            }
+          }
+          // the same shape as one persistent launch per period (time_shape
+          // fails unless every item's block can be resident at once)
+          if (c->fp32 && tpl == 1 && c->persist_mode != 1 && c->cl_mode != 2) {
+            Shape sp = s;
+            sp.persist = 1;
+            const float mp = time_shape(c, sp);
+            if (mp > 0.f && mp < best) {
+              best = mp;
+              bs = sp;
             }
           }
         }
@@ -998,7 +1084,7 @@ void free_ctx(kmc_ctx *c) {
                   c->d_dh,    c->d_pos64,  c->d_phi,     c->d_nodes,    c->d_possi, c->d_phif,
                   c->d_loop,  c->d_cnt,    c->d_err,     c->d_rs,       c->d_items,
                   c->d_partial, c->d_arrivals, c->d_dbg, c->d_dbg_flags, c->d_sitems,
-                  c->d_supd,  c->d_sfwd,   c->d_srev};
+                  c->d_supd,  c->d_sfwd,   c->d_srev,    c->d_cosk,     c->d_gbar};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < kMaxChains; ++q) {
@@ -1395,6 +1481,24 @@ kmc_status kmc_pair_form(kmc_ctx *c, int32_t form, int32_t *form_out) {
   return KMC_OK;
 }
 
+kmc_status kmc_persistent(kmc_ctx *c, int32_t mode, int32_t *mode_out) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  if (mode != -1) {
+    if (mode < 0 || mode > 2) return fail(KMC_EINVAL, "persistent period: 0 (autotuned), 1 (off), 2 (on)");
+    if (mode == 2 && !c->fp32) return fail(KMC_EINVAL, "the persistent period runs on FP32 contexts");
+    c->persist_mode = mode;
+    if (mode != 0 && c->shape.warps != 0) {
+      Shape s = c->shape;
+      s.persist = mode == 2 ? 1 : 0;
+      c->shape = shape_ok(c, s) ? s : Shape();
+    }
+  }
+  if (mode_out)
+    *mode_out = c->persist_mode != 0 ? c->persist_mode
+                                     : (c->shape.warps ? (c->shape.persist ? 2 : 1) : 0);
+  return KMC_OK;
+}
+
 kmc_status kmc_sym_update(kmc_ctx *c, int32_t mode, int32_t *mode_out) {
   if (!c) return fail(KMC_EINVAL, "ctx is NULL");
   if (mode != -1) {
@@ -1443,6 +1547,7 @@ kmc_status kmc_tuning(kmc_ctx *c, int32_t warps, int32_t tile, int32_t chunk,
     s.tpl = c->tpl_mode != 0 ? c->tpl_mode : 1;
     s.rpl = c->rpl_mode > 1 ? c->rpl_mode : 1;
     s.cl = (c->cl_mode == 2 && s.tpl == 1 && s.rpl == 1) ? 2 : 0;
+    s.persist = (c->persist_mode == 2 && s.tpl == 1 && s.rpl == 1 && s.cl == 0) ? 1 : 0;
     if (c->form_mode == 2 || c->tpl_mode == 4) {  // symmetric form; the tile does not apply
       s.cl = 0;
       s.supd = c->supd_mode == 2 ? 1 : 0;
@@ -1512,10 +1617,21 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
   KMC_TRY(refresh_sources(c, static_cast<int>(c->step_global & 1)));
   RunState rs{c->step_global, 0, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
-  // one field period (S step launches + the period advance) as a CUDA graph
   const Shape &sh = c->shape;
-  if (!c->gexec || c->g_S != S || c->g_discard != discard || c->g_nrec != n_rec ||
-      !(c->g_shape == sh) || c->g_seed != seed) {
+  if (sh.persist) {  // one persistent launch per period, then the period advance
+    StepArgs a = base_args(c);
+    a.seed = seed;
+    a.discard = discard;
+    a.n_rec = static_cast<int>(std::max(n_rec, 1ll));
+    KMC_TRY(prepare_persist(c, S));
+    for (int p = 0; p < periods; ++p) {
+      KMC_CUDA(launch_period(c, a, sh, S));
+      KMC_CUDA(kmc::launch_advance(c->d_rs, S, c->stream));
+    }
+  }
+  // otherwise one field period (S step launches + the period advance) as a CUDA graph
+  if (!sh.persist && (!c->gexec || c->g_S != S || c->g_discard != discard || c->g_nrec != n_rec ||
+      !(c->g_shape == sh) || c->g_seed != seed)) {
     drop_graph(c);
     StepArgs a = base_args(c);
     a.seed = seed;
@@ -1529,7 +1645,8 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
     c->g_shape = sh;
     c->g_seed = seed;
   }
-  for (int p = 0; p < periods; ++p) KMC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+  for (int p = 0; p < periods && !sh.persist; ++p)
+    KMC_CUDA(cudaGraphLaunch(c->gexec, c->stream));
   c->step_global += static_cast<long long>(S) * periods;
   c->have_run = true;
   c->S = S;
@@ -2181,6 +2298,34 @@ kmc_status kmc_regenerate(kmc_ctx *c, int32_t lys, int32_t what, double disorder
   }
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   return KMC_OK;
+}
+
+kmc_status kmc_debug_grid_stall(kmc_ctx *c) {
+  if (!c) return fail(KMC_EINVAL, "ctx is NULL");
+  KMC_TRY(check_device_error(c));
+  KMC_TRY(ensure_shape(c));
+  if (!c->shape.persist)
+    return fail(KMC_EINVAL, "the grid-stall hook needs the persistent period (kmc_persistent)");
+  constexpr int kSteps = 4;
+  KMC_TRY(prepare_persist(c, kSteps));
+  RunState rs{c->step_global, -1, 0};
+  KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
+  if (c->arrivals_cap)
+    KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  StepArgs a = base_args(c);
+  a.n_rec = 1;
+  a.stall_block = 0;  // block 0 does not arrive at the barrier after step 1
+  a.stall_step = 1;
+  a.barrier_ns = 1000000ull;  // 1 ms
+  KMC_CUDA(launch_period(c, a, c->shape, kSteps));
+  const kmc_status st = check_device_error(c);  // KMC_ETIMEOUT when the barrier gave up
+  // the blocks left the period at a step boundary: clear the flag and the
+  // arrival counters; the moments have advanced by up to two steps
+  KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
+  if (c->arrivals_cap)
+    KMC_CUDA(cudaMemsetAsync(c->d_arrivals, 0, sizeof(int32_t) * c->arrivals_cap, c->stream));
+  KMC_CUDA(cudaStreamSynchronize(c->stream));
+  return st == KMC_OK ? fail(KMC_ESTATE, "the stalled grid barrier did not run out") : st;
 }
 
 kmc_status kmc_debug_stall(kmc_ctx *c) {

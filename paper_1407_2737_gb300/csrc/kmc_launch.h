@@ -27,6 +27,13 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
                         cudaStream_t st, bool pdl = false, int tpl = 1, int rpl = 1,
                         int cl = 0);
 
+// Persistent period (FP32, one target per lane, warps 4 or 8): one cooperative
+// launch of n_items blocks runs steps 0 .. a.S - 1 with a grid barrier after
+// each (a.cosk, a.gbar zeroed before the launch, a.barrier_ns); every block
+// must be resident at once (persist_blocks_per_sm x SMs >= n_items).
+cudaError_t launch_persist(const StepArgs &a, int warps, int tile, int n_items, cudaStream_t st);
+cudaError_t persist_blocks_per_sm(int warps, int tile, int *blocks);
+
 // Symmetric pair form (FP32): one step = kmc_field_sym<warps, cells> over
 // a.sitems[0 .. n_field) and then kmc_update_sym over a.supd[0 .. a.n_upd).
 // (warps, cells) in {(2, 2), (4, 1), (4, 2), (8, 1)}; row groups of warps x cells

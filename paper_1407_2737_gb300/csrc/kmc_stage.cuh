@@ -19,6 +19,12 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
                : "memory");
 }
 
+// Ends an mbarrier's use (all its phases complete), so that its memory can
+// be initialised again.
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -90,6 +96,65 @@ __device__ __forceinline__ bool arrive_last(int32_t *counter, int nsplit, int *f
                  : "l"(counter)
                  : "memory");
     *flag = old == nsplit - 1;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns();
+
+// Grid-wide barrier of a cooperative launch (every block resident), bounded in
+// time. gbar[0] counts the arrivals at the current generation gbar[1]: the
+// last block to arrive resets the count and advances the generation (release);
+// the others wait (acquire) for the generation to change, for at most
+// limit_ns, or until another block has reported a timeout in the error word.
+// The block's stores before the barrier are published by thread 0's
+// release-acquire arrival (after a block barrier) and read after the second
+// block barrier. Returns, to every thread, false if the barrier was not
+// completed. skip: the block does not arrive (failure-detection test hook).
+__device__ __forceinline__ bool grid_barrier(uint32_t *gbar, uint32_t nblocks, int32_t *err,
+                                             unsigned long long limit_ns, bool skip, int *flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (*reinterpret_cast<volatile int32_t *>(err) & kErrTimeout) {
+      ok = 0;
+    } else {
+      uint32_t g;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gbar + 1) : "memory");
+      bool wait = true;
+      if (!skip) {
+        uint32_t old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                     : "=r"(old)
+                     : "l"(gbar)
+                     : "memory");
+        if (old == nblocks - 1) {
+          asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(gbar) : "memory");
+          asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(gbar + 1), "r"(g + 1)
+                       : "memory");
+          wait = false;
+        }
+      }
+      if (wait) {
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+          uint32_t gn;
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gn) : "l"(gbar + 1) : "memory");
+          if (gn != g) break;
+          if (*reinterpret_cast<volatile int32_t *>(err) & kErrTimeout) {
+            ok = 0;
+            break;
+          }
+          if (global_ns() - t0 > limit_ns) {
+            atomicOr(err, kErrTimeout);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    *flag = ok;
   }
   __syncthreads();
   return *flag != 0;

@@ -716,6 +716,12 @@ __device__ __forceinline__ bool staged_loop(int ntiles, uint64_t *bar, int32_t *
       issue(t + 2);
     }
   }
+  // every phase is complete: the barriers may be initialised again (the
+  // persistent kernel stages every step)
+  if (threadIdx.x == 0) {
+    mbar_inval(&bar[0]);
+    mbar_inval(&bar[1]);
+  }
   return true;
 }
 
@@ -771,14 +777,16 @@ __device__ __forceinline__ bool tile_in_bounds(const StepArgs &a, const Item &it
 // arrival counter, and part 0 adds them in split order (the same operations,
 // so the same bits) and runs the update. Every thread of both CTAs passes the
 // same two cluster barriers, on the failure paths too.
-template <int NW, bool CL = false>
-__global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int tile) {
-  extern __shared__ __align__(128) unsigned char smem[];
+// One step of the block's work item (kmc_step_f32 runs it once per launch,
+// kmc_persist_f32 once per step of a field period). PERSIST: the state of the
+// previous step is already visible (a grid barrier), so there is no
+// programmatic-launch wait. Returns early for items whose group is finished by
+// another item.
+template <int NW, bool CL, bool PERSIST>
+__device__ __forceinline__ void step_f32_item(const StepArgs &a, int tile, unsigned char *smem,
+                                              int &s_last, const GridTables<float> &tab) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *dyn = smem + 16;
-  __shared__ int s_last;
-  __shared__ GridTables<float> tab;
-  tab.load();
   if (!item_in_bounds(a, 1, true) ||
       (CL && !KMC_DCHECK(a.items[blockIdx.x].nsplit == 2 &&
                              static_cast<int>(blockIdx.x & 1) == a.items[blockIdx.x].split,
@@ -794,7 +802,7 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // items, lysosome constants and positions do not change during a run
   const float4 pi = static_cast<const float4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
-  grid_dependency_wait();
+  if constexpr (!PERSIST) grid_dependency_wait();
   const long long step = a.rs->step_base + a.k_local;
   const int per = a.rs->period;
   const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
@@ -919,9 +927,46 @@ __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int ti
   }
   __syncthreads();
   block_update<float4, true>(a, L, it, step, rec, tin, sm, tab);
+}
+
+template <int NW, bool CL = false>
+__global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int tile) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_last;
+  __shared__ GridTables<float> tab;
+  tab.load();
+  step_f32_item<NW, CL, false>(a, tile, smem, s_last, tab);
   // the next step's blocks may now be scheduled; triggering earlier lets them
   // take the slots of early-finishing blocks and unbalances the next step
   grid_launch_dependents();
+}
+
+// Persistent form of kmc_step_f32 (one target per lane): one cooperative
+// launch runs a whole field period. Every block keeps its work item and runs
+// steps 0 .. S - 1, with a bounded grid barrier after each step in place of
+// the launch boundary; the step is the same code with the same cosine, so the
+// results are the bits of the per-step launches. A barrier that times out
+// sets KMC_ETIMEOUT in the error word and every block leaves the period.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) kmc_persist_f32(const StepArgs a, int tile) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_last;
+  __shared__ int s_ok;
+  __shared__ GridTables<float> tab;
+  __shared__ StepArgs sa;  // a with this step's k_local and cos_k
+  tab.load();
+  if (threadIdx.x == 0) sa = a;
+#pragma unroll 1
+  for (int k = 0; k < a.S; ++k) {
+    if (threadIdx.x == 0) {
+      sa.k_local = k;
+      sa.cos_k = a.cosk[k];
+    }
+    __syncthreads();
+    step_f32_item<NW, false, true>(sa, tile, smem, s_last, tab);
+    const bool skip = a.stall_block == static_cast<int>(blockIdx.x) && a.stall_step == k;
+    if (!grid_barrier(a.gbar, gridDim.x, a.err, a.barrier_ns, skip, &s_ok)) break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -2019,6 +2064,23 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
   }
 }
 
+cudaError_t launch_persist(const StepArgs &a, int warps, int tile, int n_items, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(n_items));
+  cfg.blockDim = dim3(static_cast<unsigned>(warps * 32));
+  cfg.dynamicSmemBytes = step_smem_bytes(1, warps, tile, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (warps == 4) return cudaLaunchKernelEx(&cfg, kmc_persist_f32<4>, a, tile);
+  if (warps == 8) return cudaLaunchKernelEx(&cfg, kmc_persist_f32<8>, a, tile);
+  return cudaErrorInvalidValue;
+}
+
 // Symmetric form: the field kernel over n_field items, then the update kernel
 // over the a.n_upd target groups, both on st.
 template <int W, int C>
@@ -2054,6 +2116,14 @@ size_t sym_smem_bytes(int warps, int cells) { return sym_field_smem(warps, cells
 template <typename K>
 static cudaError_t occupancy(K kernel, int threads, size_t smem, int *blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, threads, smem);
+}
+
+cudaError_t persist_blocks_per_sm(int warps, int tile, int *blocks) {
+  *blocks = 0;
+  const size_t smem = step_smem_bytes(1, warps, tile, 1);
+  if (warps == 4) return occupancy(kmc_persist_f32<4>, 128, smem, blocks);
+  if (warps == 8) return occupancy(kmc_persist_f32<8>, 256, smem, blocks);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t sym_blocks_per_sm(int warps, int cells, int *blocks) {
@@ -2163,6 +2233,8 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<16>);
+  if (e == cudaSuccess) e = allow_smem(kmc_persist_f32<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_persist_f32<8>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<4, true>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<8, true>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32<16, true>);

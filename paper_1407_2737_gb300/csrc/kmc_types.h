@@ -186,7 +186,16 @@ struct StepArgs {
   float *sfwd;
   float *srev;
   int32_t n_upd;
-  int32_t pad4;
+  // persistent period kernel (kmc_persist_f32): the cosine of each step of the
+  // period (host-computed, as the per-step launches receive it), the grid
+  // barrier's counters and its time limit; failure-detection test hook: block
+  // stall_block does not arrive at the barrier of step stall_step (-1: none)
+  int32_t stall_block;
+  const double *cosk;
+  uint32_t *gbar;
+  unsigned long long barrier_ns;
+  int32_t stall_step;
+  int32_t pad5;
 };
 
 // Ref. [8] mode (kmc_mean.cuh): per lysosome, per work item, arguments.

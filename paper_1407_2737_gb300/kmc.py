@@ -36,7 +36,7 @@ EXPORTS = ("kmc_create", "kmc_set_stream", "kmc_run", "kmc_read", "kmc_sync",
            "kmc_shell_profile", "kmc_mean_run", "kmc_regenerate", "kmc_debug_stall",
            "kmc_regenerate_rsa", "kmc_targets_per_lane", "kmc_plan_items",
            "kmc_replicas_per_lane", "kmc_pair_form", "kmc_plan_sym", "kmc_cluster_split",
-           "kmc_sym_update")
+           "kmc_sym_update", "kmc_persistent", "kmc_debug_grid_stall")
 KMC_NOALLOC_MAX_N = 8192
 KMC_MAX_CHAINS = 8  # parallel step-kernel chains of a batch (kmc_run)
 KMC_ITEM_FIELDS = 8  # per work item in kmc_plan_items
@@ -108,6 +108,8 @@ def lib():
             L.kmc_pair_form.argtypes = [vp, C.c_int32, _I32]
             L.kmc_cluster_split.argtypes = [vp, C.c_int32, _I32]
             L.kmc_sym_update.argtypes = [vp, C.c_int32, _I32]
+            L.kmc_persistent.argtypes = [vp, C.c_int32, _I32]
+            L.kmc_debug_grid_stall.argtypes = [vp]
             L.kmc_plan_sym.argtypes = [_I32, C.c_int32, C.c_int32, C.c_int32, _I32, C.c_int64,
                                        _I64, _I32, C.c_int64, _I64, _I64, _I32, _I32, _I32]
             L.kmc_plan_items.argtypes = [_I32, C.c_int32, C.c_int, C.c_int32, C.c_int32,
@@ -273,6 +275,21 @@ def kmc_pair_form(ctx, form=None):
     r = C.c_int32()
     _check(lib().kmc_pair_form(ctx.handle, -1 if form is None else int(form), C.byref(r)))
     return int(r.value)
+
+
+def kmc_persistent(ctx, mode=None):
+    """Pins the persistent period (1 = off, 2 = on: one cooperative launch per
+    field period with a grid barrier between steps; 0 = autotuned) or, with no
+    argument, returns the value in use."""
+    r = C.c_int32()
+    _check(lib().kmc_persistent(ctx.handle, -1 if mode is None else int(mode), C.byref(r)))
+    return int(r.value)
+
+
+def kmc_debug_grid_stall(ctx):
+    """Failure-detection hook of the persistent period: raises
+    KmcError(KMC_ETIMEOUT) when the stalled grid barrier runs out as designed."""
+    _check(lib().kmc_debug_grid_stall(ctx.handle))
 
 
 def kmc_sym_update(ctx, mode=None):
