@@ -138,13 +138,18 @@ def launch_info(kmc, ctx, lyss):
         return {"launch": launch, "kernel": "kmc_field_sym<%d, %d> + kmc_update_sym%s<%d>" % (
                     warps, cells, "_block" if block else "", gc),
                 "lane_ops_per_pair": ops / pairs, "chains": chains,
-                "launches_per_step": 2 * chains,
+                "launches_per_period": lambda S: 2 * S * chains,
                 "key": (warps, tile, chunk, tpl, rpl, "sym") + (("block",) if block else ())}
+    if kmc.kmc_persistent(ctx) == 2:  # one cooperative launch per period, then the advance
+        launch.update({"pair_form": "ordered", "chains": 1, "persistent": True})
+        return {"launch": launch, "kernel": "kmc_persist_f32<%d>" % warps,
+                "lane_ops_per_pair": lane_ops_per_pair(rpl), "chains": 1,
+                "launches_per_period": lambda S: 1, "key": (warps, tile, chunk, tpl, rpl, "persist")}
     chains = min(len(lyss) // max(rpl, 1), kmc.KMC_MAX_CHAINS)
     launch.update({"pair_form": "ordered", "chains": chains})
     return {"launch": launch, "kernel": step_kernel(warps, tpl, rpl),
             "lane_ops_per_pair": lane_ops_per_pair(rpl), "chains": chains,
-            "launches_per_step": chains, "key": (warps, tile, chunk, tpl, rpl)}
+            "launches_per_period": lambda S: S * chains, "key": (warps, tile, chunk, tpl, rpl)}
 
 
 def fp32_lane_ops_peak():
@@ -646,7 +651,7 @@ def measure_sub_config(name, kmc, inputs, torch, stream, flush, warmup, uuid=Non
         "e2e": {"value": n_np * n_steps / te, "unit": UNIT,
                 "h2d_bytes_per_step": sum(l.n * 7 * 8 for l in lyss) + 8 * len(lyss),
                 "d2h_bytes_per_step": sum(8 + 8 * n_rec + 8 * l.n for l in lyss)},
-        "gpu_launches": 1 + run["periods"] * (run["S"] * info["launches_per_step"] + 1),
+        "gpu_launches": 1 + run["periods"] * (info["launches_per_period"](run["S"]) + 1),
         "clocks": clk.summary(),
     }
 
@@ -753,7 +758,7 @@ def main():
     # one step = one step-kernel launch per chain (equal lysosomes: one chain
     # each, up to KMC_MAX_CHAINS; with replicas per lane one per set of them),
     # run concurrently; one period advance
-    launches_per_step = 1 + run["periods"] * (run["S"] * info["launches_per_step"] + 1)
+    launches_per_step = 1 + run["periods"] * (info["launches_per_period"](run["S"]) + 1)
     # roofline of the fused step kernel over one kMC step (all chains' launches)
     launch_s = t_total / (args.steps * n_steps)
     achieved = FLOPS_PER_PAIR * pairs_per_launch / launch_s / 1e12
