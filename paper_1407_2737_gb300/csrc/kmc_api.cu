@@ -930,6 +930,16 @@ kmc_status autotune(kmc_ctx *c) {
   KMC_TRY(refresh_sources(c, static_cast<int>(c->step_global & 1)));
   float best = 1e30f;
   Shape bs;
+  // every shape that timed, for the finalists' second look
+  std::vector<std::pair<float, Shape>> timed;
+  auto consider = [&](const Shape &s, float ms) {
+    if (!(ms > 0.f)) return;
+    timed.emplace_back(ms, s);
+    if (ms < best) {
+      best = ms;
+      bs = s;
+    }
+  };
   bs.warps = 4;
   bs.tile = 64;
   bs.chunk = 0;
@@ -964,10 +974,7 @@ kmc_status autotune(kmc_ctx *c) {
         s.sym = v[1];
         s.supd = c->supd_mode == 2 ? 1 : 0;
         const float ms = time_shape(c, s);
-        if (ms > 0.f && ms < best) {
-          best = ms;
-          bs = s;
-        }
+        consider(s, ms);
       }
     }
     // the best symmetric shape with the other update kernel
@@ -975,10 +982,7 @@ kmc_status autotune(kmc_ctx *c) {
       Shape s = bs;
       s.supd = 1;
       const float ms = time_shape(c, s);
-      if (ms > 0.f && ms < best) {
-        best = ms;
-        bs = s;
-      }
+      consider(s, ms);
     }
   }
   const int warps_c[] = {4, 8};
@@ -1001,10 +1005,7 @@ kmc_status autotune(kmc_ctx *c) {
           s.tpl = 1;
           s.rpl = rpl;
           const float ms = time_shape(c, s);
-          if (ms > 0.f && ms < best) {
-            best = ms;
-            bs = s;
-          }
+          consider(s, ms);
         }
       }
     }
@@ -1028,10 +1029,7 @@ kmc_status autotune(kmc_ctx *c) {
           s.tpl = tpl;
           if (c->cl_mode != 2 && c->persist_mode != 2) {
             const float ms = time_shape(c, s);
-            if (ms > 0.f && ms < best) {
-              best = ms;
-              bs = s;
-            }
+            consider(s, ms);
           }
           // the same shape with each group's two parts as a two-CTA cluster
           // (time_shape fails unless every group has exactly two parts)
@@ -1039,10 +1037,7 @@ kmc_status autotune(kmc_ctx *c) {
             Shape sc = s;
             sc.cl = 2;
             const float mc = time_shape(c, sc);
-            if (mc > 0.f && mc < best) {
-              best = mc;
-              bs = sc;
-            }
+            consider(sc, mc);
           }
           // the same shape as one persistent launch per period (time_shape
           // fails unless every item's block can be resident at once)
@@ -1050,13 +1045,35 @@ kmc_status autotune(kmc_ctx *c) {
             Shape sp = s;
             sp.persist = 1;
             const float mp = time_shape(c, sp);
-            if (mp > 0.f && mp < best) {
-              best = mp;
-              bs = sp;
-            }
+            consider(sp, mp);
           }
         }
       }
+    }
+  }
+  // Shapes within a few per cent of the best are timed twice more, in turn, and
+  // the one with the lowest of its times wins: one timing of a few hundred
+  // microseconds moves by about a per cent from launch to launch.
+  {
+    std::vector<std::pair<float, Shape>> fin;
+    for (const auto &t : timed)
+      if (t.first <= 1.03f * best) fin.push_back(t);
+    std::sort(fin.begin(), fin.end(),
+              [](const std::pair<float, Shape> &x, const std::pair<float, Shape> &y) {
+                return x.first < y.first;
+              });
+    if (fin.size() > 6) fin.resize(6);
+    if (fin.size() > 1) {
+      for (int r = 0; r < 2; ++r)
+        for (auto &f : fin) {
+          const float ms = time_shape(c, f.second);
+          if (ms > 0.f && ms < f.first) f.first = ms;
+        }
+      for (const auto &f : fin)
+        if (f.first < best) {
+          best = f.first;
+          bs = f.second;
+        }
     }
   }
   KMC_CUDA(cudaGetLastError());

@@ -1028,11 +1028,19 @@ __device__ __forceinline__ AccF32N<3> pair_tile_f32_3t(const ulonglong2 *__restr
   return acc;
 }
 
+// Warps that update each 32-target part of the multi-target kernel when its
+// parts update side by side (four or more warps per part, as the scan needs),
+// else 0: the parts update in turn on the whole block.
+constexpr int tn_group(int warps, int tpl) {
+  return (warps % tpl == 0 && warps / tpl >= 4) ? warps / tpl : 0;
+}
+
 // Dynamic shared memory of the multi-target kernel after its pair loop: the
-// warps' (sum, -error) pairs of every target, then the update state.
+// warps' (sum, -error) pairs of every target, then the update state (one per
+// part when the parts update side by side).
 constexpr size_t epi_bytes_tn(int warps, int tpl) {
   return static_cast<size_t>(warps) * 6 * tpl * kTargets * sizeof(float) +
-         sizeof(EpiShared<float>) + 64;
+         (tn_group(warps, tpl) ? tpl : 1) * sizeof(EpiShared<float>) + 64;
 }
 
 // Three targets per lane, 4 warps: held at 4 blocks per SM (128 registers).
@@ -1074,10 +1082,16 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
   const int par = static_cast<int>(step & 1);
   const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
 
+  // the part whose update this warp runs, and whether it leads it (holds the
+  // part's inputs and combines its sums)
+  constexpr int kGrp = tn_group(NW, TPL);
+  const int gk = kGrp ? warp / kGrp : 0;
+  const bool lead = kGrp ? (warp % kGrp == 0) : (warp == 0);
   Item h0 = it;
-  h0.nt = ntk[0];
+  h0.t0 = it.t0 + gk * kTargets;
+  h0.nt = ntk[gk];
   TargetIn<float4> tin;
-  if (warp == 0) tin = load_target<float4>(a, L, h0, step, lane);
+  if (lead && h0.nt > 0) tin = load_target<float4>(a, L, h0, step, lane);
   float sk[3 * TPL], ck[3 * TPL];  // Kahan sums: target k, component c at 3 k + c
 #pragma unroll
   for (int c = 0; c < 3 * TPL; ++c) sk[c] = ck[c] = 0.f;
@@ -1130,8 +1144,60 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
     wp[(warp * kW + 3 * TPL + c) * 32 + lane] = -ck[c];
   }
   __syncthreads();
-  EpiShared<float> &sm =
-      *reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * kW * 32 * 4);
+  EpiShared<float> *sms =
+      reinterpret_cast<EpiShared<float> *>(dyn + static_cast<size_t>(NW) * kW * 32 * 4);
+  if constexpr (kGrp > 0) {
+    // each part's lead warp combines the part's sums in kmc_step_f32's order;
+    // the groups then run steps iii-vii side by side
+    EpiShared<float> &sm = sms[gk];
+    float hi[3], lo[3];
+    if (lead) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float s = 0.f, e = 0.f;
+        for (int w = 0; w < NW; ++w) {
+          neumaier_add(s, e, wp[(w * kW + 3 * gk + c) * 32 + lane]);
+          e += wp[(w * kW + 3 * TPL + 3 * gk + c) * 32 + lane];
+        }
+        hi[c] = s;
+        lo[c] = e;
+      }
+      if (it.nsplit > 1) {
+        float *part = a.partial + (static_cast<size_t>(blockIdx.x) * TPL + gk) * kPartF32;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          __stcg(part + c * 32 + lane, hi[c]);
+          __stcg(part + (3 + c) * 32 + lane, lo[c]);
+        }
+      }
+    }
+    if (it.nsplit > 1) {
+      if (!arrive_last(&a.arrivals[it.gid], it.nsplit, &s_last)) return;
+      if (lead) {
+        const float *base =
+            a.partial + (static_cast<size_t>(blockIdx.x - it.split) * TPL + gk) * kPartF32;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float s = 0.f, e = 0.f;
+          for (int q = 0; q < it.nsplit; ++q) {
+            neumaier_add(s, e, __ldcg(base + q * TPL * kPartF32 + c * 32 + lane));
+            e += __ldcg(base + q * TPL * kPartF32 + (3 + c) * 32 + lane);
+          }
+          hi[c] = s;
+          lo[c] = e;
+        }
+      }
+      if (threadIdx.x == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
+    }
+    if (lead) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sm.h[c][lane] = hi[c] + lo[c];
+    }
+    if (h0.nt > 0) block_update<float4, true, false, kGrp>(a, L, h0, step, rec, tin, sm, tab, gk);
+    grid_launch_dependents();
+    return;
+  }
+  EpiShared<float> &sm = sms[0];
   float hi[3 * TPL], lo[3 * TPL];
   if (warp == 0) {
 #pragma unroll

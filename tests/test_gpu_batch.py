@@ -140,9 +140,11 @@ def test_two_and_three_targets_per_lane_give_the_same_bits():
     """The multi-target kernels (64- or 96-target groups, two or three per lane)
     form every target's sums with the same operations in the same order as the
     one-target kernel and run the same update: identical outputs at the same
-    shape, including ragged last groups and split source ranges."""
+    shape, including ragged last groups and split source ranges. With 8 or 16
+    warps and two targets per lane the two parts update side by side, each on
+    half of the warps."""
     lyss = [inputs.make_lysosome(n, 12e-9, 0.05, seed=70 + q) for q, n in enumerate([700, 97, 33, 1])]
-    for shape in [(4, 64, 0), (4, 128, 256), (8, 64, 128)]:
+    for shape in [(4, 64, 0), (4, 128, 256), (8, 64, 128), (8, 128, 0), (16, 64, 256)]:
         out = []
         for tpl in (1, 2, 3):
             ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))

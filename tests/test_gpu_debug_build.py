@@ -33,13 +33,14 @@ checked = 0
 for prec, tile, sizes in ((kmc.KMC_FP32_MIXED, 64, (1, 2, 3, 33, 127, 128, 129)),
                           (kmc.KMC_FP64_PLAIN, 64, (1, 2, 3, 33, 63, 64, 65))):
     lyss = [inputs.make_lysosome(n, 12e-9, 0.05 if n > 3 else 0.01, seed=40 + n) for n in sizes]
-    tpls = (1, 2) if prec == kmc.KMC_FP32_MIXED else (1,)
-    for tpl in tpls:
+    # (targets per lane, warps): with 8 warps the two parts update side by side
+    tpls = ((1, 4), (2, 4), (2, 8)) if prec == kmc.KMC_FP32_MIXED else ((1, 4),)
+    for tpl, warps in tpls:
         for chunk in (0, 128):
             ctx = kmc.kmc_create(lyss, prec, center=np.zeros(3))
             if prec == kmc.KMC_FP32_MIXED:
                 kmc.kmc_targets_per_lane(ctx, tpl)
-            kmc.kmc_tuning(ctx, 4, tile, chunk)
+            kmc.kmc_tuning(ctx, warps, tile, chunk)
             rng = np.random.default_rng(tpl * 10 + chunk)
             m = np.concatenate([oracle.initial_moments(l.axis) + 0.3 * rng.normal(size=(l.n, 3))
                                 for l in lyss])
