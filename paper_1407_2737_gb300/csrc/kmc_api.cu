@@ -750,8 +750,9 @@ bool shape_ok(const kmc_ctx *c, const Shape &s) {
 
 // Captures `steps` step launches of shape sh as a graph: the chains of the
 // current items as parallel branches (fork on c->stream, join back onto it),
-// step k of a run when `period` (k_local = k, then the period advance), else
-// `steps` repeats of one unrecorded step.
+// the field at phase 2 pi k / steps in launch k. With `period` launch k is
+// step k of a run (k_local = k, then the period advance), else a repeat of one
+// unrecorded step.
 kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int steps, bool period,
                          cudaGraphExec_t *out) {
   Phase phase("kmc_capture");
@@ -782,10 +783,8 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
       b.n_upd = c->sym_cut_upd[q + 1] - v0;
       b.gc = sh.warps * sh.sym;
       for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
-        if (period) {
-          b.k_local = k;
-          b.cos_k = std::cos(2.0 * kPi * k / steps);
-        }
+        if (period) b.k_local = k;
+        b.cos_k = std::cos(2.0 * kPi * k / steps);
         ce = kmc::launch_sym(b, sh.warps, sh.sym, b.n_items, st, true, sh.supd);
       }
       continue;
@@ -800,10 +799,8 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
       b.partial = c->d_partial +
                   static_cast<size_t>(u0) * (c->fp32 ? 6 : 12) * kmc::kTargets * sh.tpl * sh.rpl;
     for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
-      if (period) {
-        b.k_local = k;
-        b.cos_k = std::cos(2.0 * kPi * k / steps);
-      }
+      if (period) b.k_local = k;
+      b.cos_k = std::cos(2.0 * kPi * k / steps);
       ce = kmc::launch_step(c->fp32, sh.warps, sh.tile, b, c->chain_cut[q + 1] - u0, st, true,
                             sh.tpl, sh.rpl, sh.cl);
     }
@@ -880,8 +877,12 @@ float time_shape(kmc_ctx *c, const Shape &s) {
     if (gx) cudaGraphExecDestroy(gx);
     return -1.f;
   }
+  int k_one = 0;
   auto one = [&]() {
-    return gx ? cudaGraphLaunch(gx, c->stream) : launch_one_step(c, a, s, c->stream, true);
+    if (gx) return cudaGraphLaunch(gx, c->stream);
+    StepArgs b = a;  // the field sweeps its cycle in 8 launches
+    b.cos_k = std::cos(2.0 * kPi * (k_one++ % 8) / 8);
+    return launch_one_step(c, b, s, c->stream, true);
   };
   float ms = -1.f;
   bool ok = true;
@@ -921,7 +922,10 @@ kmc_status autotune(kmc_ctx *c) {
   RunState rs{c->step_global, -1, 0};
   KMC_CUDA(cudaMemcpyAsync(c->d_rs, &rs, sizeof(rs), cudaMemcpyHostToDevice, c->stream));
   std::vector<LysDev> keep = c->h_lys;
+  // the run's field amplitude and rate when known (kmc_run sets them first),
+  // else a typical pair
   for (auto &L : c->h_lys) {
+    if (L.bmax > 0.0) continue;
     L.bmax = 0.01;
     L.lognu0t = std::log(5e-8 / 1e-10);
   }
@@ -1604,7 +1608,6 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
     return fail(KMC_EINVAL, "need 0 <= discard_periods <= periods");
   const long long n_rec = static_cast<long long>(S) * (periods - discard);
   if (n_rec > (1ll << 28)) return fail(KMC_EINVAL, "too many recorded steps");
-  KMC_TRY(ensure_shape(c));
   const double t_step = 1.0 / (f * S);
   c->Hmax.assign(c->n_lys, 0.0);
   for (int l = 0; l < c->n_lys; ++l) {
@@ -1612,6 +1615,7 @@ kmc_status kmc_run(kmc_ctx *c, const double *mu0Hmax, int32_t n_amp, double f, i
     c->h_lys[l].bmax = c->Hmax[l] / (kMu0 * c->Ms[l]);
     c->h_lys[l].lognu0t = std::log(t_step / c->tau0[l]);
   }
+  KMC_TRY(ensure_shape(c));  // the tuner times the shapes at this amplitude and rate
   KMC_TRY(upload_lys(c));
   const size_t need = static_cast<size_t>(c->n_lys) * static_cast<size_t>(std::max(n_rec, 1ll));
   if (need > c->loop_cap) {

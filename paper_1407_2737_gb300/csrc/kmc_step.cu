@@ -114,8 +114,9 @@ struct EpiShared {
 };
 
 
-// Scan of step iv: lane = target, warp w = the w-th of nw contiguous segments
-// of the 200 nodes (nw >= 4, so a segment holds at most 50). A first pass
+// Scan of step iv: lane = target, the 200 nodes cut into max(nw, 4) contiguous
+// segments (so that a segment holds at most 50), warp w taking segments w,
+// w + nw, ... (MULTI, for nw < 4), else segment w alone (nw >= 4). A first pass
 // evaluates de/dth at the segment's nodes and at the node after it (cyclically:
 // the cell after node 199 ends at node 0) and keeps only their signs, as a bit
 // mask, so that its loads and arithmetic pipeline freely; a second pass visits
@@ -123,45 +124,54 @@ struct EpiShared {
 // its target (shared-memory counter). All lanes of a warp read the same node,
 // a shared-memory broadcast.
 constexpr int kMaxSeg = 50;
-template <typename R>
+template <typename R, bool MULTI = false>
 __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<R> &tab,
                                              int warp, int nw, int lane, int nt) {
-  const int seg = (kGrid + nw - 1) / nw;
-  const int j0 = warp * seg, len = min(kGrid, j0 + seg) - j0;
-  if (lane >= nt || len <= 0) return;
+  if (lane >= nt) return;
   const R k2 = sm.k2[lane], bc = sm.bc[lane], bs = sm.bs[lane];
   auto d1 = [&](int j) {
     const auto sc = tab.sc[j];
     return profile_d1(k2, bc, bs, sc.x, sc.y);
   };
-  // bit q: de/dth < 0 at node j0 + q (q = len: the next node). Batches of 13
-  // independent evaluations keep about 40 registers in flight: a fully
-  // unrolled pass would hold 51 table entries and, inside this kernel's
-  // register budget, the compiler serialises it (measured 4x slower).
-  constexpr int kBatch = 13;
-  unsigned long long neg = 0;
+  auto scan = [&](int j0, int len) {
+    // bit q: de/dth < 0 at node j0 + q (q = len: the next node). Batches of 13
+    // independent evaluations keep about 40 registers in flight: a fully
+    // unrolled pass would hold 51 table entries and, inside this kernel's
+    // register budget, the compiler serialises it (measured 4x slower).
+    constexpr int kBatch = 13;
+    unsigned long long neg = 0;
 #pragma unroll 1
-  for (int q0 = 0; q0 <= len; q0 += kBatch) {
-    unsigned bits = 0;
+    for (int q0 = 0; q0 <= len; q0 += kBatch) {
+      unsigned bits = 0;
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      int j = j0 + q0 + u;
-      j = j < kGrid ? j : j - kGrid;  // q0 + u <= kMaxSeg + kBatch - 1: one wrap at most
-      bits |= static_cast<unsigned>(d1(j) < R(0)) << u;
+      for (int u = 0; u < kBatch; ++u) {
+        int j = j0 + q0 + u;
+        j = j < kGrid ? j : j - kGrid;  // q0 + u <= kMaxSeg + kBatch - 1: one wrap at most
+        bits |= static_cast<unsigned>(d1(j) < R(0)) << u;
+      }
+      neg |= static_cast<unsigned long long>(bits) << q0;
     }
-    neg |= static_cast<unsigned long long>(bits) << q0;
-  }
-  unsigned long long chg = (neg ^ (neg >> 1)) & ((1ull << len) - 1);
-  while (chg) {
-    const int q = __ffsll(static_cast<long long>(chg)) - 1;
-    chg &= chg - 1;
-    const int j = j0 + q;
-    const int slot = atomicAdd(&sm.cnt[lane], 1);
-    if (slot < 4) {
-      sm.ju[lane][slot] = j;
-      sm.du[lane][slot] = d1(j);
-      sm.duh[lane][slot] = d1(j + 1 < kGrid ? j + 1 : 0);
+    unsigned long long chg = (neg ^ (neg >> 1)) & ((1ull << len) - 1);
+    while (chg) {
+      const int q = __ffsll(static_cast<long long>(chg)) - 1;
+      chg &= chg - 1;
+      const int j = j0 + q;
+      const int slot = atomicAdd(&sm.cnt[lane], 1);
+      if (slot < 4) {
+        sm.ju[lane][slot] = j;
+        sm.du[lane][slot] = d1(j);
+        sm.duh[lane][slot] = d1(j + 1 < kGrid ? j + 1 : 0);
+      }
     }
+  };
+  if constexpr (MULTI) {
+    constexpr int nseg = (kGrid + kMaxSeg - 1) / kMaxSeg, seg = (kGrid + nseg - 1) / nseg;
+#pragma unroll 1
+    for (int sg = warp; sg < nseg; sg += nw) scan(sg * seg, min(kGrid, sg * seg + seg) - sg * seg);
+  } else {
+    const int seg = (kGrid + nw - 1) / nw;
+    const int j0 = warp * seg, len = min(kGrid, j0 + seg) - j0;
+    if (len > 0) scan(j0, len);
   }
 }
 
@@ -572,7 +582,7 @@ __device__ __forceinline__ void block_update(
   } else {
     Sync::sync(gid);
     // iv) scan: lanes over targets, warps over segments of the grid
-    segment_scan<R>(sm, tab, warp, nw, lane, nt);
+    segment_scan<R, (GROUP > 0 && GROUP < 4)>(sm, tab, warp, nw, lane, nt);
     Sync::sync(gid);
     if constexpr (MIXED) {
       noisy = warp == 0 && lane < nt && (sm.cnt[lane] > 4 || a.force_rescan);
@@ -1029,10 +1039,10 @@ __device__ __forceinline__ AccF32N<3> pair_tile_f32_3t(const ulonglong2 *__restr
 }
 
 // Warps that update each 32-target part of the multi-target kernel when its
-// parts update side by side (four or more warps per part, as the scan needs),
-// else 0: the parts update in turn on the whole block.
+// parts update side by side (two or more warps per part), else 0: the parts
+// update in turn on the whole block.
 constexpr int tn_group(int warps, int tpl) {
-  return (warps % tpl == 0 && warps / tpl >= 4) ? warps / tpl : 0;
+  return (warps % tpl == 0 && warps / tpl >= 2) ? warps / tpl : 0;
 }
 
 // Dynamic shared memory of the multi-target kernel after its pair loop: the
