@@ -665,7 +665,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison")
     ap.add_argument("--shape", default="",
-                    help="pin the FP32 launch shape as warps,tile,chunk[,targets per lane] "
+                    help="pin the FP32 launch shape as warps,tile,chunk[,targets per lane"
+                         "[,symmetric update kernel: 1 = a warp per item, 2 = a block]] "
                          "(default: autotuned)")
     ap.add_argument("--shape64", default="",
                     help="pin the FP64-plain launch shape as warps,tile,chunk (default: autotuned)")
@@ -725,8 +726,10 @@ def main():
     kmc.kmc_set_stream(ctx, stream.cuda_stream)
     if args.shape:
         sh = [int(x) for x in args.shape.split(",")]
-        if len(sh) == 4:
+        if len(sh) >= 4:
             kmc.kmc_targets_per_lane(ctx, sh[3])
+        if len(sh) >= 5:
+            kmc.kmc_sym_update(ctx, sh[4])
         kmc.kmc_tuning(ctx, *sh[:3])
     for _ in range(args.warmup):
         kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], run["periods"], run["discard"],

@@ -986,8 +986,9 @@ __global__ void __launch_bounds__(NW * 32) kmc_persist_f32(const StepArgs a, int
 // are formed by the same packed operations over the same records as in
 // kmc_step_f32, and the warps and source parts are combined in the same order,
 // so the fields, and hence the whole step, are the same bits. The 32-target
-// parts of the group then run steps iii-vii one after the other with the same
-// update code.
+// parts of the group then run steps iii-vii with the same update code: side
+// by side, each on its own group of warps, when the warps divide evenly among
+// the parts (two or more each), else one after the other on the whole block.
 template <int TPL>
 struct AccF32N {
   AccF32 t[TPL];  // the lane's targets, in order
