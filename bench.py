@@ -76,15 +76,15 @@ CONFIGS = {
 }
 FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA = 2
 # DRAM bytes (read + write) of one kMC step in steady state, by (workload,
-# warps, tile, chunk, targets per lane, replicas per lane[, "sym"]), from ncu
+# warps, tile, chunk, targets per lane, replicas per lane[, "sym"[, "block"]]), from ncu
 # captures of the committed kernels with --cache-control none (the state stays
 # in L2 between launches, as in the bench). c1: 8 chains, one launch each: 8 x
 # the mean over 16 launches. In the symmetric form a kMC step is one field and
 # one update launch per chain, which write and read back the partial sums:
 # c4 (one chain) the sum of the two launches' means over 2 each, c3 (8 chains)
 # 8 x the sum of the means over 16 launches of each kernel.
-STEP_DRAM_BYTES = {("c1", 4, 256, 1024, 1, 1): 384.0,
-                   ("c4", 4, 32, 1024, 4, 1, "sym"): 16.2e6,
+STEP_DRAM_BYTES = {("c1", 4, 256, 512, 2, 1): 256.0,
+                   ("c4", 4, 32, 1024, 4, 1, "sym", "block"): 17.47e6,
                    ("c3", 4, 32, 512, 4, 1, "sym"): 17.52e6}
 
 
