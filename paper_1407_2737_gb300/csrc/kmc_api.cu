@@ -343,7 +343,7 @@ std::vector<Item> build_items(const std::vector<int> &np, bool fp32, int chunk,
     const Group &gr = groups[g];
     const int S = parts[g];
     for (int s = 0; s < S; ++s) {
-      Item it;
+      Item it{};
       it.l = gr.l;
       it.t0 = gr.t0;
       it.nt = gr.nt;
@@ -541,6 +541,10 @@ kmc_status set_items(kmc_ctx *c, const Shape &sh) {
     for (size_t u = 0; u < plan.items.size(); ++u)
       if (plan.items[u].nsplit != 2 || plan.items[u].split != static_cast<int>(u & 1))
         return fail(KMC_EINVAL, "the cluster split needs exactly two source parts per group");
+  }
+  for (Item &it : plan.items) {
+    it.off = c->h_lys[it.l].off;
+    it.roff = c->h_lys[it.l].roff;
   }
   const std::vector<Item> &items = plan.items;
   const int groups = plan.groups;

@@ -14,8 +14,9 @@ namespace kmc {
 // Grid of step iv: theta_j = 2 pi (j + 1/2) / 200 and (sin, cos) of it,
 // written once per device by init_device (kmc_step.cu, the only translation
 // unit that includes this header).
-__device__ float g_theta_f[kGrid];
-__device__ float2 g_sc_f[kGrid];
+// (16-byte aligned: the FP32 step kernels copy them to shared memory in bulk)
+__device__ __align__(16) float g_theta_f[kGrid];
+__device__ __align__(16) float2 g_sc_f[kGrid];
 __device__ double g_theta_d[kGrid];
 __device__ double2 g_sc_d[kGrid];
 
@@ -112,6 +113,8 @@ struct GridTables {
     }
   }
 };
+static_assert(sizeof(GridTables<float>::sc) % 16 == 0 && sizeof(GridTables<float>::th) % 16 == 0,
+              "the FP32 tables are copied in bulk");
 
 // de/dth of Eq. 2 at (sin, cos) = (s, c): s (2k c + b cos phi) - b sin phi c,
 // with its roundings spelled out so that every evaluation at a node gives the

@@ -757,6 +757,7 @@ __device__ __forceinline__ bool item_in_bounds(const StepArgs &a, int tpl, bool 
   const Item it = a.items[blockIdx.x];
   if (!KMC_DCHECK(it.l >= 0 && it.l < a.n_lys, a.err, kSiteLys)) return false;
   const LysDev L = a.lys[it.l];
+  if (!KMC_DCHECK(it.off == L.off && it.roff == L.roff, a.err, kSiteLys)) return false;
   if (!KMC_DCHECK(it.t0 >= 0 && it.nt >= 1 && it.nt <= kTargets * tpl && it.t0 + it.nt <= L.n,
                   a.err, kSiteTargets))
     return false;
@@ -794,7 +795,7 @@ __device__ __forceinline__ bool tile_in_bounds(const StepArgs &a, const Item &it
 // another item.
 template <int NW, bool CL, bool PERSIST>
 __device__ __forceinline__ void step_f32_item(const StepArgs &a, int tile, unsigned char *smem,
-                                              int &s_last, const GridTables<float> &tab) {
+                                              int &s_last, GridTables<float> &tab) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *dyn = smem + 16;
   if (!item_in_bounds(a, 1, true) ||
@@ -808,16 +809,21 @@ __device__ __forceinline__ void step_f32_item(const StepArgs &a, int tile, unsig
     return;
   }
   const Item it = a.items[blockIdx.x];
-  const LysDev L = a.lys[it.l];
+  const LysDev L = a.lys[it.l];  // for the update; positions and sources use it.off, it.roff
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // items, lysosome constants and positions do not change during a run
-  const float4 pi = static_cast<const float4 *>(a.pos)[L.off + it.t0 + min(lane, it.nt - 1)];
-  if constexpr (!PERSIST) grid_dependency_wait();
+  const float4 pi = static_cast<const float4 *>(a.pos)[it.off + it.t0 + min(lane, it.nt - 1)];
+  // The run state changes only between field periods (the period advance, or
+  // a copy before a run), never across a programmatic-launch edge: a period's
+  // step launches follow one another inside its graph, and the graph starts
+  // after the previous one, advance included, has completed. So it is read
+  // before the wait, and the first tile's copy follows the wait at once.
   const long long step = a.rs->step_base + a.k_local;
   const int per = a.rs->period;
+  if constexpr (!PERSIST) grid_dependency_wait();
   const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
   const int par = static_cast<int>(step & 1);
-  const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
+  const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + it.roff;
 
   TargetIn<float4> tin;
   if (warp == 0) tin = load_target<float4>(a, L, it, step, lane);
@@ -831,13 +837,18 @@ __device__ __forceinline__ void step_f32_item(const StepArgs &a, int tile, unsig
     const int b = t & 1;
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
-    if (!tile_in_bounds(a, it, r0, cnt, tile)) {
-      mbar_expect_tx(&bar[b], 0);  // no copy: the phase completes, the error is set
-      return;
+    // tile 0 also brings the grid tables (the persistent kernel loads them
+    // once), so that no thread waits on them
+    const uint32_t tab_bytes =
+        (!PERSIST && t == 0) ? sizeof(GridTables<float>::sc) + sizeof(GridTables<float>::th) : 0;
+    const bool ok = tile_in_bounds(a, it, r0, cnt, tile);  // else no tile: the error is set
+    const uint32_t bytes = ok ? static_cast<uint32_t>(cnt) * sizeof(SrcPair) : 0;
+    mbar_expect_tx(&bar[b], bytes + tab_bytes);
+    if (tab_bytes) {
+      bulk_g2s(tab.sc, g_sc_f, sizeof(tab.sc), &bar[b]);
+      bulk_g2s(tab.th, g_theta_f, sizeof(tab.th), &bar[b]);
     }
-    const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
-    mbar_expect_tx(&bar[b], bytes);
-    bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
+    if (ok) bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
   };
   auto body = [&](int b, int t) {
     const int r0 = it.j0 + t * tile;
@@ -943,8 +954,7 @@ template <int NW, bool CL = false>
 __global__ void __launch_bounds__(NW * 32) kmc_step_f32(const StepArgs a, int tile) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_last;
-  __shared__ GridTables<float> tab;
-  tab.load();
+  __shared__ __align__(16) GridTables<float> tab;  // copied in bulk with the first tile
   step_f32_item<NW, CL, false>(a, tile, smem, s_last, tab);
   // the next step's blocks may now be scheduled; triggering earlier lets them
   // take the slots of early-finishing blocks and unbalances the next step
@@ -1063,12 +1073,12 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *dyn = smem + 16;
   __shared__ int s_last;
-  __shared__ GridTables<float> tab;
+  // the update's grid tables: two bulk copies on the first tile's barrier
+  __shared__ __align__(16) GridTables<float> tab;
   __shared__ float s_hr[TPL - 1][3][kTargets];  // later parts' fields while the first updates
-  tab.load();
   if (!item_in_bounds(a, TPL, true)) return;
   const Item it = a.items[blockIdx.x];
-  const LysDev L = a.lys[it.l];
+  const LysDev L = a.lys[it.l];  // for the update; positions and sources use it.off, it.roff
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int ntk[TPL];  // targets of each 32-target part
 #pragma unroll
@@ -1076,22 +1086,27 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
   const float4 *pos = static_cast<const float4 *>(a.pos);
   f2 X[TPL], Y[TPL], Z[TPL];
   {
-    const float4 p0 = pos[L.off + it.t0 + min(lane, ntk[0] - 1)];
+    const float4 p0 = pos[it.off + it.t0 + min(lane, ntk[0] - 1)];
 #pragma unroll
     for (int k = 0; k < TPL; ++k) {
       const float4 p =
-          ntk[k] > 0 ? pos[L.off + it.t0 + k * kTargets + min(lane, ntk[k] - 1)] : p0;
+          ntk[k] > 0 ? pos[it.off + it.t0 + k * kTargets + min(lane, ntk[k] - 1)] : p0;
       X[k] = pk(p.x, p.x);
       Y[k] = pk(p.y, p.y);
       Z[k] = pk(p.z, p.z);
     }
   }
-  grid_dependency_wait();
+  // The run state changes only between field periods (the period advance, or
+  // a copy before a run), never across a programmatic-launch edge: a period's
+  // step launches follow one another inside its graph, and the graph starts
+  // after the previous one, advance included, has completed. So it is read
+  // before the wait, and the first tile's copy follows the wait at once.
   const long long step = a.rs->step_base + a.k_local;
   const int per = a.rs->period;
+  grid_dependency_wait();
   const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
   const int par = static_cast<int>(step & 1);
-  const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + L.roff;
+  const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]) + it.roff;
 
   // the part whose update this warp runs, and whether it leads it (holds the
   // part's inputs and combines its sums)
@@ -1114,13 +1129,16 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
     const int b = t & 1;
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
-    if (!tile_in_bounds(a, it, r0, cnt, tile)) {
-      mbar_expect_tx(&bar[b], 0);  // no copy: the phase completes, the error is set
-      return;
+    // tile 0 also brings the grid tables, so that no thread waits on them
+    const uint32_t tab_bytes = t == 0 ? sizeof(tab.sc) + sizeof(tab.th) : 0;
+    const bool ok = tile_in_bounds(a, it, r0, cnt, tile);  // else no tile: the error is set
+    const uint32_t bytes = ok ? static_cast<uint32_t>(cnt) * sizeof(SrcPair) : 0;
+    mbar_expect_tx(&bar[b], bytes + tab_bytes);
+    if (tab_bytes) {
+      bulk_g2s(tab.sc, g_sc_f, sizeof(tab.sc), &bar[b]);
+      bulk_g2s(tab.th, g_theta_f, sizeof(tab.th), &bar[b]);
     }
-    const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
-    mbar_expect_tx(&bar[b], bytes);
-    bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
+    if (ok) bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
   };
   auto body = [&](int b, int t) {
     const int r0 = it.j0 + t * tile;

@@ -88,6 +88,8 @@ struct Item {
   int32_t j0, j1;  // source records of this item (relative to the lysosome)
   int32_t split;   // index of this item within its group
   int32_t nsplit;  // items in the group
+  int32_t off;     // the lysosome's first NP and first source record (its
+  int32_t roff;    // LysDev off and roff), so that one load reaches both
 };
 
 // Symmetric pair form (FP32-mixed, kmc_field_sym / kmc_update_sym). A
