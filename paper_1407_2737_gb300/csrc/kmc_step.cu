@@ -747,6 +747,40 @@ constexpr size_t epi_bytes(int warps) {
 // The buffer is sized for the FP64 kernel's 6 doubles per target.
 constexpr int kPartF32 = 6 * kTargets;
 
+// The sums of a split target group for one lane's target: part by part in
+// split order, per component the Neumaier sum of the parts' sums and then
+// their compensations added. Part q's six floats (three sums, three
+// compensations, each 32 lanes wide) start at base + q stride. The loads of
+// four parts are issued before any of them is added, so that one L2 round
+// trip, not one per part, precedes every four.
+__device__ __forceinline__ void combine_split(const float *base, size_t stride, int nsplit,
+                                              int lane, float *hi, float *lo) {
+  float s[3] = {0.f, 0.f, 0.f}, e[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+  for (int q0 = 0; q0 < nsplit; q0 += 4) {
+    float v[4][6];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        v[u][k] = q0 + u < nsplit ? __ldcg(base + (q0 + u) * stride + k * 32 + lane) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (q0 + u >= nsplit) break;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        neumaier_add(s[c], e[c], v[u][c]);
+        e[c] += v[u][3 + c];
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    hi[c] = s[c];
+    lo[c] = e[c];
+  }
+}
+
 // KMC_DEBUG builds: the block's work item lies inside the launch, its
 // lysosome and that lysosome's target and source ranges (records of NPs:
 // pairs in FP32, single NPs in FP64), and its part index is consistent; a
@@ -928,17 +962,8 @@ __device__ __forceinline__ void step_f32_item(const StepArgs &a, int tile, unsig
     // another item of the group finishes the step
     if (!arrive_last(&a.arrivals[it.gid], it.nsplit, &s_last)) return;
     if (warp == 0) {
-      const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * kPartF32;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float s = 0.f, e = 0.f;
-        for (int q = 0; q < it.nsplit; ++q) {
-          neumaier_add(s, e, __ldcg(base + q * kPartF32 + c * 32 + lane));
-          e += __ldcg(base + q * kPartF32 + (3 + c) * 32 + lane);
-        }
-        hi[c] = s;
-        lo[c] = e;
-      }
+      combine_split(a.partial + static_cast<size_t>(blockIdx.x - it.split) * kPartF32, kPartF32,
+                    it.nsplit, lane, hi, lo);
       if (lane == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
     }
   }
@@ -1203,18 +1228,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
     if (it.nsplit > 1) {
       if (!arrive_last(&a.arrivals[it.gid], it.nsplit, &s_last)) return;
       if (lead) {
-        const float *base =
-            a.partial + (static_cast<size_t>(blockIdx.x - it.split) * TPL + gk) * kPartF32;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float s = 0.f, e = 0.f;
-          for (int q = 0; q < it.nsplit; ++q) {
-            neumaier_add(s, e, __ldcg(base + q * TPL * kPartF32 + c * 32 + lane));
-            e += __ldcg(base + q * TPL * kPartF32 + (3 + c) * 32 + lane);
-          }
-          hi[c] = s;
-          lo[c] = e;
-        }
+        combine_split(a.partial + (static_cast<size_t>(blockIdx.x - it.split) * TPL + gk) * kPartF32,
+                      TPL * kPartF32, it.nsplit, lane, hi, lo);
       }
       if (threadIdx.x == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
     }
@@ -1257,16 +1272,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
     if (warp == 0) {
       const float *base = a.partial + static_cast<size_t>(blockIdx.x - it.split) * TPL * kPartF32;
 #pragma unroll
-      for (int c = 0; c < 3 * TPL; ++c) {
-        const int o = (c / 3) * kPartF32 + (c % 3) * 32 + lane;
-        float s = 0.f, e = 0.f;
-        for (int q = 0; q < it.nsplit; ++q) {
-          neumaier_add(s, e, __ldcg(base + q * TPL * kPartF32 + o));
-          e += __ldcg(base + q * TPL * kPartF32 + o + 3 * 32);
-        }
-        hi[c] = s;
-        lo[c] = e;
-      }
+      for (int k = 0; k < TPL; ++k)
+        combine_split(base + k * kPartF32, TPL * kPartF32, it.nsplit, lane, hi + 3 * k, lo + 3 * k);
       if (lane == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
     }
   }
@@ -1472,18 +1479,8 @@ __global__ void __launch_bounds__(RPL * WPR * 32, (RPL == 2 && WPR == 4) ? 2 : 0
     // another item of the group finishes the step
     if (!arrive_last(&a.arrivals[it.gid], it.nsplit, &s_last)) return;
     if (lead) {
-      const float *base =
-          a.partial + (static_cast<size_t>(blockIdx.x - it.split) * RPL + rk) * kPartF32;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float s = 0.f, e = 0.f;
-        for (int q = 0; q < it.nsplit; ++q) {
-          neumaier_add(s, e, __ldcg(base + q * RPL * kPartF32 + c * 32 + lane));
-          e += __ldcg(base + q * RPL * kPartF32 + (3 + c) * 32 + lane);
-        }
-        hi[c] = s;
-        lo[c] = e;
-      }
+      combine_split(a.partial + (static_cast<size_t>(blockIdx.x - it.split) * RPL + rk) * kPartF32,
+                    RPL * kPartF32, it.nsplit, lane, hi, lo);
     }
     __syncthreads();
     if (threadIdx.x == 0) a.arrivals[it.gid] = 0;  // ready for the next launch
