@@ -133,24 +133,23 @@ __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<
     const auto sc = tab.sc[j];
     return profile_d1(k2, bc, bs, sc.x, sc.y);
   };
-  auto scan = [&](int j0, int len) {
-    // bit q: de/dth < 0 at node j0 + q (q = len: the next node). Batches of 13
-    // independent evaluations keep about 40 registers in flight: a fully
-    // unrolled pass would hold 51 table entries and, inside this kernel's
-    // register budget, the compiler serialises it (measured 4x slower).
-    constexpr int kBatch = 13;
-    unsigned long long neg = 0;
-#pragma unroll 1
-    for (int q0 = 0; q0 <= len; q0 += kBatch) {
-      unsigned bits = 0;
+  // bit q of the mask: de/dth < 0 at node j0 + q (q = len: the next node).
+  // Batches of 13 independent evaluations keep about 40 registers in flight: a
+  // fully unrolled pass would hold 51 table entries and, inside the step
+  // kernel's register budget, the compiler serialises it (measured 4x slower).
+  constexpr int kBatch = 13;
+  auto batch = [&](int j0, int q0) {
+    unsigned bits = 0;
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        int j = j0 + q0 + u;
-        j = j < kGrid ? j : j - kGrid;  // q0 + u <= kMaxSeg + kBatch - 1: one wrap at most
-        bits |= static_cast<unsigned>(d1(j) < R(0)) << u;
-      }
-      neg |= static_cast<unsigned long long>(bits) << q0;
+    for (int u = 0; u < kBatch; ++u) {
+      int j = j0 + q0 + u;
+      j = j < kGrid ? j : j - kGrid;  // q0 + u <= kMaxSeg + kBatch - 1: one wrap at most
+      bits |= static_cast<unsigned>(d1(j) < R(0)) << u;
     }
+    return static_cast<unsigned long long>(bits) << q0;
+  };
+  // the sign changes of a segment's mask: each in a free slot of the target
+  auto record = [&](int j0, int len, unsigned long long neg) {
     unsigned long long chg = (neg ^ (neg >> 1)) & ((1ull << len) - 1);
     while (chg) {
       const int q = __ffsll(static_cast<long long>(chg)) - 1;
@@ -164,10 +163,31 @@ __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<
       }
     }
   };
+  auto scan = [&](int j0, int len) {
+    unsigned long long neg = 0;
+#pragma unroll 1
+    for (int q0 = 0; q0 <= len; q0 += kBatch) neg |= batch(j0, q0);
+    record(j0, len, neg);
+  };
   if constexpr (MULTI) {
     constexpr int nseg = (kGrid + kMaxSeg - 1) / kMaxSeg, seg = (kGrid + nseg - 1) / nseg;
+    static_assert(nseg * seg == kGrid && nseg % 2 == 0, "whole segments, in pairs");
+    if (nw == 2) {
+      // two segments per warp, w and w + 2, their batches interleaved (twice
+      // the independent evaluations in flight)
+      const int ja = warp * seg, jb = (warp + 2) * seg;
+      unsigned long long na = 0, nb = 0;
 #pragma unroll 1
-    for (int sg = warp; sg < nseg; sg += nw) scan(sg * seg, min(kGrid, sg * seg + seg) - sg * seg);
+      for (int q0 = 0; q0 <= seg; q0 += kBatch) {
+        na |= batch(ja, q0);
+        nb |= batch(jb, q0);
+      }
+      record(ja, seg, na);
+      record(jb, seg, nb);
+    } else {
+#pragma unroll 1
+      for (int sg = warp; sg < nseg; sg += nw) scan(sg * seg, seg);
+    }
   } else {
     const int seg = (kGrid + nw - 1) / nw;
     const int j0 = warp * seg, len = min(kGrid, j0 + seg) - j0;
