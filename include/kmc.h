@@ -181,7 +181,7 @@ kmc_status kmc_info(const kmc_ctx *ctx, int64_t *n_total, int32_t *n_lys,
 
 /* Launch shape of the fused step kernel. warps: warps per block, each taking
  * every warps-th source record of a tile (4, 8 or 16; with replicas per lane
- * pinned, warps = replicas and tile <= 128). tile: source records per
+ * pinned, warps = 1, 2 or 4 times the replicas and tile <= 128). tile: source records per
  * shared-memory tile (a power of two, 32..1024; an FP32 record holds two NPs,
  * an FP64 record one). chunk: sources per work item when a lysosome's sources
  * are split over several blocks (0 = never split; else a multiple of 64).
@@ -207,17 +207,17 @@ kmc_status kmc_targets_per_lane(kmc_ctx *ctx, int32_t tpl, int32_t *tpl_out);
  * of k identical consecutive ones (the same NPs, axes, volumes, material,
  * temperature, attempt time, density and frame origin; only the random
  * streams, the amplitudes and hence the moments differ: seeds of one sample),
- * a block of k warps (or 4 k) can take 32 targets of all k lysosomes of a set
+ * a block of k warps (or 2 k, or 4 k) can take 32 targets of all k lysosomes of a set
  * at once: each staged source record's geometry (separation, distance, its
  * powers) is formed once and serves all k, which add only their own moments'
  * terms. Every lysosome's field, and its whole step, are the bits it gets with
  * one target per lane and as many warps at the same tile and chunk; each warp
- * (or group of four warps) then runs one lysosome's steps iii-vii. rpl: 0 lets the autotuner choose (the
+ * (or group of two or four warps) then runs one lysosome's steps iii-vii. rpl: 0 lets the autotuner choose (the
  * default; it considers k = 2 and 4 where the sets exist), 1 turns replicas
  * off, 2 or 4 pins them (KMC_EINVAL on FP64 contexts, with two or three
  * targets per lane pinned, or unless n_lys is a multiple of rpl and every set
- * of rpl consecutive lysosomes is identical). A pinned value takes warps = rpl
- * or 4 rpl in kmc_tuning and drops a shape of another kind. The value in use (0 before
+ * of rpl consecutive lysosomes is identical). A pinned value takes warps = rpl,
+ * 2 rpl or 4 rpl in kmc_tuning and drops a shape of another kind. The value in use (0 before
  * the first tuning) is returned through rpl_out (may be NULL); rpl = -1 only
  * reads it. */
 kmc_status kmc_replicas_per_lane(kmc_ctx *ctx, int32_t rpl, int32_t *rpl_out);

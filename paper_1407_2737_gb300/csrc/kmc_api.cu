@@ -117,7 +117,7 @@ struct Shape {
   int warps = 0, tile = 0, chunk = 0;
   int tpl = 1;  // targets per lane: 2 or 3 run 64- or 96-target groups (FP32 only)
   int rpl = 1;  // replicas per lane: 2 or 4 run replica lysosomes together (FP32, warps =
-                // rpl or 4 rpl: one or four warps per replica)
+                // rpl, 2 rpl or 4 rpl: one, two or four warps per replica)
   // symmetric pair form (FP32): cells per warp (1 or 2; tpl = 2 sym, tile = 32,
   // chunk = source NPs per field item, 0 = a whole row); 0 = the ordered kernels
   int sym = 0;
@@ -740,7 +740,8 @@ bool shape_ok(const kmc_ctx *c, const Shape &s) {
   if (s.cl != 0 && (s.cl != 2 || !c->fp32 || s.tpl != 1 || s.rpl != 1 || s.chunk <= 0))
     return false;
   if (s.rpl > 1) {  // replicas: their kernel has one warp per replica
-    if (!c->fp32 || s.tpl != 1 || (s.warps != s.rpl && s.warps != 4 * s.rpl) ||
+    if (!c->fp32 || s.tpl != 1 ||
+        (s.warps != s.rpl && s.warps != 2 * s.rpl && s.warps != 4 * s.rpl) ||
         !c->rep_ok[s.rpl])
       return false;
     if (s.tile < 32 || s.tile > 128 || (s.tile & (s.tile - 1))) return false;
@@ -1001,7 +1002,7 @@ kmc_status autotune(kmc_ctx *c) {
   // per replica, one target per lane, tiles of 32..128 records per replica
   for (int rpl = 2; rpl <= 4 && c->fp32 && c->tpl_mode <= 1 && !sym_only; rpl += 2) {
     if (!c->rep_ok[rpl] || (c->rpl_mode != 0 && c->rpl_mode != rpl)) continue;
-    for (int wpr : {1, 4}) {
+    for (int wpr : {1, 2, 4}) {
       for (int t : {32, 64, 128}) {
         if (2 * t > 2 * std::max(max_n, 64) && t > 32) continue;
         for (int ch : chunks) {

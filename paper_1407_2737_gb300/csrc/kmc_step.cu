@@ -1340,8 +1340,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
 // replica r's warp sums and source parts in kmc_step_f32's order, so each
 // replica's field, and its whole step, are the bits it gets alone. Group r
 // then runs replica r's steps iii-vii (the groups in parallel): one warp by
-// itself (WPR = 1), or four warps block-cooperatively on named barriers
-// (WPR = 4), which keeps the update's latency that of one block.
+// itself (WPR = 1), or two or four warps block-cooperatively on named
+// barriers (WPR = 2, 4), which keeps the update's latency near that of one
+// block.
 template <bool MASK, int RPL, int NW>
 __device__ __forceinline__ void pair_tile_f32_rep(const ulonglong2 *__restrict__ sp,
                                                   size_t rstride, int cnt, int first, f2 X,
@@ -1388,14 +1389,14 @@ template <int RPL, int WPR = 1>
 __global__ void __launch_bounds__(RPL * WPR * 32, (RPL == 2 && WPR == 4) ? 2 : 0)
     kmc_step_f32_rep(const StepArgs a, int tile) {
   static_assert(RPL == 2 || RPL == 4, "two or four replicas per lane");
-  static_assert(WPR == 1 || WPR == 4, "one or four warps per replica");
+  static_assert(WPR == 1 || WPR == 2 || WPR == 4, "one, two or four warps per replica");
   constexpr int NW = RPL * WPR;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *dyn = smem + 16;
   __shared__ int s_last;
-  __shared__ GridTables<float> tab;
-  tab.load();
+  // the update's grid tables: two bulk copies on the first tile's barrier
+  __shared__ __align__(16) GridTables<float> tab;
   if (!item_in_bounds(a, 1, true)) return;
   const Item it = a.items[blockIdx.x];  // it.l: the first replica
   if (!KMC_DCHECK(it.l + RPL <= a.n_lys, a.err, kSiteLys)) return;
@@ -1404,10 +1405,15 @@ __global__ void __launch_bounds__(RPL * WPR * 32, (RPL == 2 && WPR == 4) ? 2 : 0
   const bool lead = WPR == 1 || warp % WPR == 0;      // the group's first warp
   const LysDev L0 = a.lys[it.l];
   const LysDev Lw = a.lys[it.l + rk];
-  const float4 pi = static_cast<const float4 *>(a.pos)[L0.off + it.t0 + min(lane, it.nt - 1)];
-  grid_dependency_wait();
+  const float4 pi = static_cast<const float4 *>(a.pos)[it.off + it.t0 + min(lane, it.nt - 1)];
+  int roff[RPL];  // every replica's first source record
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) roff[k] = a.lys[it.l + k].roff;
+  // The run state changes only between field periods, never across a
+  // programmatic-launch edge (as in kmc_step_f32): read before the wait.
   const long long step = a.rs->step_base + a.k_local;
   const int per = a.rs->period;
+  grid_dependency_wait();
   const int rec = (per >= a.discard) ? (per - a.discard) * a.S + a.k_local : -1;
   const int par = static_cast<int>(step & 1);
   const SrcPair *__restrict__ gsrc = static_cast<const SrcPair *>(a.src[par]);
@@ -1428,16 +1434,20 @@ __global__ void __launch_bounds__(RPL * WPR * 32, (RPL == 2 && WPR == 4) ? 2 : 0
     const int b = t & 1;
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
-    if (!tile_in_bounds(a, it, r0, cnt, tile)) {
-      mbar_expect_tx(&bar[b], 0);  // no copy: the phase completes, the error is set
-      return;
+    // tile 0 also brings the grid tables, so that no thread waits on them
+    const uint32_t tab_bytes = t == 0 ? sizeof(tab.sc) + sizeof(tab.th) : 0;
+    const bool ok = tile_in_bounds(a, it, r0, cnt, tile);  // else no tile: the error is set
+    const uint32_t bytes = ok ? static_cast<uint32_t>(cnt) * sizeof(SrcPair) : 0;
+    mbar_expect_tx(&bar[b], RPL * bytes + tab_bytes);
+    if (tab_bytes) {
+      bulk_g2s(tab.sc, g_sc_f, sizeof(tab.sc), &bar[b]);
+      bulk_g2s(tab.th, g_theta_f, sizeof(tab.th), &bar[b]);
     }
-    const uint32_t bytes = static_cast<uint32_t>(cnt) * sizeof(SrcPair);
-    mbar_expect_tx(&bar[b], RPL * bytes);
-#pragma unroll 1
+    if (!ok) return;
+#pragma unroll
     for (int k = 0; k < RPL; ++k)
-      bulk_g2s(buf + (static_cast<size_t>(b) * RPL + k) * rstride,
-               gsrc + a.lys[it.l + k].roff + r0, bytes, &bar[b]);
+      bulk_g2s(buf + (static_cast<size_t>(b) * RPL + k) * rstride, gsrc + roff[k] + r0, bytes,
+               &bar[b]);
   };
   auto body = [&](int b, int t) {
     const int r0 = it.j0 + t * tile;
@@ -2146,13 +2156,18 @@ cudaError_t launch_step(int prec_fp32, int warps, int tile, const StepArgs &a, i
   if (n_items <= 0) return cudaSuccess;
   if (cl != 0 && (!prec_fp32 || rpl > 1)) return cudaErrorInvalidValue;
   if (rpl > 1) {
-    if (!prec_fp32 || tpl != 1 || (warps != rpl && warps != 4 * rpl)) return cudaErrorInvalidValue;
+    if (!prec_fp32 || tpl != 1 || (warps != rpl && warps != 2 * rpl && warps != 4 * rpl))
+      return cudaErrorInvalidValue;
     const size_t smem = step_smem_bytes(1, warps, tile, 1, rpl);
     const int th = warps * 32;
     if (rpl == 2 && warps == 2)
       return launch_items(kmc_step_f32_rep<2>, a, n_items, th, smem, tile, st, pdl);
     if (rpl == 4 && warps == 4)
       return launch_items(kmc_step_f32_rep<4>, a, n_items, th, smem, tile, st, pdl);
+    if (rpl == 2 && warps == 4)
+      return launch_items(kmc_step_f32_rep<2, 2>, a, n_items, th, smem, tile, st, pdl);
+    if (rpl == 4 && warps == 8)
+      return launch_items(kmc_step_f32_rep<4, 2>, a, n_items, th, smem, tile, st, pdl);
     if (rpl == 2 && warps == 8)
       return launch_items(kmc_step_f32_rep<2, 4>, a, n_items, th, smem, tile, st, pdl);
     if (rpl == 4 && warps == 16)
@@ -2256,6 +2271,8 @@ cudaError_t step_blocks_per_sm(int prec_fp32, int warps, int tile, int tpl, int 
   if (prec_fp32 && rpl > 1) {
     if (rpl == 2 && warps == 2) return occupancy(kmc_step_f32_rep<2>, th, smem, blocks);
     if (rpl == 4 && warps == 4) return occupancy(kmc_step_f32_rep<4>, th, smem, blocks);
+    if (rpl == 2 && warps == 4) return occupancy(kmc_step_f32_rep<2, 2>, th, smem, blocks);
+    if (rpl == 4 && warps == 8) return occupancy(kmc_step_f32_rep<4, 2>, th, smem, blocks);
     if (rpl == 2 && warps == 8) return occupancy(kmc_step_f32_rep<2, 4>, th, smem, blocks);
     if (rpl == 4 && warps == 16) return occupancy(kmc_step_f32_rep<4, 4>, th, smem, blocks);
     return cudaErrorInvalidValue;
@@ -2358,6 +2375,8 @@ cudaError_t init_device() {
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_tn<16, 3>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<2>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<4>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<2, 2>);
+  if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<4, 2>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<2, 4>);
   if (e == cudaSuccess) e = allow_smem(kmc_step_f32_rep<4, 4>);
   if (e == cudaSuccess) e = allow_smem(kmc_field_sym<2, 2>);

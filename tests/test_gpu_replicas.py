@@ -2,13 +2,14 @@
 different random streams, as seed averages are) stepped together, each staged
 source record's geometry serving every lysosome of the set.
 
-With four replicas per lane (four warps, one per lysosome; or sixteen, four
-per lysosome) every lysosome's sums are formed by the same operations in the
-same order as with one target per lane and as many warps, and its update is
-the same code run by one warp or a group of four, so whole runs must give the
-same bits. With two (two warps, records interleaved
-over two warps) the summation order differs: the fields are checked against
-the oracle within the FP32 field tolerance of the other tests (1e-5 of rms)."""
+With four replicas per lane (four warps, one per lysosome; or eight or
+sixteen, two or four per lysosome), and with two replicas on four or eight
+warps, every lysosome's sums are formed by the same operations in the same
+order as with one target per lane and as many warps, and its update is the
+same code run by one warp or a group of two or four, so whole runs must give
+the same bits. With two replicas on two warps (records interleaved over two
+warps) the summation order differs: the fields are checked against the oracle
+within the FP32 field tolerance of the other tests (1e-5 of rms)."""
 import numpy as np
 import pytest
 
@@ -57,16 +58,18 @@ def test_four_replicas_per_lane_give_the_bits_of_one_target_per_lane(tile, chunk
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("rpl,tile,chunk", [(4, 64, 0), (4, 32, 128), (2, 128, 256), (2, 64, 0)])
-def test_four_warps_per_replica_give_the_bits_of_one_target_per_lane(rpl, tile, chunk):
-    """Four warps per replica (4 rpl warps; each replica's steps iii-vii run by
-    its own group of four warps on named barriers) against one target per lane
-    with as many warps, at the same tile and source split."""
+@pytest.mark.parametrize("wpr,rpl,tile,chunk", [(4, 4, 64, 0), (4, 4, 32, 128), (4, 2, 128, 256),
+                                              (4, 2, 64, 0), (2, 2, 64, 0), (2, 2, 128, 256),
+                                              (2, 4, 32, 128), (2, 4, 64, 0)])
+def test_warp_groups_per_replica_give_the_bits_of_one_target_per_lane(wpr, rpl, tile, chunk):
+    """Two or four warps per replica (wpr rpl warps; each replica's steps
+    iii-vii run by its own group of wpr warps on named barriers) against one
+    target per lane with as many warps, at the same tile and source split."""
     ly = inputs.make_lysosome(300, 12e-9, 0.06, seed=83)
     lyss = inputs.replicate(ly, 8)
     H = [0.012 + 0.003 * q for q in range(8)]
-    ref, used1 = _run(lyss, 1, (4 * rpl, tile, chunk), H)
-    got, usedr = _run(lyss, rpl, (4 * rpl, tile, chunk), H)
+    ref, used1 = _run(lyss, 1, (wpr * rpl, tile, chunk), H)
+    got, usedr = _run(lyss, rpl, (wpr * rpl, tile, chunk), H)
     assert (used1, usedr) == (1, rpl)
     for x, y in zip(ref, got):
         assert np.array_equal(x, y)
@@ -110,6 +113,6 @@ def test_replicas_are_refused_where_the_lysosomes_differ():
     ctx = kmc.kmc_create(inputs.replicate(a, 6), kmc.KMC_FP32_MIXED, center=np.zeros(3))
     kmc.kmc_replicas_per_lane(ctx, 2)  # 6 = 3 sets of two
     with pytest.raises(kmc.KmcError) as e:
-        kmc.kmc_tuning(ctx, 4, 64, 0)  # two replicas take two warps
+        kmc.kmc_tuning(ctx, 16, 64, 0)  # two replicas take two, four or eight warps
     assert e.value.status == kmc.KMC_EINVAL
     kmc.kmc_destroy(ctx)
