@@ -1054,8 +1054,10 @@ struct AccF32N {
 // one-target loop they are inlined: out of line, the call's argument passing
 // held 122 (two targets) and 164 (three) registers where inlined they take 107
 // and 128, and the 50 000-NP and 512-lysosome workloads ran 5-6 % faster. The
-// two-target loop is unrolled twice (four independent chains per lane; +1 %
-// on the batch), the three-target loop not at all (its three chains suffice).
+// two-target loop is unrolled eight times, held at 4 blocks of 4 warps per SM
+// (127 registers, no spill): against twice, -1.6 % per step at 8 x 2000 NPs
+// and -4.5 % at 50 000 NPs; four times lies between, once was 8 % slower. The
+// three-target loop is not unrolled (its three chains suffice).
 template <bool MASK>
 __device__ __forceinline__ AccF32N<2> pair_tile_f32_2t(const ulonglong2 *__restrict__ sp, int cnt,
                                                        int first, int stride, f2 X0, f2 Y0, f2 Z0,
@@ -1063,7 +1065,7 @@ __device__ __forceinline__ AccF32N<2> pair_tile_f32_2t(const ulonglong2 *__restr
   AccF32N<2> acc;
   acc.t[0].x = acc.t[0].y = acc.t[0].z = 0ull;
   acc.t[1] = acc.t[0];
-#pragma unroll 2
+#pragma unroll 8
   for (int r = first; r < cnt; r += stride) {
     ulonglong2 a, b, c, d;
     f2 e;
@@ -1109,9 +1111,9 @@ constexpr size_t epi_bytes_tn(int warps, int tpl) {
          (tn_group(warps, tpl) ? tpl : 1) * sizeof(EpiShared<float>) + 64;
 }
 
-// Three targets per lane, 4 warps: held at 4 blocks per SM (128 registers).
+// Four warps: held at 4 blocks per SM (128 registers).
 template <int NW, int TPL>
-__global__ void __launch_bounds__(NW * 32, (NW == 4 && TPL == 3) ? 4 : 0)
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 0)
     kmc_step_f32_tn(const StepArgs a, int tile) {
   static_assert(TPL == 2 || TPL == 3, "two or three targets per lane");
   extern __shared__ __align__(128) unsigned char smem[];
