@@ -209,23 +209,19 @@ __device__ __forceinline__ void lane_scan(EpiShared<R> &sm, const GridTables<R> 
     return profile_d1(k2, bc, bs, sc.x, sc.y);
   };
   constexpr int kBatch = 13;
-  int cnt = 0;
-#pragma unroll 1
-  for (int j0 = 0; j0 < kGrid; j0 += kMaxSeg) {
-    const int len = min(kMaxSeg, kGrid - j0);
-    unsigned long long neg = 0;
-#pragma unroll 1
-    for (int q0 = 0; q0 <= len; q0 += kBatch) {
-      unsigned bits = 0;
+  auto batch = [&](int j0, int q0) {
+    unsigned bits = 0;
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        int j = j0 + q0 + u;
-        j = j < kGrid ? j : j - kGrid;
-        bits |= static_cast<unsigned>(d1(j) < R(0)) << u;
-      }
-      neg |= static_cast<unsigned long long>(bits) << q0;
+    for (int u = 0; u < kBatch; ++u) {
+      int j = j0 + q0 + u;
+      j = j < kGrid ? j : j - kGrid;
+      bits |= static_cast<unsigned>(d1(j) < R(0)) << u;
     }
-    unsigned long long chg = (neg ^ (neg >> 1)) & ((1ull << len) - 1);
+    return static_cast<unsigned long long>(bits) << q0;
+  };
+  int cnt = 0;
+  auto record = [&](int j0, unsigned long long neg) {
+    unsigned long long chg = (neg ^ (neg >> 1)) & ((1ull << kMaxSeg) - 1);
     while (chg) {
       const int q = __ffsll(static_cast<long long>(chg)) - 1;
       chg &= chg - 1;
@@ -237,6 +233,21 @@ __device__ __forceinline__ void lane_scan(EpiShared<R> &sm, const GridTables<R> 
       }
       ++cnt;
     }
+  };
+  // segments of kMaxSeg nodes in pairs, the two segments' batches interleaved
+  // (twice the independent evaluations in flight); the sign changes are then
+  // recorded in grid order
+  static_assert(kGrid % (2 * kMaxSeg) == 0, "whole pairs of segments");
+#pragma unroll 1
+  for (int j0 = 0; j0 < kGrid; j0 += 2 * kMaxSeg) {
+    unsigned long long na = 0, nb = 0;
+#pragma unroll 1
+    for (int q0 = 0; q0 <= kMaxSeg; q0 += kBatch) {
+      na |= batch(j0, q0);
+      nb |= batch(j0 + kMaxSeg, q0);
+    }
+    record(j0, na);
+    record(j0 + kMaxSeg, nb);
   }
   sm.cnt[lane] = cnt;
 }
