@@ -832,9 +832,10 @@ kmc_status capture_steps(kmc_ctx *c, const StepArgs &a, const Shape &sh, int ste
   return KMC_OK;
 }
 
-// Times one candidate shape on the current state (restored by the caller).
-// Returns milliseconds per step, or a negative value on error.
-float time_shape(kmc_ctx *c, const Shape &s) {
+// Times one candidate shape on the current state (restored by the caller),
+// over `scale` times the usual number of steps. Returns milliseconds per step,
+// or a negative value on error.
+float time_shape(kmc_ctx *c, const Shape &s, int scale = 1) {
   if (set_items(c, s) != KMC_OK) return -1.f;
   StepArgs a = base_args(c);
   a.cos_k = 1.0;
@@ -892,7 +893,7 @@ float time_shape(kmc_ctx *c, const Shape &s) {
   float ms = -1.f;
   bool ok = true;
   for (int r = 0; r < 2 && ok; ++r) ok = one() == cudaSuccess;
-  const int reps = gx ? 2 : 5;
+  const int reps = (gx ? 2 : 5) * scale;
   if (ok) ok = cudaEventRecord(e0, c->stream) == cudaSuccess;
   for (int r = 0; r < reps && ok; ++r) ok = one() == cudaSuccess;
   if (ok) ok = cudaEventRecord(e1, c->stream) == cudaSuccess;
@@ -1060,9 +1061,10 @@ kmc_status autotune(kmc_ctx *c) {
       }
     }
   }
-  // Shapes within a few per cent of the best are timed twice more, in turn, and
-  // the one with the lowest of its times wins: one timing of a few hundred
-  // microseconds moves by about a per cent from launch to launch.
+  // Shapes within a few per cent of the best are timed twice more, in turn,
+  // each time over three times the steps, and the one with the lowest of its
+  // times wins: one timing of a few milliseconds moves by about a per cent
+  // from launch to launch.
   {
     std::vector<std::pair<float, Shape>> fin;
     for (const auto &t : timed)
@@ -1075,7 +1077,7 @@ kmc_status autotune(kmc_ctx *c) {
     if (fin.size() > 1) {
       for (int r = 0; r < 2; ++r)
         for (auto &f : fin) {
-          const float ms = time_shape(c, f.second);
+          const float ms = time_shape(c, f.second, 3);
           if (ms > 0.f && ms < f.first) f.first = ms;
         }
       for (const auto &f : fin)
