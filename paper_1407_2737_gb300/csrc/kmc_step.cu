@@ -534,8 +534,9 @@ __device__ __forceinline__ TargetIn<V> load_target(const StepArgs &a, const LysD
 // scan the whole grid for their targets and each lane refines its own
 // brackets. GROUP > 0: they are run by the gid-th group of GROUP warps of the
 // block on that group's update state, with named barriers, several groups
-// side by side (the replica kernel with several warps per replica). The
-// results are the same bits as the block's.
+// side by side (the replica kernel with several warps per replica, the
+// multi-target kernel with its 32-target parts side by side). The results are
+// the same bits as the block's.
 // Barriers of a block_update that the whole block runs (GROUP = 0:
 // __syncthreads), or that a group of GROUP warps runs (warps gid GROUP ..
 // gid GROUP + GROUP - 1, named barrier 1 + gid), several groups side by side.
