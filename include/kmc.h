@@ -187,7 +187,10 @@ kmc_status kmc_info(const kmc_ctx *ctx, int64_t *n_total, int32_t *n_lys,
  * are split over several blocks (0 = never split; else a multiple of 64).
  * All three 0 (or warps = 0) lets the autotuner choose on the next kmc_run or
  * kmc_debug_step. The shape in use is returned through the out pointers (each
- * may be NULL); call with warps = tile = chunk = -1 to only read it. */
+ * may be NULL); call with warps = tile = chunk = -1 to only read it. With the
+ * environment variable KMC_TUNE_LOG set (and not "0") the autotuner prints
+ * every shape it times, the finalists' second timings and its choice on
+ * standard error. */
 kmc_status kmc_tuning(kmc_ctx *ctx, int32_t warps, int32_t tile, int32_t chunk,
                       int32_t *warps_out, int32_t *tile_out, int32_t *chunk_out);
 

@@ -942,7 +942,17 @@ kmc_status autotune(kmc_ctx *c) {
   Shape bs;
   // every shape that timed, for the finalists' second look
   std::vector<std::pair<float, Shape>> timed;
+  const char *log_env = std::getenv("KMC_TUNE_LOG");
+  const bool log = log_env && log_env[0] && std::strcmp(log_env, "0") != 0;
+  auto show = [&](const char *what, const Shape &s, float ms) {
+    if (!log) return;
+    std::fprintf(stderr,
+                 "kmc tune %s: warps %d tile %d chunk %d tpl %d rpl %d sym %d cl %d supd %d "
+                 "persist %d: %.4f ms per step\n",
+                 what, s.warps, s.tile, s.chunk, s.tpl, s.rpl, s.sym, s.cl, s.supd, s.persist, ms);
+  };
   auto consider = [&](const Shape &s, float ms) {
+    show("shape", s, ms);
     if (!(ms > 0.f)) return;
     timed.emplace_back(ms, s);
     if (ms < best) {
@@ -987,12 +997,22 @@ kmc_status autotune(kmc_ctx *c) {
         consider(s, ms);
       }
     }
-    // the best symmetric shape with the other update kernel
+    // the symmetric shapes within 3 % of the best with the other update kernel
+    // (shapes that tie with one update kernel can part with the other)
     if (bs.sym && c->supd_mode == 0) {
-      Shape s = bs;
-      s.supd = 1;
-      const float ms = time_shape(c, s);
-      consider(s, ms);
+      std::vector<std::pair<float, Shape>> near;
+      for (const auto &t : timed)
+        if (t.second.sym && t.first <= 1.03f * best) near.push_back(t);
+      std::sort(near.begin(), near.end(),
+                [](const std::pair<float, Shape> &x, const std::pair<float, Shape> &y) {
+                  return x.first < y.first;
+                });
+      if (near.size() > 4) near.resize(4);
+      for (auto &t : near) {
+        Shape s = t.second;
+        s.supd = 1;
+        consider(s, time_shape(c, s));
+      }
     }
   }
   const int warps_c[] = {4, 8};
@@ -1078,6 +1098,7 @@ kmc_status autotune(kmc_ctx *c) {
       for (int r = 0; r < 2; ++r)
         for (auto &f : fin) {
           const float ms = time_shape(c, f.second, 3);
+          show("finalist", f.second, ms);
           if (ms > 0.f && ms < f.first) f.first = ms;
         }
       for (const auto &f : fin)
@@ -1092,6 +1113,7 @@ kmc_status autotune(kmc_ctx *c) {
   KMC_CUDA(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int32_t), c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   c->shape = bs;
+  show("chosen", bs, best);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = bs;
