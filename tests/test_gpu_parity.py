@@ -266,8 +266,11 @@ def test_errors_and_capacity(tmp_path):
 
 def test_full_size_sampled():
     """The 8 x 2000-NP workload in the launch shape the benchmark uses: sampled
-    fields against the oracle one target at a time, draws bit-exact,
-    invariants everywhere."""
+    fields against the oracle one target at a time, draws bit-exact, steps
+    iii-vii of the sampled targets against the oracle's update fed the GPU's
+    field (the tolerances of tests/test_gpu_workloads.py), invariants
+    everywhere."""
+    from test_gpu_workloads import check_update
     lyss, run = inputs.config_single2000(replicas=8, seed=0)
     ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
     kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"])  # tunes, warms
@@ -275,6 +278,7 @@ def test_full_size_sampled():
     t_step = 1 / (run["f"] * run["S"])
     g = kmc.kmc_debug_step(ctx, 0.02, t_step, 1, 200, m_all)
     rng = np.random.default_rng(0)
+    compared = ambiguous = 0
     for l in (0, 7):
         idx = rng.choice(2000, 64, replace=False)
         m = m_all[2000 * l:2000 * (l + 1)]
@@ -284,5 +288,12 @@ def test_full_size_sampled():
         assert np.max(np.linalg.norm(Bg - B, axis=1)) / rms <= 1e-5
         assert np.array_equal(g["u"][2000 * l + idx],
                               [oracle.uniform(1, 200, int(i), l) for i in idx])
+        axes = kmc.kmc_read(ctx, kmc.KMC_READ_AXES, l)
+        m32 = m.astype(np.float32).astype(np.float64)
+        c, a = check_update(lyss[l], axes[idx], m32[idx], Bg, 0.02, t_step, g, 2000 * l + idx)
+        compared += c
+        ambiguous += a
+    kmc.kmc_destroy(ctx)
+    assert compared >= 0.95 * (compared + ambiguous), (compared, ambiguous)
     np.testing.assert_allclose(np.linalg.norm(g["m_out"], axis=1), 1.0, atol=2e-6)
     assert np.all((g["P"] >= 0) & (g["P"] <= 1))
