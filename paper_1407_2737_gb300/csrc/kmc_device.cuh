@@ -17,6 +17,12 @@ namespace kmc {
 // (16-byte aligned: the FP32 step kernels copy them to shared memory in bulk)
 __device__ __align__(16) float g_theta_f[kGrid];
 __device__ __align__(16) float2 g_sc_f[kGrid];
+// The same sin and cos in two arrays of their own, node j at j mod kGrid for
+// j < kGridPad, so that the FP32 scan reads two consecutive nodes as one
+// packed pair, past the end of the grid too.
+constexpr int kGridPad = kGrid + 16;
+__device__ __align__(16) float g_ss_f[kGridPad];
+__device__ __align__(16) float g_cc_f[kGridPad];
 __device__ double g_theta_d[kGrid];
 __device__ double2 g_sc_d[kGrid];
 
@@ -103,7 +109,13 @@ struct Prec<double> {
 // start (the pair loop hides the loads); the scan reads one node per warp
 // (a broadcast), Newton one node per thread.
 template <typename R>
-struct GridTables {
+struct ScanPairs {};
+template <>
+struct ScanPairs<float> {
+  float ss[kGridPad], cc[kGridPad];  // g_ss_f, g_cc_f
+};
+template <typename R>
+struct GridTables : ScanPairs<R> {
   typename std::conditional<std::is_same<R, float>::value, float2, double2>::type sc[kGrid];
   R th[kGrid];
   __device__ void load() {
@@ -111,9 +123,16 @@ struct GridTables {
       sc[j] = Prec<R>::sc(j);
       th[j] = Prec<R>::theta(j);
     }
+    if constexpr (std::is_same<R, float>::value) {
+      for (int j = threadIdx.x; j < kGridPad; j += blockDim.x) {
+        this->ss[j] = g_ss_f[j];
+        this->cc[j] = g_cc_f[j];
+      }
+    }
   }
 };
-static_assert(sizeof(GridTables<float>::sc) % 16 == 0 && sizeof(GridTables<float>::th) % 16 == 0,
+static_assert(sizeof(GridTables<float>::sc) % 16 == 0 && sizeof(GridTables<float>::th) % 16 == 0 &&
+                  sizeof(ScanPairs<float>::ss) % 16 == 0 && sizeof(ScanPairs<float>) % 16 == 0,
               "the FP32 tables are copied in bulk");
 
 // de/dth of Eq. 2 at (sin, cos) = (s, c): s (2k c + b cos phi) - b sin phi c,

@@ -124,6 +124,29 @@ struct EpiShared {
 // its target (shared-memory counter). All lanes of a warp read the same node,
 // a shared-memory broadcast.
 constexpr int kMaxSeg = 50;
+
+// FP32 sign pass over kPairBatch consecutive nodes j0 + q0 .. (j0 + q0 even):
+// two nodes per packed instruction, read as pairs from the split sin and cos
+// tables, each node with profile_d1's roundings (s (2k c + b cos phi) +
+// (-b sin phi) c; a packed operation rounds each half as the scalar one), so
+// the signs are those of the scalar pass. Bit q of the result: node q0 + q.
+constexpr int kPairBatch = 14;
+__device__ __forceinline__ unsigned long long pair_signs(const GridTables<float> &tab, f2 K2,
+                                                         f2 BC, f2 NBS, int j0, int q0) {
+  unsigned bits = 0;
+#pragma unroll
+  for (int u = 0; u < kPairBatch; u += 2) {
+    const int j = j0 + q0 + u;  // < kGridPad: the tables repeat the grid past its end
+    const f2 s = *reinterpret_cast<const f2 *>(&tab.ss[j]);
+    const f2 c = *reinterpret_cast<const f2 *>(&tab.cc[j]);
+    const f2 d = fma2(s, fma2(K2, c, BC), mul2(NBS, c));
+    float dl, dh;
+    upk(d, dl, dh);
+    bits |= (static_cast<unsigned>(dl < 0.f) << u) | (static_cast<unsigned>(dh < 0.f) << (u + 1));
+  }
+  return static_cast<unsigned long long>(bits) << q0;
+}
+
 template <typename R, bool MULTI = false>
 __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<R> &tab,
                                              int warp, int nw, int lane, int nt) {
@@ -163,24 +186,49 @@ __device__ __forceinline__ void segment_scan(EpiShared<R> &sm, const GridTables<
       }
     }
   };
+  // FP32 segments that start on an even node take the packed pass
+  constexpr bool kPairs = std::is_same<R, float>::value;
+  f2 K2 = 0, BC = 0, NBS = 0;
+  if constexpr (kPairs) {
+    K2 = pk(k2, k2);
+    BC = pk(bc, bc);
+    NBS = pk(-bs, -bs);
+  }
   auto scan = [&](int j0, int len) {
     unsigned long long neg = 0;
+    if constexpr (kPairs) {
+      if ((j0 & 1) == 0) {
+#pragma unroll 1
+        for (int q0 = 0; q0 <= len; q0 += kPairBatch) neg |= pair_signs(tab, K2, BC, NBS, j0, q0);
+        record(j0, len, neg);
+        return;
+      }
+    }
 #pragma unroll 1
     for (int q0 = 0; q0 <= len; q0 += kBatch) neg |= batch(j0, q0);
     record(j0, len, neg);
   };
   if constexpr (MULTI) {
     constexpr int nseg = (kGrid + kMaxSeg - 1) / kMaxSeg, seg = (kGrid + nseg - 1) / nseg;
-    static_assert(nseg * seg == kGrid && nseg % 2 == 0, "whole segments, in pairs");
+    static_assert(nseg * seg == kGrid && nseg % 2 == 0 && seg % 2 == 0,
+                  "whole segments, in pairs, starting on even nodes");
     if (nw == 2) {
       // two segments per warp, w and w + 2, their batches interleaved (twice
       // the independent evaluations in flight)
       const int ja = warp * seg, jb = (warp + 2) * seg;
       unsigned long long na = 0, nb = 0;
+      if constexpr (kPairs) {
 #pragma unroll 1
-      for (int q0 = 0; q0 <= seg; q0 += kBatch) {
-        na |= batch(ja, q0);
-        nb |= batch(jb, q0);
+        for (int q0 = 0; q0 <= seg; q0 += kPairBatch) {
+          na |= pair_signs(tab, K2, BC, NBS, ja, q0);
+          nb |= pair_signs(tab, K2, BC, NBS, jb, q0);
+        }
+      } else {
+#pragma unroll 1
+        for (int q0 = 0; q0 <= seg; q0 += kBatch) {
+          na |= batch(ja, q0);
+          nb |= batch(jb, q0);
+        }
       }
       record(ja, seg, na);
       record(jb, seg, nb);
@@ -237,14 +285,30 @@ __device__ __forceinline__ void lane_scan(EpiShared<R> &sm, const GridTables<R> 
   // segments of kMaxSeg nodes in pairs, the two segments' batches interleaved
   // (twice the independent evaluations in flight); the sign changes are then
   // recorded in grid order
-  static_assert(kGrid % (2 * kMaxSeg) == 0, "whole pairs of segments");
+  static_assert(kGrid % (2 * kMaxSeg) == 0 && kMaxSeg % 2 == 0,
+                "whole pairs of segments, starting on even nodes");
+  constexpr bool kPairs = std::is_same<R, float>::value;  // FP32: the packed pass
+  f2 K2 = 0, BC = 0, NBS = 0;
+  if constexpr (kPairs) {
+    K2 = pk(k2, k2);
+    BC = pk(bc, bc);
+    NBS = pk(-bs, -bs);
+  }
 #pragma unroll 1
   for (int j0 = 0; j0 < kGrid; j0 += 2 * kMaxSeg) {
     unsigned long long na = 0, nb = 0;
+    if constexpr (kPairs) {
 #pragma unroll 1
-    for (int q0 = 0; q0 <= kMaxSeg; q0 += kBatch) {
-      na |= batch(j0, q0);
-      nb |= batch(j0 + kMaxSeg, q0);
+      for (int q0 = 0; q0 <= kMaxSeg; q0 += kPairBatch) {
+        na |= pair_signs(tab, K2, BC, NBS, j0, q0);
+        nb |= pair_signs(tab, K2, BC, NBS, j0 + kMaxSeg, q0);
+      }
+    } else {
+#pragma unroll 1
+      for (int q0 = 0; q0 <= kMaxSeg; q0 += kBatch) {
+        na |= batch(j0, q0);
+        nb |= batch(j0 + kMaxSeg, q0);
+      }
     }
     record(j0, na);
     record(j0 + kMaxSeg, nb);
@@ -906,13 +970,15 @@ __device__ __forceinline__ void step_f32_item(const StepArgs &a, int tile, unsig
     // tile 0 also brings the grid tables (the persistent kernel loads them
     // once), so that no thread waits on them
     const uint32_t tab_bytes =
-        (!PERSIST && t == 0) ? sizeof(GridTables<float>::sc) + sizeof(GridTables<float>::th) : 0;
+        (!PERSIST && t == 0) ? sizeof(tab.sc) + sizeof(tab.th) + sizeof(tab.ss) + sizeof(tab.cc) : 0;
     const bool ok = tile_in_bounds(a, it, r0, cnt, tile);  // else no tile: the error is set
     const uint32_t bytes = ok ? static_cast<uint32_t>(cnt) * sizeof(SrcPair) : 0;
     mbar_expect_tx(&bar[b], bytes + tab_bytes);
     if (tab_bytes) {
       bulk_g2s(tab.sc, g_sc_f, sizeof(tab.sc), &bar[b]);
       bulk_g2s(tab.th, g_theta_f, sizeof(tab.th), &bar[b]);
+      bulk_g2s(tab.ss, g_ss_f, sizeof(tab.ss), &bar[b]);
+      bulk_g2s(tab.cc, g_cc_f, sizeof(tab.cc), &bar[b]);
     }
     if (ok) bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
   };
@@ -1189,13 +1255,16 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 0)
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
     // tile 0 also brings the grid tables, so that no thread waits on them
-    const uint32_t tab_bytes = t == 0 ? sizeof(tab.sc) + sizeof(tab.th) : 0;
+    const uint32_t tab_bytes =
+        t == 0 ? sizeof(tab.sc) + sizeof(tab.th) + sizeof(tab.ss) + sizeof(tab.cc) : 0;
     const bool ok = tile_in_bounds(a, it, r0, cnt, tile);  // else no tile: the error is set
     const uint32_t bytes = ok ? static_cast<uint32_t>(cnt) * sizeof(SrcPair) : 0;
     mbar_expect_tx(&bar[b], bytes + tab_bytes);
     if (tab_bytes) {
       bulk_g2s(tab.sc, g_sc_f, sizeof(tab.sc), &bar[b]);
       bulk_g2s(tab.th, g_theta_f, sizeof(tab.th), &bar[b]);
+      bulk_g2s(tab.ss, g_ss_f, sizeof(tab.ss), &bar[b]);
+      bulk_g2s(tab.cc, g_cc_f, sizeof(tab.cc), &bar[b]);
     }
     if (ok) bulk_g2s(buf + static_cast<size_t>(b) * tile * kRecU2, gsrc + r0, bytes, &bar[b]);
   };
@@ -1449,13 +1518,16 @@ __global__ void __launch_bounds__(RPL * WPR * 32, (RPL == 2 && WPR == 4) ? 2 : 0
     const int r0 = it.j0 + t * tile;
     const int cnt = min(tile, it.j1 - r0);
     // tile 0 also brings the grid tables, so that no thread waits on them
-    const uint32_t tab_bytes = t == 0 ? sizeof(tab.sc) + sizeof(tab.th) : 0;
+    const uint32_t tab_bytes =
+        t == 0 ? sizeof(tab.sc) + sizeof(tab.th) + sizeof(tab.ss) + sizeof(tab.cc) : 0;
     const bool ok = tile_in_bounds(a, it, r0, cnt, tile);  // else no tile: the error is set
     const uint32_t bytes = ok ? static_cast<uint32_t>(cnt) * sizeof(SrcPair) : 0;
     mbar_expect_tx(&bar[b], RPL * bytes + tab_bytes);
     if (tab_bytes) {
       bulk_g2s(tab.sc, g_sc_f, sizeof(tab.sc), &bar[b]);
       bulk_g2s(tab.th, g_theta_f, sizeof(tab.th), &bar[b]);
+      bulk_g2s(tab.ss, g_ss_f, sizeof(tab.ss), &bar[b]);
+      bulk_g2s(tab.cc, g_cc_f, sizeof(tab.cc), &bar[b]);
     }
     if (!ok) return;
 #pragma unroll
@@ -2367,8 +2439,15 @@ cudaError_t init_device() {
     th_f[j] = static_cast<float>(th_d[j]);
     sc_f[j] = make_float2(static_cast<float>(sc_d[j].x), static_cast<float>(sc_d[j].y));
   }
+  float ss_f[kGridPad], cc_f[kGridPad];
+  for (int j = 0; j < kGridPad; ++j) {
+    ss_f[j] = sc_f[j % kGrid].x;
+    cc_f[j] = sc_f[j % kGrid].y;
+  }
   cudaError_t e = cudaMemcpyToSymbol(g_theta_f, th_f, sizeof(th_f));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_sc_f, sc_f, sizeof(sc_f));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_ss_f, ss_f, sizeof(ss_f));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cc_f, cc_f, sizeof(cc_f));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_theta_d, th_d, sizeof(th_d));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_sc_d, sc_d, sizeof(sc_d));
 
