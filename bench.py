@@ -83,10 +83,9 @@ FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA =
 # one update launch per chain, which write and read back the partial sums:
 # c4 (one chain) the sum of the two launches' means over 2 each, c3 (8 chains)
 # 8 x the sum of the means over 16 launches of each kernel.
-STEP_DRAM_BYTES = {("c1", 4, 256, 512, 2, 1): 384.0,
-                   ("c4", 4, 32, 1024, 4, 1, "sym", "block"): 17.29e6,
-                   ("c4", 4, 32, 512, 4, 1, "sym", "block"): 97.84e6,
-                   ("c3", 4, 32, 512, 4, 1, "sym"): 17.65e6}
+STEP_DRAM_BYTES = {("c1", 4, 256, 512, 2, 1): 0.0,
+                   ("c4", 4, 32, 512, 4, 1, "sym", "block"): 97.89e6,
+                   ("c3", 4, 32, 512, 4, 1, "sym"): 17.37e6}
 
 
 def step_kernel(warps, tpl, rpl):
