@@ -84,8 +84,8 @@ FLOPS_PER_PAIR = 30          # 20 FP32-pipe instructions per ordered pair, FMA =
 # c4 (one chain) the sum of the two launches' means over 2 each, c3 (8 chains)
 # 8 x the sum of the means over 16 launches of each kernel.
 STEP_DRAM_BYTES = {("c1", 4, 256, 512, 2, 1): 0.0,
-                   ("c4", 4, 32, 512, 4, 1, "sym", "block"): 97.89e6,
-                   ("c3", 4, 32, 512, 4, 1, "sym"): 17.37e6}
+                   ("c4", 4, 32, 512, 4, 1, "sym", "block"): 18.84e6,
+                   ("c3", 4, 32, 512, 4, 1, "sym"): 15.31e6}
 
 
 def step_kernel(warps, tpl, rpl):

@@ -484,7 +484,7 @@ kmc_status set_sym_items(kmc_ctx *c, const Shape &sh) {
   KMC_TRY(grow(c, &c->d_sitems, &c->sitems_cap, plan.items.size()));
   KMC_TRY(grow(c, &c->d_supd, &c->supd_cap, plan.upd.size()));
   KMC_TRY(grow(c, &c->d_sfwd, &c->sfwd_cap,
-               plan.items.size() * 6 * static_cast<size_t>(gc) * kmc::kCell));
+               plan.items.size() * 3 * static_cast<size_t>(gc) * kmc::kCell));
   KMC_TRY(grow(c, &c->d_srev, &c->srev_cap,
                std::max<size_t>(1, static_cast<size_t>(plan.n_rev) * 3 * kmc::kCell)));
   KMC_CUDA(cudaMemcpy(c->d_sitems, plan.items.data(), sizeof(kmc::SymItem) * plan.items.size(),

@@ -1486,7 +1486,6 @@ __global__ void __launch_bounds__(RPL * WPR * 32, (RPL == 2 && WPR == 4) ? 2 : 0
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rk = WPR == 1 ? warp : warp / WPR;        // the replica this warp's group updates
   const bool lead = WPR == 1 || warp % WPR == 0;      // the group's first warp
-  const LysDev L0 = a.lys[it.l];
   const LysDev Lw = a.lys[it.l + rk];
   const float4 pi = static_cast<const float4 *>(a.pos)[it.off + it.t0 + min(lane, it.nt - 1)];
   int roff[RPL];  // every replica's first source record
@@ -1990,8 +1989,10 @@ __global__ void __launch_bounds__(W * 32) kmc_field_sym(const StepArgs a, int /*
     if (!staged_loop(ncs, bar, a.err, issue, body)) return;
     flush_rev(ncs - 1);
   }
-  // forward partials of the warp's targets: [6][GT] at the item's slot
-  float *fw = a.sfwd + static_cast<size_t>(it.fwd) * 6 * GT;
+  // forward partials of the warp's targets: [3][GT] at the item's slot, each
+  // the Kahan sum with its compensation applied (s - c: Kahan keeps minus
+  // the error), i.e. the item's sum rounded once to float
+  float *fw = a.sfwd + static_cast<size_t>(it.fwd) * 3 * GT;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     if (cell0 + c >= nc) continue;
@@ -2000,10 +2001,7 @@ __global__ void __launch_bounds__(W * 32) kmc_field_sym(const StepArgs a, int /*
       const int k = 2 * c + h;
       const int gi = (warp * C + c) * kCell + 2 * lane + h;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        __stcg(fw + q * GT + gi, s3[k][q]);
-        __stcg(fw + (3 + q) * GT + gi, -c3[k][q]);  // Kahan keeps minus the error
-      }
+      for (int q = 0; q < 3; ++q) __stcg(fw + q * GT + gi, s3[k][q] - c3[k][q]);
     }
   }
   grid_launch_dependents();
@@ -2041,24 +2039,21 @@ __global__ void __launch_bounds__(kSymUpdWarps * 32) kmc_update_sym(const StepAr
   const int gi = u.gt0 + tl, ci = (u.t0 + tl) % kCell;
   // the slots in order; each batch's loads are issued before its additions
   float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
-  constexpr int kFwdBatch = 4, kRevBatch = 8;
+  constexpr int kFwdBatch = 8, kRevBatch = 8;
 #pragma unroll 1
   for (int s0 = 0; s0 < u.nfwd; s0 += kFwdBatch) {
-    float v[kFwdBatch][6];
+    float v[kFwdBatch][3];
 #pragma unroll
     for (int b = 0; b < kFwdBatch; ++b) {
-      const float *p = a.sfwd + static_cast<size_t>(u.fwd0 + min(s0 + b, u.nfwd - 1)) * 6 * GT;
+      const float *p = a.sfwd + static_cast<size_t>(u.fwd0 + min(s0 + b, u.nfwd - 1)) * 3 * GT;
 #pragma unroll
-      for (int q = 0; q < 6; ++q) v[b][q] = __ldcg(p + q * GT + gi);
+      for (int q = 0; q < 3; ++q) v[b][q] = __ldcg(p + q * GT + gi);
     }
 #pragma unroll
     for (int b = 0; b < kFwdBatch; ++b) {
       if (s0 + b >= u.nfwd) break;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        neumaier_add(hi[q], lo[q], v[b][q]);
-        lo[q] += v[b][3 + q];
-      }
+      for (int q = 0; q < 3; ++q) neumaier_add(hi[q], lo[q], v[b][q]);
     }
   }
 #pragma unroll 1
@@ -2126,12 +2121,9 @@ __global__ void __launch_bounds__(kSymUpdWarps * 32)
   float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
 #pragma unroll 1
   for (int sl = warp; sl < u.nfwd; sl += NW) {
-    const float *p = a.sfwd + static_cast<size_t>(u.fwd0 + sl) * 6 * GT;
+    const float *p = a.sfwd + static_cast<size_t>(u.fwd0 + sl) * 3 * GT;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      neumaier_add(hi[q], lo[q], __ldcg(p + q * GT + gi));
-      lo[q] += __ldcg(p + (3 + q) * GT + gi);
-    }
+    for (int q = 0; q < 3; ++q) neumaier_add(hi[q], lo[q], __ldcg(p + q * GT + gi));
   }
 #pragma unroll 1
   for (int sl = warp; sl < u.nrev; sl += NW) {
