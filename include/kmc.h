@@ -171,7 +171,10 @@ kmc_status kmc_debug_step(kmc_ctx *ctx, const double *mu0Hext, double t_step,
 
 /* Checkpoint: writes the moments and the global step counter to `path`;
  * kmc_load restores them into a context built from the same lysosomes and
- * precision, so that the next kmc_run continues bit for bit. */
+ * precision, so that the next kmc_run continues bit for bit. kmc_load
+ * refuses, leaving the context as it was: a file that is not a checkpoint or
+ * is cut short (KMC_EIO), one of another context (KMC_EINVAL), or one holding
+ * a moment that is not a finite unit vector (KMC_EINVAL). */
 kmc_status kmc_save(kmc_ctx *ctx, const char *path);
 kmc_status kmc_load(kmc_ctx *ctx, const char *path);
 

@@ -1963,6 +1963,25 @@ kmc_status kmc_load(kmc_ctx *c, const char *path) {
   std::fclose(fp);
   if (!ok) return fail(KMC_EIO, "truncated checkpoint %s", path);
   if (nn != c->n) return fail(KMC_EINVAL, "checkpoint does not match this context");
+  // every moment must be a finite unit vector (a step keeps |m| = 1 to the
+  // precision's rounding); anything else is a damaged file, refused before
+  // it reaches the device
+  for (long long i = 0; i < c->N; ++i) {
+    double x, y, z;
+    const unsigned char *e = raw.data() + c->vbytes * i;  // copied out: no alignment assumed
+    if (c->fp32) {
+      float v[3];
+      std::memcpy(v, e, sizeof(v));
+      x = v[0], y = v[1], z = v[2];
+    } else {
+      double v[3];
+      std::memcpy(v, e, sizeof(v));
+      x = v[0], y = v[1], z = v[2];
+    }
+    const double r2 = x * x + y * y + z * z;
+    if (!is_finite(r2) || std::fabs(r2 - 1.0) > 1e-3)
+      return fail(KMC_EINVAL, "checkpoint %s: moment %lld is not a finite unit vector", path, i);
+  }
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   KMC_CUDA(cudaMemcpy(c->d_m, raw.data(), raw.size(), cudaMemcpyHostToDevice));
   c->step_global = hdr2[1];

@@ -262,6 +262,23 @@ def test_errors_and_capacity(tmp_path):
     with pytest.raises(kmc.KmcError) as e:
         kmc.kmc_read(ctx, kmc.KMC_READ_SAR, 5)
     assert e.value.status == kmc.KMC_EINVAL
+    # a checkpoint whose moment is damaged (NaN, or no longer of unit length)
+    # is refused and leaves the context's moments as they were
+    good = tmp_path / "good.bin"
+    kmc.kmc_save(ctx, str(good))
+    m_before = kmc.kmc_read(ctx, kmc.KMC_READ_MOMENTS)
+    raw = bytearray(good.read_bytes())
+    first = 8 + 3 * 4 + 2 * 8 + 4 * 1  # magic, int32 header, int64 header, the NP counts
+    for bad_x in (float("nan"), 2.0):
+        dmg = bytearray(raw)
+        dmg[first:first + 4] = np.float32(bad_x).tobytes()  # x of NP 0 (float4 records)
+        bad.write_bytes(bytes(dmg))
+        with pytest.raises(kmc.KmcError) as e:
+            kmc.kmc_load(ctx, str(bad))
+        assert e.value.status == kmc.KMC_EINVAL and "unit vector" in str(e.value)
+        assert np.array_equal(kmc.kmc_read(ctx, kmc.KMC_READ_MOMENTS), m_before)
+    kmc.kmc_load(ctx, str(good))
+    assert np.array_equal(kmc.kmc_read(ctx, kmc.KMC_READ_MOMENTS), m_before)
 
 
 def test_full_size_sampled():
