@@ -3,7 +3,7 @@
 Tolerances (derived from the arithmetic, FP64 path):
 * dipolar field: |dB_i| <= 1e-12 * sum_j |term_ij| (the two sides sum the same
   terms in different orders; each rounding is <= 2^-53 of a partial sum), the
-  reading of the north star's "1e-12 relative" for a sum whose terms cancel;
+  reading of a "1e-12 relative" FP64 field bound for a sum whose terms cancel;
   where they cancel by at most a factor 4, also |dB_i| <= 1e-12 |B_i|;
 * barriers: |d(E3 - E_a)| <= 1e-12 |E3 - E_a| + 1e-14 E_scale, E_scale =
   K_eff V + M_S V |B| (each energy carries a few ulp of E_scale);

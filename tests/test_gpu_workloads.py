@@ -6,7 +6,8 @@ and the SAR of the 2000-NP lysosome over 32 seeds.
 
 Tolerances, derived from the arithmetic:
 * FP32 field: max_i |dB_i| <= 1e-5 rms_i |B_i| on the geometry the GPU holds
-  (float32 centres), the benchmark spec's bound for the mixed pair sum.
+  (float32 centres), the bound stated for the FP32 pair sum with a
+  compensated combine.
 * FP32 update (steps iii-vii) given the GPU's own field: each energy of
   Eq. 2 carries a few float32 roundings of E_scale = K V + M_S V |B|, so
   |d(E3 - E_a)| <= 2e-6 E_scale; the rate exponent then moves by
@@ -243,7 +244,7 @@ def test_positions_never_rounded_to_the_float32_frame(case):
     bound = representation_bound(ly.pos, ly.vol, ly.Ms, idx, L, np.zeros(3))
     assert np.all(d_raw <= 1e-5 * scale + bound)
     if case == "2000":
-        assert d_raw.max() <= 1e-5 * scale  # the benchmark spec's bound holds as it stands
+        assert d_raw.max() <= 1e-5 * scale  # the 1e-5 bound holds on the caller's positions too
 
 
 def isolated_near_switching(Keff=1.3e4, Ms=1e6, d=12e-9, T=300.0):
