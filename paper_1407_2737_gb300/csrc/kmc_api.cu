@@ -12,6 +12,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -66,6 +67,26 @@ kmc_status fail(kmc_status s, const char *fmt, ...) {
   } while (0)
 
 bool is_finite(double x) { return std::isfinite(x); }
+
+// Host staging bytes for device records (float4, dbl4, SrcPair), allocated on
+// a 64-byte boundary so that records can be written and read in place.
+template <typename T>
+struct RecordAlloc {
+  using value_type = T;
+  static constexpr std::size_t kAlign = 64;
+  RecordAlloc() = default;
+  template <typename U>
+  RecordAlloc(const RecordAlloc<U> &) {}
+  T *allocate(std::size_t n) {
+    return static_cast<T *>(::operator new(n * sizeof(T), std::align_val_t(kAlign)));
+  }
+  void deallocate(T *p, std::size_t) { ::operator delete(p, std::align_val_t(kAlign)); }
+  template <typename U>
+  bool operator==(const RecordAlloc<U> &) const { return true; }
+  template <typename U>
+  bool operator!=(const RecordAlloc<U> &) const { return false; }
+};
+using HostBytes = std::vector<unsigned char, RecordAlloc<unsigned char>>;
 
 // A named range on the host timeline of a profiler (NVTX; no cost without one).
 struct Phase {
@@ -922,7 +943,7 @@ kmc_status autotune(kmc_ctx *c) {
     }
   }
   // the timed launches advance a scratch copy of the state: save the moments
-  std::vector<unsigned char> saved(c->vbytes * c->N);
+  HostBytes saved(c->vbytes * c->N);
   KMC_CUDA(cudaMemcpyAsync(saved.data(), c->d_m, saved.size(), cudaMemcpyDeviceToHost, c->stream));
   KMC_CUDA(cudaStreamSynchronize(c->stream));
   RunState rs{c->step_global, -1, 0};
@@ -1145,10 +1166,10 @@ void free_ctx(kmc_ctx *c) {
   delete c;
 }
 
-kmc_status create_device_state(kmc_ctx *c, const std::vector<unsigned char> &h_pos,
-                               const std::vector<unsigned char> &h_axis,
-                               const std::vector<unsigned char> &h_m,
-                               const std::vector<unsigned char> &h_src,
+kmc_status create_device_state(kmc_ctx *c, const HostBytes &h_pos,
+                               const HostBytes &h_axis,
+                               const HostBytes &h_m,
+                               const HostBytes &h_src,
                                const std::vector<int> &h_slot, const std::vector<double> &h_beta,
                                const std::vector<double> &h_vfrac,
                                const std::vector<dbl4> &h_pos64) {
@@ -1281,8 +1302,8 @@ kmc_status kmc_create(const kmc_lysosome *lys, int32_t n_lys, kmc_precision prec
   long long nrec = 0;
   for (int l = 0; l < n_lys; ++l) nrec += lys_records(lys[l].n);
   c->n_records = nrec;
-  std::vector<unsigned char> h_pos(c->vbytes * N), h_axis(c->vbytes * N), h_m(c->vbytes * N);
-  std::vector<unsigned char> h_src((c->fp32 ? sizeof(SrcPair) : sizeof(dbl4)) * nrec);
+  HostBytes h_pos(c->vbytes * N), h_axis(c->vbytes * N), h_m(c->vbytes * N);
+  HostBytes h_src((c->fp32 ? sizeof(SrcPair) : sizeof(dbl4)) * nrec);
   std::vector<int> h_slot(c->fp32 ? N : 0);
   std::vector<double> h_beta(N), h_vfrac(N);
   std::vector<dbl4> h_pos64(c->fp32 ? N : 0);
@@ -1788,7 +1809,7 @@ kmc_status kmc_read(kmc_ctx *c, int32_t what, int32_t lys, double *buf, int64_t 
       break;
     case KMC_READ_AXES:
     case KMC_READ_MOMENTS: {
-      std::vector<unsigned char> raw(c->vbytes * n);
+      HostBytes raw(c->vbytes * n);
       const void *src = what == KMC_READ_AXES ? c->d_axis : c->d_m;
       KMC_CUDA(cudaMemcpy(raw.data(), static_cast<const unsigned char *>(src) + c->vbytes * o,
                           raw.size(), cudaMemcpyDeviceToHost));
@@ -1843,7 +1864,7 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
     KMC_TRY(dalloc(&c->d_dbg, sizeof(double) * N * 7));
     KMC_TRY(dalloc(&c->d_dbg_flags, sizeof(int32_t) * N));
   }
-  std::vector<unsigned char> h_m(c->vbytes * N);
+  HostBytes h_m(c->vbytes * N);
   for (long long i = 0; i < N; ++i) {
     if (c->fp32)
       reinterpret_cast<float4 *>(h_m.data())[i] =
@@ -1922,7 +1943,7 @@ kmc_status kmc_debug_step(kmc_ctx *c, const double *mu0Hext, double t_step, uint
 kmc_status kmc_save(kmc_ctx *c, const char *path) {
   if (!c || !path) return fail(KMC_EINVAL, "NULL argument");
   KMC_TRY(check_device_error(c));
-  std::vector<unsigned char> raw(c->vbytes * c->N);
+  HostBytes raw(c->vbytes * c->N);
   KMC_CUDA(cudaMemcpy(raw.data(), c->d_m, raw.size(), cudaMemcpyDeviceToHost));
   FILE *fp = std::fopen(path, "wb");
   if (!fp) return fail(KMC_EIO, "cannot open %s for writing", path);
@@ -1957,7 +1978,7 @@ kmc_status kmc_load(kmc_ctx *c, const char *path) {
     return fail(KMC_EINVAL, "checkpoint does not match this context");
   }
   std::vector<int> nn(c->n_lys);
-  std::vector<unsigned char> raw(c->vbytes * c->N);
+  HostBytes raw(c->vbytes * c->N);
   ok = std::fread(nn.data(), sizeof(int), c->n_lys, fp) == static_cast<size_t>(c->n_lys) &&
        std::fread(raw.data(), 1, raw.size(), fp) == raw.size();
   std::fclose(fp);
