@@ -7,6 +7,8 @@ Sec. III.2.c) and the SAR conversion of Sec. III.2.a.
   (textbook Stoner-Wohlfarth), and dimensionless area A / K_eff = 2, the value
   the paper gives for randomly oriented NPs at low concentration.
 * 10^4 J/m^3 at 100 kHz and rho = 5200 kg/m^3 is 192 W/g.
+* The per-NP energies: exact in the isolated square-loop limit, and with
+  dipolar coupling their sum is the area of the recorded M(H) loop.
 """
 import math
 
@@ -111,3 +113,31 @@ def test_per_np_energy_of_isolated_square_loops():
     E = MS * lys.vol * 2.0 * (H[k_up] - H[k_down])
     nper = periods - discard
     np.testing.assert_allclose(out["E_diss"] / nper, E, rtol=1e-12)
+
+
+def test_per_np_energies_sum_to_the_loop_area_with_interactions():
+    # Sec. III.2.a defines the heating through the area of the M(H) loop. With
+    # strong dipolar coupling the split between NPs is a reading (reading 12),
+    # but the total is not: sum_i V_i dm_z,i over a step is V_tot dM over that
+    # step, so the per-NP energies must add up to M_S V_tot sum_k mu0H_k
+    # (M_k - M_(k-1)) of the recorded loop, M_(-1) being the volume-weighted
+    # m_z before the first recorded step. A dropped volume weight, a shifted
+    # field index or a wrong sign in the per-NP accumulation breaks it.
+    lys = inputs.make_lysosome(60, 14e-9, 0.2, Ms=MS, Keff=2e4, T=300.0, tau0=1e-10,
+                               seed=7)
+    lys.vol = lys.vol * np.random.default_rng(1).uniform(0.6, 1.0, lys.n)  # polydisperse
+    mz0 = oracle.initial_moments(lys.axis)[:, 2]
+    vtot = float(lys.vol.sum())
+    S, periods = 120, 2
+    out = oracle.run(lys, 0, 0.03, 1e5, S, periods, 0, seed=3)
+    H, M = out["loop_H"], out["loop_M"]
+    assert out["counters"]["flips"] > 0  # thermal jumps happened on the way
+    M_prev = np.concatenate([[float(np.dot(lys.vol, mz0)) / vtot], M[:-1]])
+    loop = MS * vtot * np.sum(H * (M - M_prev))
+    scale = MS * vtot * np.sum(np.abs(H) * np.abs(M - M_prev))
+    total = float(out["E_diss"].sum())
+    assert abs(total - loop) <= 1e-12 * scale, (total, loop, scale)
+    # the same total as the area per unit volume and cycle
+    assert abs(out["area"] * vtot * periods - total) <= 1e-12 * scale
+    # dipolar coupling moves the individual NPs' shares: they are not all alike
+    assert np.std(out["E_diss"] / lys.vol) > 0
