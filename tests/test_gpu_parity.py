@@ -286,11 +286,25 @@ def test_full_size_sampled():
     fields against the oracle one target at a time, draws bit-exact, steps
     iii-vii of the sampled targets against the oracle's update fed the GPU's
     field (the tolerances of tests/test_gpu_workloads.py), invariants
-    everywhere."""
+    everywhere: after one recorded period every lysosome's per-NP energies add
+    up to the area of its recorded M(H) loop."""
     from test_gpu_workloads import check_update
     lyss, run = inputs.config_single2000(replicas=8, seed=0)
     ctx = kmc.kmc_create(lyss, kmc.KMC_FP32_MIXED, center=np.zeros(3))
     kmc.kmc_run(ctx, run["mu0Hmax"], run["f"], run["S"], 1, 0, run["seed"])  # tunes, warms
+    # that recorded period, every lysosome: the per-NP energies add up to the
+    # area of the recorded M(H) loop (Sec. III.2.a), M_(-1) being the initial
+    # state (moments along the float32 axes, m_z >= 0)
+    H = kmc.kmc_read(ctx, kmc.KMC_READ_LOOP_H, 0)
+    for l in range(8):
+        ly = lyss[l]
+        M = kmc.kmc_read(ctx, kmc.KMC_READ_LOOP_M, l)
+        E = kmc.kmc_read(ctx, kmc.KMC_READ_NP_ENERGY, l)
+        vtot = float(ly.vol.sum())
+        mz0 = np.abs(kmc.kmc_read(ctx, kmc.KMC_READ_AXES, l).reshape(-1, 3)[:, 2])
+        dM = M - np.concatenate([[float(np.dot(ly.vol, mz0)) / vtot], M[:-1]])
+        scale = ly.Ms * vtot * np.sum(np.abs(H) * np.abs(dM))
+        assert abs(E.sum() - ly.Ms * vtot * np.sum(H * dM)) <= 1e-9 * scale, l
     m_all = np.concatenate([kmc.kmc_read(ctx, kmc.KMC_READ_MOMENTS, l) for l in range(8)])
     t_step = 1 / (run["f"] * run["S"])
     g = kmc.kmc_debug_step(ctx, 0.02, t_step, 1, 200, m_all)
