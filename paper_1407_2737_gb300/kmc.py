@@ -146,6 +146,20 @@ def _f64(a, shape=None):
     return a.reshape(shape) if shape is not None else a
 
 
+def _lysosome_arrays(ly, q):
+    """pos [n][3], axis [n][3] and vol [n] of lysosome q as contiguous float64,
+    refused (KMC_EINVAL) unless all three describe the same n NPs: the C side
+    takes n from vol and reads n rows of the others."""
+    pos = _f64(ly.pos)
+    axis = _f64(ly.axis)
+    vol = _f64(ly.vol).reshape(-1)
+    n = vol.shape[0]
+    if pos.size != 3 * n or axis.size != 3 * n:
+        raise KmcError(KMC_EINVAL, "lysosome %d: pos (%d values) and axis (%d) must hold 3 per "
+                       "NP for %d volumes" % (q, pos.size, axis.size, n))
+    return pos.reshape(n, 3), axis.reshape(n, 3), vol
+
+
 class Context:
     """An opened kmc_ctx; keeps the host arrays it was built from alive."""
 
@@ -170,9 +184,7 @@ def kmc_create(lysosomes, precision=KMC_FP32_MIXED, center=None):
     arr = (kmc_lysosome * len(lysosomes))()
     cen = None if center is None else _f64(center, (3,))
     for q, ly in enumerate(lysosomes):
-        pos = _f64(ly.pos, (-1, 3))
-        axis = _f64(ly.axis, (-1, 3))
-        vol = _f64(ly.vol, (-1,))
+        pos, axis, vol = _lysosome_arrays(ly, q)
         keep += [pos, axis, vol]
         arr[q] = kmc_lysosome(len(vol), _dp(pos), _dp(axis), _dp(vol), _dp(cen), float(ly.Ms),
                               float(ly.Keff), float(ly.T), float(ly.tau0),
@@ -188,9 +200,7 @@ def kmc_mean_run(lysosomes, mu0Hmax, f, steps_per_period, periods, discard_perio
     keep = []
     arr = (kmc_lysosome * len(lysosomes))()
     for q, ly in enumerate(lysosomes):
-        pos = _f64(ly.pos, (-1, 3))
-        axis = _f64(ly.axis, (-1, 3))
-        vol = _f64(ly.vol, (-1,))
+        pos, axis, vol = _lysosome_arrays(ly, q)
         keep += [pos, axis, vol]
         arr[q] = kmc_lysosome(len(vol), _dp(pos), _dp(axis), _dp(vol), None, float(ly.Ms),
                               float(ly.Keff), float(ly.T), float(ly.tau0),

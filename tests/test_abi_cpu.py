@@ -58,6 +58,50 @@ def test_bad_arguments_are_rejected_on_the_host(L):
     L.kmc_destroy(None)  # NULL-safe
 
 
+def _bad(field):
+    lys = inputs.make_lysosome(10, 12e-9, 0.05, seed=0)
+    if field == "empty":
+        lys.pos, lys.axis, lys.vol = np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0)
+    elif field == "nan_pos":
+        lys.pos = lys.pos.copy()
+        lys.pos[3, 1] = np.nan
+    elif field == "zero_axis":
+        lys.axis = lys.axis.copy()
+        lys.axis[7] = 0.0
+    elif field == "inf_axis":
+        lys.axis = lys.axis.copy()
+        lys.axis[0, 2] = np.inf
+    elif field == "neg_vol":
+        lys.vol = lys.vol.copy()
+        lys.vol[2] = -lys.vol[2]
+    elif field == "short_pos":
+        lys.pos = lys.pos[:9]
+    elif field == "long_axis":
+        lys.axis = np.concatenate([lys.axis, lys.axis[:1]])
+    else:
+        setattr(lys, field[0], field[1])
+    return lys
+
+
+@pytest.mark.parametrize("field", ["empty", "nan_pos", "zero_axis", "inf_axis", "neg_vol",
+                                   "short_pos", "long_axis", ("Ms", 0.0), ("Ms", np.inf),
+                                   ("Keff", -1.0), ("Keff", np.nan), ("T", -1.0),
+                                   ("tau0", 0.0), ("tau0", np.nan)],
+                         ids=str)
+def test_bad_lysosomes_are_rejected_before_any_device_call(L, field):
+    """Each bad lysosome is refused with KMC_EINVAL, on the host, in both
+    precisions and in the mean mode: validation comes before the device is
+    looked for, so a machine without a GPU gives the same answer."""
+    lys = _bad(field)
+    for prec in (kmc.KMC_FP64_PLAIN, kmc.KMC_FP32_MIXED):
+        with pytest.raises(kmc.KmcError) as e:
+            kmc.kmc_create([inputs.make_lysosome(5, 12e-9, 0.05, seed=1), lys], prec)
+        assert e.value.status == kmc.KMC_EINVAL, (field, str(e.value))
+    with pytest.raises(kmc.KmcError) as e:
+        kmc.kmc_mean_run([lys], 0.02, 1e5, 20, 2, 1)
+    assert e.value.status == kmc.KMC_EINVAL, (field, str(e.value))
+
+
 def test_no_device_is_an_error_not_a_fallback(L):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
